@@ -1,0 +1,431 @@
+/*
+ * c8r_oracle.c -- plain, slow, single-threaded FP64 reference ("oracle") of the
+ * track x antenna radio-emission step that the CORSIKA 8 radio module runs for
+ * every particle track and every antenna (paper §2, the radio process flow:
+ * track -> track filter -> formalism -> propagator -> antenna store).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or calls
+ * this file.  Only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark may use it.  It shares no code, header, table or constant generator
+ * with the CUDA path.
+ *
+ * The paper names the two formalisms (§1: "Endpoint", after James et al.,
+ * Phys. Rev. E 84, 056602 (2011); "ZHS", after Zas, Halzen & Stanev,
+ * Phys. Rev. D 45, 362 (1992)) and the flow (§2), but prints no equation.  The
+ * formulas below are those of the cited works, written in SI units for a charge
+ * q*e moving with constant velocity beta*c along a straight track inside a
+ * medium of refractive index n.  Readings of points where the paper is silent:
+ *
+ *  F  track filter (§2 names it, no criteria): keep a track iff q != 0, all
+ *     twelve fields are finite, t1 > t0, |x1 - x0| > 0 and 0 < |beta| < 1.
+ *  M  straight-line propagator (§2, §4 "simple" propagator): one straight path
+ *     x_e -> x_a; uniform medium n_avg = n_src = n; exponential medium
+ *     n(z) = 1 + N0 exp(-z/H), n_src = n(z_e), n_avg = path average of n(z),
+ *     evaluated in the expm1 form that is exact for every dz; arrival time
+ *     t_arr = t_e + n_avg R / c.  The Doppler factor uses n_src.
+ *  T  binning: bin k of antenna a covers [t_ref + k dt, t_ref + (k+1) dt); a
+ *     deposit with k outside [0, N) is dropped.
+ *  E  Endpoint: at the start (sign +1) and the end (sign -1) of the track a
+ *     field s K V / (D R dt) lands in the arrival bin, K = q e / (4 pi eps0 c),
+ *     V = rhat x (rhat x beta), D = 1 - n_src beta.rhat (signed).
+ *  C  near-Cherenkov Endpoint: if min(|D0|,|D1|) < eps_C the pair is evaluated
+ *     at the track midpoint with linearised arrival times t_arr,m -/+ D_m dt_e/2;
+ *     a pair whose two arrivals share a bin contributes exactly zero.
+ *  Z  ZHS: bin average of the midpoint step potential K_A beta_perp/(R |D|) over
+ *     the arrival interval t_arr,m -/+ |D| dt_e / 2; if the interval lies in one
+ *     bin the deposit is K_A beta_perp dt_e / (R dt) (no division by D).
+ *  G  adjoint (Endpoint): gradient of a scalar loss whose derivative with respect
+ *     to the traces is given, with every bin index and branch decision held
+ *     fixed (the traces are piecewise constant in the times).
+ *
+ * Parity unpinned: the value eps_C = 1e-3 itself (any value gives a consistent
+ * result; the tests pin the branch's formula, not the threshold), and the choice
+ * of n_src over n_avg in the Doppler factor for a non-uniform medium (the two
+ * coincide in a uniform medium, where the closed-form pins run).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#define OR_C_LIGHT 299792458.0          /* m/s                        */
+#define OR_EPS0 8.8541878128e-12        /* F/m                        */
+#define OR_QE 1.602176634e-19           /* C                          */
+#define OR_PI 3.14159265358979323846
+
+enum { OR_UNIFORM = 0, OR_EXPONENTIAL = 1 };
+enum { OR_ENDPOINT = 0, OR_ZHS = 1 };
+/* oracle-only evaluation modes used by the identity tests */
+enum { OR_MODE_NORMAL = 0, OR_MODE_FORCE_MIDPOINT = 1, OR_MODE_ZHS_EDGE_SAMPLED = 2 };
+
+typedef struct {
+  const double *x0, *y0, *z0, *x1, *y1, *z1; /* m                          */
+  const double *t0, *t1;                     /* s                          */
+  const double *bx, *by, *bz;                /* velocity / c               */
+  const double *q;                           /* charge in units of e       */
+} or_tracks;
+
+typedef struct {
+  int kind;        /* OR_UNIFORM or OR_EXPONENTIAL                          */
+  double n;        /* uniform: refractive index                             */
+  double N0;       /* exponential: refractivity at z = 0                    */
+  double H;        /* exponential: scale height, m                          */
+} or_medium;
+
+typedef struct {
+  const double* xyz;   /* [n_ant][3] m                                       */
+  const double* t_ref; /* [n_ant] s, start time of bin 0                     */
+  int n_ant;
+  int n_bins;
+  double dt;           /* s                                                  */
+} or_antennas;
+
+/* ------------------------------------------------------------------------ */
+/* reading F: the track filter                                               */
+static int track_kept(const or_tracks* T, int64_t i) {
+  double v[12] = {T->x0[i], T->y0[i], T->z0[i], T->x1[i], T->y1[i], T->z1[i],
+                  T->t0[i], T->t1[i], T->bx[i], T->by[i], T->bz[i], T->q[i]};
+  for (int k = 0; k < 12; ++k)
+    if (!isfinite(v[k])) return 0;
+  if (T->q[i] == 0.0) return 0;
+  if (!(T->t1[i] > T->t0[i])) return 0;
+  double lx = v[3] - v[0], ly = v[4] - v[1], lz = v[5] - v[2];
+  if (!(lx * lx + ly * ly + lz * lz > 0.0)) return 0;
+  double b = sqrt(v[8] * v[8] + v[9] * v[9] + v[10] * v[10]);
+  if (!(b > 0.0 && b < 1.0)) return 0;
+  return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* reading M: refractive index at the source and averaged over the path      */
+static void medium_indices(const or_medium* m, double z_e, double z_a, double* n_src, double* n_avg,
+                           double* dn_src_dN0, double* dn_src_dze) {
+  if (m->kind == OR_UNIFORM) {
+    *n_src = m->n;
+    *n_avg = m->n;
+    *dn_src_dN0 = 1.0; /* n = 1 + N0 in the uniform case */
+    *dn_src_dze = 0.0;
+    return;
+  }
+  double E_e = exp(-z_e / m->H);
+  *n_src = 1.0 + m->N0 * E_e;
+  /* (1/dz) * integral_{z_e}^{z_a} N0 exp(-z/H) dz = N0 E_e (1 - exp(-x)) / x, x = dz/H */
+  double x = (z_a - z_e) / m->H;
+  double ratio = (x == 0.0) ? 1.0 : (-expm1(-x)) / x;
+  *n_avg = 1.0 + m->N0 * E_e * ratio;
+  *dn_src_dN0 = E_e;
+  *dn_src_dze = -m->N0 * E_e / m->H;
+}
+
+/* straight emission path from x_e to antenna x_a (reading M) */
+typedef struct {
+  double d[3];   /* x_a - x_e                                               */
+  double R;      /* |d|                                                     */
+  double rh[3];  /* d / R                                                   */
+  double n_src, n_avg, dn_src_dN0, dn_src_dze;
+} or_path;
+
+static void propagate(const or_medium* m, const double xe[3], const double xa[3], or_path* p) {
+  for (int c = 0; c < 3; ++c) p->d[c] = xa[c] - xe[c];
+  p->R = sqrt(p->d[0] * p->d[0] + p->d[1] * p->d[1] + p->d[2] * p->d[2]);
+  for (int c = 0; c < 3; ++c) p->rh[c] = p->d[c] / p->R;
+  medium_indices(m, xe[2], xa[2], &p->n_src, &p->n_avg, &p->dn_src_dN0, &p->dn_src_dze);
+}
+
+/* arrival time relative to the antenna's bin-0 edge, in units of dt (reading T) */
+static double arrival_in_bins(const or_path* p, double t_e, double t_ref, double dt) {
+  return ((t_e - t_ref) + p->n_avg * p->R / OR_C_LIGHT) / dt;
+}
+
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void deposit(double* trace_a, int n_bins, int64_t k, const double v[3], double scale) {
+  if (k < 0 || k >= n_bins) return;
+  for (int c = 0; c < 3; ++c) trace_a[(int64_t)c * n_bins + k] += scale * v[c];
+}
+
+static double K_endpoint(double q) { return q * OR_QE / (4.0 * OR_PI * OR_EPS0 * OR_C_LIGHT); }
+static double K_zhs(double q) {
+  double mu0 = 1.0 / (OR_EPS0 * OR_C_LIGHT * OR_C_LIGHT);
+  return mu0 * q * OR_QE * OR_C_LIGHT / (4.0 * OR_PI);
+}
+
+static void track_points(const or_tracks* T, int64_t i, double x0[3], double x1[3], double xm[3], double beta[3]) {
+  x0[0] = T->x0[i]; x0[1] = T->y0[i]; x0[2] = T->z0[i];
+  x1[0] = T->x1[i]; x1[1] = T->y1[i]; x1[2] = T->z1[i];
+  for (int c = 0; c < 3; ++c) xm[c] = 0.5 * (x0[c] + x1[c]);
+  beta[0] = T->bx[i]; beta[1] = T->by[i]; beta[2] = T->bz[i];
+}
+
+/* V = rhat x (rhat x beta) = (beta.rhat) rhat - beta = -beta_perp */
+static void endpoint_vector(const double beta[3], const double rh[3], double V[3]) {
+  double c = dot3(beta, rh);
+  for (int k = 0; k < 3; ++k) V[k] = c * rh[k] - beta[k];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per (track, antenna) evaluation shared by the forward pass and the bin    */
+/* listing.  Returns the branch taken: 0 two-endpoint, 1 midpoint (C),       */
+/* 2 ZHS single bin, 3 ZHS multi-bin.  u_a/u_b are arrival positions in bins */
+/* (start/end, or t1/t2 for branch C, or interval ends for ZHS).             */
+typedef struct {
+  int branch;
+  double u_a, u_b;
+} or_pair_info;
+
+static or_pair_info endpoint_pair(const or_tracks* T, int64_t i, const double xa[3], double t_ref, double dt,
+                                  int n_bins, const or_medium* m, double eps_C, int mode, double* trace_a) {
+  double x0[3], x1[3], xm[3], beta[3];
+  track_points(T, i, x0, x1, xm, beta);
+  double K = K_endpoint(T->q[i]);
+  double t0 = T->t0[i], t1 = T->t1[i], dte = t1 - t0;
+  or_pair_info info;
+  or_path p0, p1;
+  propagate(m, x0, xa, &p0);
+  propagate(m, x1, xa, &p1);
+  double D0 = 1.0 - p0.n_src * dot3(beta, p0.rh);
+  double D1 = 1.0 - p1.n_src * dot3(beta, p1.rh);
+  if (mode != OR_MODE_FORCE_MIDPOINT && fmin(fabs(D0), fabs(D1)) >= eps_C) {
+    /* reading E: one deposit per endpoint, start +, end - */
+    double u0 = arrival_in_bins(&p0, t0, t_ref, dt);
+    double u1 = arrival_in_bins(&p1, t1, t_ref, dt);
+    double V[3];
+    if (trace_a) {
+      endpoint_vector(beta, p0.rh, V);
+      deposit(trace_a, n_bins, (int64_t)floor(u0), V, +K / (D0 * p0.R * dt));
+      endpoint_vector(beta, p1.rh, V);
+      deposit(trace_a, n_bins, (int64_t)floor(u1), V, -K / (D1 * p1.R * dt));
+    }
+    info.branch = 0; info.u_a = u0; info.u_b = u1;
+    return info;
+  }
+  /* reading C: midpoint geometry, linearised arrival times */
+  or_path pm;
+  propagate(m, xm, xa, &pm);
+  double Dm = 1.0 - pm.n_src * dot3(beta, pm.rh);
+  double tm = 0.5 * (t0 + t1);
+  double tarr_rel = (tm - t_ref) + pm.n_avg * pm.R / OR_C_LIGHT;
+  double ua = (tarr_rel - Dm * dte / 2.0) / dt; /* arrival of the start */
+  double ub = (tarr_rel + Dm * dte / 2.0) / dt; /* arrival of the end   */
+  int64_t ka = (int64_t)floor(ua), kb = (int64_t)floor(ub);
+  if (trace_a && ka != kb) {
+    double V[3];
+    endpoint_vector(beta, pm.rh, V);
+    double amp = K / (Dm * pm.R * dt);
+    deposit(trace_a, n_bins, ka, V, +amp);
+    deposit(trace_a, n_bins, kb, V, -amp);
+  }
+  info.branch = 1; info.u_a = ua; info.u_b = ub;
+  return info;
+}
+
+static or_pair_info zhs_pair(const or_tracks* T, int64_t i, const double xa[3], double t_ref, double dt, int n_bins,
+                             const or_medium* m, int mode, double* trace_a) {
+  double x0[3], x1[3], xm[3], beta[3];
+  track_points(T, i, x0, x1, xm, beta);
+  double KA = K_zhs(T->q[i]);
+  double t0 = T->t0[i], t1 = T->t1[i], dte = t1 - t0;
+  or_path pm;
+  propagate(m, xm, xa, &pm);
+  double bdr = dot3(beta, pm.rh);
+  double Dm = 1.0 - pm.n_src * bdr;
+  double bperp[3];
+  for (int c = 0; c < 3; ++c) bperp[c] = beta[c] - bdr * pm.rh[c];
+  double tm = 0.5 * (t0 + t1);
+  double tarr_rel = (tm - t_ref) + pm.n_avg * pm.R / OR_C_LIGHT;
+  double half = fabs(Dm) * dte / 2.0;
+  double t_lo = tarr_rel - half, t_hi = tarr_rel + half;
+  double u_lo = t_lo / dt, u_hi = t_hi / dt;
+  int64_t k_lo = (int64_t)floor(u_lo), k_hi = (int64_t)floor(u_hi);
+  or_pair_info info;
+  info.u_a = u_lo; info.u_b = u_hi;
+  if (mode == OR_MODE_ZHS_EDGE_SAMPLED) {
+    /* the step potential sampled at bin edges e_k = t_ref + k dt, nonzero for
+       t_lo < e_k <= t_hi: the form whose edge differences equal the Endpoint
+       field of the same track forced to its midpoint */
+    info.branch = 3;
+    if (trace_a) {
+      for (int64_t k = k_lo + 1; k <= k_hi; ++k) {
+        if (k < 0 || k >= n_bins) continue;
+        deposit(trace_a, n_bins, k, bperp, KA / (pm.R * fabs(Dm)));
+      }
+    }
+    return info;
+  }
+  if (k_lo == k_hi) {
+    info.branch = 2;
+    if (trace_a) deposit(trace_a, n_bins, k_lo, bperp, KA * dte / (pm.R * dt));
+    return info;
+  }
+  info.branch = 3;
+  if (trace_a) {
+    int64_t kb = k_lo < 0 ? 0 : k_lo;
+    int64_t ke = k_hi > n_bins - 1 ? n_bins - 1 : k_hi;
+    for (int64_t k = kb; k <= ke; ++k) {
+      double e_lo = (double)k * dt, e_hi = (double)(k + 1) * dt;
+      double o = fmin(t_hi, e_hi) - fmax(t_lo, e_lo);
+      if (o <= 0.0) continue;
+      deposit(trace_a, n_bins, k, bperp, KA / pm.R * (o / fabs(Dm)) / dt);
+    }
+  }
+  return info;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward: traces[a][c][k] (row-major [n_ant][3][n_bins]) are ACCUMULATED.  */
+/* Returns the number of tracks kept by the filter.                          */
+int64_t oracle_forward(const or_tracks* T, int64_t n, const or_antennas* A, const or_medium* m, int formalism,
+                       double eps_C, int mode, double* traces) {
+  int64_t kept = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!track_kept(T, i)) continue;
+    ++kept;
+    for (int a = 0; a < A->n_ant; ++a) {
+      const double* xa = A->xyz + 3 * (int64_t)a;
+      double* tr = traces + (int64_t)a * 3 * A->n_bins;
+      if (formalism == OR_ENDPOINT)
+        endpoint_pair(T, i, xa, A->t_ref[a], A->dt, A->n_bins, m, eps_C, mode, tr);
+      else
+        zhs_pair(T, i, xa, A->t_ref[a], A->dt, A->n_bins, m, mode, tr);
+    }
+  }
+  return kept;
+}
+
+/* Per (track, antenna) arrival positions: branch[i*n_ant+a] (-1 if the track is
+   filtered out), u[2*(i*n_ant+a)+{0,1}] in bins relative to the antenna's bin-0
+   edge: Endpoint start/end (branch 0), t1/t2 (branch C), ZHS interval ends. */
+void oracle_arrivals(const or_tracks* T, int64_t n, const or_antennas* A, const or_medium* m, int formalism,
+                     double eps_C, int32_t* branch, double* u) {
+  for (int64_t i = 0; i < n; ++i) {
+    int keep = track_kept(T, i);
+    for (int a = 0; a < A->n_ant; ++a) {
+      int64_t j = i * A->n_ant + a;
+      if (!keep) { branch[j] = -1; u[2 * j] = u[2 * j + 1] = 0.0; continue; }
+      const double* xa = A->xyz + 3 * (int64_t)a;
+      or_pair_info info = (formalism == OR_ENDPOINT)
+                              ? endpoint_pair(T, i, xa, A->t_ref[a], A->dt, A->n_bins, m, eps_C, OR_MODE_NORMAL, 0)
+                              : zhs_pair(T, i, xa, A->t_ref[a], A->dt, A->n_bins, m, OR_MODE_NORMAL, 0);
+      branch[j] = info.branch;
+      u[2 * j] = info.u_a;
+      u[2 * j + 1] = info.u_b;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* reading G: reverse-mode gradient of the Endpoint traces.                  */
+/* One deposit l = kappa (g.V)/(D R) with upstream g = dL/dtrace at its bin: */
+/*   dl/dd    = kappa/(D R^2) [ -(rhat.g) V + c (g - rhat (rhat.g))           */
+/*                               - (g.V) (n V / D + rhat) ]                  */
+/*   dl/dbeta = kappa/(D R)   [ (rhat.g) rhat - g + (g.V) n rhat / D ]        */
+/*   dl/dn    = kappa (g.V) c / (D^2 R)                                       */
+/* with d = x_a - x_e, c = beta.rhat, V = c rhat - beta, D = 1 - n c.        */
+static void deposit_adjoint(const or_path* p, const double beta[3], const double g[3], double kappa,
+                            double gd[3], double gbeta[3], double* gn) {
+  const double* rh = p->rh;
+  double R = p->R, n = p->n_src;
+  double c = dot3(beta, rh);
+  double V[3];
+  for (int k = 0; k < 3; ++k) V[k] = c * rh[k] - beta[k];
+  double D = 1.0 - n * c;
+  double gV = dot3(g, V), rg = dot3(rh, g);
+  for (int k = 0; k < 3; ++k) {
+    gd[k] = kappa / (D * R * R) * (-rg * V[k] + c * (g[k] - rh[k] * rg) - gV * (n * V[k] / D + rh[k]));
+    gbeta[k] = kappa / (D * R) * (rg * rh[k] - g[k] + gV * n * rh[k] / D);
+  }
+  *gn = kappa * gV * c / (D * D * R);
+}
+
+static void gather_g(const double* G_a, int n_bins, int64_t k, double g[3]) {
+  for (int c = 0; c < 3; ++c) g[c] = (k >= 0 && k < n_bins) ? G_a[(int64_t)c * n_bins + k] : 0.0;
+}
+
+/* G: dL/dtraces [n_ant][3][n_bins].  Outputs are ACCUMULATED:
+   track_grad[i][11] = d/d{x0,y0,z0,x1,y1,z1,t0,t1,bx,by,bz}, ant_grad[a][3],
+   *dN0 = d/dN0 (exponential) or d/d(n-1) (uniform). */
+void oracle_backward(const or_tracks* T, int64_t n, const or_antennas* A, const or_medium* m, double eps_C,
+                     const double* G, double* track_grad, double* ant_grad, double* dN0) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (!track_kept(T, i)) continue;
+    double x0[3], x1[3], xm[3], beta[3];
+    track_points(T, i, x0, x1, xm, beta);
+    double K = K_endpoint(T->q[i]);
+    double t0 = T->t0[i], t1 = T->t1[i], dte = t1 - t0;
+    double* tg = track_grad + 11 * i;
+    for (int a = 0; a < A->n_ant; ++a) {
+      const double* xa = A->xyz + 3 * (int64_t)a;
+      const double* G_a = G + (int64_t)a * 3 * A->n_bins;
+      double dt = A->dt, t_ref = A->t_ref[a];
+      or_path p0, p1;
+      propagate(m, x0, xa, &p0);
+      propagate(m, x1, xa, &p1);
+      double D0 = 1.0 - p0.n_src * dot3(beta, p0.rh);
+      double D1 = 1.0 - p1.n_src * dot3(beta, p1.rh);
+      double gd[3], gb[3], gn, g[3];
+      if (fmin(fabs(D0), fabs(D1)) >= eps_C) {
+        const or_path* ps[2] = {&p0, &p1};
+        double ts[2] = {t0, t1};
+        for (int j = 0; j < 2; ++j) {
+          double u = arrival_in_bins(ps[j], ts[j], t_ref, dt);
+          gather_g(G_a, A->n_bins, (int64_t)floor(u), g);
+          double kappa = (j == 0 ? +K : -K) / dt;
+          deposit_adjoint(ps[j], beta, g, kappa, gd, gb, &gn);
+          for (int k = 0; k < 3; ++k) {
+            tg[3 * j + k] -= gd[k];
+            ant_grad[3 * a + k] += gd[k];
+            tg[8 + k] += gb[k];
+          }
+          tg[3 * j + 2] += gn * ps[j]->dn_src_dze;
+          *dN0 += gn * ps[j]->dn_src_dN0;
+        }
+      } else {
+        or_path pm;
+        propagate(m, xm, xa, &pm);
+        double Dm = 1.0 - pm.n_src * dot3(beta, pm.rh);
+        double tm = 0.5 * (t0 + t1);
+        double tarr_rel = (tm - t_ref) + pm.n_avg * pm.R / OR_C_LIGHT;
+        double ua = (tarr_rel - Dm * dte / 2.0) / dt;
+        double ub = (tarr_rel + Dm * dte / 2.0) / dt;
+        int64_t ka = (int64_t)floor(ua), kb = (int64_t)floor(ub);
+        if (ka == kb) continue;
+        double ga[3], gbv[3];
+        gather_g(G_a, A->n_bins, ka, ga);
+        gather_g(G_a, A->n_bins, kb, gbv);
+        for (int k = 0; k < 3; ++k) g[k] = ga[k] - gbv[k];
+        deposit_adjoint(&pm, beta, g, K / dt, gd, gb, &gn);
+        for (int k = 0; k < 3; ++k) {
+          tg[k] -= 0.5 * gd[k];
+          tg[3 + k] -= 0.5 * gd[k];
+          ant_grad[3 * a + k] += gd[k];
+          tg[8 + k] += gb[k];
+        }
+        tg[2] += 0.5 * gn * pm.dn_src_dze;
+        tg[5] += 0.5 * gn * pm.dn_src_dze;
+        *dN0 += gn * pm.dn_src_dN0;
+      }
+      /* d/dt0 and d/dt1 stay zero: with bins held fixed the deposits do not
+         depend on the times (reading G). */
+    }
+  }
+}
+
+/* filter only: writes keep[i] in {0,1}, returns the kept count */
+int64_t oracle_filter(const or_tracks* T, int64_t n, uint8_t* keep) {
+  int64_t kept = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    keep[i] = (uint8_t)track_kept(T, i);
+    kept += keep[i];
+  }
+  return kept;
+}
+
+/* straight-path quantities for one emission point / antenna pair:
+   out = {R, n_src, n_avg, arrival delay n_avg R / c (s)} */
+void oracle_propagate(const or_medium* m, const double* xe, const double* xa, double* out) {
+  or_path p;
+  propagate(m, xe, xa, &p);
+  out[0] = p.R;
+  out[1] = p.n_src;
+  out[2] = p.n_avg;
+  out[3] = p.n_avg * p.R / OR_C_LIGHT;
+}
