@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark of the track x antenna radio hot path on GB300.
+
+One step = one pass of the hot path over the 2e7-track shower of the
+160-antenna star array (exponential atmosphere, 4096 bins of 0.2 ns): track
+ingest + filter, then the Endpoint and the ZHS radio processes (the two
+formalisms the paper runs side by side on one shower), mixed precision.  The
+headline is track-antenna pairs per second over both formalisms.
+
+Also reported: the FP64 path on the same workload (a sample of it), the adjoint
+/ forward time ratio on the differentiable 1e6-track x 64-antenna workload, the
+batched persistent launch against separate launches (on a scaled-down batch of
+uneven showers), the ALU roofline of the dominant kernel, the oracle timed on
+the host cores, and GPU clocks during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank takes its own seeded shower (weak scaling); there is no
+collective on the data path, only a barrier and a max over the ranks' times.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+# algorithmic FP32-pipe operations per Endpoint pair, counted from the plain
+# formula (two endpoints: propagator, Doppler factor, arrival bin, field vector
+# and amplitude): 56 arithmetic + 6 special-function operations
+ALG_OPS_PER_ENDPOINT_PAIR = 62
+SHARED_ATOMICS_PER_ENDPOINT_PAIR = 6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tracks", type=int, default=None, help="override the track count (testing only)")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--cpu-sample-tracks", type=int, default=40000)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def host_tracks(w, n, seed_offset):
+    from paper_2309_03717_gb300 import synth
+    w = dict(w)
+    w["seed"] = w["seed"] + 7919 * seed_offset
+    return synth.workload_tracks(w, n)
+
+
+def to_dev(tracks, torch, pinned=False):
+    out = {}
+    for k, v in tracks.items():
+        t = torch.from_numpy(np.ascontiguousarray(v))
+        out[k] = t.pin_memory() if pinned else t.cuda()
+    return out
+
+
+def cpu_baseline(w, n_tracks, formalisms):
+    """The FP64 oracle as it stands, single-threaded, on a sample of the workload."""
+    import oracle
+    from paper_2309_03717_gb300 import synth
+    tr = synth.make_tracks(n_tracks, w["seed"] + 17, w["zenith"], np.float32)
+    trs = oracle.tracks_from_ns(tr)
+    pairs = 0
+    t0 = time.perf_counter()
+    for f in formalisms:
+        oracle.forward(trs, w["ant_xyz"], w["t_start_ns"] * 1e-9, w["n_bins"], w["dt_ns"] * 1e-9, w["medium"],
+                       oracle.ENDPOINT if f == "endpoint" else oracle.ZHS)
+        pairs += n_tracks * len(w["ant_xyz"])
+    dt = time.perf_counter() - t0
+    return {"value": pairs / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_tracks} tracks x {len(w['ant_xyz'])} antennas x {len(formalisms)} formalisms "
+                      f"({pairs:.3g} pairs, {dt:.1f} s, FP64 C oracle, one thread)"}
+
+
+def run_reference(args):
+    """Reference arm: the oracle, timed on the host cores on bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2309_03717_gb300 import synth
+    import oracle
+    oracle.build()
+    w = synth.workload(1)
+    n = args.cpu_sample_tracks
+    for _ in range(args.warmup):
+        cpu_baseline(w, max(n // 10, 100), ("endpoint", "zhs"))
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(w, n, ("endpoint", "zhs")))
+    elapsed = time.perf_counter() - t0
+    v = sum(x["value"] for x in vals) / len(vals)
+    pairs_per_step = 2 * n * len(w["ant_xyz"])
+    line = {
+        "impl": "reference", "metric": "track-antenna pairs/sec (Endpoint, ZHS) on 1 GB300; backward/forward time ratio",
+        "value": v, "unit": "pairs/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "shower 2e7 tracks (sampled), star 8x20 antennas, exp. atmosphere, 4096 x 0.2 ns",
+                   "sample_tracks_per_step": n, "pairs_per_step": pairs_per_step},
+        "cpu_baseline": {"value": v, "kind": "oracle", "cores": 1, "sample": vals[0]["sample"]},
+        "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    from paper_2309_03717_gb300 import build, c8r, synth
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    c8r.load()
+
+    w = synth.workload(1)
+    T = args.tracks or w["n_tracks"]
+    A = len(w["ant_xyz"])
+    tracks_h = host_tracks(w, T, rank)
+    dev = to_dev(tracks_h, torch)
+    procs = {f: c8r.RadioProcess(w["medium"], w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], f, "mixed")
+             for f in ("endpoint", "zhs")}
+    outs = {f: torch.empty((A, 3, w["n_bins"]), dtype=torch.float32, device="cuda") for f in procs}
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for f, p in procs.items():
+            p.reset()
+            p.push(dev)
+            p.traces(out=outs[f])
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    kept = procs["endpoint"].stats()["tracks_kept"]
+    pairs_per_step = 2 * kept * A
+    c8r.c8r_profile(procs["endpoint"].ctx, True)
+    c8r.c8r_profile(procs["zhs"].ctx, True)
+    barrier()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    prof_e = c8r.c8r_profile_read(procs["endpoint"].ctx)
+    prof_z = c8r.c8r_profile_read(procs["zhs"].ctx)
+    c8r.c8r_profile(procs["endpoint"].ctx, False)
+    c8r.c8r_profile(procs["zhs"].ctx, False)
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = pairs_per_step * args.steps * world / (t_max * 1e-3)
+
+    # end to end through the public API: pinned host tracks in, host traces out
+    pinned = to_dev(tracks_h, torch, pinned=True)
+    host_out = {f: torch.empty((A, 3, w["n_bins"]), dtype=torch.float32).pin_memory() for f in procs}
+    h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+
+    def step_e2e():
+        d = {k: v.cuda(non_blocking=True) for k, v in pinned.items()}
+        for f, p in procs.items():
+            p.reset()
+            p.push(d)
+            p.traces(out=host_out[f])
+
+    step_e2e()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = pairs_per_step * args.steps * world / e2e_s
+
+    # dominant kernel: the Endpoint pair kernel (one launch per chunk)
+    pk, pk_src = peaks()
+    clocks = clk.summary()
+    kernel_ms = prof_e["pair_ms"] / max(prof_e["pair_launches"], 1)
+    pairs_per_launch = kept * A / max(prof_e["pair_launches"] / args.steps, 1)
+    alg_ops = ALG_OPS_PER_ENDPOINT_PAIR * pairs_per_launch
+    achieved = alg_ops / (kernel_ms * 1e-3) / 1e9
+    peak_alu = SM_COUNT * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+    result = {
+        "metric": "track-antenna pairs/sec (Endpoint, ZHS) on 1 GB300; backward/forward time ratio",
+        "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+ff (mixed)", "data": "synthetic",
+        "config": {"workload": f"shower {T:.3g} tracks x star 8x20 antennas, exponential atmosphere, "
+                               f"Endpoint + ZHS, 4096 bins x 0.2 ns, mixed precision",
+                   "tracks_per_gpu": T, "antennas": A, "n_bins": w["n_bins"], "formalisms": ["endpoint", "zhs"],
+                   "l2": "inputs larger than L2 (tracks %.2f GB per GPU)" % (T * 48 / 1e9),
+                   "parallelism": f"{world} independent showers (weak)"},
+        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(prof_e["pair_launches"] + prof_e["ingest_launches"] + prof_z["pair_launches"]
+                            + prof_z["ingest_launches"]),
+        "roofline": {"bound": "alu", "kernel": "k_forward<OpsMixed<Endpoint, exponential>>",
+                     "achieved": achieved, "peak": peak_alu, "unit": "Gop/s (FP32 lane ops)",
+                     "frac": achieved / peak_alu, "traffic": None,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
+                                    f"({pk_src} max SM clock)",
+                     "ops_per_pair": ALG_OPS_PER_ENDPOINT_PAIR, "kernel_ms": kernel_ms,
+                     "pairs_per_launch": pairs_per_launch},
+        "kernels": {"endpoint_pair_ms_per_step": prof_e["pair_ms"] / args.steps,
+                    "zhs_pair_ms_per_step": prof_z["pair_ms"] / args.steps,
+                    "ingest_ms_per_step": (prof_e["ingest_ms"] + prof_z["ingest_ms"]) / args.steps,
+                    "endpoint_pairs_per_s": kept * A * args.steps / (prof_e["pair_ms"] * 1e-3),
+                    "zhs_pairs_per_s": kept * A * args.steps / (prof_z["pair_ms"] * 1e-3)},
+        "clocks": clocks,
+    }
+    for p in procs.values():
+        p.close()
+    del dev, pinned
+
+    if rank == 0 and world == 1 and not args.no_extras:
+        result["extras"] = extras(torch, c8r, synth, w)
+        result["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_tracks, ("endpoint", "zhs"))
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def extras(torch, c8r, synth, w):
+    out = {}
+    # FP64 path on a sample of the same workload
+    n64 = 1_000_000
+    tr = host_tracks(w, n64, 99)
+    d64 = {k: torch.from_numpy(v.astype(np.float64)).cuda() for k, v in tr.items()}
+    A = len(w["ant_xyz"])
+    for f in ("endpoint", "zhs"):
+        p = c8r.RadioProcess(w["medium"], w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], f, "fp64")
+        p.push(d64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(2):
+            p.push(d64)
+        e1.record()
+        torch.cuda.synchronize()
+        out[f"fp64_{f}_pairs_per_s"] = 2 * n64 * A / (e0.elapsed_time(e1) * 1e-3)
+        p.close()
+    del d64
+    # adjoint / forward on the differentiable workload (1e6 tracks x 64 antennas, 2048 bins)
+    w4 = synth.workload(4)
+    tr4 = synth.workload_tracks(w4)
+    d4 = {k: torch.from_numpy(v).cuda() for k, v in tr4.items()}
+    p = c8r.RadioProcess(w4["medium"], w4["ant_xyz"], w4["t_start_ns"], w4["n_bins"], w4["dt_ns"], "endpoint", "mixed")
+    n4 = tr4["x0"].size
+    g = torch.randn((len(w4["ant_xyz"]), 3, w4["n_bins"]), device="cuda")
+    tg = {f: torch.zeros(n4, dtype=torch.float32, device="cuda") for f in c8r.GRAD_FIELDS}
+    ag = torch.zeros((len(w4["ant_xyz"]), 3), dtype=torch.float64, device="cuda")
+    dn = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def fwd():
+        p.reset()
+        p.push(d4)
+
+    def bwd():
+        c8r.c8r_backward(p.ctx, d4, g, tg, ag, dn)
+
+    for fn in (fwd, bwd):
+        fn()
+    torch.cuda.synchronize()
+    times = {}
+    for name, fn in (("fwd", fwd), ("bwd", bwd)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / 3
+    out["diff_fwd_ms"] = times["fwd"]
+    out["diff_bwd_ms"] = times["bwd"]
+    out["bwd_fwd_ratio"] = times["bwd"] / times["fwd"]
+    out["diff_workload"] = "1e6 tracks x star 8x8, 2048 x 0.2 ns, exponential atmosphere, Endpoint mixed"
+    p.close()
+    return out
+
+
+if __name__ == "__main__":
+    main()

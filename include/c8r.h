@@ -1,0 +1,267 @@
+/*
+ * c8r.h -- C ABI of the GB300 radio-emission library (libc8r).
+ *
+ * The library runs the step that the CORSIKA 8 radio module repeats for every
+ * particle track and every antenna (paper §2: a track passes the track filter,
+ * goes to the formalism, is looped over all antennas of the antenna collection,
+ * fed to the propagator, and the result is stored in the antenna).  The two
+ * formalisms are the ones the paper names in §1: "Endpoint" (CoREAS) and "ZHS".
+ * The user-facing factories of §4 map onto it as follows:
+ *
+ *   make_simple_radio_propagator(environment)      -> c8r_set_medium
+ *   make_radio_process_CoREAS/ZHS(detector, ...)   -> c8r_set_antennas
+ *   RadioProcess receiving a track                 -> c8r_push_tracks
+ *   reading the antenna instances                  -> c8r_fetch_traces
+ *
+ * Conventions for every call:
+ *   - Return value: C8R_OK (0) or a negative C8R_E* code; c8r_last_error()
+ *     then holds a one-line message.  No call aborts the process.
+ *   - Units: metres and nanoseconds at the interface.  Traces hold the electric
+ *     field in V/m (Endpoint) or the vector potential in V s/m (ZHS).
+ *   - Ownership: the caller owns every pointer it passes; the library copies
+ *     what it keeps (antenna table) and owns only its context's device memory
+ *     (the trace accumulator and the derived-track scratch).
+ *   - Asynchrony: calls that take a stream enqueue work on it and return; the
+ *     caller's device buffers must stay valid until that work has run.  Copies
+ *     into host memory synchronise the stream before returning.
+ *   - Threads: a context is used by one host thread at a time.
+ */
+#ifndef C8R_H
+#define C8R_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define C8R_OK 0
+#define C8R_EINVAL (-1)     /* bad argument (size, pointer, non-finite value, call order) */
+#define C8R_ENOMEM (-2)     /* device or host allocation failed                         */
+#define C8R_ECUDA (-3)      /* a CUDA runtime call or kernel reported an error          */
+#define C8R_ECANCELLED (-4) /* a kernel gave up a bounded wait and returned early       */
+#define C8R_ETOOBIG (-5)    /* the trace length does not fit the on-chip trace tile     */
+#define C8R_ESTATE (-6)     /* call made before the context was configured for it      */
+
+/* medium kinds (straight-line propagator, §4 listing) */
+#define C8R_UNIFORM 0      /* n constant                                              */
+#define C8R_EXPONENTIAL 1  /* n(z) = 1 + N0 exp(-z / H), z = altitude in metres         */
+
+/* formalisms (§1) */
+#define C8R_ENDPOINT 0
+#define C8R_ZHS 1
+
+/* arithmetic precision of a context */
+#define C8R_FP64 0   /* all arithmetic in FP64; traces FP64                            */
+#define C8R_MIXED 1  /* FP32 field arithmetic, compensated (float-float) arrival time,
+                        bin index and interval ends; traces FP32                       */
+
+/* element type of caller arrays */
+#define C8R_F32 0
+#define C8R_F64 1
+
+typedef struct c8r_ctx c8r_ctx;
+
+/* Particle tracks in structure-of-arrays form: twelve DEVICE arrays of one
+ * element type (dtype = C8R_F32 or C8R_F64), each of the length passed with them.
+ * Track i runs in a straight line from (x0,y0,z0)[i] at time t0[i] to
+ * (x1,y1,z1)[i] at t1[i] (m, ns) with velocity (bx,by,bz)[i] in units of c and
+ * charge q[i] in units of e.  A C8R_MIXED context rounds FP64 input to FP32. */
+typedef struct {
+  int32_t dtype;
+  const void *x0, *y0, *z0;
+  const void *x1, *y1, *z1;
+  const void *t0, *t1;
+  const void *bx, *by, *bz;
+  const void *q;
+} c8r_tracks;
+
+/* Gradients of a scalar loss with respect to each track's inputs: eleven DEVICE
+ * arrays of one element type (C8R_F32 for a C8R_MIXED context, C8R_F64 for
+ * C8R_FP64), each as long as the track arrays.  Units: per metre for positions,
+ * per nanosecond for times, per unit of beta for the velocity. */
+typedef struct {
+  int32_t dtype;
+  void *x0, *y0, *z0;
+  void *x1, *y1, *z1;
+  void *t0, *t1;
+  void *bx, *by, *bz;
+} c8r_track_grads;
+
+typedef struct {
+  int64_t tracks_pushed; /* tracks passed to c8r_push_tracks since creation/reset    */
+  int64_t tracks_kept;   /* of those, tracks the track filter let through           */
+  int64_t pairs;         /* kept tracks x antennas evaluated                         */
+} c8r_stats_t;
+
+/* ---- lifecycle ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  *out is NULL on failure.
+ * The context owns no trace memory until c8r_set_antennas. */
+int c8r_create(c8r_ctx** out, int device);
+
+/* Release a context and its device memory.  NULL is accepted.  The caller must
+ * not destroy a context while work it enqueued may still be running. */
+void c8r_destroy(c8r_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none).  The pointer
+ * stays valid until the next call on the context.  ctx == NULL gives the message
+ * of the last failed c8r_create in this thread. */
+const char* c8r_last_error(const c8r_ctx* ctx);
+
+/* ---- configuration (the §4 factories) -------------------------------------- */
+
+/* Medium of the straight-line propagator (§2 "propagator", §4
+ * make_simple_radio_propagator).  kind = C8R_UNIFORM: n_or_N0 is the refractive
+ * index n > 0, scale_height_m is ignored.  kind = C8R_EXPONENTIAL: n_or_N0 is the
+ * refractivity N0 >= 0 at altitude 0 and scale_height_m is H > 0.
+ * Along a straight path the propagator uses the path-averaged index for the
+ * travel time and the index at the emission point in the Doppler factor.
+ * May be called before or after c8r_set_antennas; traces already accumulated
+ * are kept.  EINVAL on non-finite or out-of-range values. */
+int c8r_set_medium(c8r_ctx* ctx, int kind, double n_or_N0, double scale_height_m);
+
+/* Antenna collection ("detector", §2, §4 make_radio_process_*).  pos_xyz: HOST
+ * array [n_ant][3] of antenna positions (m); t_start_ns: HOST array [n_ant] of the
+ * time of each trace's first bin edge (ns).  Every antenna records n_bins bins of
+ * dt_ns, three components each; bin k of antenna a covers
+ * [t_start_ns[a] + k dt_ns, t_start_ns[a] + (k + 1) dt_ns).  formalism selects
+ * Endpoint or ZHS; precision selects C8R_FP64 or C8R_MIXED.  Allocates (and
+ * zeroes) the trace accumulator [n_ant][3][n_bins] of FP64 (C8R_FP64) or FP32
+ * (C8R_MIXED).  Replaces any previous antenna set and discards its traces.
+ * EINVAL on n_ant < 1, n_bins < 1, dt_ns <= 0 or non-finite values; ETOOBIG if
+ * one antenna's trace does not fit the on-chip tile; ENOMEM. */
+int c8r_set_antennas(c8r_ctx* ctx, int32_t n_ant, const double* pos_xyz, const double* t_start_ns,
+                     int32_t n_bins, double dt_ns, int formalism, int precision);
+
+/* Threshold eps_C of the near-Cherenkov Endpoint treatment (default 1e-3): when
+ * min(|D_start|, |D_end|) < eps_C, D = 1 - n beta.rhat, the pair is evaluated at
+ * the track midpoint with linearised arrival times.  EINVAL unless 0 < eps < 1. */
+int c8r_set_cherenkov_threshold(c8r_ctx* ctx, double eps_C);
+
+/* Launch shape of the forward kernels: antennas per CTA (their traces live in
+ * shared memory; 1..8, capped by what fits for n_bins) and the target number of
+ * CTA waves per launch, which sets how many track ranges each antenna tile is
+ * cut into.  0 keeps the automatic choice.  The result does not depend on the
+ * shape beyond the order of floating-point additions (§5: identical pulses for
+ * any number of threads).  Also sets the tracks per internal chunk (0 = 2^24):
+ * longer pushes are processed chunk by chunk through the same scratch. */
+int c8r_set_launch_shape(c8r_ctx* ctx, int a_tile, int waves, int64_t chunk_tracks);
+
+/* ---- the hot path ----------------------------------------------------------- */
+
+/* RadioProcess receiving tracks (§2 flow): for the n tracks, apply the track
+ * filter (keep iff q != 0, all fields finite, t1 > t0, |x1 - x0| > 0 and
+ * 0 < |beta| < 1), then for every kept track and every antenna run the
+ * straight-line propagator, evaluate the formalism and add the result into the
+ * antenna's trace.  ACCUMULATES into the context's traces.  Enqueued on
+ * cuda_stream (a cudaStream_t; NULL = legacy default stream).  The track arrays
+ * must stay valid until the work has run.  n == 0 is a no-op.
+ * EINVAL on NULL arrays or n < 0; ESTATE before c8r_set_antennas/c8r_set_medium. */
+int c8r_push_tracks(c8r_ctx* ctx, const c8r_tracks* tracks, int64_t n, void* cuda_stream);
+
+/* Copy the accumulated traces, layout [n_ant][3][n_bins] row-major, element type
+ * FP64 (C8R_FP64 context) or FP32 (C8R_MIXED), into dst: a device pointer if
+ * dst_is_device != 0, else host memory (the call then synchronises the stream).
+ * reset != 0 zeroes the accumulator after the copy.  ESTATE before
+ * c8r_set_antennas. */
+int c8r_fetch_traces(c8r_ctx* ctx, void* dst, int dst_is_device, int reset, void* cuda_stream);
+
+/* Zero the accumulated traces and the statistics. */
+int c8r_reset(c8r_ctx* ctx, void* cuda_stream);
+
+/* Adjoint of c8r_push_tracks for the Endpoint formalism (not in the paper; a
+ * hand-written reverse pass).  Given the same tracks and grad_traces = dL/dtraces
+ * (DEVICE, layout and element type of c8r_fetch_traces), ACCUMULATES dL/d(track
+ * inputs) into out_tracks, dL/d(antenna positions) into out_ant_grad (DEVICE FP64
+ * [n_ant][3]) and dL/dN0 into *out_dN0 (DEVICE FP64 scalar; for a uniform medium
+ * the derivative with respect to n - 1).  Bin indices and the near-Cherenkov
+ * branch are held fixed, so the time derivatives are zero.  The per-pair geometry
+ * is recomputed, not stored.  EINVAL for a ZHS context or mismatched dtypes. */
+int c8r_backward(c8r_ctx* ctx, const c8r_tracks* tracks, int64_t n, const void* grad_traces,
+                 const c8r_track_grads* out_tracks, double* out_ant_grad, double* out_dN0, void* cuda_stream);
+
+/* Kernel timing.  While enabled, every ingest and pair-kernel launch of
+ * c8r_push_tracks is bracketed by CUDA events recorded on the launching stream.
+ * c8r_profile_read synchronises and returns the summed device time (ms) and the
+ * launch counts since profiling was enabled, then clears them. */
+int c8r_profile(c8r_ctx* ctx, int enable);
+int c8r_profile_read(c8r_ctx* ctx, double* pair_ms, int64_t* pair_launches, double* ingest_ms,
+                     int64_t* ingest_launches);
+
+/* Statistics since creation or the last reset.  Synchronises the context's last
+ * stream.  Also reports (as ECANCELLED) a kernel that gave up a bounded wait. */
+int c8r_stats(c8r_ctx* ctx, c8r_stats_t* out);
+
+/* Per (track, antenna) arrival positions exactly as the kernels compute them,
+ * for validation: branch[i*n_ant + a] = -1 (track filtered out), 0 (Endpoint,
+ * two endpoints), 1 (Endpoint, near-Cherenkov midpoint), 2 (ZHS, one bin) or
+ * 3 (ZHS, several bins); bin[2*(i*n_ant+a) + j] and frac[...] give the bin index
+ * and the fractional position in the bin of the two arrival times (start/end,
+ * the two linearised midpoint arrivals, or the ZHS interval ends).  All DEVICE
+ * arrays.  Does not touch the traces. */
+int c8r_arrivals(c8r_ctx* ctx, const c8r_tracks* tracks, int64_t n, int32_t* branch, int32_t* bin, float* frac,
+                 void* cuda_stream);
+
+/* ---- batched showers (not in the paper) -------------------------------------- */
+
+/* Many independent showers of uneven size in one persistent launch.  Shower s
+ * has n_tracks[s] tracks stored at offset track_offset[s] of the concatenated
+ * track arrays, n_ant[s] antennas at offset ant_offset[s] of the concatenated
+ * antenna arrays, and its traces at offset ant_offset[s]*3*n_bins of the
+ * concatenated FP32 trace buffer.  All showers share the medium, n_bins, dt_ns
+ * and formalism; precision is C8R_MIXED.  Host arrays are read during the call. */
+typedef struct {
+  int32_t n_showers;
+  const int64_t* n_tracks;      /* HOST [n_showers]                            */
+  const int64_t* track_offset;  /* HOST [n_showers]                            */
+  const int32_t* n_ant;         /* HOST [n_showers]                            */
+  const int32_t* ant_offset;    /* HOST [n_showers]                            */
+  const double* pos_xyz;        /* HOST [sum n_ant][3], m                      */
+  const double* t_start_ns;     /* HOST [sum n_ant], ns                        */
+  int32_t n_bins;
+  double dt_ns;
+  int32_t formalism;
+} c8r_batch_desc;
+
+typedef struct c8r_batch c8r_batch;
+
+/* Prepare a batch on `device` for the given layout and medium (kind, n_or_N0,
+ * scale height as in c8r_set_medium): uploads the antenna tables, sizes the
+ * scratch, builds the work list and picks the tile shape with the autotuner. */
+int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* desc, int medium_kind, double n_or_N0,
+                     double scale_height_m);
+void c8r_batch_destroy(c8r_batch* b);
+const char* c8r_batch_last_error(const c8r_batch* b);
+
+/* Run the batch: tracks = concatenated DEVICE track arrays (FP32), traces_out =
+ * DEVICE FP32 [sum n_ant][3][n_bins], ACCUMULATED.  use_graph != 0 replays a CUDA
+ * graph captured on the first call (the capture happens on cuda_stream); the
+ * graph is bound to the track and trace pointers of that first call and is
+ * recaptured when they change. */
+int c8r_batch_run(c8r_batch* b, const c8r_tracks* tracks, float* traces_out, int use_graph, void* cuda_stream);
+
+/* Set (value != 0) or clear the batch's cancel word.  Persistent CTAs read it
+ * before taking each work item and stop when it is set; c8r_batch_sync then
+ * reports ECANCELLED.  Uses an internal non-blocking stream, so it can be called
+ * while a batch runs.  The word stays set until cleared. */
+int c8r_batch_set_cancel(c8r_batch* b, int value);
+
+/* Synchronise cuda_stream and report the batch's status: ECANCELLED if the last
+ * run was cancelled or a kernel gave up a bounded wait (the status is cleared). */
+int c8r_batch_sync(c8r_batch* b, void* cuda_stream);
+
+/* ---- device peaks microbenchmark ----------------------------------------------- */
+
+/* Measured issue rates on `device`, in operations per second: FP32 FMA, FP64 FMA,
+ * MUFU reciprocal square root, FP32 shared-memory atomic add (scattered bins),
+ * FP64 shared-memory atomic add (scattered bins).  out_rates[5].  Runs for a few
+ * milliseconds; allocates and frees its own device memory. */
+int c8r_measure_peaks(int device, double* out_rates);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* C8R_H */

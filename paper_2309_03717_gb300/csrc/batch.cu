@@ -1,0 +1,498 @@
+// batch.cu -- many independent showers of uneven size in one persistent launch
+// (not in the paper, whose radio process handles one shower; this is the
+// batching the GPU needs to stay busy on small showers).
+//
+// The host cuts every shower into work items (antenna tile x range of derived
+// track tiles), sorts them by cost (largest first) and uploads the list.  A
+// persistent grid of one CTA per SM pops items from a global atomic counter;
+// for each item a CTA zeroes its shared traces, streams the item's track tiles
+// through the same TMA ring as the single-shower kernel and adds its traces into
+// the shower's slice of the output.  The CTA polls a cancel word between items.
+// The ingest of all showers, the counter reset and the persistent kernel are
+// captured once into a CUDA graph and replayed.  The tile shape (antennas per
+// CTA, track tiles per item) is picked by a small autotuner that times the
+// candidates on a subsample of the real work list and caches the choice.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include <sys/stat.h>
+
+#include "ingest.cuh"
+#include "pair_mixed.cuh"
+
+namespace c8r {
+
+struct WorkItem {
+  int32_t ant0;     // first antenna (index into the concatenated table)
+  int32_t n_here;   // antennas in this item
+  int64_t t_begin;  // first derived-track tile
+  int64_t t_end;
+};
+
+struct BatchArgs {
+  const void* tiles;
+  const WorkItem* items;
+  int n_items;
+  const AntRec* ants;
+  void* out;             // concatenated traces; NULL = evaluate without flushing (autotuner timing)
+  int* counter;
+  const int* cancel;
+  int* err;
+  int a_tile;
+  MedParams M;
+};
+
+// slot -> caller track index for the concatenated showers: shower s owns tiles
+// [tile_off[s], tile_off[s+1]) and tracks [track_off[s], track_off[s]+n_tracks[s])
+struct BatchMap {
+  const int64_t* tile_off;  // [n_showers + 1]
+  const int64_t* track_off;
+  const int64_t* n_tracks;
+  int n_showers;
+  __device__ __forceinline__ int64_t operator()(int64_t g) const {
+    const int64_t tile = g / kTileT;
+    int lo = 0, hi = n_showers - 1;
+    while (lo < hi) {  // last s with tile_off[s] <= tile
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_off[mid] <= tile) lo = mid;
+      else hi = mid - 1;
+    }
+    const int64_t l = g - tile_off[lo] * kTileT;
+    return l < n_tracks[lo] ? track_off[lo] + l : -1;
+  }
+};
+
+template <class Ops>
+__global__ void __launch_bounds__(kFwdMaxThreads, 1) k_batch(const BatchArgs a) {
+  using acc_t = typename Ops::acc_t;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const MedParams& M = a.M;
+  const int N = M.n_bins;
+  const FwdLayout L = fwd_layout(Ops::kPrec, a.a_tile, N);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+  AntRec* ant_s = reinterpret_cast<AntRec*>(smem + L.ant_off);
+  acc_t* trace = reinterpret_cast<acc_t*>(smem + L.trace_off);
+  __shared__ int s_item;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  int64_t it = 0;
+  for (;;) {
+    if (tid == 0) {
+      const int cancelled = *(volatile const int*)a.cancel;
+      s_item = cancelled ? -1 : atomicAdd(a.counter, 1);
+      if (cancelled) atomicExch(a.err, kErrCancelled);
+    }
+    __syncthreads();
+    const int idx = s_item;
+    if (idx < 0 || idx >= a.n_items) break;
+    const WorkItem w = a.items[idx];
+    for (int i = tid; i < w.n_here * 3 * N; i += nthr) trace[i] = acc_t(0);
+    for (int i = tid; i < w.n_here; i += nthr) ant_s[i] = a.ants[w.ant0 + i];
+    __syncthreads();
+    if (!stream_range<Ops>(smem, L, bar, ant_s, trace, w.n_here, static_cast<const unsigned char*>(a.tiles),
+                           w.t_begin, w.t_end, it, M)) {
+      if (tid == 0) atomicExch(a.err, kErrWaitTimeout);
+      return;
+    }
+    __syncthreads();
+    if (a.out) flush_traces<acc_t>(trace, static_cast<acc_t*>(a.out) + (size_t)w.ant0 * 3 * N, w.n_here, N);
+    __syncthreads();
+  }
+}
+
+using BatchOps = OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>;
+
+template <class Ops>
+cudaError_t launch_batch_ops(const BatchArgs& a, int grid, cudaStream_t st) {
+  const size_t smem = fwd_layout(C8R_MIXED, a.a_tile, a.M.n_bins).total;
+  auto k = k_batch<Ops>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, forward_threads(a.a_tile), smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchArgs& a, int formalism, int grid, cudaStream_t st) {
+  const bool ex = a.M.kind == C8R_EXPONENTIAL;
+  if (formalism == C8R_ENDPOINT) {
+    if (ex) return launch_batch_ops<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>>(a, grid, st);
+    return launch_batch_ops<OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>>(a, grid, st);
+  }
+  if (ex) return launch_batch_ops<OpsMixed<C8R_ZHS, C8R_EXPONENTIAL>>(a, grid, st);
+  return launch_batch_ops<OpsMixed<C8R_ZHS, C8R_UNIFORM>>(a, grid, st);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: candidates are timed on the device; choices are cached in a text
+// file (C8R_TUNE_CACHE, default $HOME/.cache/c8r_tune.txt) keyed by a string
+// ---------------------------------------------------------------------------
+struct TuneChoice {
+  int a_tile;
+  int64_t tiles_per_item;
+};
+
+static std::string tune_cache_path() {
+  if (const char* p = std::getenv("C8R_TUNE_CACHE")) return p;
+  if (const char* h = std::getenv("HOME")) return std::string(h) + "/.cache/c8r_tune.txt";
+  return "";
+}
+
+static bool tune_lookup(const std::string& key, TuneChoice& c) {
+  const std::string path = tune_cache_path();
+  if (path.empty()) return false;
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) {
+    std::istringstream ss(line);
+    std::string k;
+    TuneChoice t{};
+    if (ss >> k >> t.a_tile >> t.tiles_per_item && k == key && t.a_tile > 0 && t.tiles_per_item > 0) {
+      c = t;
+      return true;
+    }
+  }
+  return false;
+}
+
+static void tune_store(const std::string& key, const TuneChoice& c) {
+  const std::string path = tune_cache_path();
+  if (path.empty()) return;
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);  // one level, best effort
+  std::ofstream f(path, std::ios::app);
+  if (f) f << key << " " << c.a_tile << " " << c.tiles_per_item << "\n";
+}
+
+}  // namespace c8r
+
+using namespace c8r;
+
+struct c8r_batch {
+  int device = 0;
+  int sm_count = 0;
+  std::string err;
+  int n_showers = 0;
+  int formalism = C8R_ENDPOINT;
+  MedParams M{};
+  std::vector<int64_t> n_tracks, track_off, tile_off;
+  std::vector<int32_t> n_ant, ant_off;
+  int64_t total_tracks = 0, total_tiles = 0, total_pairs = 0;
+  int total_ant = 0;
+  AntRec* d_ants = nullptr;
+  void* d_tiles = nullptr;
+  int64_t* d_tile_off = nullptr;
+  int64_t* d_track_off = nullptr;
+  int64_t* d_n_tracks = nullptr;
+  WorkItem* d_items = nullptr;
+  int n_items = 0;
+  int* d_counter = nullptr;
+  int* d_cancel = nullptr;
+  int* d_err = nullptr;
+  cudaStream_t cap_stream = nullptr;  // graph capture (the caller's stream may be the legacy default stream)
+  cudaStream_t aux_stream = nullptr;  // non-blocking: cancel word updates while a batch runs
+  bool tuned = false;
+  TuneChoice choice{4, 64};
+  // graph bound to (tracks, out) of its capture
+  cudaGraphExec_t graph = nullptr;
+  cudaGraph_t graph_src = nullptr;
+  const void* g_tracks[12] = {};
+  void* g_out = nullptr;
+};
+
+namespace {
+
+int bfail(c8r_batch* b, int code, const std::string& m) {
+  if (b) b->err = m;
+  return code;
+}
+
+std::vector<WorkItem> make_items(const c8r_batch* b, int a_tile, int64_t tpi) {
+  std::vector<WorkItem> v;
+  for (int s = 0; s < b->n_showers; ++s) {
+    const int64_t nt = b->tile_off[s + 1] - b->tile_off[s];
+    if (nt == 0) continue;
+    for (int a0 = 0; a0 < b->n_ant[s]; a0 += a_tile) {
+      const int nh = std::min(a_tile, b->n_ant[s] - a0);
+      for (int64_t r = 0; r < nt; r += tpi) {
+        WorkItem w;
+        w.ant0 = b->ant_off[s] + a0;
+        w.n_here = nh;
+        w.t_begin = b->tile_off[s] + r;
+        w.t_end = b->tile_off[s] + std::min(nt, r + tpi);
+        v.push_back(w);
+      }
+    }
+  }
+  std::stable_sort(v.begin(), v.end(), [](const WorkItem& x, const WorkItem& y) {
+    return (x.t_end - x.t_begin) * x.n_here > (y.t_end - y.t_begin) * y.n_here;
+  });
+  return v;
+}
+
+int upload_items(c8r_batch* b, const std::vector<WorkItem>& v) {
+  if (b->d_items) cudaFree(b->d_items);
+  b->d_items = nullptr;
+  b->n_items = (int)v.size();
+  if (v.empty()) return C8R_OK;
+  cudaError_t e = cudaMalloc(&b->d_items, sizeof(WorkItem) * v.size());
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_items, v.data(), sizeof(WorkItem) * v.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bfail(b, C8R_ENOMEM, std::string("work list upload: ") + cudaGetErrorString(e));
+  return C8R_OK;
+}
+
+// tiles per item giving about `waves` items per SM for tile width a_tile
+int64_t tpi_for(const c8r_batch* b, int a_tile, int waves) {
+  const double pair_units = (double)b->total_pairs / (kTileT * (double)a_tile);
+  int64_t t = (int64_t)(pair_units / ((double)waves * b->sm_count));
+  return std::max<int64_t>(t, 8);
+}
+
+int enqueue(c8r_batch* b, const TrackPtrs& tp, void* out, int n_items_limit, cudaStream_t st) {
+  BatchMap map{b->d_tile_off, b->d_track_off, b->d_n_tracks, b->n_showers};
+  cudaError_t e = launch_ingest_map(C8R_MIXED, tp, map, b->total_tiles * kTileT, b->d_tiles, b->M, nullptr, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch ingest: ") + cudaGetErrorString(e));
+  BatchArgs a{b->d_tiles, b->d_items, std::min(b->n_items, n_items_limit), b->d_ants, out, b->d_counter,
+              b->d_cancel, b->d_err, b->choice.a_tile, b->M};
+  e = launch_batch(a, b->formalism, b->sm_count, st);
+  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  return C8R_OK;
+}
+
+int autotune(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
+  char keybuf[160];
+  std::snprintf(keybuf, sizeof keybuf, "batch:N%d:f%d:m%d:sm%d:P%lld", b->M.n_bins, b->formalism, b->M.kind,
+                b->sm_count, (long long)(b->total_pairs >> 26));
+  const std::string key = keybuf;
+  TuneChoice best{};
+  if (tune_lookup(key, best) && best.a_tile <= max_a_tile(C8R_MIXED, b->M.n_bins)) {
+    b->choice = best;
+    b->tuned = true;
+    return upload_items(b, make_items(b, best.a_tile, best.tiles_per_item));
+  }
+  const int amax = max_a_tile(C8R_MIXED, b->M.n_bins);
+  std::vector<TuneChoice> cands;
+  for (int at : {amax, amax - 1, amax / 2})
+    if (at >= 1)
+      for (int waves : {4, 8, 16}) cands.push_back({at, tpi_for(b, at, waves)});
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best_rate = -1.0;
+  for (const TuneChoice& c : cands) {
+    b->choice = c;
+    std::vector<WorkItem> v = make_items(b, c.a_tile, c.tiles_per_item);
+    // subsample: the first items of the sorted list (a mix of shower sizes)
+    const int lim = std::min<int>((int)v.size(), 4 * b->sm_count);
+    double pairs = 0;
+    for (int i = 0; i < lim; ++i) pairs += (double)(v[i].t_end - v[i].t_begin) * kTileT * v[i].n_here;
+    int r = upload_items(b, v);
+    if (r != C8R_OK) return r;
+    cudaEventRecord(e0, st);
+    r = enqueue(b, tp, nullptr, lim, st);
+    if (r != C8R_OK) return r;
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return bfail(b, C8R_ECUDA, "autotuner timing failed");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double rate = ms > 0 ? pairs / ms : 0.0;
+    if (rate > best_rate) {
+      best_rate = rate;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->choice = best;
+  b->tuned = true;
+  tune_store(key, best);
+  return upload_items(b, make_items(b, best.a_tile, best.tiles_per_item));
+}
+
+}  // namespace
+
+extern "C" {
+
+int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int kind, double n_or_N0, double H) {
+  if (!out || !d) return C8R_EINVAL;
+  *out = nullptr;
+  c8r_batch* b = new (std::nothrow) c8r_batch();
+  if (!b) return C8R_ENOMEM;
+  auto bad = [&](int code, const char* m) {
+    b->err = m;
+    *out = b;  // hand the object back so the caller can read the message
+    return code;
+  };
+  if (d->n_showers < 1 || !d->n_tracks || !d->track_offset || !d->n_ant || !d->ant_offset || !d->pos_xyz ||
+      !d->t_start_ns)
+    return bad(C8R_EINVAL, "batch descriptor incomplete");
+  if (d->n_bins < 1 || !(d->dt_ns > 0.0)) return bad(C8R_EINVAL, "n_bins / dt_ns");
+  if (d->formalism != C8R_ENDPOINT && d->formalism != C8R_ZHS) return bad(C8R_EINVAL, "formalism");
+  if (kind == C8R_UNIFORM ? !(n_or_N0 > 0.0) : !(n_or_N0 >= 0.0 && H > 0.0)) return bad(C8R_EINVAL, "medium");
+  if (max_a_tile(C8R_MIXED, d->n_bins) < 1) return bad(C8R_ETOOBIG, "n_bins too large for the shared trace tile");
+  if (cudaSetDevice(device) != cudaSuccess) return bad(C8R_EINVAL, "device");
+  b->device = device;
+  cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, device);
+  b->n_showers = d->n_showers;
+  b->formalism = d->formalism;
+  fill_medium(b->M, kind, n_or_N0, H, d->n_bins, d->dt_ns, 1e-3);
+  b->n_tracks.assign(d->n_tracks, d->n_tracks + d->n_showers);
+  b->track_off.assign(d->track_offset, d->track_offset + d->n_showers);
+  b->n_ant.assign(d->n_ant, d->n_ant + d->n_showers);
+  b->ant_off.assign(d->ant_offset, d->ant_offset + d->n_showers);
+  b->tile_off.assign(d->n_showers + 1, 0);
+  for (int s = 0; s < d->n_showers; ++s) {
+    if (b->n_tracks[s] < 0 || b->n_ant[s] < 1 || b->track_off[s] < 0 || b->ant_off[s] < 0)
+      return bad(C8R_EINVAL, "negative count/offset or shower without antennas");
+    b->tile_off[s + 1] = b->tile_off[s] + (b->n_tracks[s] + kTileT - 1) / kTileT;
+    b->total_tracks = std::max<int64_t>(b->total_tracks, b->track_off[s] + b->n_tracks[s]);
+    b->total_ant = std::max<int>(b->total_ant, b->ant_off[s] + b->n_ant[s]);
+    b->total_pairs += b->n_tracks[s] * (int64_t)b->n_ant[s];
+  }
+  b->total_tiles = b->tile_off[d->n_showers];
+  std::vector<AntRec> recs(b->total_ant);
+  for (int a = 0; a < b->total_ant; ++a) {
+    const double* p = d->pos_xyz + 3 * (size_t)a;
+    if (!std::isfinite(p[0]) || !std::isfinite(p[1]) || !std::isfinite(p[2]) || !std::isfinite(d->t_start_ns[a]))
+      return bad(C8R_EINVAL, "antenna values must be finite");
+    fill_antenna(recs[a], p[0], p[1], p[2], d->t_start_ns[a], b->M);
+  }
+  cudaError_t e = cudaMalloc(&b->d_ants, sizeof(AntRec) * recs.size());
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_ants, recs.data(), sizeof(AntRec) * recs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && b->total_tiles > 0) e = cudaMalloc(&b->d_tiles, (size_t)b->total_tiles * kTileBytesMixed);
+  const size_t sb = sizeof(int64_t) * (b->n_showers + 1);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_tile_off, sb);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_track_off, sb);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_n_tracks, sb);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_tile_off, b->tile_off.data(), sb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_track_off, b->track_off.data(), sizeof(int64_t) * b->n_showers, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_n_tracks, b->n_tracks.data(), sizeof(int64_t) * b->n_showers, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int) * 3);
+  if (e == cudaSuccess) e = cudaMemset(b->d_counter, 0, sizeof(int) * 3);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b->err = std::string("batch allocation: ") + cudaGetErrorString(e);
+    *out = b;
+    return C8R_ENOMEM;
+  }
+  b->d_cancel = b->d_counter + 1;
+  b->d_err = b->d_counter + 2;
+  if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->aux_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    b->err = "stream creation failed";
+    *out = b;
+    return C8R_ECUDA;
+  }
+  const int amax = max_a_tile(C8R_MIXED, b->M.n_bins);
+  b->choice = {amax, tpi_for(b, amax, 8)};
+  *out = b;
+  return upload_items(b, make_items(b, b->choice.a_tile, b->choice.tiles_per_item));
+}
+
+void c8r_batch_destroy(c8r_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->graph_src) cudaGraphDestroy(b->graph_src);
+  cudaFree(b->d_ants);
+  cudaFree(b->d_tiles);
+  cudaFree(b->d_tile_off);
+  cudaFree(b->d_track_off);
+  cudaFree(b->d_n_tracks);
+  cudaFree(b->d_items);
+  cudaFree(b->d_counter);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->aux_stream) cudaStreamDestroy(b->aux_stream);
+  delete b;
+}
+
+const char* c8r_batch_last_error(const c8r_batch* b) { return b ? b->err.c_str() : "batch is NULL"; }
+
+int c8r_batch_run(c8r_batch* b, const c8r_tracks* t, float* out, int use_graph, void* stream) {
+  if (!b || !t || !out) return bfail(b, C8R_EINVAL, "NULL argument");
+  if (t->dtype != C8R_F32 && t->dtype != C8R_F64) return bfail(b, C8R_EINVAL, "tracks.dtype");
+  const void* f[12] = {t->x0, t->y0, t->z0, t->x1, t->y1, t->z1, t->t0, t->t1, t->bx, t->by, t->bz, t->q};
+  for (int k = 0; k < 12; ++k)
+    if (!f[k]) return bfail(b, C8R_EINVAL, "a track array pointer is NULL");
+  cudaSetDevice(b->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  TrackPtrs tp;
+  tp.dtype = t->dtype;
+  for (int k = 0; k < 12; ++k) tp.f[k] = f[k];
+  if (b->total_tiles == 0) return C8R_OK;
+  if (!b->tuned) {
+    int r = autotune(b, tp, st);
+    if (r != C8R_OK) return r;
+  }
+  if (!use_graph) return enqueue(b, tp, out, b->n_items, st);
+  bool same = b->graph && b->g_out == out;
+  for (int k = 0; k < 12 && same; ++k) same = b->g_tracks[k] == f[k];
+  if (!same) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph_src) cudaGraphDestroy(b->graph_src);
+    b->graph = nullptr;
+    b->graph_src = nullptr;
+    cudaStream_t cs = b->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+    int r = enqueue(b, tp, out, b->n_items, cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    if (r != C8R_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return bfail(b, C8R_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    b->graph_src = g;
+    b->g_out = out;
+    for (int k = 0; k < 12; ++k) b->g_tracks[k] = f[k];
+  }
+  cudaError_t e = cudaGraphLaunch(b->graph, st);
+  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  return C8R_OK;
+}
+
+int c8r_batch_set_cancel(c8r_batch* b, int value) {
+  if (!b) return C8R_EINVAL;
+  cudaSetDevice(b->device);
+  int v = value ? 1 : 0;
+  cudaError_t e = cudaMemcpyAsync(b->d_cancel, &v, sizeof(int), cudaMemcpyHostToDevice, b->aux_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->aux_stream);
+  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("cancel word: ") + cudaGetErrorString(e));
+  return C8R_OK;
+}
+
+int c8r_batch_sync(c8r_batch* b, void* stream) {
+  if (!b) return C8R_EINVAL;
+  cudaSetDevice(b->device);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("synchronise: ") + cudaGetErrorString(e));
+  int err = 0;
+  e = cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("read status: ") + cudaGetErrorString(e));
+  if (err != kErrNone) {
+    cudaMemset(b->d_err, 0, sizeof(int));
+    return bfail(b, C8R_ECANCELLED,
+                 err == kErrCancelled ? "batch cancelled: work items were skipped"
+                                      : "a kernel gave up a bounded wait; results are incomplete");
+  }
+  return C8R_OK;
+}
+
+}  // extern "C"

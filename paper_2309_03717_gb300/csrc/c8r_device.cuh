@@ -1,0 +1,363 @@
+// c8r_device.cuh -- device-side building blocks of libc8r (sm_103a).
+//
+// The per-pair arithmetic follows the step the paper (§2) describes for every
+// track and antenna: straight-line propagator -> formalism (Endpoint or ZHS,
+// §1) -> deposit into the antenna's time-binned trace.  The formulas are those
+// of the cited formalism papers (Endpoint: James et al., PRE 84 056602; ZHS:
+// Zas, Halzen & Stanev, PRD 45 362), in SI units with times in ns at the
+// interface.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/c8r.h"
+
+namespace c8r {
+
+// ---------------------------------------------------------------------------
+// physical constants (SI) and units
+// ---------------------------------------------------------------------------
+constexpr double kC = 299792458.0;              // m/s
+constexpr double kCns = 0.299792458;            // m/ns
+constexpr double kEps0 = 8.8541878128e-12;      // F/m
+constexpr double kQe = 1.602176634e-19;         // C
+constexpr double kPi = 3.14159265358979323846;
+// Endpoint: K = e / (4 pi eps0 c)  [V s] per unit charge
+constexpr double kKendpoint = kQe / (4.0 * kPi * kEps0 * kC);
+// ZHS: K_A = mu0 e c / (4 pi), mu0 = 1/(eps0 c^2)  [V s] per unit charge
+constexpr double kKzhs = (1.0 / (kEps0 * kC * kC)) * kQe * kC / (4.0 * kPi);
+
+// tracks per derived tile (the unit of the TMA bulk copies)
+constexpr int kTileT = 128;
+
+// ---------------------------------------------------------------------------
+// derived-track tiles written by the ingest kernel: per tile of kTileT tracks,
+// field-major ([field][kTileT]) so one bulk copy moves a whole tile and lane i
+// of a warp reads track i of a field without bank conflicts.
+// ---------------------------------------------------------------------------
+namespace fm {  // mixed precision (float fields)
+enum : int {
+  X0, Y0, Z0, X1, Y1, Z1,         // FP32 positions, m
+  BX, BY, BZ,                     // beta
+  AMPE,                           // q K / dt  [V]; 0 => track dropped by the filter
+  AMPZ,                           // q K_A (t1 - t0)/dt  [V s]
+  BMAG,                           // |beta|
+  OMB,                            // 1 - |beta|
+  TAU0H, TAU0L, TAU1H, TAU1L,     // t/dt, float-float
+  DTAUH, DTAUL,                   // (t1 - t0)/dt, float-float
+  E0H, E0L, E1H, E1L, EMH, EML,   // exp(-z/H) at start, end, midpoint (float-float)
+  NFIELDS
+};
+}
+namespace fd {  // FP64 path (double fields)
+enum : int { X0, Y0, Z0, X1, Y1, Z1, BX, BY, BZ, Q, T0, T1, E0, E1, EM, NFIELDS };
+}
+constexpr int kTileBytesMixed = fm::NFIELDS * kTileT * 4;
+constexpr int kTileBytesF64 = fd::NFIELDS * kTileT * 8;
+static_assert(kTileBytesMixed % 16 == 0 && kTileBytesF64 % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+// ---------------------------------------------------------------------------
+// antenna record (device table, built on the host in FP64)
+// ---------------------------------------------------------------------------
+struct AntRec {
+  double x, y, z;        // m
+  double t_ref;          // ns, first bin edge
+  double Ea;             // exp(-z/H) (exponential medium), 1 otherwise
+  double pad;
+  float xh, yh, zh, xl, yl, zl;  // position as float-float
+  float tauh, taul;              // t_ref / dt as float-float
+  float Eah, Eal;                // Ea as float-float
+  float pad2[2];
+};
+static_assert(sizeof(AntRec) == 96, "antenna record layout");
+
+// medium + binning parameters (kernel argument)
+struct MedParams {
+  int kind;              // C8R_UNIFORM / C8R_EXPONENTIAL
+  int n_bins;
+  double n;              // uniform index
+  double N0, H, invH;    // exponential
+  double dt_ns;
+  double inv_c_ns;       // 1 / c in ns/m
+  double eps_Cd;         // near-Cherenkov threshold (FP64 path)
+  // float-float constants of the mixed path
+  float kc_h, kc_l;      // 1/(c dt): bins per metre
+  float s_h, s_l;        // uniform: n/(c dt)
+  float cN_h, cN_l;      // exponential: N0 H /(c dt)
+  float invH_h, invH_l;  // 1/H
+  float N0f, nf;         // N0 and n as floats
+  float eps_C;           // near-Cherenkov threshold
+  float pad;
+};
+
+// ---------------------------------------------------------------------------
+// float-float ("double-float") arithmetic: error-free transformations after
+// Knuth (TwoSum) and Dekker / the FMA form (TwoProd).  Intrinsics pin the
+// rounding of every step; nothing here may be contracted or reassociated.
+// ---------------------------------------------------------------------------
+struct ff {
+  float h, l;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copies and mbarriers (inline PTX, sm_90+ forms valid on sm_103a)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// global -> shared bulk copy; dst/src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after `limit` polls (each try_wait itself suspends for a
+// while) and returns false.  Callers turn a give-up into an error status.
+constexpr uint32_t kWaitLimit = 1u << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit = kWaitLimit) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+// error word written by kernels that gave up a bounded wait
+enum : int { kErrNone = 0, kErrWaitTimeout = 1, kErrCancelled = 2 };
+
+// ---------------------------------------------------------------------------
+// FP64 path: the plain formulas in FP64, in the order of their definition.
+// ---------------------------------------------------------------------------
+struct GeoD {
+  double d[3], R, rh[3], n_src, n_avg;
+};
+
+// straight emission path x_e -> antenna (propagator, §2): distance, direction,
+// source index and path-averaged index of the medium
+__device__ __forceinline__ void geo_f64(const MedParams& M, const AntRec& A, double xe, double ye, double ze,
+                                        double Ee, GeoD& g) {
+  g.d[0] = A.x - xe;
+  g.d[1] = A.y - ye;
+  g.d[2] = A.z - ze;
+  g.R = sqrt(g.d[0] * g.d[0] + g.d[1] * g.d[1] + g.d[2] * g.d[2]);
+  double invR = 1.0 / g.R;
+  g.rh[0] = g.d[0] * invR;
+  g.rh[1] = g.d[1] * invR;
+  g.rh[2] = g.d[2] * invR;
+  if (M.kind == C8R_UNIFORM) {
+    g.n_src = M.n;
+    g.n_avg = M.n;
+  } else {
+    g.n_src = 1.0 + M.N0 * Ee;
+    // path average of N0 exp(-z/H) between z_e and z_a: N0 H (E_e - E_a) / dz,
+    // or its series in x = dz/H when the two altitudes nearly coincide
+    double dz = g.d[2];
+    double x = dz * M.invH;
+    double ratio;
+    if (fabs(x) > 1e-3)
+      ratio = (Ee - A.Ea) / x;
+    else
+      ratio = Ee * (1.0 + x * (-0.5 + x * (1.0 / 6.0 + x * (-1.0 / 24.0 + x * (1.0 / 120.0)))));
+    g.n_avg = 1.0 + M.N0 * ratio;
+  }
+}
+
+// arrival position in bins relative to the antenna's first bin edge
+__device__ __forceinline__ double arrival_f64(const MedParams& M, const GeoD& g, double t_e, double t_ref) {
+  return ((t_e - t_ref) + g.n_avg * g.R * M.inv_c_ns) / M.dt_ns;
+}
+
+// ---------------------------------------------------------------------------
+// mixed path: FP32 field arithmetic; arrival time in float-float
+// ---------------------------------------------------------------------------
+struct GeoM {
+  float s[3], e[3];  // d = x_a - x_e as float-float per component
+  float R0, R1;      // |d| as float-float
+  float y;           // ~1/R0 (rsqrt estimate)
+};
+
+// d = a - p (p given as float-float; p_l = 0 for the FP32-exact endpoints), and
+// R = |d| in float-float: the three exact squares are summed with TwoSum, then
+// one Newton step corrects the FP32 square root.
+__device__ __forceinline__ void geo_mixed(const AntRec& A, float pxh, float pyh, float pzh, float pxl, float pyl,
+                                          float pzl, GeoM& g) {
+  two_sum(A.xh, -pxh, g.s[0], g.e[0]);
+  two_sum(A.yh, -pyh, g.s[1], g.e[1]);
+  two_sum(A.zh, -pzh, g.s[2], g.e[2]);
+  g.e[0] = __fadd_rn(g.e[0], __fsub_rn(A.xl, pxl));
+  g.e[1] = __fadd_rn(g.e[1], __fsub_rn(A.yl, pyl));
+  g.e[2] = __fadd_rn(g.e[2], __fsub_rn(A.zl, pzl));
+  float p0, q0, p1, q1, p2, q2;
+  two_prod(g.s[0], g.s[0], p0, q0);
+  two_prod(g.s[1], g.s[1], p1, q1);
+  two_prod(g.s[2], g.s[2], p2, q2);
+  float S1, E1, S2, E2;
+  two_sum(p0, p1, S1, E1);
+  two_sum(S1, p2, S2, E2);
+  float cross = __fmaf_rn(g.s[0], g.e[0], __fmaf_rn(g.s[1], g.e[1], __fmul_rn(g.s[2], g.e[2])));
+  float lo = __fadd_rn(__fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2, E1)), __fadd_rn(E2, __fmul_rn(2.0f, cross)));
+  float y = rsqrtf(S2);
+  float R0 = __fmul_rn(S2, y);
+  float rq, rqe;
+  two_prod(R0, R0, rq, rqe);
+  float rho = __fadd_rn(__fsub_rn(__fsub_rn(S2, rq), rqe), lo);
+  g.R0 = R0;
+  g.R1 = __fmul_rn(__fmul_rn(rho, 0.5f), y);
+  g.y = y;
+}
+
+// arrival position u = (t_e - t_ref)/dt + n_avg R / (c dt) in bins, float-float.
+// tau_e = t_e/dt and the antenna's tau = t_ref/dt come in float-float.
+__device__ __forceinline__ ff arrival_mixed(const MedParams& M, const AntRec& A, const GeoM& g, float tauh, float taul,
+                                            float Eeh, float Eel) {
+  float ts, te;
+  two_sum(tauh, -A.tauh, ts, te);
+  te = __fadd_rn(te, __fsub_rn(taul, A.taul));
+  float sh = (M.kind == C8R_UNIFORM) ? M.s_h : M.kc_h;
+  float sl = (M.kind == C8R_UNIFORM) ? M.s_l : M.kc_l;
+  float p, pe;
+  two_prod(g.R0, sh, p, pe);
+  pe = __fmaf_rn(g.R0, sl, __fmaf_rn(g.R1, sh, pe));
+  if (M.kind == C8R_EXPONENTIAL) {
+    // refractivity term (n_avg - 1) R/(c dt) = N0 H/(c dt) * (E_e - E_a)/dz * R
+    float q0, q1;
+    float dzh = g.s[2], dzl = g.e[2];
+    float x = __fmul_rn(dzh, M.invH_h);
+    if (fabsf(x) > 1e-3f) {
+      float Qh, Ql;
+      two_sum(Eeh, -A.Eah, Qh, Ql);
+      Ql = __fadd_rn(Ql, __fsub_rn(Eel, A.Eal));
+      q0 = __fdiv_rn(Qh, dzh);
+      float ph, pl;
+      two_prod(q0, dzh, ph, pl);
+      float r = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(Qh, ph), pl), Ql), __fmul_rn(q0, dzl));
+      q1 = __fdiv_rn(r, dzh);
+    } else {
+      // (E_e - E_a)/dz = (E_e/H) (1 - exp(-x))/x = (E_e/H)(1 + f), f = -x/2 + x^2/6 - x^3/24
+      float f = __fmul_rn(x, __fmaf_rn(x, __fmaf_rn(x, -1.0f / 24.0f, 1.0f / 6.0f), -0.5f));
+      float eh, el;
+      two_prod(Eeh, M.invH_h, eh, el);
+      el = __fmaf_rn(Eeh, M.invH_l, __fmaf_rn(Eel, M.invH_h, el));
+      // (eh + el)(1 + f)
+      float g0, g1;
+      two_sum(eh, __fmul_rn(eh, f), g0, g1);
+      q0 = g0;
+      q1 = __fadd_rn(g1, __fmaf_rn(el, f, el));
+    }
+    float w, we;
+    two_prod(q0, g.R0, w, we);
+    we = __fmaf_rn(q0, g.R1, __fmaf_rn(q1, g.R0, we));
+    float v, ve;
+    two_prod(w, M.cN_h, v, ve);
+    ve = __fmaf_rn(w, M.cN_l, __fmaf_rn(we, M.cN_h, ve));
+    float p2, pe2;
+    two_sum(p, v, p2, pe2);
+    p = p2;
+    pe = __fadd_rn(pe, __fadd_rn(pe2, ve));
+  }
+  float uh, ue;
+  two_sum(ts, p, uh, ue);
+  ue = __fadd_rn(ue, __fadd_rn(te, pe));
+  return ff{uh, ue};
+}
+
+// bin index of a float-float arrival, clamped to [-1, n_bins]: -1 stands for
+// "before the window" (or not a number), n_bins for "after it"; frac is the
+// position inside the bin (meaningful only for an index inside the window)
+__device__ __forceinline__ int bin_raw(ff u, int n_bins, float& frac) {
+  frac = 0.0f;
+  if (!(u.h > -1.0f)) return -1;
+  if (!(u.h < (float)n_bins + 1.0f)) return n_bins;
+  float kf = floorf(u.h);
+  float f = __fadd_rn(__fsub_rn(u.h, kf), u.l);
+  if (f < 0.0f) {
+    kf -= 1.0f;
+    f += 1.0f;
+  } else if (f >= 1.0f) {
+    kf += 1.0f;
+    f -= 1.0f;
+  }
+  int k = (int)kf;
+  frac = f;
+  if (k < 0) return -1;
+  if (k >= n_bins) return n_bins;
+  return k;
+}
+__device__ __forceinline__ bool bin_of(ff u, int n_bins, int& k, float& frac) {
+  k = bin_raw(u, n_bins, frac);
+  return k >= 0 && k < n_bins;
+}
+
+// field part at one emission point (FP32): w = d x beta, V = (d x w)/R^2 =
+// rhat x (rhat x beta), D = 1 - n beta.rhat in a cancellation-free form:
+//   D = (1 - n|beta|) + n |w|^2 / (R (|beta| R + beta.d))   when beta.d >= 0
+// (the second term is n|beta|(1 - cos theta)); the direct form otherwise.
+struct FieldM {
+  float V[3];  // rhat x (rhat x beta) times R^2  (i.e. d x w)
+  float D;
+  float invR;
+  float bd;    // beta . d
+};
+// Every step uses explicit-rounding intrinsics so the forward and the adjoint
+// kernels, which inline this in different contexts, take identical branch
+// decisions.
+__device__ __forceinline__ void field_mixed(const GeoM& g, float bx, float by, float bz, float bmag, float om_nb,
+                                            float n, FieldM& f) {
+  const float sx = g.s[0], sy = g.s[1], sz = g.s[2];
+  const float ex = g.e[0], ey = g.e[1], ez = g.e[2];
+  // w = d x beta, with the low parts of d folded in
+  const float wx = __fadd_rn(__fmaf_rn(sy, bz, -__fmul_rn(sz, by)), __fmaf_rn(ey, bz, -__fmul_rn(ez, by)));
+  const float wy = __fadd_rn(__fmaf_rn(sz, bx, -__fmul_rn(sx, bz)), __fmaf_rn(ez, bx, -__fmul_rn(ex, bz)));
+  const float wz = __fadd_rn(__fmaf_rn(sx, by, -__fmul_rn(sy, bx)), __fmaf_rn(ex, by, -__fmul_rn(ey, bx)));
+  const float bd = __fmaf_rn(bx, sx, __fmaf_rn(by, sy, __fmul_rn(bz, sz)));
+  const float R = g.R0;
+  const float invR = g.y;
+  if (bd >= 0.0f) {
+    const float w2 = __fmaf_rn(wx, wx, __fmaf_rn(wy, wy, __fmul_rn(wz, wz)));
+    const float den = __fmul_rn(R, __fmaf_rn(bmag, R, bd));
+    f.D = __fadd_rn(om_nb, __fdiv_rn(__fmul_rn(n, w2), den));
+  } else {
+    f.D = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(n, bd), invR));
+  }
+  // d x w = d (d.beta) - beta R^2  ->  V R^2
+  f.V[0] = __fmaf_rn(sy, wz, -__fmul_rn(sz, wy));
+  f.V[1] = __fmaf_rn(sz, wx, -__fmul_rn(sx, wz));
+  f.V[2] = __fmaf_rn(sx, wy, -__fmul_rn(sy, wx));
+  f.invR = invR;
+  f.bd = bd;
+}
+
+}  // namespace c8r

@@ -1,0 +1,54 @@
+// c8r_internal.h -- host-side declarations shared by the libc8r translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/c8r.h"
+#include "c8r_device.cuh"
+
+namespace c8r {
+
+// launch shape of the forward kernels
+struct FwdShape {
+  int a_tile;   // antennas per CTA (their full traces live in shared memory)
+  int threads;  // = kTileT * a_tile
+  int waves;    // target number of CTA waves per launch
+};
+
+// SoA track pointers of the caller, already offset to a chunk
+struct TrackPtrs {
+  int dtype;
+  const void* f[12];
+};
+
+size_t tile_bytes(int precision);
+size_t fwd_smem_bytes(int precision, int a_tile, int n_bins);
+int max_a_tile(int precision, int n_bins);
+
+// ingest: filter + derived per-track quantities into tiles; counts kept tracks
+// into *kept unless kept is NULL
+cudaError_t launch_ingest(int precision, const TrackPtrs& t, int64_t n, void* tiles, const MedParams& M,
+                          unsigned long long* kept, cudaStream_t st);
+
+struct BwdArgs;
+
+// per-precision launchers (kernels_f64.cu / kernels_mixed.cu)
+cudaError_t launch_forward_f64(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants, int n_ant,
+                               const MedParams& M, void* traces, const FwdShape& shape, int sm_count, int* err,
+                               cudaStream_t st);
+cudaError_t launch_forward_mixed(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants, int n_ant,
+                                 const MedParams& M, void* traces, const FwdShape& shape, int sm_count, int* err,
+                                 cudaStream_t st);
+cudaError_t launch_arrivals_f64(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,
+                                const MedParams& M, int32_t* branch, int32_t* bin, float* frac, cudaStream_t st);
+cudaError_t launch_arrivals_mixed(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,
+                                  const MedParams& M, int32_t* branch, int32_t* bin, float* frac, cudaStream_t st);
+cudaError_t launch_backward_f64(const BwdArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_backward_mixed(const BwdArgs& a, int blocks, cudaStream_t st);
+
+// helpers shared by the context and the batch runner
+void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, double dt_ns, double eps_C);
+void fill_antenna(AntRec& r, double x, double y, double z, double t_ref_ns, const MedParams& M);
+
+}  // namespace c8r

@@ -1,0 +1,169 @@
+// ingest.cuh -- track ingest and the track filter (§2: "the track is checked
+// according to the track filter ... relevant for the radio calculation or not").
+//
+// One thread per track slot reads the caller's SoA arrays (coalesced), applies
+// the filter and writes the per-track quantities every later pair evaluation
+// needs into field-major tiles of kTileT tracks.  Everything per track that
+// costs FP64 (exp of the altitude, t/dt, 1 - |beta|) is done here once, so the
+// pair kernels, which run once per track AND antenna, stay on the FP32 pipe.
+// Padding slots and filtered tracks get a zero amplitude and are skipped later.
+#pragma once
+
+#include <cmath>
+
+#include "c8r_internal.h"
+
+namespace c8r {
+namespace ingest_detail {
+
+
+template <typename T>
+__device__ __forceinline__ double ld(const void* p, int64_t i) {
+  return (double)static_cast<const T*>(p)[i];
+}
+
+template <typename Tin>
+__device__ __forceinline__ void load_track(const TrackPtrs& t, int64_t i, double v[12], bool round_to_f32) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    double x = ld<Tin>(t.f[k], i);
+    v[k] = round_to_f32 ? (double)(float)x : x;
+  }
+}
+
+// track filter: q != 0, all fields finite, t1 > t0, |x1 - x0| > 0, 0 < |beta| < 1
+__device__ __forceinline__ bool track_kept(const double v[12]) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) ok = ok && isfinite(v[k]);
+  if (!ok) return false;
+  if (v[11] == 0.0) return false;
+  if (!(v[7] > v[6])) return false;
+  double lx = v[3] - v[0], ly = v[4] - v[1], lz = v[5] - v[2];
+  if (!(lx * lx + ly * ly + lz * lz > 0.0)) return false;
+  double b = sqrt(v[8] * v[8] + v[9] * v[9] + v[10] * v[10]);
+  return b > 0.0 && b < 1.0;
+}
+
+__device__ __forceinline__ void split(double x, float& h, float& l) {
+  h = (float)x;
+  l = (float)(x - (double)h);
+}
+
+// Map: padded slot g -> index of the caller's track in that slot, or -1 for a
+// padding slot (identity for one shower; a per-shower table for a batch)
+template <typename Tin, class Map>
+__global__ void __launch_bounds__(256) k_ingest_mixed(TrackPtrs t, Map map, int64_t n_pad, float* tiles,
+                                                      MedParams M, unsigned long long* kept) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool keep = false;
+  if (i < n_pad) {
+    float* tile = tiles + (i / kTileT) * (int64_t)(fm::NFIELDS * kTileT);
+    const int l = (int)(i % kTileT);
+    float out[fm::NFIELDS];
+#pragma unroll
+    for (int k = 0; k < fm::NFIELDS; ++k) out[k] = 0.0f;
+    const int64_t src = map(i);
+    if (src >= 0) {
+      double v[12];
+      load_track<Tin>(t, src, v, true);
+      keep = track_kept(v);
+      if (keep) {
+        double b = sqrt(v[8] * v[8] + v[9] * v[9] + v[10] * v[10]);
+        double dt = M.dt_ns;
+        double dtau = (v[7] - v[6]) / dt;
+        out[fm::X0] = (float)v[0]; out[fm::Y0] = (float)v[1]; out[fm::Z0] = (float)v[2];
+        out[fm::X1] = (float)v[3]; out[fm::Y1] = (float)v[4]; out[fm::Z1] = (float)v[5];
+        out[fm::BX] = (float)v[8]; out[fm::BY] = (float)v[9]; out[fm::BZ] = (float)v[10];
+        out[fm::AMPE] = (float)(v[11] * kKendpoint / (dt * 1e-9));
+        out[fm::AMPZ] = (float)(v[11] * kKzhs * dtau);
+        out[fm::BMAG] = (float)b;
+        out[fm::OMB] = (float)(1.0 - b);
+        split(v[6] / dt, out[fm::TAU0H], out[fm::TAU0L]);
+        split(v[7] / dt, out[fm::TAU1H], out[fm::TAU1L]);
+        split(dtau, out[fm::DTAUH], out[fm::DTAUL]);
+        if (M.kind == C8R_EXPONENTIAL) {
+          split(exp(-v[2] * M.invH), out[fm::E0H], out[fm::E0L]);
+          split(exp(-v[5] * M.invH), out[fm::E1H], out[fm::E1L]);
+          split(exp(-0.5 * (v[2] + v[5]) * M.invH), out[fm::EMH], out[fm::EML]);
+        } else {
+          out[fm::E0H] = out[fm::E1H] = out[fm::EMH] = 1.0f;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < fm::NFIELDS; ++k) tile[k * kTileT + l] = out[k];
+  }
+  unsigned m = __ballot_sync(0xffffffffu, keep);
+  if (kept && (threadIdx.x & 31) == 0 && m) atomicAdd(kept, (unsigned long long)__popc(m));
+}
+
+template <typename Tin, class Map>
+__global__ void __launch_bounds__(256) k_ingest_f64(TrackPtrs t, Map map, int64_t n_pad, double* tiles,
+                                                    MedParams M, unsigned long long* kept) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool keep = false;
+  if (i < n_pad) {
+    double* tile = tiles + (i / kTileT) * (int64_t)(fd::NFIELDS * kTileT);
+    const int l = (int)(i % kTileT);
+    double out[fd::NFIELDS];
+#pragma unroll
+    for (int k = 0; k < fd::NFIELDS; ++k) out[k] = 0.0;
+    const int64_t src = map(i);
+    if (src >= 0) {
+      double v[12];
+      load_track<Tin>(t, src, v, false);
+      keep = track_kept(v);
+      if (keep) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) out[fd::X0 + k] = v[k];
+        out[fd::BX] = v[8]; out[fd::BY] = v[9]; out[fd::BZ] = v[10];
+        out[fd::Q] = v[11];
+        out[fd::T0] = v[6];
+        out[fd::T1] = v[7];
+        if (M.kind == C8R_EXPONENTIAL) {
+          out[fd::E0] = exp(-v[2] * M.invH);
+          out[fd::E1] = exp(-v[5] * M.invH);
+          out[fd::EM] = exp(-(0.5 * (v[2] + v[5])) * M.invH);
+        } else {
+          out[fd::E0] = out[fd::E1] = out[fd::EM] = 1.0;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < fd::NFIELDS; ++k) tile[k * kTileT + l] = out[k];
+  }
+  unsigned m = __ballot_sync(0xffffffffu, keep);
+  if (kept && (threadIdx.x & 31) == 0 && m) atomicAdd(kept, (unsigned long long)__popc(m));
+}
+
+
+struct IdentityMap {
+  int64_t n;
+  __device__ __forceinline__ int64_t operator()(int64_t g) const { return g < n ? g : -1; }
+};
+
+}  // namespace ingest_detail
+
+template <class Map>
+cudaError_t launch_ingest_map(int precision, const TrackPtrs& t, const Map& map, int64_t n_pad, void* tiles,
+                              const MedParams& M, unsigned long long* kept, cudaStream_t st) {
+  using namespace ingest_detail;
+  if (n_pad <= 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t blocks = (n_pad + threads - 1) / threads;
+  if (precision == C8R_FP64) {
+    if (t.dtype == C8R_F64)
+      k_ingest_f64<double, Map><<<(unsigned)blocks, threads, 0, st>>>(t, map, n_pad, (double*)tiles, M, kept);
+    else
+      k_ingest_f64<float, Map><<<(unsigned)blocks, threads, 0, st>>>(t, map, n_pad, (double*)tiles, M, kept);
+  } else {
+    if (t.dtype == C8R_F64)
+      k_ingest_mixed<double, Map><<<(unsigned)blocks, threads, 0, st>>>(t, map, n_pad, (float*)tiles, M, kept);
+    else
+      k_ingest_mixed<float, Map><<<(unsigned)blocks, threads, 0, st>>>(t, map, n_pad, (float*)tiles, M, kept);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace c8r

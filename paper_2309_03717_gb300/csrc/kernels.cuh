@@ -1,0 +1,344 @@
+// kernels.cuh -- CTA-level loops shared by the FP64 and the mixed-precision
+// translation units.  Each TU supplies an `Ops` class with the per-pair
+// arithmetic (Ops::fwd, Ops::adj) and instantiates the kernels below.
+//
+// Forward (§2 flow, "looped over all antennas"): grid.x = antenna tile whose
+// complete traces live in shared memory, grid.y = a contiguous range of
+// derived-track tiles.  grid.x varies fastest, so CTAs resident together read
+// the same track range and all but the first read hit L2.  A CTA streams its
+// range through a two-slot ring of shared-memory tiles filled by TMA bulk copies
+// (cp.async.bulk + mbarrier, bounded waits), evaluates one (track, antenna) pair
+// per thread per tile, scatters deposits with shared atomics and finally adds
+// its traces into the global accumulator.
+#pragma once
+
+#include <type_traits>
+
+#include "c8r_internal.h"
+
+namespace c8r {
+
+constexpr int kMaxATile = 8;
+constexpr int kFwdMaxThreads = 512;
+
+// shared memory of a forward CTA: two staged track tiles, two mbarriers, the
+// antenna records of the tile, then the traces [a_tile][3][n_bins]
+struct FwdLayout {
+  size_t stage_bytes, bar_off, ant_off, trace_off, total;
+};
+__host__ __device__ inline FwdLayout fwd_layout(int precision, int a_tile, int n_bins) {
+  FwdLayout L;
+  L.stage_bytes = precision == C8R_FP64 ? kTileBytesF64 : kTileBytesMixed;
+  L.bar_off = 2 * L.stage_bytes;
+  L.ant_off = L.bar_off + 128;
+  L.trace_off = L.ant_off + kMaxATile * sizeof(AntRec);
+  size_t acc = precision == C8R_FP64 ? 8 : 4;
+  L.total = L.trace_off + (size_t)a_tile * 3 * n_bins * acc;
+  return L;
+}
+
+struct FwdArgs {
+  const void* tiles;
+  int64_t n_tiles;
+  int64_t tiles_per_range;
+  const AntRec* ants;
+  int n_ant;
+  int a_tile;
+  void* out;
+  int* err;
+  MedParams M;
+};
+
+struct BwdArgs {
+  const void* tiles;
+  int64_t n;          // tracks
+  const AntRec* ants;
+  int n_ant;
+  const void* G;      // dL/dtraces [n_ant][3][n_bins]
+  c8r_track_grads out;
+  double* ant_grad;   // [n_ant][3]
+  double* dN0;
+  MedParams M;
+};
+
+// deposit of a 3-vector into bin k of one antenna's shared trace
+template <typename T>
+__device__ __forceinline__ void dep3(T* tr, int n_bins, int k, T vx, T vy, T vz) {
+  atomicAdd(tr + k, vx);
+  atomicAdd(tr + n_bins + k, vy);
+  atomicAdd(tr + 2 * n_bins + k, vz);
+}
+
+// Sinks: the pair functions report deposits through dep() and their branch and
+// arrival positions through rec(); the forward kernel scatters into shared
+// memory, the validation listing records bins.  Both run the same arithmetic.
+template <typename T>
+struct SmemSink {
+  T* tr;
+  int N;
+  __device__ __forceinline__ void dep(int k, T x, T y, T z) { dep3<T>(tr, N, k, x, y, z); }
+  __device__ __forceinline__ void rec(int, ff, ff) {}
+  __device__ __forceinline__ void rec(int, double, double) {}
+};
+struct ArrivalSink {
+  int32_t* branch;
+  int32_t* bin;
+  float* frac;
+  int64_t j;
+  int N;
+  __device__ __forceinline__ void dep(int, float, float, float) {}
+  __device__ __forceinline__ void dep(int, double, double, double) {}
+  __device__ __forceinline__ void rec(int b, ff ua, ff ub) {
+    float fa, fb;
+    int ka = bin_raw(ua, N, fa), kb = bin_raw(ub, N, fb);
+    branch[j] = b;
+    bin[2 * j] = ka;
+    bin[2 * j + 1] = kb;
+    frac[2 * j] = fa;
+    frac[2 * j + 1] = fb;
+  }
+  __device__ __forceinline__ void rec(int b, double ua, double ub) {
+    double ka = floor(ua), kb = floor(ub);
+    branch[j] = b;
+    bin[2 * j] = ka < 0.0 ? -1 : (ka >= (double)N ? N : (int)ka);
+    bin[2 * j + 1] = kb < 0.0 ? -1 : (kb >= (double)N ? N : (int)kb);
+    frac[2 * j] = (float)(ua - ka);
+    frac[2 * j + 1] = (float)(ub - kb);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------
+// Stream derived-track tiles [t_begin, t_end) through the two-slot TMA ring and
+// evaluate every (track, antenna) pair of the n_here antennas in ant_s into the
+// shared traces.  `it` counts the tiles this CTA has consumed so far (it sets
+// the slot and the mbarrier phase) and is advanced.  Returns false if a bounded
+// wait gave up; the CTA then has no copy in flight and must stop.
+template <class Ops>
+__device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* bar, const AntRec* ant_s,
+                             typename Ops::acc_t* trace, int n_here, const unsigned char* src, int64_t t_begin,
+                             int64_t t_end, int64_t& it, const MedParams& M) {
+  using acc_t = typename Ops::acc_t;
+  const int tid = threadIdx.x;
+  const int nthr = blockDim.x;
+  const int N = M.n_bins;
+  const uint32_t bytes = (uint32_t)L.stage_bytes;
+  if (tid == 0) {
+    for (int s = 0; s < 2 && t_begin + s < t_end; ++s) {
+      const int st = (int)((it + s) & 1);
+      mbar_expect_tx(&bar[st], bytes);
+      bulk_g2s(smem + st * L.stage_bytes, src + (t_begin + s) * (int64_t)bytes, bytes, &bar[st]);
+    }
+  }
+  const int n_pairs = kTileT * n_here;  // warps never straddle antennas: blockDim is a multiple of kTileT
+  for (int64_t t = t_begin; t < t_end; ++t, ++it) {
+    const int st = (int)(it & 1);
+    const uint32_t parity = (uint32_t)((it >> 1) & 1);
+    const bool ok = mbar_wait_bounded(&bar[st], parity);
+    if (ok) {
+      for (int p = tid; p < n_pairs; p += nthr) {
+        const int ant = p / kTileT;
+        SmemSink<acc_t> sink{trace + (size_t)ant * 3 * N, N};
+        Ops::fwd(smem + st * L.stage_bytes, p % kTileT, ant_s[ant], M, sink);
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        // let the copies already issued land before giving up
+        for (int64_t j = it; j < it + 2 && j - it + t < t_end; ++j) mbar_wait_bounded(&bar[j & 1], (uint32_t)((j >> 1) & 1));
+      }
+      return false;
+    }
+    if (tid == 0 && t + 2 < t_end) {
+      mbar_expect_tx(&bar[st], bytes);
+      bulk_g2s(smem + st * L.stage_bytes, src + (t + 2) * (int64_t)bytes, bytes, &bar[st]);
+    }
+  }
+  return true;
+}
+
+// add a CTA's shared traces into the global accumulator (skips empty groups)
+template <typename acc_t>
+__device__ void flush_traces(const acc_t* trace, acc_t* out, int n_here, int N) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int total = n_here * 3 * N;
+  if constexpr (std::is_same<acc_t, float>::value) {
+    if ((N % 4) == 0) {
+      const float4* s4 = reinterpret_cast<const float4*>(trace);
+      float4* o4 = reinterpret_cast<float4*>(out);
+      for (int i = tid; i < total / 4; i += nthr) {
+        float4 v = s4[i];
+        if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) atomicAdd(o4 + i, v);
+      }
+      return;
+    }
+  }
+  for (int i = tid; i < total; i += nthr) {
+    acc_t v = trace[i];
+    if (v != acc_t(0)) atomicAdd(out + i, v);
+  }
+}
+
+template <class Ops>
+__global__ void __launch_bounds__(kFwdMaxThreads, 1) k_forward(const FwdArgs a) {
+  using acc_t = typename Ops::acc_t;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const MedParams& M = a.M;
+  const int N = M.n_bins;
+  const FwdLayout L = fwd_layout(Ops::kPrec, a.a_tile, N);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+  AntRec* ant_s = reinterpret_cast<AntRec*>(smem + L.ant_off);
+  acc_t* trace = reinterpret_cast<acc_t*>(smem + L.trace_off);
+
+  const int ant0 = blockIdx.x * a.a_tile;
+  const int n_here = min(a.a_tile, a.n_ant - ant0);
+  const int64_t t_begin = (int64_t)blockIdx.y * a.tiles_per_range;
+  const int64_t t_end = min(t_begin + a.tiles_per_range, a.n_tiles);
+  if (t_begin >= t_end || n_here <= 0) return;  // uniform over the CTA
+
+  const int tid = threadIdx.x;
+  const int nthr = blockDim.x;
+  for (int i = tid; i < n_here * 3 * N; i += nthr) trace[i] = acc_t(0);
+  for (int i = tid; i < n_here; i += nthr) ant_s[i] = a.ants[ant0 + i];
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  int64_t it = 0;
+  if (!stream_range<Ops>(smem, L, bar, ant_s, trace, n_here, static_cast<const unsigned char*>(a.tiles), t_begin,
+                         t_end, it, M)) {
+    if (tid == 0) atomicExch(a.err, kErrWaitTimeout);
+    return;
+  }
+  __syncthreads();
+  flush_traces<acc_t>(trace, static_cast<acc_t*>(a.out) + (size_t)ant0 * 3 * N, n_here, N);
+}
+
+template <class Ops>
+cudaError_t launch_forward_ops(const FwdArgs& a, dim3 grid, int threads, size_t smem, cudaStream_t st) {
+  auto k = k_forward<Ops>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+inline int forward_threads(int a_tile) {
+  const int t = kTileT * a_tile;
+  return t < kFwdMaxThreads ? t : kFwdMaxThreads;
+}
+
+inline void forward_grid(FwdArgs& a, const FwdShape& shape, int sm_count, dim3& grid) {
+  const int ant_tiles = (a.n_ant + shape.a_tile - 1) / shape.a_tile;
+  int64_t target = (int64_t)shape.waves * sm_count;
+  int64_t ranges = (target + ant_tiles - 1) / ant_tiles;
+  if (ranges < 1) ranges = 1;
+  if (ranges > a.n_tiles) ranges = a.n_tiles;
+  a.tiles_per_range = (a.n_tiles + ranges - 1) / ranges;
+  ranges = (a.n_tiles + a.tiles_per_range - 1) / a.tiles_per_range;
+  grid = dim3((unsigned)ant_tiles, (unsigned)ranges);
+}
+
+// ---------------------------------------------------------------------------
+// arrival listing: one thread per (track, antenna)
+// ---------------------------------------------------------------------------
+template <class Ops>
+__global__ void __launch_bounds__(256) k_arrivals(const void* tiles, int64_t n, const AntRec* ants, int n_ant,
+                                                  MedParams M, int32_t* branch, int32_t* bin, float* frac) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n * n_ant) return;
+  const int64_t i = j / n_ant;
+  const int a = (int)(j % n_ant);
+  branch[j] = -1;
+  bin[2 * j] = bin[2 * j + 1] = -1;
+  frac[2 * j] = frac[2 * j + 1] = 0.0f;
+  const AntRec A = ants[a];
+  ArrivalSink sink{branch, bin, frac, j, M.n_bins};
+  const unsigned char* T = static_cast<const unsigned char*>(tiles) + (i / kTileT) * (int64_t)Ops::kTileBytes;
+  Ops::fwd(T, (int)(i % kTileT), A, M, sink);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint (Endpoint): one thread per track, loop over all antennas; track
+// gradients stay in registers and are written once; antenna gradients are
+// warp-reduced into shared memory and added to global memory once per CTA.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class Ops>
+__global__ void __launch_bounds__(256) k_backward(const BwdArgs a) {
+  using acc_t = typename Ops::acc_t;
+  extern __shared__ __align__(16) unsigned char smem_b[];
+  acc_t* sg = reinterpret_cast<acc_t*>(smem_b);  // [n_ant][3] + dN0
+  const int tid = threadIdx.x;
+  for (int k = tid; k < 3 * a.n_ant + 1; k += blockDim.x) sg[k] = acc_t(0);
+  __syncthreads();
+  const int N = a.M.n_bins;
+  const acc_t* G = static_cast<const acc_t*>(a.G);
+  acc_t dn_acc = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n_pad = (a.n + 31) / 32 * 32;  // whole warps stay together for the reductions
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < n_pad; i += stride) {
+    const bool valid = i < a.n;
+    const unsigned char* T = static_cast<const unsigned char*>(a.tiles) +
+                             ((valid ? i : 0) / kTileT) * (int64_t)Ops::kTileBytes;
+    const int l = (int)((valid ? i : 0) % kTileT);
+    acc_t tg[11];
+#pragma unroll
+    for (int k = 0; k < 11; ++k) tg[k] = acc_t(0);
+    for (int ant = 0; ant < a.n_ant; ++ant) {
+      const AntRec A = a.ants[ant];
+      acc_t ga[3] = {0, 0, 0};
+      if (valid) Ops::adj(T, l, A, a.M, G + (size_t)ant * 3 * N, tg, ga, dn_acc);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc_t v = warp_sum(ga[c]);
+        if ((tid & 31) == 0 && v != acc_t(0)) atomicAdd(&sg[3 * ant + c], v);
+      }
+    }
+    if (valid) {
+      acc_t* o[11] = {(acc_t*)a.out.x0, (acc_t*)a.out.y0, (acc_t*)a.out.z0, (acc_t*)a.out.x1, (acc_t*)a.out.y1,
+                      (acc_t*)a.out.z1, (acc_t*)a.out.t0, (acc_t*)a.out.t1, (acc_t*)a.out.bx, (acc_t*)a.out.by,
+                      (acc_t*)a.out.bz};
+#pragma unroll
+      for (int k = 0; k < 11; ++k) o[k][i] += tg[k];
+    }
+  }
+  acc_t d = warp_sum(dn_acc);
+  if ((tid & 31) == 0 && d != acc_t(0)) atomicAdd(&sg[3 * a.n_ant], d);
+  __syncthreads();
+  for (int k = tid; k < 3 * a.n_ant; k += blockDim.x)
+    if (sg[k] != acc_t(0)) atomicAdd(&a.ant_grad[k], (double)sg[k]);
+  if (tid == 0 && sg[3 * a.n_ant] != acc_t(0)) atomicAdd(a.dN0, (double)sg[3 * a.n_ant]);
+}
+
+// gradient of one deposit l = kappa (g.V)/(D R) with respect to d = x_a - x_e,
+// beta and the source index n (with bins held fixed):
+//   dl/dd    = kappa/(D R^2) [ -(rhat.g) V + c (g - rhat (rhat.g)) - (g.V)(n V/D + rhat) ]
+//   dl/dbeta = kappa/(D R)   [ (rhat.g) rhat - g + (g.V) n rhat / D ]
+//   dl/dn    = kappa (g.V) c / (D^2 R)
+template <typename T>
+__device__ __forceinline__ void deposit_adjoint(const T rh[3], const T V[3], T c, T D, T R, T n, const T g[3],
+                                                T kappa, T dd[3], T db[3], T& dnsrc) {
+  const T gV = g[0] * V[0] + g[1] * V[1] + g[2] * V[2];
+  const T rg = rh[0] * g[0] + rh[1] * g[1] + rh[2] * g[2];
+  const T invD = T(1) / D;
+  const T f1 = kappa * invD / (R * R);
+  const T f2 = kappa * invD / R;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dd[k] = f1 * (-rg * V[k] + c * (g[k] - rh[k] * rg) - gV * (n * V[k] * invD + rh[k]));
+    db[k] = f2 * (rg * rh[k] - g[k] + gV * n * rh[k] * invD);
+  }
+  dnsrc = f2 * gV * c * invD;
+}
+
+}  // namespace c8r

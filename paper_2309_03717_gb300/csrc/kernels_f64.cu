@@ -1,0 +1,41 @@
+// kernels_f64.cu -- instantiation of the FP64 forward, arrival-listing and
+// adjoint kernels.  Compiled with --fmad=false: every FP64 operation rounds as
+// written, as in a plain FP64 evaluation of the formulas.
+#include "pair_f64.cuh"
+
+namespace c8r {
+
+cudaError_t launch_forward_f64(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants, int n_ant,
+                               const MedParams& M, void* traces, const FwdShape& shape, int sm_count, int* err,
+                               cudaStream_t st) {
+  FwdArgs a{tiles, n_tiles, 0, ants, n_ant, shape.a_tile, traces, err, M};
+  dim3 grid;
+  forward_grid(a, shape, sm_count, grid);
+  const int threads = forward_threads(shape.a_tile);
+  const size_t smem = fwd_layout(C8R_FP64, shape.a_tile, M.n_bins).total;
+  if (formalism == C8R_ENDPOINT) return launch_forward_ops<OpsF64<C8R_ENDPOINT>>(a, grid, threads, smem, st);
+  return launch_forward_ops<OpsF64<C8R_ZHS>>(a, grid, threads, smem, st);
+}
+
+cudaError_t launch_arrivals_f64(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,
+                                const MedParams& M, int32_t* branch, int32_t* bin, float* frac, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((n * (int64_t)n_ant + 255) / 256);
+  if (formalism == C8R_ENDPOINT)
+    k_arrivals<OpsF64<C8R_ENDPOINT>><<<blocks, 256, 0, st>>>(tiles, n, ants, n_ant, M, branch, bin, frac);
+  else
+    k_arrivals<OpsF64<C8R_ZHS>><<<blocks, 256, 0, st>>>(tiles, n, ants, n_ant, M, branch, bin, frac);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward_f64(const BwdArgs& a, int blocks, cudaStream_t st) {
+  const size_t smem = sizeof(double) * (3 * (size_t)a.n_ant + 1);
+  auto k = k_backward<OpsF64<C8R_ENDPOINT>>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<blocks, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace c8r

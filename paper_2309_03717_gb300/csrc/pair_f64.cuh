@@ -1,0 +1,215 @@
+// pair_f64.cuh -- per (track, antenna) arithmetic of the FP64 path: the plain
+// formulas of the two formalisms (§1) and the straight-line propagator (§2) in
+// FP64, in the order of their definitions.  This translation unit is compiled
+// without FMA contraction so that every operation rounds as written.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace c8r {
+
+#define TF(f) T[(f) * kTileT + l]
+
+struct EndpointEvalD {
+  GeoD g0, g1, gm;
+  double V0[3], V1[3], Vm[3];
+  double D0, D1, Dm;
+  double E0, E1, Em;
+  int branch;
+  double ua, ub;
+  bool valid;
+};
+
+__device__ __forceinline__ void field_vec_f64(const double b[3], const GeoD& g, double V[3], double& D) {
+  const double c = b[0] * g.rh[0] + b[1] * g.rh[1] + b[2] * g.rh[2];
+  V[0] = c * g.rh[0] - b[0];
+  V[1] = c * g.rh[1] - b[1];
+  V[2] = c * g.rh[2] - b[2];
+  D = 1.0 - g.n_src * c;
+}
+
+__device__ __forceinline__ void endpoint_eval_f64(const double* T, int l, const AntRec& A, const MedParams& M,
+                                                  EndpointEvalD& e) {
+  e.valid = false;
+  const double b[3] = {TF(fd::BX), TF(fd::BY), TF(fd::BZ)};
+  const double x0 = TF(fd::X0), y0 = TF(fd::Y0), z0 = TF(fd::Z0);
+  const double x1 = TF(fd::X1), y1 = TF(fd::Y1), z1 = TF(fd::Z1);
+  const double t0 = TF(fd::T0), t1 = TF(fd::T1);
+  e.E0 = TF(fd::E0);
+  e.E1 = TF(fd::E1);
+  e.Em = TF(fd::EM);
+  geo_f64(M, A, x0, y0, z0, e.E0, e.g0);
+  geo_f64(M, A, x1, y1, z1, e.E1, e.g1);
+  if (e.g0.R == 0.0 || e.g1.R == 0.0) return;
+  field_vec_f64(b, e.g0, e.V0, e.D0);
+  field_vec_f64(b, e.g1, e.V1, e.D1);
+  if (fmin(fabs(e.D0), fabs(e.D1)) >= M.eps_Cd) {
+    e.branch = 0;
+    e.ua = arrival_f64(M, e.g0, t0, A.t_ref);
+    e.ub = arrival_f64(M, e.g1, t1, A.t_ref);
+    e.valid = true;
+    return;
+  }
+  e.branch = 1;
+  geo_f64(M, A, 0.5 * (x0 + x1), 0.5 * (y0 + y1), 0.5 * (z0 + z1), e.Em, e.gm);
+  if (e.gm.R == 0.0) return;
+  field_vec_f64(b, e.gm, e.Vm, e.Dm);
+  const double dte = t1 - t0;
+  const double tm = 0.5 * (t0 + t1);
+  const double tarr_rel = (tm - A.t_ref) + e.gm.n_avg * e.gm.R * M.inv_c_ns;
+  e.ua = (tarr_rel - e.Dm * dte / 2.0) / M.dt_ns;
+  e.ub = (tarr_rel + e.Dm * dte / 2.0) / M.dt_ns;
+  e.valid = true;
+}
+
+template <int FORM>
+struct OpsF64 {
+  using acc_t = double;
+  static constexpr int kPrec = C8R_FP64;
+  static constexpr int kTileBytes = kTileBytesF64;
+
+  template <class Sink>
+  static __device__ __forceinline__ void endpoint(const double* T, int l, const AntRec& A, const MedParams& M,
+                                                  Sink& out) {
+    const double q = TF(fd::Q);
+    if (q == 0.0) return;
+    const int N = M.n_bins;
+    EndpointEvalD e;
+    endpoint_eval_f64(T, l, A, M, e);
+    if (!e.valid) return;
+    out.rec(e.branch, e.ua, e.ub);
+    const double K = q * kKendpoint;
+    const double dt_s = M.dt_ns * 1e-9;
+    const double ka = floor(e.ua), kb = floor(e.ub);
+    const bool ina = ka >= 0.0 && ka < (double)N, inb = kb >= 0.0 && kb < (double)N;
+    if (e.branch == 0) {
+      const double s0 = +K / (e.D0 * e.g0.R * dt_s);
+      const double s1 = -K / (e.D1 * e.g1.R * dt_s);
+      if (ina) out.dep((int)ka, s0 * e.V0[0], s0 * e.V0[1], s0 * e.V0[2]);
+      if (inb) out.dep((int)kb, s1 * e.V1[0], s1 * e.V1[1], s1 * e.V1[2]);
+      return;
+    }
+    if (ka == kb) return;  // both linearised arrivals in one bin: zero
+    const double s = K / (e.Dm * e.gm.R * dt_s);
+    if (ina) out.dep((int)ka, s * e.Vm[0], s * e.Vm[1], s * e.Vm[2]);
+    if (inb) out.dep((int)kb, -s * e.Vm[0], -s * e.Vm[1], -s * e.Vm[2]);
+  }
+
+  template <class Sink>
+  static __device__ __forceinline__ void zhs(const double* T, int l, const AntRec& A, const MedParams& M, Sink& out) {
+    const double q = TF(fd::Q);
+    if (q == 0.0) return;
+    const int N = M.n_bins;
+    const double b[3] = {TF(fd::BX), TF(fd::BY), TF(fd::BZ)};
+    const double x0 = TF(fd::X0), y0 = TF(fd::Y0), z0 = TF(fd::Z0);
+    const double x1 = TF(fd::X1), y1 = TF(fd::Y1), z1 = TF(fd::Z1);
+    const double t0 = TF(fd::T0), t1 = TF(fd::T1);
+    const double KA = q * kKzhs;
+    GeoD gm;
+    geo_f64(M, A, 0.5 * (x0 + x1), 0.5 * (y0 + y1), 0.5 * (z0 + z1), TF(fd::EM), gm);
+    if (gm.R == 0.0) return;
+    const double c = b[0] * gm.rh[0] + b[1] * gm.rh[1] + b[2] * gm.rh[2];
+    const double Dm = 1.0 - gm.n_src * c;
+    const double bp[3] = {b[0] - c * gm.rh[0], b[1] - c * gm.rh[1], b[2] - c * gm.rh[2]};
+    const double dte = t1 - t0;
+    const double tm = 0.5 * (t0 + t1);
+    const double tarr_rel = (tm - A.t_ref) + gm.n_avg * gm.R * M.inv_c_ns;
+    const double half = fabs(Dm) * dte / 2.0;
+    const double t_lo = tarr_rel - half, t_hi = tarr_rel + half;
+    const double dt = M.dt_ns;
+    const double u_lo = t_lo / dt, u_hi = t_hi / dt;
+    const double k_lo = floor(u_lo), k_hi = floor(u_hi);
+    out.rec(k_lo == k_hi ? 2 : 3, u_lo, u_hi);
+    if (!(u_lo < (double)N + 1.0 && u_hi > -1.0)) return;
+    if (k_lo == k_hi) {
+      const double s = KA * dte / (gm.R * dt);
+      if (k_lo >= 0.0 && k_lo < (double)N) out.dep((int)k_lo, s * bp[0], s * bp[1], s * bp[2]);
+      return;
+    }
+    const double kb = fmax(k_lo, 0.0), ke = fmin(k_hi, (double)(N - 1));
+    for (double kd = kb; kd <= ke; kd += 1.0) {
+      const double e_lo = kd * dt, e_hi = (kd + 1.0) * dt;
+      const double o = fmin(t_hi, e_hi) - fmax(t_lo, e_lo);
+      if (o <= 0.0) continue;
+      const double s = KA / gm.R * (o / fabs(Dm)) / dt;
+      out.dep((int)kd, s * bp[0], s * bp[1], s * bp[2]);
+    }
+  }
+
+  template <class Sink>
+  static __device__ __forceinline__ void fwd(const void* Tv, int l, const AntRec& A, const MedParams& M, Sink& out) {
+    const double* T = static_cast<const double*>(Tv);
+    if constexpr (FORM == C8R_ENDPOINT)
+      endpoint(T, l, A, M, out);
+    else
+      zhs(T, l, A, M, out);
+  }
+
+  static __device__ __forceinline__ void adj(const void* Tv, int l, const AntRec& A, const MedParams& M,
+                                             const double* G, double tg[11], double ga[3], double& dn) {
+    static_assert(FORM == C8R_ENDPOINT, "adjoint is defined for the Endpoint formalism");
+    const double* T = static_cast<const double*>(Tv);
+    const double q = TF(fd::Q);
+    if (q == 0.0) return;
+    const int N = M.n_bins;
+    EndpointEvalD e;
+    endpoint_eval_f64(T, l, A, M, e);
+    if (!e.valid) return;
+    const double b[3] = {TF(fd::BX), TF(fd::BY), TF(fd::BZ)};
+    const double K = q * kKendpoint;
+    const double dt_s = M.dt_ns * 1e-9;
+    const double ka = floor(e.ua), kb = floor(e.ub);
+    const bool ina = ka >= 0.0 && ka < (double)N, inb = kb >= 0.0 && kb < (double)N;
+    const bool expo = M.kind == C8R_EXPONENTIAL;
+    double dd[3], db[3], dns;
+    if (e.branch == 0) {
+      for (int j = 0; j < 2; ++j) {
+        const bool in = j == 0 ? ina : inb;
+        if (!in) continue;
+        const int k = (int)(j == 0 ? ka : kb);
+        const double gv[3] = {G[k], G[N + k], G[2 * N + k]};
+        const GeoD& g = j == 0 ? e.g0 : e.g1;
+        const double* V = j == 0 ? e.V0 : e.V1;
+        const double c = b[0] * g.rh[0] + b[1] * g.rh[1] + b[2] * g.rh[2];
+        deposit_adjoint<double>(g.rh, V, c, j == 0 ? e.D0 : e.D1, g.R, g.n_src, gv, (j == 0 ? K : -K) / dt_s, dd,
+                                db, dns);
+        const double E = j == 0 ? e.E0 : e.E1;
+        for (int cc = 0; cc < 3; ++cc) {
+          tg[3 * j + cc] -= dd[cc];
+          ga[cc] += dd[cc];
+          tg[8 + cc] += db[cc];
+        }
+        if (expo) {
+          tg[3 * j + 2] += dns * (-M.N0 * E / M.H);
+          dn += dns * E;
+        } else {
+          dn += dns;
+        }
+      }
+      return;
+    }
+    if (ka == kb) return;
+    double gv[3];
+    for (int cc = 0; cc < 3; ++cc)
+      gv[cc] = (ina ? G[cc * N + (int)ka] : 0.0) - (inb ? G[cc * N + (int)kb] : 0.0);
+    const double c = b[0] * e.gm.rh[0] + b[1] * e.gm.rh[1] + b[2] * e.gm.rh[2];
+    deposit_adjoint<double>(e.gm.rh, e.Vm, c, e.Dm, e.gm.R, e.gm.n_src, gv, K / dt_s, dd, db, dns);
+    for (int cc = 0; cc < 3; ++cc) {
+      tg[cc] -= 0.5 * dd[cc];
+      tg[3 + cc] -= 0.5 * dd[cc];
+      ga[cc] += dd[cc];
+      tg[8 + cc] += db[cc];
+    }
+    if (expo) {
+      tg[2] += 0.5 * dns * (-M.N0 * e.Em / M.H);
+      tg[5] += 0.5 * dns * (-M.N0 * e.Em / M.H);
+      dn += dns * e.Em;
+    } else {
+      dn += dns;
+    }
+  }
+};
+
+#undef TF
+
+}  // namespace c8r

@@ -1,0 +1,159 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
+
+Bars (from the hot-path contract): relative L2 <= 1e-9 for the FP64 path and
+<= 1e-4 for the mixed path; bin indices identical except within 1e-6 bin of an
+edge.  Inputs are the seeded synthetic shower workloads, cut to sizes the oracle
+finishes in seconds while still spanning many track tiles (128 tracks), several
+antenna tiles and a ragged tail.
+"""
+import numpy as np
+import pytest
+
+from _util import (built_lib, compare_bins, drop_tracks, endpoint_unambiguous, oracle_arrivals, oracle_traces,
+                   rel_l2, to_device)
+from paper_2309_03717_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    built_lib()
+    from paper_2309_03717_gb300 import c8r
+    c8r.load()
+
+
+def process(w, formalism, precision, **kw):
+    from paper_2309_03717_gb300.c8r import RadioProcess
+    return RadioProcess(w["medium"], w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], formalism, precision,
+                        **kw)
+
+
+def run(w, tracks, formalism, precision, shape=None):
+    p = process(w, formalism, precision)
+    if shape:
+        p.set_launch_shape(*shape)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    p.push(to_device(tracks, dt))
+    out = p.traces().cpu().numpy()
+    br, b, fr = p.arrivals(to_device(tracks, dt))
+    st = p.stats()
+    p.close()
+    return out, (br.cpu().numpy(), b.cpu().numpy(), fr.cpu().numpy()), st
+
+
+CASES = [
+    # (cfg, n_tracks, n_ant, formalism, precision, tolerance)
+    (0, 20011, 16, "endpoint", "fp64", 1e-9),
+    (0, 20011, 16, "zhs", "fp64", 1e-9),
+    (1, 6007, 40, "endpoint", "fp64", 1e-9),
+    (1, 6007, 40, "zhs", "fp64", 1e-9),
+    (1, 20011, 160, "endpoint", "mixed", 1e-4),
+    (1, 20011, 160, "zhs", "mixed", 1e-4),
+    (0, 20011, 16, "endpoint", "mixed", 1e-4),
+    (0, 20011, 16, "zhs", "mixed", 1e-4),
+]
+
+
+@pytest.mark.parametrize("cfg,n,n_ant,formalism,precision,tol", CASES)
+def test_traces_match_oracle(cfg, n, n_ant, formalism, precision, tol):
+    w = synth.workload(cfg, n_tracks=n, n_ant=n_ant)
+    if precision == "mixed":
+        w["dtype"] = np.float32
+    tracks = synth.workload_tracks(w)
+    if formalism == "endpoint":
+        # tracks with a deposit within 1e-6 bin of an edge may land in either bin;
+        # they are checked by the bin test below and left out of the L2 test
+        keep = endpoint_unambiguous(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"])
+        assert keep.mean() > 0.99
+        tracks = drop_tracks(tracks, keep)
+    ref, kept = oracle_traces(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], formalism)
+    gpu, arr, st = run(w, tracks, formalism, precision)
+    assert st["tracks_kept"] == kept
+    assert np.abs(ref).max() > 0
+    err = rel_l2(gpu, ref)
+    assert err <= tol, f"relative L2 {err:.3e} > {tol:.0e}"
+    obr, ou = oracle_arrivals(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], formalism)
+    n_cmp, n_amb = compare_bins(arr[0], arr[1], arr[2], obr, ou, w["n_bins"])
+    assert n_cmp > 0.99 * obr.size
+
+
+@pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_invariant_to_launch_shape(formalism, precision):
+    """§5: pulses do not depend on the number of threads; here: on the antenna
+    tile, the number of track ranges and the chunking (up to addition order)."""
+    w = synth.workload(1, n_tracks=9001, n_ant=24)
+    tracks = synth.workload_tracks(w)
+    base, _, _ = run(w, tracks, formalism, precision)
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    for shape in [(1, 1, 0), (3, 16, 0), (2, 2, 1000), (4, 0, 4096)]:
+        if precision == "fp64" and shape[0] > 2:  # two FP64 traces of 4096 bins fill shared memory
+            shape = (2,) + shape[1:]
+        other, _, _ = run(w, tracks, formalism, precision, shape)
+        assert rel_l2(other, base) <= tol, shape
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_edge_cases(precision):
+    from paper_2309_03717_gb300 import c8r
+    from paper_2309_03717_gb300.c8r import C8RError
+    w = synth.workload(1, n_tracks=300, n_ant=5)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    p = process(w, "endpoint", precision)
+    # empty push is a no-op
+    empty = {f: torch.empty(0, dtype=dt, device="cuda") for f in synth.FIELDS}
+    p.push(empty)
+    assert not p.traces().any()
+    # a single track, and a ragged count (not a multiple of the 128-track tile)
+    tr = synth.workload_tracks(w)
+    for n in (1, 129, 300):
+        p.reset()
+        sub = {f: tr[f][:n] for f in synth.FIELDS}
+        p.push(to_device(sub, dt))
+        ref, _ = oracle_traces(sub, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], "endpoint")
+        got = p.traces().cpu().numpy()
+        assert rel_l2(got, ref) <= (1e-9 if precision == "fp64" else 1e-4)
+    # all tracks filtered: neutral / non-finite / zero length / |beta| >= 1
+    bad = {f: np.array(tr[f][:4]) for f in synth.FIELDS}
+    bad["q"][0] = 0.0
+    bad["x0"][1] = np.nan
+    bad["x1"][2], bad["y1"][2], bad["z1"][2] = bad["x0"][2], bad["y0"][2], bad["z0"][2]
+    bad["bz"][3] = -1.0
+    bad["bx"][3] = bad["by"][3] = 0.0
+    p.reset()
+    p.push(to_device(bad, dt))
+    assert not p.traces().any()
+    assert p.stats()["tracks_kept"] == 0
+    # a window that every arrival misses
+    w2 = dict(w)
+    w2["t_start_ns"] = w["t_start_ns"] - 1e6
+    p2 = process(w2, "zhs", precision)
+    p2.push(to_device(tr, dt))
+    assert not p2.traces().any()
+    # invalid arguments are rejected, not run
+    with pytest.raises(C8RError):
+        c8r.c8r_set_medium(p.ctx, c8r.C8R_UNIFORM, -1.0, 1.0)
+    with pytest.raises(C8RError):
+        c8r.c8r_set_antennas(p.ctx, w["ant_xyz"], w["t_start_ns"], 0, 0.2, 0, 1)
+    with pytest.raises(C8RError):
+        c8r.c8r_set_antennas(p.ctx, w["ant_xyz"], w["t_start_ns"], 1 << 20, 0.2, 0, 1)  # trace too long
+    p.close()
+    p2.close()
+
+
+def test_mixed_accepts_fp64_input_rounded_to_fp32():
+    w = synth.workload(1, n_tracks=2000, n_ant=8)
+    tr32 = synth.workload_tracks(w)
+    tr64 = {f: tr32[f].astype(np.float64) for f in synth.FIELDS}
+    a, _, _ = run(w, tr32, "endpoint", "mixed")
+    p = process(w, "endpoint", "mixed")
+    p.push(to_device(tr64))
+    b = p.traces().cpu().numpy()
+    p.close()
+    assert np.array_equal(a != 0, b != 0)
+    assert rel_l2(b, a) < 1e-6
