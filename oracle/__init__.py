@@ -27,7 +27,7 @@ _lib = None
 
 UNIFORM, EXPONENTIAL = 0, 1
 ENDPOINT, ZHS = 0, 1
-MODE_NORMAL, MODE_FORCE_MIDPOINT, MODE_ZHS_EDGE_SAMPLED = 0, 1, 2
+MODE_NORMAL, MODE_FORCE_MIDPOINT, MODE_ZHS_EDGE_SAMPLED, MODE_ABS = 0, 1, 2, 3
 FIELDS = ("x0", "y0", "z0", "x1", "y1", "z1", "t0", "t1", "bx", "by", "bz", "q")
 C_LIGHT = 299792458.0
 

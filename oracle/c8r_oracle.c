@@ -54,8 +54,11 @@
 
 enum { OR_UNIFORM = 0, OR_EXPONENTIAL = 1 };
 enum { OR_ENDPOINT = 0, OR_ZHS = 1 };
-/* oracle-only evaluation modes used by the identity tests */
-enum { OR_MODE_NORMAL = 0, OR_MODE_FORCE_MIDPOINT = 1, OR_MODE_ZHS_EDGE_SAMPLED = 2 };
+/* oracle-only evaluation modes used by the tests: the identity tests force the
+   Endpoint midpoint form or sample the ZHS potential at bin edges; MODE_ABS
+   accumulates |deposit| per component (the magnitude of the summed terms, the
+   scale of the rounding error of any evaluation of the sum) */
+enum { OR_MODE_NORMAL = 0, OR_MODE_FORCE_MIDPOINT = 1, OR_MODE_ZHS_EDGE_SAMPLED = 2, OR_MODE_ABS = 3 };
 
 typedef struct {
   const double *x0, *y0, *z0, *x1, *y1, *z1; /* m                          */
@@ -138,9 +141,11 @@ static double arrival_in_bins(const or_path* p, double t_e, double t_ref, double
 
 static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
+static int g_abs_mode = 0; /* set by oracle_forward for OR_MODE_ABS; single-threaded */
+
 static void deposit(double* trace_a, int n_bins, int64_t k, const double v[3], double scale) {
   if (k < 0 || k >= n_bins) return;
-  for (int c = 0; c < 3; ++c) trace_a[(int64_t)c * n_bins + k] += scale * v[c];
+  for (int c = 0; c < 3; ++c) trace_a[(int64_t)c * n_bins + k] += g_abs_mode ? fabs(scale * v[c]) : scale * v[c];
 }
 
 static double K_endpoint(double q) { return q * OR_QE / (4.0 * OR_PI * OR_EPS0 * OR_C_LIGHT); }
@@ -276,6 +281,8 @@ static or_pair_info zhs_pair(const or_tracks* T, int64_t i, const double xa[3], 
 int64_t oracle_forward(const or_tracks* T, int64_t n, const or_antennas* A, const or_medium* m, int formalism,
                        double eps_C, int mode, double* traces) {
   int64_t kept = 0;
+  g_abs_mode = (mode == OR_MODE_ABS);
+  if (g_abs_mode) mode = OR_MODE_NORMAL;
   for (int64_t i = 0; i < n; ++i) {
     if (!track_kept(T, i)) continue;
     ++kept;
@@ -288,6 +295,7 @@ int64_t oracle_forward(const or_tracks* T, int64_t n, const or_antennas* A, cons
         zhs_pair(T, i, xa, A->t_ref[a], A->dt, A->n_bins, m, mode, tr);
     }
   }
+  g_abs_mode = 0;
   return kept;
 }
 

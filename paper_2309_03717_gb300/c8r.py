@@ -379,3 +379,79 @@ class RadioTraces(torch.autograd.Function):
         c8r_backward(process.ctx, tracks, g, tg, ag, dn)
         grads = [tg[f].to(tracks[f].dtype) for f in GRAD_FIELDS] + [torch.zeros_like(tracks["q"])]
         return (None, dn.reshape(()).to(N0.dtype), *grads, ag.to(ant.dtype))
+
+
+class Batch:
+    """Many showers of uneven size in one persistent launch (c8r_batch_*).
+
+    showers: list of dicts with ``n_tracks``, ``ant_xyz`` [A, 3] and ``t_start_ns``
+    [A]; their tracks are concatenated in order, and so are the output traces
+    [sum A, 3, n_bins] (float32)."""
+
+    def __init__(self, showers, medium: dict, n_bins: int, dt_ns: float, formalism="endpoint", device=None):
+        lib = load()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = torch.device("cuda", device)
+        n_tracks = np.array([int(s["n_tracks"]) for s in showers], dtype=np.int64)
+        n_ant = np.array([len(s["ant_xyz"]) for s in showers], dtype=np.int32)
+        self.track_offset = np.concatenate([[0], np.cumsum(n_tracks)[:-1]]).astype(np.int64)
+        self.ant_offset = np.concatenate([[0], np.cumsum(n_ant)[:-1]]).astype(np.int32)
+        pos = np.ascontiguousarray(np.concatenate([np.asarray(s["ant_xyz"], np.float64) for s in showers]))
+        ts = np.ascontiguousarray(np.concatenate([np.asarray(s["t_start_ns"], np.float64) for s in showers]))
+        self._keep = (n_tracks, n_ant, pos, ts)
+        d = c8r_batch_desc()
+        d.n_showers = len(showers)
+        d.n_tracks = n_tracks.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d.track_offset = self.track_offset.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d.n_ant = n_ant.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.ant_offset = self.ant_offset.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.pos_xyz = pos.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.t_start_ns = ts.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.n_bins = int(n_bins)
+        d.dt_ns = float(dt_ns)
+        d.formalism = _FORMALISM[formalism]
+        kind = _MEDIUM[medium["kind"]]
+        a = medium["n"] if kind == C8R_UNIFORM else medium["N0"]
+        H = 1.0 if kind == C8R_UNIFORM else medium["H"]
+        h = ctypes.c_void_p()
+        rc = lib.c8r_batch_create(ctypes.byref(h), int(device), ctypes.byref(d), kind, float(a), float(H))
+        self.h = h
+        if rc < 0:
+            msg = lib.c8r_batch_last_error(h).decode() if h.value else "batch creation failed"
+            self.close()
+            raise C8RError(rc, msg)
+        self.n_ant_total = int(n_ant.sum())
+        self.n_bins = int(n_bins)
+
+    def _check(self, rc):
+        if rc < 0:
+            raise C8RError(rc, load().c8r_batch_last_error(self.h).decode())
+        return rc
+
+    def run(self, tracks: dict, out: torch.Tensor, use_graph=True, stream=None):
+        s = tracks_struct(tracks)
+        if out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float32 CUDA tensor")
+        return self._check(load().c8r_batch_run(self.h, ctypes.byref(s), _ptr(out), 1 if use_graph else 0,
+                                                _stream(stream)))
+
+    def set_cancel(self, value: bool):
+        return self._check(load().c8r_batch_set_cancel(self.h, 1 if value else 0))
+
+    def sync(self, stream=None):
+        return self._check(load().c8r_batch_sync(self.h, _stream(stream)))
+
+    def new_output(self):
+        return torch.zeros((self.n_ant_total, 3, self.n_bins), dtype=torch.float32, device=self.device)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().c8r_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

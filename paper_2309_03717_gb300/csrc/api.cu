@@ -39,6 +39,7 @@ void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, d
     M.invH = 0.0;
     split(n_or_N0 * kc, M.s_h, M.s_l);
     M.nf = (float)n_or_N0;
+    M.nm1f = (float)(n_or_N0 - 1.0);
   } else {
     M.n = 1.0;
     M.N0 = n_or_N0;
@@ -499,17 +500,23 @@ int c8r_arrivals(c8r_ctx* c, const c8r_tracks* t, int64_t n, int32_t* branch, in
   if ((r = check_tracks(c, t, n)) != C8R_OK) return r;
   if (n == 0) return C8R_OK;
   if (!branch || !bin || !frac) return fail(c, C8R_EINVAL, "output arrays are NULL");
-  if (n > c->chunk_tracks) return fail(c, C8R_EINVAL, "c8r_arrivals takes at most one chunk of tracks");
   cudaSetDevice(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   c->last_stream = st;
-  if ((r = ensure_tiles(c, n)) != C8R_OK) return r;
-  cudaError_t e = launch_ingest(c->precision, offset_tracks(t, 0), n, c->d_tiles, c->M, nullptr, st);
-  if (e == cudaSuccess)
-    e = (c->precision == C8R_FP64)
-            ? launch_arrivals_f64(c->formalism, c->d_tiles, n, c->d_ants, c->n_ant, c->M, branch, bin, frac, st)
-            : launch_arrivals_mixed(c->formalism, c->d_tiles, n, c->d_ants, c->n_ant, c->M, branch, bin, frac, st);
-  if (e != cudaSuccess) return cuda_fail(c, e, "arrivals launch");
+  const int64_t chunk = n < c->chunk_tracks ? n : c->chunk_tracks;
+  if ((r = ensure_tiles(c, chunk)) != C8R_OK) return r;
+  for (int64_t off = 0; off < n; off += chunk) {
+    const int64_t m = (n - off) < chunk ? (n - off) : chunk;
+    const int64_t j0 = off * c->n_ant;
+    cudaError_t e = launch_ingest(c->precision, offset_tracks(t, off), m, c->d_tiles, c->M, nullptr, st);
+    if (e == cudaSuccess)
+      e = (c->precision == C8R_FP64)
+              ? launch_arrivals_f64(c->formalism, c->d_tiles, m, c->d_ants, c->n_ant, c->M, branch + j0,
+                                    bin + 2 * j0, frac + 2 * j0, st)
+              : launch_arrivals_mixed(c->formalism, c->d_tiles, m, c->d_ants, c->n_ant, c->M, branch + j0,
+                                      bin + 2 * j0, frac + 2 * j0, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "arrivals launch");
+  }
   return C8R_OK;
 }
 

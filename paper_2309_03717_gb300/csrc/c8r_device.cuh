@@ -87,8 +87,8 @@ struct MedParams {
   float cN_h, cN_l;      // exponential: N0 H /(c dt)
   float invH_h, invH_l;  // 1/H
   float N0f, nf;         // N0 and n as floats
+  float nm1f;            // uniform: n - 1 formed in FP64, then rounded (never (1 + x) - 1 in FP32)
   float eps_C;           // near-Cherenkov threshold
-  float pad;
 };
 
 // ---------------------------------------------------------------------------
@@ -205,21 +205,29 @@ __device__ __forceinline__ double arrival_f64(const MedParams& M, const GeoD& g,
 // ---------------------------------------------------------------------------
 struct GeoM {
   float s[3], e[3];  // d = x_a - x_e as float-float per component
-  float R0, R1;      // |d| as float-float
+  float R0, R1;      // |d| as float-float (R1 = 0 until geo_refine)
   float y;           // ~1/R0 (rsqrt estimate)
 };
 
-// d = a - p (p given as float-float; p_l = 0 for the FP32-exact endpoints), and
-// R = |d| in float-float: the three exact squares are summed with TwoSum, then
-// one Newton step corrects the FP32 square root.
-__device__ __forceinline__ void geo_mixed(const AntRec& A, float pxh, float pyh, float pzh, float pxl, float pyl,
-                                          float pzl, GeoM& g) {
+// d = a - p (p given as float-float; p_l = 0 for the FP32-exact endpoints) and
+// an FP32 estimate of R = |d| (enough for the Doppler factor and amplitudes)
+__device__ __forceinline__ void geo_lite(const AntRec& A, float pxh, float pyh, float pzh, float pxl, float pyl,
+                                         float pzl, GeoM& g) {
   two_sum(A.xh, -pxh, g.s[0], g.e[0]);
   two_sum(A.yh, -pyh, g.s[1], g.e[1]);
   two_sum(A.zh, -pzh, g.s[2], g.e[2]);
   g.e[0] = __fadd_rn(g.e[0], __fsub_rn(A.xl, pxl));
   g.e[1] = __fadd_rn(g.e[1], __fsub_rn(A.yl, pyl));
   g.e[2] = __fadd_rn(g.e[2], __fsub_rn(A.zl, pzl));
+  const float S = __fmaf_rn(g.s[0], g.s[0], __fmaf_rn(g.s[1], g.s[1], __fmul_rn(g.s[2], g.s[2])));
+  g.y = rsqrtf(S);
+  g.R0 = __fmul_rn(S, g.y);
+  g.R1 = 0.0f;
+}
+
+// R = |d| in float-float: the three exact squares are summed with TwoSum, then
+// one Newton step corrects the FP32 estimate R0 (its square is formed exactly)
+__device__ __forceinline__ void geo_refine(GeoM& g) {
   float p0, q0, p1, q1, p2, q2;
   two_prod(g.s[0], g.s[0], p0, q0);
   two_prod(g.s[1], g.s[1], p1, q1);
@@ -227,16 +235,18 @@ __device__ __forceinline__ void geo_mixed(const AntRec& A, float pxh, float pyh,
   float S1, E1, S2, E2;
   two_sum(p0, p1, S1, E1);
   two_sum(S1, p2, S2, E2);
-  float cross = __fmaf_rn(g.s[0], g.e[0], __fmaf_rn(g.s[1], g.e[1], __fmul_rn(g.s[2], g.e[2])));
-  float lo = __fadd_rn(__fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2, E1)), __fadd_rn(E2, __fmul_rn(2.0f, cross)));
-  float y = rsqrtf(S2);
-  float R0 = __fmul_rn(S2, y);
+  const float cross = __fmaf_rn(g.s[0], g.e[0], __fmaf_rn(g.s[1], g.e[1], __fmul_rn(g.s[2], g.e[2])));
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2, E1)), __fadd_rn(E2, __fmul_rn(2.0f, cross)));
   float rq, rqe;
-  two_prod(R0, R0, rq, rqe);
-  float rho = __fadd_rn(__fsub_rn(__fsub_rn(S2, rq), rqe), lo);
-  g.R0 = R0;
-  g.R1 = __fmul_rn(__fmul_rn(rho, 0.5f), y);
-  g.y = y;
+  two_prod(g.R0, g.R0, rq, rqe);
+  const float rho = __fadd_rn(__fsub_rn(__fsub_rn(S2, rq), rqe), lo);
+  g.R1 = __fmul_rn(__fmul_rn(rho, 0.5f), g.y);
+}
+
+__device__ __forceinline__ void geo_mixed(const AntRec& A, float pxh, float pyh, float pzh, float pxl, float pyl,
+                                          float pzl, GeoM& g) {
+  geo_lite(A, pxh, pyh, pzh, pxl, pyl, pzl, g);
+  geo_refine(g);
 }
 
 // arrival position u = (t_e - t_ref)/dt + n_avg R / (c dt) in bins, float-float.
@@ -260,11 +270,11 @@ __device__ __forceinline__ ff arrival_mixed(const MedParams& M, const AntRec& A,
       float Qh, Ql;
       two_sum(Eeh, -A.Eah, Qh, Ql);
       Ql = __fadd_rn(Ql, __fsub_rn(Eel, A.Eal));
-      q0 = __fdiv_rn(Qh, dzh);
+      q0 = __fdividef(Qh, dzh);
       float ph, pl;
       two_prod(q0, dzh, ph, pl);
       float r = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(Qh, ph), pl), Ql), __fmul_rn(q0, dzl));
-      q1 = __fdiv_rn(r, dzh);
+      q1 = __fdividef(r, dzh);
     } else {
       // (E_e - E_a)/dz = (E_e/H) (1 - exp(-x))/x = (E_e/H)(1 + f), f = -x/2 + x^2/6 - x^3/24
       float f = __fmul_rn(x, __fmaf_rn(x, __fmaf_rn(x, -1.0f / 24.0f, 1.0f / 6.0f), -0.5f));
@@ -330,6 +340,7 @@ struct FieldM {
   float D;
   float invR;
   float bd;    // beta . d
+  float w[3];  // d x beta
 };
 // Every step uses explicit-rounding intrinsics so the forward and the adjoint
 // kernels, which inline this in different contexts, take identical branch
@@ -358,6 +369,44 @@ __device__ __forceinline__ void field_mixed(const GeoM& g, float bx, float by, f
   f.V[2] = __fmaf_rn(sx, wy, -__fmul_rn(sy, wx));
   f.invR = invR;
   f.bd = bd;
+  f.w[0] = wx;
+  f.w[1] = wy;
+  f.w[2] = wz;
+}
+
+// the same field quantities at the midpoint of a track, from those of its two
+// endpoints: d_m = (d0 + d1)/2 exactly (float-float), and w = d x beta and
+// beta.d are linear in d, so w_m = (w0 + w1)/2, (beta.d)_m = (bd0 + bd1)/2
+__device__ __forceinline__ void midpoint_from_endpoints(const GeoM& g0, const GeoM& g1, const FieldM& f0,
+                                                        const FieldM& f1, float bmag, float om_nb, float n, GeoM& gm,
+                                                        FieldM& fmid) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float S, E;
+    two_sum(g0.s[c], g1.s[c], S, E);
+    gm.s[c] = 0.5f * S;
+    gm.e[c] = 0.5f * __fadd_rn(E, __fadd_rn(g0.e[c], g1.e[c]));
+    fmid.w[c] = 0.5f * __fadd_rn(f0.w[c], f1.w[c]);
+  }
+  const float S2 = __fmaf_rn(gm.s[0], gm.s[0], __fmaf_rn(gm.s[1], gm.s[1], __fmul_rn(gm.s[2], gm.s[2])));
+  gm.y = rsqrtf(S2);
+  gm.R0 = __fmul_rn(S2, gm.y);
+  gm.R1 = 0.0f;
+  const float bd = 0.5f * __fadd_rn(f0.bd, f1.bd);
+  const float wx = fmid.w[0], wy = fmid.w[1], wz = fmid.w[2];
+  const float sx = gm.s[0], sy = gm.s[1], sz = gm.s[2];
+  if (bd >= 0.0f) {
+    const float w2 = __fmaf_rn(wx, wx, __fmaf_rn(wy, wy, __fmul_rn(wz, wz)));
+    const float den = __fmul_rn(gm.R0, __fmaf_rn(bmag, gm.R0, bd));
+    fmid.D = __fadd_rn(om_nb, __fdiv_rn(__fmul_rn(n, w2), den));
+  } else {
+    fmid.D = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(n, bd), gm.y));
+  }
+  fmid.V[0] = __fmaf_rn(sy, wz, -__fmul_rn(sz, wy));
+  fmid.V[1] = __fmaf_rn(sz, wx, -__fmul_rn(sx, wz));
+  fmid.V[2] = __fmaf_rn(sx, wy, -__fmul_rn(sy, wx));
+  fmid.invR = gm.y;
+  fmid.bd = bd;
 }
 
 }  // namespace c8r

@@ -32,62 +32,83 @@ __device__ __forceinline__ void endpoint_eval_mixed(const float* T, int l, const
   e.valid = false;
   const float bx = TF(fm::BX), by = TF(fm::BY), bz = TF(fm::BZ);
   const float bmag = TF(fm::BMAG), omb = TF(fm::OMB);
-  const float x0 = TF(fm::X0), y0 = TF(fm::Y0), z0 = TF(fm::Z0);
-  const float x1 = TF(fm::X1), y1 = TF(fm::Y1), z1 = TF(fm::Z1);
   e.E0h = e.E1h = e.Emh = 1.0f;
-  e.n0 = e.n1 = e.nm = M.nf;
+  // n - 1 is formed directly (N0 E, or the uniform n - 1 rounded from FP64): as
+  // (1 + x) - 1 in FP32 it would lose ~6e-8, comparable to D near Cherenkov
+  float nm1_0 = M.nm1f, nm1_1 = M.nm1f;
   if (KIND == C8R_EXPONENTIAL) {
     e.E0h = TF(fm::E0H);
     e.E1h = TF(fm::E1H);
-    e.n0 = __fmaf_rn(M.N0f, e.E0h, 1.0f);
-    e.n1 = __fmaf_rn(M.N0f, e.E1h, 1.0f);
+    nm1_0 = __fmul_rn(M.N0f, e.E0h);
+    nm1_1 = __fmul_rn(M.N0f, e.E1h);
   }
+  e.n0 = __fadd_rn(1.0f, nm1_0);
+  e.n1 = __fadd_rn(1.0f, nm1_1);
   // 1 - n|beta| = (1 - |beta|) - (n - 1)|beta|
-  const float om0 = __fsub_rn(omb, __fmul_rn(__fsub_rn(e.n0, 1.0f), bmag));
-  const float om1 = __fsub_rn(omb, __fmul_rn(__fsub_rn(e.n1, 1.0f), bmag));
-  geo_mixed(A, x0, y0, z0, 0.f, 0.f, 0.f, e.g0);
-  geo_mixed(A, x1, y1, z1, 0.f, 0.f, 0.f, e.g1);
+  const float om0 = __fsub_rn(omb, __fmul_rn(nm1_0, bmag));
+  const float om1 = __fsub_rn(omb, __fmul_rn(nm1_1, bmag));
+  geo_lite(A, TF(fm::X0), TF(fm::Y0), TF(fm::Z0), 0.f, 0.f, 0.f, e.g0);
+  geo_lite(A, TF(fm::X1), TF(fm::Y1), TF(fm::Z1), 0.f, 0.f, 0.f, e.g1);
   if (e.g0.R0 == 0.0f || e.g1.R0 == 0.0f) return;  // emission point on the antenna: outside the domain
   field_mixed(e.g0, bx, by, bz, bmag, om0, e.n0, e.f0);
   field_mixed(e.g1, bx, by, bz, bmag, om1, e.n1, e.f1);
-  if (fminf(fabsf(e.f0.D), fabsf(e.f1.D)) >= M.eps_C) {
-    e.branch = 0;
-    e.ua = arrival_mixed(M, A, e.g0, TF(fm::TAU0H), TF(fm::TAU0L), e.E0h,
-                         KIND == C8R_EXPONENTIAL ? TF(fm::E0L) : 0.0f);
-    e.ub = arrival_mixed(M, A, e.g1, TF(fm::TAU1H), TF(fm::TAU1L), e.E1h,
-                         KIND == C8R_EXPONENTIAL ? TF(fm::E1L) : 0.0f);
-    e.valid = true;
-    return;
-  }
-  // near-Cherenkov: midpoint geometry (exact in float-float), arrivals t_m -/+ D_m dt_e/2
-  e.branch = 1;
-  float mx, mxl, my, myl, mz, mzl;
-  two_sum(x0, x1, mx, mxl);
-  two_sum(y0, y1, my, myl);
-  two_sum(z0, z1, mz, mzl);
-  mx *= 0.5f; mxl *= 0.5f; my *= 0.5f; myl *= 0.5f; mz *= 0.5f; mzl *= 0.5f;
-  geo_mixed(A, mx, my, mz, mxl, myl, mzl, e.gm);
-  if (e.gm.R0 == 0.0f) return;
+  const bool mid = !(fminf(fabsf(e.f0.D), fabsf(e.f1.D)) >= M.eps_C);
+  e.branch = mid ? 1 : 0;
   float Eml = 0.0f;
-  if (KIND == C8R_EXPONENTIAL) {
-    e.Emh = TF(fm::EMH);
-    Eml = TF(fm::EML);
-    e.nm = __fmaf_rn(M.N0f, e.Emh, 1.0f);
+  if (mid) {
+    // near-Cherenkov: midpoint geometry, arrivals t_m -/+ D_m dt_e/2
+    float nm1_m = M.nm1f;
+    if (KIND == C8R_EXPONENTIAL) {
+      e.Emh = TF(fm::EMH);
+      Eml = TF(fm::EML);
+      nm1_m = __fmul_rn(M.N0f, e.Emh);
+    }
+    e.nm = __fadd_rn(1.0f, nm1_m);
+    midpoint_from_endpoints(e.g0, e.g1, e.f0, e.f1, bmag, __fsub_rn(omb, __fmul_rn(nm1_m, bmag)), e.nm, e.gm, e.fm);
+    if (e.gm.R0 == 0.0f) return;
   }
-  field_mixed(e.gm, bx, by, bz, bmag, __fsub_rn(omb, __fmul_rn(__fsub_rn(e.nm, 1.0f), bmag)), e.nm, e.fm);
-  float th, tl;
-  two_sum(TF(fm::TAU0H), TF(fm::TAU1H), th, tl);
-  tl = __fadd_rn(tl, __fadd_rn(TF(fm::TAU0L), TF(fm::TAU1L)));
-  const ff um = arrival_mixed(M, A, e.gm, 0.5f * th, 0.5f * tl, e.Emh, Eml);
-  float hh, hl;  // D_m (t1 - t0)/(2 dt)
-  two_prod(e.fm.D, TF(fm::DTAUH), hh, hl);
-  hl = __fmaf_rn(e.fm.D, TF(fm::DTAUL), hl);
-  hh *= 0.5f;
-  hl *= 0.5f;
-  two_sum(um.h, -hh, e.ua.h, e.ua.l);
-  e.ua.l = __fadd_rn(e.ua.l, __fsub_rn(um.l, hl));
-  two_sum(um.h, hh, e.ub.h, e.ub.l);
-  e.ub.l = __fadd_rn(e.ub.l, __fadd_rn(um.l, hl));
+  // arrival times: both endpoints, or the midpoint alone (one code path for both
+  // branches, so a warp mixing them does not run two copies of it)
+  ff u0 = {0.0f, 0.0f}, u1 = {0.0f, 0.0f};
+#pragma unroll 1
+  for (int j = 0; j < (mid ? 1 : 2); ++j) {
+    GeoM g = (j == 0) ? (mid ? e.gm : e.g0) : e.g1;
+    float th, tl, Eh, El;
+    if (mid) {
+      two_sum(TF(fm::TAU0H), TF(fm::TAU1H), th, tl);
+      tl = __fadd_rn(tl, __fadd_rn(TF(fm::TAU0L), TF(fm::TAU1L)));
+      th *= 0.5f;
+      tl *= 0.5f;
+      Eh = e.Emh;
+      El = Eml;
+    } else {
+      th = j == 0 ? TF(fm::TAU0H) : TF(fm::TAU1H);
+      tl = j == 0 ? TF(fm::TAU0L) : TF(fm::TAU1L);
+      Eh = j == 0 ? e.E0h : e.E1h;
+      El = KIND == C8R_EXPONENTIAL ? (j == 0 ? TF(fm::E0L) : TF(fm::E1L)) : 0.0f;
+    }
+    geo_refine(g);
+    const ff u = arrival_mixed(M, A, g, th, tl, Eh, El);
+    if (j == 0)
+      u0 = u;
+    else
+      u1 = u;
+  }
+  if (!mid) {
+    e.ua = u0;
+    e.ub = u1;
+  } else {
+    float hh, hl;  // D_m (t1 - t0)/(2 dt)
+    two_prod(e.fm.D, TF(fm::DTAUH), hh, hl);
+    hl = __fmaf_rn(e.fm.D, TF(fm::DTAUL), hl);
+    hh *= 0.5f;
+    hl *= 0.5f;
+    const ff um = u0;
+    two_sum(um.h, -hh, e.ua.h, e.ua.l);
+    e.ua.l = __fadd_rn(e.ua.l, __fsub_rn(um.l, hl));
+    two_sum(um.h, hh, e.ub.h, e.ub.l);
+    e.ub.l = __fadd_rn(e.ub.l, __fadd_rn(um.l, hl));
+  }
   e.valid = true;
 }
 
@@ -116,8 +137,8 @@ struct OpsMixed {
     const int kb = bin_raw(e.ub, N, fb);
     const bool ina = ka >= 0 && ka < N, inb = kb >= 0 && kb < N;
     if (e.branch == 0) {
-      const float c0 = amp / (e.f0.D * e.g0.R0) * (e.f0.invR * e.f0.invR);
-      const float c1 = -amp / (e.f1.D * e.g1.R0) * (e.f1.invR * e.f1.invR);
+      const float c0 = __fdividef(amp, e.f0.D * e.g0.R0) * (e.f0.invR * e.f0.invR);
+      const float c1 = __fdividef(-amp, e.f1.D * e.g1.R0) * (e.f1.invR * e.f1.invR);
       if (ina && inb && ka == kb) {
         // both deposits in one bin: add them in registers, one set of atomics
         out.dep(ka, c0 * e.f0.V[0] + c1 * e.f1.V[0], c0 * e.f0.V[1] + c1 * e.f1.V[1],
@@ -129,7 +150,7 @@ struct OpsMixed {
       return;
     }
     if (ka == kb) return;  // one bin (or both outside on one side): the bin average of E vanishes
-    const float c = amp / (e.fm.D * e.gm.R0) * (e.fm.invR * e.fm.invR);
+    const float c = __fdividef(amp, e.fm.D * e.gm.R0) * (e.fm.invR * e.fm.invR);
     if (ina) out.dep(ka, c * e.fm.V[0], c * e.fm.V[1], c * e.fm.V[2]);
     if (inb) out.dep(kb, -c * e.fm.V[0], -c * e.fm.V[1], -c * e.fm.V[2]);
   }
@@ -155,14 +176,14 @@ struct OpsMixed {
     GeoM gm;
     geo_mixed(A, mx, my, mz, mxl, myl, mzl, gm);
     if (gm.R0 == 0.0f) return;
-    float Emh = 1.0f, Eml = 0.0f, nm = M.nf;
+    float Emh = 1.0f, Eml = 0.0f, nm1 = M.nm1f;
     if (KIND == C8R_EXPONENTIAL) {
       Emh = TF(fm::EMH);
       Eml = TF(fm::EML);
-      nm = __fmaf_rn(M.N0f, Emh, 1.0f);
+      nm1 = __fmul_rn(M.N0f, Emh);
     }
     FieldM f;
-    field_mixed(gm, bx, by, bz, bmag, __fsub_rn(omb, __fmul_rn(__fsub_rn(nm, 1.0f), bmag)), nm, f);
+    field_mixed(gm, bx, by, bz, bmag, __fsub_rn(omb, __fmul_rn(nm1, bmag)), __fadd_rn(1.0f, nm1), f);
     float th, tl;
     two_sum(TF(fm::TAU0H), TF(fm::TAU1H), th, tl);
     tl = __fadd_rn(tl, __fadd_rn(TF(fm::TAU0L), TF(fm::TAU1L)));
@@ -188,7 +209,7 @@ struct OpsMixed {
       if (klo >= 0 && klo < N) out.dep(klo, Mx, My, Mz);
       return;
     }
-    const float invW = 1.0f / (2.0f * hh);  // 1 / interval length in bins
+    const float invW = __fdividef(1.0f, 2.0f * hh);  // 1 / interval length in bins
     const int kb = klo < 0 ? 0 : klo;
     const int ke = khi > N - 1 ? N - 1 : khi;
     for (int k = kb; k <= ke; ++k) {

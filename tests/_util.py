@@ -44,6 +44,21 @@ def oracle_traces(tracks, ant, t_start_ns, n_bins, dt_ns, medium, formalism, eps
     return out, kept
 
 
+def oracle_abs_traces(tracks, ant, t_start_ns, n_bins, dt_ns, medium, formalism, eps_C=1e-3):
+    """Sum of |deposit| per bin and component: the magnitude of the summed terms."""
+    tr = oracle.tracks_from_ns(tracks)
+    out, _ = oracle.forward(tr, ant, np.asarray(t_start_ns) * 1e-9, n_bins, dt_ns * 1e-9, medium,
+                            oracle.ENDPOINT if formalism == "endpoint" else oracle.ZHS, eps_C, oracle.MODE_ABS)
+    return out
+
+
+def cond_err(got, ref, absref):
+    """Error relative to the magnitude of the summed deposits (condition-aware):
+    a trace whose start and end deposits nearly cancel has a tiny norm, and
+    relative to it any rounding looks large."""
+    return np.linalg.norm((np.asarray(got, np.float64) - ref).ravel()) / np.linalg.norm(absref.ravel())
+
+
 def oracle_arrivals(tracks, ant, t_start_ns, n_bins, dt_ns, medium, formalism, eps_C=1e-3):
     tr = oracle.tracks_from_ns(tracks)
     return oracle.arrivals(tr, ant, np.asarray(t_start_ns) * 1e-9, n_bins, dt_ns * 1e-9, medium,

@@ -9,8 +9,8 @@ antenna tiles and a ragged tail.
 import numpy as np
 import pytest
 
-from _util import (built_lib, compare_bins, drop_tracks, endpoint_unambiguous, oracle_arrivals, oracle_traces,
-                   rel_l2, to_device)
+from _util import (built_lib, compare_bins, cond_err, drop_tracks, endpoint_unambiguous, oracle_abs_traces,
+                   oracle_arrivals, oracle_traces, rel_l2, to_device)
 from paper_2309_03717_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -109,15 +109,18 @@ def test_edge_cases(precision):
     empty = {f: torch.empty(0, dtype=dt, device="cuda") for f in synth.FIELDS}
     p.push(empty)
     assert not p.traces().any()
-    # a single track, and a ragged count (not a multiple of the 128-track tile)
+    # a single track, and a ragged count (not a multiple of the 128-track tile);
+    # with so few tracks the start and end deposits of a track can nearly cancel,
+    # so the error is measured against the magnitude of the summed deposits
     tr = synth.workload_tracks(w)
     for n in (1, 129, 300):
         p.reset()
         sub = {f: tr[f][:n] for f in synth.FIELDS}
         p.push(to_device(sub, dt))
-        ref, _ = oracle_traces(sub, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], "endpoint")
+        args = (sub, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], "endpoint")
+        ref, _ = oracle_traces(*args)
         got = p.traces().cpu().numpy()
-        assert rel_l2(got, ref) <= (1e-9 if precision == "fp64" else 1e-4)
+        assert cond_err(got, ref, oracle_abs_traces(*args)) <= (1e-12 if precision == "fp64" else 1e-6), n
     # all tracks filtered: neutral / non-finite / zero length / |beta| >= 1
     bad = {f: np.array(tr[f][:4]) for f in synth.FIELDS}
     bad["q"][0] = 0.0
