@@ -41,7 +41,7 @@ extern "C" {
 #define C8R_ENOMEM (-2)     /* device or host allocation failed                         */
 #define C8R_ECUDA (-3)      /* a CUDA runtime call or kernel reported an error          */
 #define C8R_ECANCELLED (-4) /* a kernel gave up a bounded wait and returned early       */
-#define C8R_ETOOBIG (-5)    /* the trace length does not fit the on-chip trace tile     */
+#define C8R_ETOOBIG (-5)    /* a size beyond the library's limits (n_bins > 2^24)       */
 #define C8R_ESTATE (-6)     /* call made before the context was configured for it      */
 
 /* medium kinds (straight-line propagator, §4 listing) */
@@ -128,10 +128,10 @@ int c8r_set_medium(c8r_ctx* ctx, int kind, double n_or_N0, double scale_height_m
  * dt_ns, three components each; bin k of antenna a covers
  * [t_start_ns[a] + k dt_ns, t_start_ns[a] + (k + 1) dt_ns).  formalism selects
  * Endpoint or ZHS; precision selects C8R_FP64 or C8R_MIXED.  Allocates (and
- * zeroes) the trace accumulator [n_ant][3][n_bins] of FP64 (C8R_FP64) or FP32
- * (C8R_MIXED).  Replaces any previous antenna set and discards its traces.
- * EINVAL on n_ant < 1, n_bins < 1, dt_ns <= 0 or non-finite values; ETOOBIG if
- * one antenna's trace does not fit the on-chip tile; ENOMEM. */
+ * zeroes) the context's trace accumulator, one (x, y, z) element per antenna and
+ * bin, FP64 (C8R_FP64) or FP32 (C8R_MIXED), 32 or 16 bytes per element.  Replaces
+ * any previous antenna set and discards its traces.  EINVAL on n_ant < 1,
+ * n_bins < 1, dt_ns <= 0 or non-finite values; ETOOBIG if n_bins > 2^24; ENOMEM. */
 int c8r_set_antennas(c8r_ctx* ctx, int32_t n_ant, const double* pos_xyz, const double* t_start_ns,
                      int32_t n_bins, double dt_ns, int formalism, int precision);
 
@@ -140,10 +140,10 @@ int c8r_set_antennas(c8r_ctx* ctx, int32_t n_ant, const double* pos_xyz, const d
  * the track midpoint with linearised arrival times.  EINVAL unless 0 < eps < 1. */
 int c8r_set_cherenkov_threshold(c8r_ctx* ctx, double eps_C);
 
-/* Launch shape of the forward kernels: antennas per CTA (their traces live in
- * shared memory; 1..8, capped by what fits for n_bins) and the target number of
- * CTA waves per launch, which sets how many track ranges each antenna tile is
- * cut into.  0 keeps the automatic choice.  The result does not depend on the
+/* Launch shape of the forward kernels: antennas per CTA (1..32; every staged
+ * track tile is evaluated against all of them) and the target number of CTA
+ * waves per launch, which sets how many track ranges each antenna tile is cut
+ * into.  0 keeps the automatic choice (8 antennas, 4 waves).  The result does not depend on the
  * shape beyond the order of floating-point additions (§5: identical pulses for
  * any number of threads).  Also sets the tracks per internal chunk (0 = 2^24):
  * longer pushes are processed chunk by chunk through the same scratch. */

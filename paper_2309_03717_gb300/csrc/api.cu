@@ -70,14 +70,8 @@ void fill_antenna(AntRec& r, double x, double y, double z, double t_ref_ns, cons
   split(r.Ea, r.Eah, r.Eal);
 }
 
-size_t fwd_smem_bytes(int precision, int a_tile, int n_bins) { return fwd_layout(precision, a_tile, n_bins).total; }
-
-int max_a_tile(int precision, int n_bins) {
-  int best = 0;
-  for (int a = 1; a <= kMaxATile; ++a)
-    if (fwd_smem_bytes(precision, a, n_bins) <= 227 * 1024) best = a;
-  return best;
-}
+constexpr int kDefaultATile = 8;
+constexpr int kMaxBins = 1 << 24;
 
 }  // namespace c8r
 
@@ -98,7 +92,9 @@ struct c8r_ctx {
   double dt_ns = 0.0;
   std::vector<double> pos, t_start;
   AntRec* d_ants = nullptr;
-  void* d_traces = nullptr;
+  void* d_acc = nullptr;     // accumulator [n_ant][n_bins][x, y, z, pad]
+  size_t acc_bytes = 0;
+  void* d_stage = nullptr;   // [n_ant][3][n_bins] staging for copies to host
   size_t trace_bytes = 0;
   // scratch: derived-track tiles for one chunk
   void* d_tiles = nullptr;
@@ -147,9 +143,11 @@ int rebuild_tables(c8r_ctx* c) {
 
 void free_antenna_state(c8r_ctx* c) {
   if (c->d_ants) cudaFree(c->d_ants);
-  if (c->d_traces) cudaFree(c->d_traces);
+  if (c->d_acc) cudaFree(c->d_acc);
+  if (c->d_stage) cudaFree(c->d_stage);
   c->d_ants = nullptr;
-  c->d_traces = nullptr;
+  c->d_acc = nullptr;
+  c->d_stage = nullptr;
   c->ants_set = false;
 }
 
@@ -305,9 +303,7 @@ int c8r_set_antennas(c8r_ctx* c, int32_t n_ant, const double* pos, const double*
   if (precision != C8R_FP64 && precision != C8R_MIXED) return fail(c, C8R_EINVAL, "unknown precision");
   if (!finite_all(pos, 3 * (size_t)n_ant) || !finite_all(t_start, n_ant))
     return fail(c, C8R_EINVAL, "antenna positions / start times must be finite");
-  const int at = max_a_tile(precision, n_bins);
-  if (at < 1)
-    return fail(c, C8R_ETOOBIG, "n_bins = " + std::to_string(n_bins) + " does not fit one antenna's trace in shared memory");
+  if (n_bins > kMaxBins) return fail(c, C8R_ETOOBIG, "n_bins = " + std::to_string(n_bins) + " exceeds 2^24");
   cudaSetDevice(c->device);
   free_antenna_state(c);
   if (c->precision != precision && c->d_tiles) {
@@ -322,14 +318,15 @@ int c8r_set_antennas(c8r_ctx* c, int32_t n_ant, const double* pos, const double*
   c->precision = precision;
   c->pos.assign(pos, pos + 3 * (size_t)n_ant);
   c->t_start.assign(t_start, t_start + n_ant);
-  int want = (c->user_a_tile > 0 && c->user_a_tile < at) ? c->user_a_tile : at;
+  const int want = c->user_a_tile > 0 ? c->user_a_tile : kDefaultATile;
   c->shape.a_tile = want < n_ant ? want : n_ant;
   c->shape.threads = forward_threads(c->shape.a_tile);
   c->shape.waves = c->user_waves > 0 ? c->user_waves : 4;
   c->trace_bytes = (size_t)n_ant * 3 * n_bins * (precision == C8R_FP64 ? 8 : 4);
+  c->acc_bytes = (size_t)n_ant * n_bins * acc_elem_bytes(precision);
   cudaError_t e = cudaMalloc(&c->d_ants, sizeof(AntRec) * n_ant);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_traces, c->trace_bytes);
-  if (e == cudaSuccess) e = cudaMemset(c->d_traces, 0, c->trace_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_acc, c->acc_bytes);
+  if (e == cudaSuccess) e = cudaMemset(c->d_acc, 0, c->acc_bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_antenna_state(c);
@@ -349,9 +346,7 @@ int c8r_set_launch_shape(c8r_ctx* c, int a_tile, int waves, int64_t chunk_tracks
   c->user_waves = waves;
   c->chunk_tracks = chunk_tracks > 0 ? chunk_tracks : (int64_t)1 << 25;
   if (c->ants_set) {
-    const int at = max_a_tile(c->precision, c->n_bins);
-    int want = a_tile > 0 ? a_tile : at;
-    if (want > at) return fail(c, C8R_ETOOBIG, "a_tile antennas do not fit shared memory at this n_bins");
+    const int want = a_tile > 0 ? a_tile : kDefaultATile;
     c->shape.a_tile = want < c->n_ant ? want : c->n_ant;
     c->shape.threads = forward_threads(c->shape.a_tile);
     c->shape.waves = waves > 0 ? waves : 4;
@@ -384,10 +379,10 @@ int c8r_push_tracks(c8r_ctx* c, const c8r_tracks* t, int64_t n, void* stream) {
     if (c->profiling) cudaEventRecord(e1, st);
     const int64_t n_tiles = (m + kTileT - 1) / kTileT;
     e = (c->precision == C8R_FP64)
-            ? launch_forward_f64(c->formalism, c->d_tiles, n_tiles, c->d_ants, c->n_ant, c->M, c->d_traces, c->shape,
+            ? launch_forward_f64(c->formalism, c->d_tiles, n_tiles, c->d_ants, c->n_ant, c->M, c->d_acc, c->shape,
                                  c->sm_count, c->d_err, st)
-            : launch_forward_mixed(c->formalism, c->d_tiles, n_tiles, c->d_ants, c->n_ant, c->M, c->d_traces,
-                                   c->shape, c->sm_count, c->d_err, st);
+            : launch_forward_mixed(c->formalism, c->d_tiles, n_tiles, c->d_ants, c->n_ant, c->M, c->d_acc, c->shape,
+                                   c->sm_count, c->d_err, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "forward launch");
     if (c->profiling) {
       cudaEventRecord(e2, st);
@@ -405,11 +400,24 @@ int c8r_fetch_traces(c8r_ctx* c, void* dst, int dst_is_device, int reset, void* 
   if (!dst) return fail(c, C8R_EINVAL, "dst is NULL");
   cudaSetDevice(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(dst, c->d_traces, c->trace_bytes,
-                                  dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+  cudaError_t e;
+  if (dst_is_device) {
+    e = launch_acc_to_traces(c->precision, c->d_acc, c->n_ant, c->n_bins, dst, 0, st);
+  } else {
+    if (!c->d_stage) {
+      e = cudaMalloc(&c->d_stage, c->trace_bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->d_stage = nullptr;
+        return fail(c, C8R_ENOMEM, "staging buffer for the host copy");
+      }
+    }
+    e = launch_acc_to_traces(c->precision, c->d_acc, c->n_ant, c->n_bins, c->d_stage, 0, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, c->d_stage, c->trace_bytes, cudaMemcpyDeviceToHost, st);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "trace copy");
   if (reset) {
-    e = cudaMemsetAsync(c->d_traces, 0, c->trace_bytes, st);
+    e = cudaMemsetAsync(c->d_acc, 0, c->acc_bytes, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "trace reset");
   }
   if (!dst_is_device) {
@@ -424,7 +432,7 @@ int c8r_reset(c8r_ctx* c, void* stream) {
   if (!c->ants_set) return fail(c, C8R_ESTATE, "c8r_set_antennas has not been called");
   cudaSetDevice(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(c->d_traces, 0, c->trace_bytes, st);
+  cudaError_t e = cudaMemsetAsync(c->d_acc, 0, c->acc_bytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_kept, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return cuda_fail(c, e, "reset");
   c->pushed = 0;

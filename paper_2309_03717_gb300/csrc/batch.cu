@@ -3,12 +3,14 @@
 // batching the GPU needs to stay busy on small showers).
 //
 // The host cuts every shower into work items (antenna tile x range of derived
-// track tiles), sorts them by cost (largest first) and uploads the list.  A
-// persistent grid of one CTA per SM pops items from a global atomic counter;
-// for each item a CTA zeroes its shared traces, streams the item's track tiles
-// through the same TMA ring as the single-shower kernel and adds its traces into
-// the shower's slice of the output.  The CTA polls a cancel word between items.
-// The ingest of all showers, the counter reset and the persistent kernel are
+// track tiles) and uploads the list, largest shower first and, inside a shower,
+// antenna tiles fastest (so the items in flight share track tiles in L2 and add
+// into one shower's accumulator rows).  A persistent grid of one CTA per SM pops
+// items from a global atomic counter; for each item a CTA streams the item's
+// track tiles through the same TMA ring as the single-shower kernel and adds the
+// deposits into the batch accumulator.  The CTA polls a cancel word between
+// items.  Zeroing the accumulator, the ingest of all showers, the counter reset,
+// the persistent kernel and the conversion into the caller's trace layout are
 // captured once into a CUDA graph and replayed.  The tile shape (antennas per
 // CTA, track tiles per item) is picked by a small autotuner that times the
 // candidates on a subsample of the real work list and caches the choice.
@@ -39,7 +41,7 @@ struct BatchArgs {
   const WorkItem* items;
   int n_items;
   const AntRec* ants;
-  void* out;             // concatenated traces; NULL = evaluate without flushing (autotuner timing)
+  float4* acc;           // [sum n_ant][n_bins] accumulator
   int* counter;
   const int* cancel;
   int* err;
@@ -69,14 +71,11 @@ struct BatchMap {
 
 template <class Ops>
 __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_batch(const BatchArgs a) {
-  using acc_t = typename Ops::acc_t;
   extern __shared__ __align__(128) unsigned char smem[];
   const MedParams& M = a.M;
-  const int N = M.n_bins;
-  const FwdLayout L = fwd_layout(Ops::kPrec, a.a_tile, N);
+  const FwdLayout L = fwd_layout(Ops::kPrec, a.a_tile);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar_off);
   AntRec* ant_s = reinterpret_cast<AntRec*>(smem + L.ant_off);
-  acc_t* trace = reinterpret_cast<acc_t*>(smem + L.trace_off);
   __shared__ int s_item;
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (tid == 0) {
@@ -95,16 +94,13 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_batch(const BatchArgs a) 
     const int idx = s_item;
     if (idx < 0 || idx >= a.n_items) break;
     const WorkItem w = a.items[idx];
-    for (int i = tid; i < w.n_here * 3 * N; i += nthr) trace[i] = acc_t(0);
     for (int i = tid; i < w.n_here; i += nthr) ant_s[i] = a.ants[w.ant0 + i];
     __syncthreads();
-    if (!stream_range<Ops>(smem, L, bar, ant_s, trace, w.n_here, static_cast<const unsigned char*>(a.tiles),
-                           w.t_begin, w.t_end, it, M)) {
+    if (!stream_range<Ops>(smem, L, bar, ant_s, a.acc + (size_t)w.ant0 * M.n_bins, w.n_here,
+                           static_cast<const unsigned char*>(a.tiles), w.t_begin, w.t_end, it, M)) {
       if (tid == 0) atomicExch(a.err, kErrWaitTimeout);
       return;
     }
-    __syncthreads();
-    if (a.out) flush_traces<acc_t>(trace, static_cast<acc_t*>(a.out) + (size_t)w.ant0 * 3 * N, w.n_here, N);
     __syncthreads();
   }
 }
@@ -113,7 +109,7 @@ using BatchOps = OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>;
 
 template <class Ops>
 cudaError_t launch_batch_ops(const BatchArgs& a, int grid, cudaStream_t st) {
-  const size_t smem = fwd_layout(C8R_MIXED, a.a_tile, a.M.n_bins).total;
+  const size_t smem = fwd_layout(C8R_MIXED, a.a_tile).total;
   auto k = k_batch<Ops>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -197,6 +193,8 @@ struct c8r_batch {
   int* d_counter = nullptr;
   int* d_cancel = nullptr;
   int* d_err = nullptr;
+  float4* d_acc = nullptr;  // [total_ant][n_bins] accumulator
+  size_t acc_bytes = 0;
   cudaStream_t cap_stream = nullptr;  // graph capture (the caller's stream may be the legacy default stream)
   cudaStream_t aux_stream = nullptr;  // non-blocking: cancel word updates while a batch runs
   bool tuned = false;
@@ -216,25 +214,26 @@ int bfail(c8r_batch* b, int code, const std::string& m) {
 }
 
 std::vector<WorkItem> make_items(const c8r_batch* b, int a_tile, int64_t tpi) {
+  std::vector<int> order(b->n_showers);
+  for (int s = 0; s < b->n_showers; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return b->n_tracks[x] * (int64_t)b->n_ant[x] > b->n_tracks[y] * (int64_t)b->n_ant[y];
+  });
   std::vector<WorkItem> v;
-  for (int s = 0; s < b->n_showers; ++s) {
+  for (int s : order) {
     const int64_t nt = b->tile_off[s + 1] - b->tile_off[s];
     if (nt == 0) continue;
-    for (int a0 = 0; a0 < b->n_ant[s]; a0 += a_tile) {
-      const int nh = std::min(a_tile, b->n_ant[s] - a0);
-      for (int64_t r = 0; r < nt; r += tpi) {
+    for (int64_t r = 0; r < nt; r += tpi) {
+      for (int a0 = 0; a0 < b->n_ant[s]; a0 += a_tile) {
         WorkItem w;
         w.ant0 = b->ant_off[s] + a0;
-        w.n_here = nh;
+        w.n_here = std::min(a_tile, b->n_ant[s] - a0);
         w.t_begin = b->tile_off[s] + r;
         w.t_end = b->tile_off[s] + std::min(nt, r + tpi);
         v.push_back(w);
       }
     }
   }
-  std::stable_sort(v.begin(), v.end(), [](const WorkItem& x, const WorkItem& y) {
-    return (x.t_end - x.t_begin) * x.n_here > (y.t_end - y.t_begin) * y.n_here;
-  });
   return v;
 }
 
@@ -256,14 +255,19 @@ int64_t tpi_for(const c8r_batch* b, int a_tile, int waves) {
   return std::max<int64_t>(t, 8);
 }
 
-int enqueue(c8r_batch* b, const TrackPtrs& tp, void* out, int n_items_limit, cudaStream_t st) {
+// zero the accumulator, ingest, run the persistent kernel over the first
+// n_items_limit items, and (out != NULL) add the accumulator into out
+int enqueue(c8r_batch* b, const TrackPtrs& tp, float* out, int n_items_limit, cudaStream_t st) {
   BatchMap map{b->d_tile_off, b->d_track_off, b->d_n_tracks, b->n_showers};
-  cudaError_t e = launch_ingest_map(C8R_MIXED, tp, map, b->total_tiles * kTileT, b->d_tiles, b->M, nullptr, st);
+  cudaError_t e = cudaMemsetAsync(b->d_acc, 0, b->acc_bytes, st);
+  if (e == cudaSuccess)
+    e = launch_ingest_map(C8R_MIXED, tp, map, b->total_tiles * kTileT, b->d_tiles, b->M, nullptr, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch ingest: ") + cudaGetErrorString(e));
-  BatchArgs a{b->d_tiles, b->d_items, std::min(b->n_items, n_items_limit), b->d_ants, out, b->d_counter,
+  BatchArgs a{b->d_tiles, b->d_items, std::min(b->n_items, n_items_limit), b->d_ants, b->d_acc, b->d_counter,
               b->d_cancel, b->d_err, b->choice.a_tile, b->M};
   e = launch_batch(a, b->formalism, b->sm_count, st);
+  if (e == cudaSuccess && out) e = launch_acc_to_traces(C8R_MIXED, b->d_acc, b->total_ant, b->M.n_bins, out, 1, st);
   if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   return C8R_OK;
 }
@@ -274,16 +278,14 @@ int autotune(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
                 b->sm_count, (long long)(b->total_pairs >> 26));
   const std::string key = keybuf;
   TuneChoice best{};
-  if (tune_lookup(key, best) && best.a_tile <= max_a_tile(C8R_MIXED, b->M.n_bins)) {
+  if (tune_lookup(key, best) && best.a_tile <= kMaxATile) {
     b->choice = best;
     b->tuned = true;
     return upload_items(b, make_items(b, best.a_tile, best.tiles_per_item));
   }
-  const int amax = max_a_tile(C8R_MIXED, b->M.n_bins);
   std::vector<TuneChoice> cands;
-  for (int at : {amax, amax - 1, amax / 2})
-    if (at >= 1)
-      for (int waves : {4, 8, 16}) cands.push_back({at, tpi_for(b, at, waves)});
+  for (int at : {4, 8, 16})
+    for (int waves : {4, 8, 16}) cands.push_back({at, tpi_for(b, at, waves)});
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -338,7 +340,7 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
   if (d->n_bins < 1 || !(d->dt_ns > 0.0)) return bad(C8R_EINVAL, "n_bins / dt_ns");
   if (d->formalism != C8R_ENDPOINT && d->formalism != C8R_ZHS) return bad(C8R_EINVAL, "formalism");
   if (kind == C8R_UNIFORM ? !(n_or_N0 > 0.0) : !(n_or_N0 >= 0.0 && H > 0.0)) return bad(C8R_EINVAL, "medium");
-  if (max_a_tile(C8R_MIXED, d->n_bins) < 1) return bad(C8R_ETOOBIG, "n_bins too large for the shared trace tile");
+  if (d->n_bins > (1 << 24)) return bad(C8R_ETOOBIG, "n_bins exceeds 2^24");
   if (cudaSetDevice(device) != cudaSuccess) return bad(C8R_EINVAL, "device");
   b->device = device;
   cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, device);
@@ -394,8 +396,15 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
     *out = b;
     return C8R_ECUDA;
   }
-  const int amax = max_a_tile(C8R_MIXED, b->M.n_bins);
-  b->choice = {amax, tpi_for(b, amax, 8)};
+  b->acc_bytes = (size_t)b->total_ant * b->M.n_bins * sizeof(float4);
+  if (cudaMalloc(&b->d_acc, b->acc_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    b->d_acc = nullptr;
+    b->err = "batch accumulator allocation failed";
+    *out = b;
+    return C8R_ENOMEM;
+  }
+  b->choice = {8, tpi_for(b, 8, 8)};
   *out = b;
   return upload_items(b, make_items(b, b->choice.a_tile, b->choice.tiles_per_item));
 }
@@ -412,6 +421,7 @@ void c8r_batch_destroy(c8r_batch* b) {
   cudaFree(b->d_n_tracks);
   cudaFree(b->d_items);
   cudaFree(b->d_counter);
+  cudaFree(b->d_acc);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->aux_stream) cudaStreamDestroy(b->aux_stream);
   delete b;

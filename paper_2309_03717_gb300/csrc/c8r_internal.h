@@ -11,8 +11,8 @@ namespace c8r {
 
 // launch shape of the forward kernels
 struct FwdShape {
-  int a_tile;   // antennas per CTA (their full traces live in shared memory)
-  int threads;  // = kTileT * a_tile
+  int a_tile;   // antennas per CTA (the track tile in shared memory is reused for each)
+  int threads;  // min(kTileT * a_tile, 512)
   int waves;    // target number of CTA waves per launch
 };
 
@@ -23,8 +23,12 @@ struct TrackPtrs {
 };
 
 size_t tile_bytes(int precision);
-size_t fwd_smem_bytes(int precision, int a_tile, int n_bins);
-int max_a_tile(int precision, int n_bins);
+// bytes of one accumulator element (one bin of one antenna: x, y, z, pad)
+inline size_t acc_elem_bytes(int precision) { return precision == C8R_FP64 ? 32 : 16; }
+
+// accumulator [n_ant][n_bins] -> traces [n_ant][3][n_bins]; add != 0 adds into out (FP32 only)
+cudaError_t launch_acc_to_traces(int precision, const void* acc, int n_ant, int n_bins, void* out, int add,
+                                 cudaStream_t st);
 
 // ingest: filter + derived per-track quantities into tiles; counts kept tracks
 // into *kept unless kept is NULL
@@ -35,10 +39,10 @@ struct BwdArgs;
 
 // per-precision launchers (kernels_f64.cu / kernels_mixed.cu)
 cudaError_t launch_forward_f64(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants, int n_ant,
-                               const MedParams& M, void* traces, const FwdShape& shape, int sm_count, int* err,
+                               const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
                                cudaStream_t st);
 cudaError_t launch_forward_mixed(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants, int n_ant,
-                                 const MedParams& M, void* traces, const FwdShape& shape, int sm_count, int* err,
+                                 const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
                                  cudaStream_t st);
 cudaError_t launch_arrivals_f64(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,
                                 const MedParams& M, int32_t* branch, int32_t* bin, float* frac, cudaStream_t st);

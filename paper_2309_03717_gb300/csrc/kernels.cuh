@@ -2,14 +2,15 @@
 // translation units.  Each TU supplies an `Ops` class with the per-pair
 // arithmetic (Ops::fwd, Ops::adj) and instantiates the kernels below.
 //
-// Forward (§2 flow, "looped over all antennas"): grid.x = antenna tile whose
-// complete traces live in shared memory, grid.y = a contiguous range of
-// derived-track tiles.  grid.x varies fastest, so CTAs resident together read
-// the same track range and all but the first read hit L2.  A CTA streams its
-// range through a two-slot ring of shared-memory tiles filled by TMA bulk copies
-// (cp.async.bulk + mbarrier, bounded waits), evaluates one (track, antenna) pair
-// per thread per tile, scatters deposits with shared atomics and finally adds
-// its traces into the global accumulator.
+// Forward (§2 flow, "looped over all antennas"): a CTA owns a tile of antennas
+// and a contiguous range of derived-track tiles.  It streams its range through a
+// two-slot ring of shared-memory tiles filled by TMA bulk copies (cp.async.bulk
+// + mbarrier, bounded waits); for every staged tile each thread evaluates
+// (track, antenna) pairs (warps never straddle antennas) and adds each deposit
+// into the L2-resident accumulator [antenna][bin][x, y, z, 0] with one native
+// vector reduction (atomicAdd on float4; three FP64 reductions in the FP64
+// path).  Shared-memory atomics are not used: FP32 shared atomic adds stall the
+// issuing warp, while the global reductions are fire-and-forget.
 #pragma once
 
 #include <type_traits>
@@ -18,34 +19,66 @@
 
 namespace c8r {
 
-constexpr int kMaxATile = 8;
+constexpr int kMaxATile = 32;
 constexpr int kFwdMaxThreads = 512;
 
-// shared memory of a forward CTA: two staged track tiles, two mbarriers, the
-// antenna records of the tile, then the traces [a_tile][3][n_bins]
+// shared memory of a forward CTA: two staged track tiles, two mbarriers and the
+// antenna records of the tile
 struct FwdLayout {
-  size_t stage_bytes, bar_off, ant_off, trace_off, total;
+  size_t stage_bytes, bar_off, ant_off, total;
 };
-__host__ __device__ inline FwdLayout fwd_layout(int precision, int a_tile, int n_bins) {
+__host__ __device__ inline FwdLayout fwd_layout(int precision, int a_tile) {
   FwdLayout L;
   L.stage_bytes = precision == C8R_FP64 ? kTileBytesF64 : kTileBytesMixed;
   L.bar_off = 2 * L.stage_bytes;
   L.ant_off = L.bar_off + 128;
-  L.trace_off = L.ant_off + kMaxATile * sizeof(AntRec);
-  size_t acc = precision == C8R_FP64 ? 8 : 4;
-  L.total = L.trace_off + (size_t)a_tile * 3 * n_bins * acc;
+  L.total = L.ant_off + (size_t)a_tile * sizeof(AntRec);
   return L;
 }
+
+// accumulator element: one bin of one antenna, components x, y, z (+ padding)
+struct alignas(32) Acc4D {
+  double x, y, z, w;
+};
+template <typename T>
+struct AccOf;
+template <>
+struct AccOf<float> {
+  using type = float4;
+};
+template <>
+struct AccOf<double> {
+  using type = Acc4D;
+};
+
+// CTA -> (antenna tile, track range).  Antenna tiles are grouped into blocks
+// whose accumulators fit comfortably in L2; inside a block the antenna tile
+// varies fastest, so CTAs resident together read the same track range (L2
+// reuse of the track tiles) and add into a bounded set of accumulator rows.
+struct FwdGrid {
+  int ant_tiles;        // total antenna tiles
+  int tiles_per_block;  // antenna tiles per L2 block
+  int64_t ranges;       // track ranges
+  int64_t tiles_per_range;
+  __host__ __device__ inline void decode(int64_t cta, int& ant_tile, int64_t& range) const {
+    const int64_t per_block = (int64_t)tiles_per_block * ranges;
+    const int64_t b = cta / per_block;
+    const int64_t rem = cta - b * per_block;
+    const int nb = min(tiles_per_block, ant_tiles - (int)b * tiles_per_block);
+    range = rem / nb;
+    ant_tile = (int)(b * tiles_per_block + rem % nb);
+  }
+};
 
 struct FwdArgs {
   const void* tiles;
   int64_t n_tiles;
-  int64_t tiles_per_range;
   const AntRec* ants;
   int n_ant;
   int a_tile;
-  void* out;
+  void* acc;  // [n_ant][n_bins] accumulator elements
   int* err;
+  FwdGrid g;
   MedParams M;
 };
 
@@ -70,16 +103,32 @@ __device__ __forceinline__ void dep3(T* tr, int n_bins, int k, T vx, T vy, T vz)
 }
 
 // Sinks: the pair functions report deposits through dep() and their branch and
-// arrival positions through rec(); the forward kernel scatters into shared
-// memory, the validation listing records bins.  Both run the same arithmetic.
+// arrival positions through rec(); the forward kernel adds deposits into the
+// global accumulator, the validation listing records bins.  Both run the same
+// arithmetic.
 template <typename T>
-struct SmemSink {
-  T* tr;
-  int N;
-  __device__ __forceinline__ void dep(int k, T x, T y, T z) { dep3<T>(tr, N, k, x, y, z); }
+struct GlobalSink;
+template <>
+struct GlobalSink<float> {
+  float4* row;  // accumulator row of one antenna
+  __device__ __forceinline__ void dep(int k, float x, float y, float z) {
+    atomicAdd(row + k, make_float4(x, y, z, 0.0f));
+  }
   __device__ __forceinline__ void rec(int, ff, ff) {}
   __device__ __forceinline__ void rec(int, double, double) {}
 };
+template <>
+struct GlobalSink<double> {
+  Acc4D* row;
+  __device__ __forceinline__ void dep(int k, double x, double y, double z) {
+    atomicAdd(&row[k].x, x);
+    atomicAdd(&row[k].y, y);
+    atomicAdd(&row[k].z, z);
+  }
+  __device__ __forceinline__ void rec(int, ff, ff) {}
+  __device__ __forceinline__ void rec(int, double, double) {}
+};
+
 struct ArrivalSink {
   int32_t* branch;
   int32_t* bin;
@@ -111,14 +160,16 @@ struct ArrivalSink {
 // forward
 // ---------------------------------------------------------------------------
 // Stream derived-track tiles [t_begin, t_end) through the two-slot TMA ring and
-// evaluate every (track, antenna) pair of the n_here antennas in ant_s into the
-// shared traces.  `it` counts the tiles this CTA has consumed so far (it sets
-// the slot and the mbarrier phase) and is advanced.  Returns false if a bounded
-// wait gave up; the CTA then has no copy in flight and must stop.
+// evaluate every (track, antenna) pair of the n_here antennas in ant_s, adding
+// deposits into the accumulator rows starting at acc_row0 (the row of ant_s[0]).
+// `it` counts the tiles this CTA has consumed so far (it sets the slot and the
+// mbarrier phase) and is advanced.  Returns false if a bounded wait gave up; the
+// CTA then has no copy in flight and must stop.
 template <class Ops>
 __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* bar, const AntRec* ant_s,
-                             typename Ops::acc_t* trace, int n_here, const unsigned char* src, int64_t t_begin,
-                             int64_t t_end, int64_t& it, const MedParams& M) {
+                             typename AccOf<typename Ops::acc_t>::type* acc_row0, int n_here,
+                             const unsigned char* src, int64_t t_begin, int64_t t_end, int64_t& it,
+                             const MedParams& M) {
   using acc_t = typename Ops::acc_t;
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
@@ -139,7 +190,7 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
     if (ok) {
       for (int p = tid; p < n_pairs; p += nthr) {
         const int ant = p / kTileT;
-        SmemSink<acc_t> sink{trace + (size_t)ant * 3 * N, N};
+        GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * N};
         Ops::fwd(smem + st * L.stage_bytes, p % kTileT, ant_s[ant], M, sink);
       }
     }
@@ -158,49 +209,24 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
   return true;
 }
 
-// add a CTA's shared traces into the global accumulator (skips empty groups)
-template <typename acc_t>
-__device__ void flush_traces(const acc_t* trace, acc_t* out, int n_here, int N) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int total = n_here * 3 * N;
-  if constexpr (std::is_same<acc_t, float>::value) {
-    if ((N % 4) == 0) {
-      const float4* s4 = reinterpret_cast<const float4*>(trace);
-      float4* o4 = reinterpret_cast<float4*>(out);
-      for (int i = tid; i < total / 4; i += nthr) {
-        float4 v = s4[i];
-        if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) atomicAdd(o4 + i, v);
-      }
-      return;
-    }
-  }
-  for (int i = tid; i < total; i += nthr) {
-    acc_t v = trace[i];
-    if (v != acc_t(0)) atomicAdd(out + i, v);
-  }
-}
-
 template <class Ops>
 __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_forward(const FwdArgs a) {
   using acc_t = typename Ops::acc_t;
+  using acc4 = typename AccOf<acc_t>::type;
   extern __shared__ __align__(128) unsigned char smem[];
-  const MedParams& M = a.M;
-  const int N = M.n_bins;
-  const FwdLayout L = fwd_layout(Ops::kPrec, a.a_tile, N);
+  const FwdLayout L = fwd_layout(Ops::kPrec, a.a_tile);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar_off);
   AntRec* ant_s = reinterpret_cast<AntRec*>(smem + L.ant_off);
-  acc_t* trace = reinterpret_cast<acc_t*>(smem + L.trace_off);
-
-  const int ant0 = blockIdx.x * a.a_tile;
+  int ant_tile;
+  int64_t range;
+  a.g.decode(blockIdx.x, ant_tile, range);
+  const int ant0 = ant_tile * a.a_tile;
   const int n_here = min(a.a_tile, a.n_ant - ant0);
-  const int64_t t_begin = (int64_t)blockIdx.y * a.tiles_per_range;
-  const int64_t t_end = min(t_begin + a.tiles_per_range, a.n_tiles);
+  const int64_t t_begin = range * a.g.tiles_per_range;
+  const int64_t t_end = min(t_begin + a.g.tiles_per_range, a.n_tiles);
   if (t_begin >= t_end || n_here <= 0) return;  // uniform over the CTA
-
   const int tid = threadIdx.x;
-  const int nthr = blockDim.x;
-  for (int i = tid; i < n_here * 3 * N; i += nthr) trace[i] = acc_t(0);
-  for (int i = tid; i < n_here; i += nthr) ant_s[i] = a.ants[ant0 + i];
+  for (int i = tid; i < n_here; i += blockDim.x) ant_s[i] = a.ants[ant0 + i];
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -208,22 +234,11 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_forward(const FwdArgs a) 
   }
   __syncthreads();
   int64_t it = 0;
-  if (!stream_range<Ops>(smem, L, bar, ant_s, trace, n_here, static_cast<const unsigned char*>(a.tiles), t_begin,
-                         t_end, it, M)) {
+  acc4* row0 = static_cast<acc4*>(a.acc) + (size_t)ant0 * a.M.n_bins;
+  if (!stream_range<Ops>(smem, L, bar, ant_s, row0, n_here, static_cast<const unsigned char*>(a.tiles), t_begin,
+                         t_end, it, a.M)) {
     if (tid == 0) atomicExch(a.err, kErrWaitTimeout);
-    return;
   }
-  __syncthreads();
-  flush_traces<acc_t>(trace, static_cast<acc_t*>(a.out) + (size_t)ant0 * 3 * N, n_here, N);
-}
-
-template <class Ops>
-cudaError_t launch_forward_ops(const FwdArgs& a, dim3 grid, int threads, size_t smem, cudaStream_t st) {
-  auto k = k_forward<Ops>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k<<<grid, threads, smem, st>>>(a);
-  return cudaGetLastError();
 }
 
 inline int forward_threads(int a_tile) {
@@ -231,15 +246,32 @@ inline int forward_threads(int a_tile) {
   return t < kFwdMaxThreads ? t : kFwdMaxThreads;
 }
 
-inline void forward_grid(FwdArgs& a, const FwdShape& shape, int sm_count, dim3& grid) {
-  const int ant_tiles = (a.n_ant + shape.a_tile - 1) / shape.a_tile;
+// grid of the forward launch: `waves` x SMs CTAs in total, antenna tiles grouped
+// so that one block's accumulator rows take at most l2_budget bytes
+inline int64_t forward_grid(FwdArgs& a, const FwdShape& shape, int sm_count, size_t acc_elem_bytes) {
+  FwdGrid& g = a.g;
+  g.ant_tiles = (a.n_ant + shape.a_tile - 1) / shape.a_tile;
+  const size_t l2_budget = (size_t)48 << 20;
+  const size_t tile_bytes = (size_t)shape.a_tile * a.M.n_bins * acc_elem_bytes;
+  int tpb = (int)(l2_budget / (tile_bytes > 0 ? tile_bytes : 1));
+  g.tiles_per_block = tpb < 1 ? 1 : (tpb > g.ant_tiles ? g.ant_tiles : tpb);
   int64_t target = (int64_t)shape.waves * sm_count;
-  int64_t ranges = (target + ant_tiles - 1) / ant_tiles;
+  int64_t ranges = (target + g.ant_tiles - 1) / g.ant_tiles;
   if (ranges < 1) ranges = 1;
   if (ranges > a.n_tiles) ranges = a.n_tiles;
-  a.tiles_per_range = (a.n_tiles + ranges - 1) / ranges;
-  ranges = (a.n_tiles + a.tiles_per_range - 1) / a.tiles_per_range;
-  grid = dim3((unsigned)ant_tiles, (unsigned)ranges);
+  g.tiles_per_range = (a.n_tiles + ranges - 1) / ranges;
+  g.ranges = (a.n_tiles + g.tiles_per_range - 1) / g.tiles_per_range;
+  return (int64_t)g.ant_tiles * g.ranges;
+}
+
+template <class Ops>
+cudaError_t launch_forward_ops(const FwdArgs& a, int64_t ctas, int threads, cudaStream_t st) {
+  const size_t smem = fwd_layout(Ops::kPrec, a.a_tile).total;
+  auto k = k_forward<Ops>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)ctas, threads, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -6,15 +6,13 @@
 namespace c8r {
 
 cudaError_t launch_forward_f64(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants, int n_ant,
-                               const MedParams& M, void* traces, const FwdShape& shape, int sm_count, int* err,
+                               const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
                                cudaStream_t st) {
-  FwdArgs a{tiles, n_tiles, 0, ants, n_ant, shape.a_tile, traces, err, M};
-  dim3 grid;
-  forward_grid(a, shape, sm_count, grid);
+  FwdArgs a{tiles, n_tiles, ants, n_ant, shape.a_tile, acc, err, FwdGrid{}, M};
+  const int64_t ctas = forward_grid(a, shape, sm_count, sizeof(Acc4D));
   const int threads = forward_threads(shape.a_tile);
-  const size_t smem = fwd_layout(C8R_FP64, shape.a_tile, M.n_bins).total;
-  if (formalism == C8R_ENDPOINT) return launch_forward_ops<OpsF64<C8R_ENDPOINT>>(a, grid, threads, smem, st);
-  return launch_forward_ops<OpsF64<C8R_ZHS>>(a, grid, threads, smem, st);
+  if (formalism == C8R_ENDPOINT) return launch_forward_ops<OpsF64<C8R_ENDPOINT>>(a, ctas, threads, st);
+  return launch_forward_ops<OpsF64<C8R_ZHS>>(a, ctas, threads, st);
 }
 
 cudaError_t launch_arrivals_f64(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,

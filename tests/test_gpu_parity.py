@@ -91,9 +91,7 @@ def test_invariant_to_launch_shape(formalism, precision):
     tracks = synth.workload_tracks(w)
     base, _, _ = run(w, tracks, formalism, precision)
     tol = 1e-12 if precision == "fp64" else 2e-6
-    for shape in [(1, 1, 0), (3, 16, 0), (2, 2, 1000), (4, 0, 4096)]:
-        if precision == "fp64" and shape[0] > 2:  # two FP64 traces of 4096 bins fill shared memory
-            shape = (2,) + shape[1:]
+    for shape in [(1, 1, 0), (3, 16, 0), (2, 2, 1000), (4, 0, 4096), (32, 1, 0), (16, 64, 2048)]:
         other, _, _ = run(w, tracks, formalism, precision, shape)
         assert rel_l2(other, base) <= tol, shape
 
@@ -144,7 +142,7 @@ def test_edge_cases(precision):
     with pytest.raises(C8RError):
         c8r.c8r_set_antennas(p.ctx, w["ant_xyz"], w["t_start_ns"], 0, 0.2, 0, 1)
     with pytest.raises(C8RError):
-        c8r.c8r_set_antennas(p.ctx, w["ant_xyz"], w["t_start_ns"], 1 << 20, 0.2, 0, 1)  # trace too long
+        c8r.c8r_set_antennas(p.ctx, w["ant_xyz"], w["t_start_ns"], (1 << 24) + 1, 0.2, 0, 1)  # beyond 2^24 bins
     p.close()
     p2.close()
 
