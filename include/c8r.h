@@ -252,6 +252,37 @@ int c8r_batch_set_cancel(c8r_batch* b, int value);
  * run was cancelled or a kernel gave up a bounded wait (the status is cleared). */
 int c8r_batch_sync(c8r_batch* b, void* cuda_stream);
 
+/* ---- forward pass without device allocation ------------------------------------ */
+
+/* The paper has no counterpart to this entry point.  It is the mixed-precision
+ * forward pass (c8r_push_tracks of a C8R_MIXED context) for callers that cannot
+ * allocate device memory: code running inside another framework's allocator or
+ * memory pool, code that may only touch memory it was handed, or services that
+ * must not grow their device footprint after start-up.  It allocates nothing:
+ * its scratch (the derived-track tiles of one chunk of 65536 tracks, 6.6 MB; an
+ * antenna table of at most 1024 antennas, 96 KB; a status word) is a set of
+ * fixed-size __device__ arrays that every GPU which loads the library holds until
+ * the process exits.  Tracks are processed in chunks of 65536 through that
+ * scratch, so n is not limited.
+ *
+ * Arguments as c8r_set_medium / c8r_set_antennas / c8r_push_tracks: tracks are
+ * DEVICE arrays, pos_xyz [n_ant][3] (m) and t_start_ns [n_ant] are HOST arrays,
+ * out_traces is a DEVICE FP32 array [n_ant][3][n_bins] that the call ACCUMULATES
+ * into (zero it first for a fresh result).  Enqueued on cuda_stream on the
+ * current device.  Returns C8R_ETOOBIG if n_ant > 1024 or n_bins > 2^24,
+ * C8R_EINVAL for other invalid arguments, C8R_ECUDA if a CUDA call fails.
+ *
+ * The first call on a device looks up the device addresses of the scratch
+ * arrays (once per device, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the same scratch,
+ * which keeps the last call's contents (the status word is cleared at the start
+ * of each call): calls whose work overlaps on the GPU race, so issue them on one
+ * stream or synchronise between them.  The antenna table is copied from pageable
+ * host memory, which synchronises the stream before the copy. */
+int c8r_traces_noalloc(const c8r_tracks* tracks, int64_t n, int32_t n_ant, const double* pos_xyz,
+                       const double* t_start_ns, int32_t n_bins, double dt_ns, int formalism, int medium_kind,
+                       double n_or_N0, double scale_height_m, float* out_traces, void* cuda_stream);
+
 /* ---- device peaks microbenchmark ----------------------------------------------- */
 
 /* Measured issue rates on `device`, in operations per second: FP32 FMA, FP64 FMA,

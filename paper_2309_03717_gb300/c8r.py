@@ -99,6 +99,10 @@ _SIGNATURES = [
     ("c8r_batch_set_cancel", ctypes.c_int, [_P, ctypes.c_int]),
     ("c8r_batch_sync", ctypes.c_int, [_P, _P]),
     ("c8r_measure_peaks", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    ("c8r_traces_noalloc", ctypes.c_int, [ctypes.POINTER(c8r_tracks), ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_int32, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_double, _P, _P]),
 ]
 
 
