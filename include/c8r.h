@@ -140,13 +140,16 @@ int c8r_set_antennas(c8r_ctx* ctx, int32_t n_ant, const double* pos_xyz, const d
  * the track midpoint with linearised arrival times.  EINVAL unless 0 < eps < 1. */
 int c8r_set_cherenkov_threshold(c8r_ctx* ctx, double eps_C);
 
-/* Launch shape of the forward kernels: antennas per CTA (1..32; every staged
- * track tile is evaluated against all of them) and the target number of CTA
- * waves per launch, which sets how many track ranges each antenna tile is cut
- * into.  0 keeps the automatic choice (8 antennas, 4 waves).  The result does not depend on the
- * shape beyond the order of floating-point additions (§5: identical pulses for
- * any number of threads).  Also sets the tracks per internal chunk (0 = 2^24):
- * longer pushes are processed chunk by chunk through the same scratch. */
+/* Launch shape of the forward kernels: antennas per CTA (1..32; each thread
+ * holds one track of a staged tile and evaluates it against all of them) and
+ * the target number of waves per launch, a wave being every CTA the device
+ * holds at once; it sets how many track ranges each antenna tile is cut into.
+ * 0 keeps the automatic choice (16 antennas, 8 waves).  The result does not
+ * depend on the shape beyond the order of floating-point additions (§5:
+ * identical pulses for any number of threads).  Also sets the tracks per
+ * internal chunk (0 = 2^25): longer pushes are processed chunk by chunk
+ * through the same scratch.  EINVAL outside a_tile 0..32, waves 0..1024,
+ * chunk_tracks >= 0. */
 int c8r_set_launch_shape(c8r_ctx* ctx, int a_tile, int waves, int64_t chunk_tracks);
 
 /* ---- the hot path ----------------------------------------------------------- */

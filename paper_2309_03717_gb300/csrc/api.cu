@@ -70,7 +70,7 @@ void fill_antenna(AntRec& r, double x, double y, double z, double t_ref_ns, cons
   split(r.Ea, r.Eah, r.Eal);
 }
 
-constexpr int kDefaultATile = 8;
+constexpr int kDefaultATile = 16;
 constexpr int kMaxBins = 1 << 24;
 
 }  // namespace c8r
@@ -105,7 +105,7 @@ struct c8r_ctx {
   int* d_err = nullptr;
   int64_t pushed = 0;
   cudaStream_t last_stream = nullptr;
-  FwdShape shape{1, kTileT, 4};
+  FwdShape shape{1, 8};
   int user_a_tile = 0, user_waves = 0;
   // kernel timing (c8r_profile): event pairs of pair-kernel and ingest launches
   bool profiling = false;
@@ -320,8 +320,7 @@ int c8r_set_antennas(c8r_ctx* c, int32_t n_ant, const double* pos, const double*
   c->t_start.assign(t_start, t_start + n_ant);
   const int want = c->user_a_tile > 0 ? c->user_a_tile : kDefaultATile;
   c->shape.a_tile = want < n_ant ? want : n_ant;
-  c->shape.threads = forward_threads(c->shape.a_tile);
-  c->shape.waves = c->user_waves > 0 ? c->user_waves : 4;
+  c->shape.waves = c->user_waves > 0 ? c->user_waves : 8;
   c->trace_bytes = (size_t)n_ant * 3 * n_bins * (precision == C8R_FP64 ? 8 : 4);
   c->acc_bytes = (size_t)n_ant * n_bins * acc_elem_bytes(precision);
   cudaError_t e = cudaMalloc(&c->d_ants, sizeof(AntRec) * n_ant);
@@ -348,8 +347,7 @@ int c8r_set_launch_shape(c8r_ctx* c, int a_tile, int waves, int64_t chunk_tracks
   if (c->ants_set) {
     const int want = a_tile > 0 ? a_tile : kDefaultATile;
     c->shape.a_tile = want < c->n_ant ? want : c->n_ant;
-    c->shape.threads = forward_threads(c->shape.a_tile);
-    c->shape.waves = waves > 0 ? waves : 4;
+    c->shape.waves = waves > 0 ? waves : 8;
   }
   return C8R_OK;
 }

@@ -70,7 +70,7 @@ struct BatchMap {
 };
 
 template <class Ops>
-__global__ void __launch_bounds__(kFwdMaxThreads, 1) k_batch(const BatchArgs a) {
+__global__ void __launch_bounds__(kTileT, Ops::kMinBlocks) k_batch(const BatchArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const MedParams& M = a.M;
   const FwdLayout L = fwd_layout(Ops::kPrec, a.a_tile);
@@ -107,13 +107,18 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_batch(const BatchArgs a) 
 
 using BatchOps = OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>;
 
+// persistent grid: every CTA that fits on the device at once
 template <class Ops>
-cudaError_t launch_batch_ops(const BatchArgs& a, int grid, cudaStream_t st) {
+cudaError_t launch_batch_ops(const BatchArgs& a, int sm_count, cudaStream_t st) {
   const size_t smem = fwd_layout(C8R_MIXED, a.a_tile).total;
   auto k = k_batch<Ops>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<grid, forward_threads(a.a_tile), smem, st>>>(a);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTileT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  k<<<sm_count * per_sm, kTileT, smem, st>>>(a);
   return cudaGetLastError();
 }
 

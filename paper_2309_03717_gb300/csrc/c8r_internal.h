@@ -11,9 +11,8 @@ namespace c8r {
 
 // launch shape of the forward kernels
 struct FwdShape {
-  int a_tile;   // antennas per CTA (the track tile in shared memory is reused for each)
-  int threads;  // min(kTileT * a_tile, 512)
-  int waves;    // target number of CTA waves per launch
+  int a_tile;  // antennas per CTA: each thread holds one staged track and loops over them
+  int waves;   // target number of waves (all CTAs resident at once) per launch
 };
 
 // SoA track pointers of the caller, already offset to a chunk

@@ -182,16 +182,21 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
       bulk_g2s(smem + st * L.stage_bytes, src + (t_begin + s) * (int64_t)bytes, bytes, &bar[st]);
     }
   }
-  const int n_pairs = kTileT * n_here;  // warps never straddle antennas: blockDim is a multiple of kTileT
   for (int64_t t = t_begin; t < t_end; ++t, ++it) {
     const int st = (int)(it & 1);
     const uint32_t parity = (uint32_t)((it >> 1) & 1);
     const bool ok = mbar_wait_bounded(&bar[st], parity);
     if (ok) {
-      for (int p = tid; p < n_pairs; p += nthr) {
-        const int ant = p / kTileT;
-        GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * N};
-        Ops::fwd(smem + st * L.stage_bytes, p % kTileT, ant_s[ant], M, sink);
+      // one track per thread, held in registers, against every antenna of the tile
+      for (int l = tid; l < kTileT; l += nthr) {
+        typename Ops::Track tr;
+        Ops::load(smem + st * L.stage_bytes, l, M, tr);
+        if (!Ops::live(tr)) continue;
+#pragma unroll 1
+        for (int ant = 0; ant < n_here; ++ant) {
+          GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * N};
+          Ops::pair(tr, ant_s[ant], M, sink);
+        }
       }
     }
     if (__syncthreads_or(!ok)) {
@@ -210,7 +215,7 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
 }
 
 template <class Ops>
-__global__ void __launch_bounds__(kFwdMaxThreads, 1) k_forward(const FwdArgs a) {
+__global__ void __launch_bounds__(kTileT, Ops::kMinBlocks) k_forward(const FwdArgs a) {
   using acc_t = typename Ops::acc_t;
   using acc4 = typename AccOf<acc_t>::type;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -246,17 +251,30 @@ inline int forward_threads(int a_tile) {
   return t < kFwdMaxThreads ? t : kFwdMaxThreads;
 }
 
-// grid of the forward launch: `waves` x SMs CTAs in total, antenna tiles grouped
-// so that one block's accumulator rows take at most l2_budget bytes
-inline int64_t forward_grid(FwdArgs& a, const FwdShape& shape, int sm_count, size_t acc_elem_bytes) {
+// grid of the forward launch: about `waves` full waves of resident CTAs (a whole
+// number of them when the antenna tiles allow, so no wave runs part-empty);
+// antenna tiles grouped so that one block's accumulator rows take at most
+// l2_budget bytes
+inline int64_t forward_grid(FwdArgs& a, const FwdShape& shape, int resident, size_t acc_elem_bytes) {
   FwdGrid& g = a.g;
   g.ant_tiles = (a.n_ant + shape.a_tile - 1) / shape.a_tile;
   const size_t l2_budget = (size_t)48 << 20;
   const size_t tile_bytes = (size_t)shape.a_tile * a.M.n_bins * acc_elem_bytes;
   int tpb = (int)(l2_budget / (tile_bytes > 0 ? tile_bytes : 1));
   g.tiles_per_block = tpb < 1 ? 1 : (tpb > g.ant_tiles ? g.ant_tiles : tpb);
-  int64_t target = (int64_t)shape.waves * sm_count;
+  int64_t target = (int64_t)shape.waves * resident;
   int64_t ranges = (target + g.ant_tiles - 1) / g.ant_tiles;
+  {
+    // round the CTA count up to a whole number of waves: ranges x ant_tiles = k x resident
+    int64_t x = resident, y = g.ant_tiles;
+    while (y) {
+      const int64_t r = x % y;
+      x = y;
+      y = r;
+    }
+    const int64_t step = resident / x;  // ranges must be a multiple of this
+    if (step > 0 && step <= 4 * ranges) ranges = (ranges + step - 1) / step * step;
+  }
   if (ranges < 1) ranges = 1;
   if (ranges > a.n_tiles) ranges = a.n_tiles;
   g.tiles_per_range = (a.n_tiles + ranges - 1) / ranges;
@@ -265,13 +283,23 @@ inline int64_t forward_grid(FwdArgs& a, const FwdShape& shape, int sm_count, siz
 }
 
 template <class Ops>
-cudaError_t launch_forward_ops(const FwdArgs& a, int64_t ctas, int threads, cudaStream_t st) {
+cudaError_t launch_forward_ops(const FwdArgs& a, int64_t ctas, cudaStream_t st) {
   const size_t smem = fwd_layout(Ops::kPrec, a.a_tile).total;
   auto k = k_forward<Ops>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)ctas, threads, smem, st>>>(a);
+  k<<<(unsigned)ctas, kTileT, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+// resident CTAs of the forward kernel per SM
+template <class Ops>
+int forward_blocks_per_sm(int a_tile) {
+  int n = 0;
+  const size_t smem = fwd_layout(Ops::kPrec, a_tile).total;
+  cudaFuncSetAttribute(k_forward<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward<Ops>, kTileT, smem) != cudaSuccess) n = 1;
+  return n < 1 ? 1 : n;
 }
 
 // ---------------------------------------------------------------------------
@@ -326,10 +354,13 @@ __global__ void __launch_bounds__(256) k_backward(const BwdArgs a) {
     acc_t tg[11];
 #pragma unroll
     for (int k = 0; k < 11; ++k) tg[k] = acc_t(0);
+    typename Ops::Track tr;
+    Ops::load(T, l, a.M, tr);
+    const bool live = valid && Ops::live(tr);
     for (int ant = 0; ant < a.n_ant; ++ant) {
       const AntRec A = a.ants[ant];
       acc_t ga[3] = {0, 0, 0};
-      if (valid) Ops::adj(T, l, A, a.M, G + (size_t)ant * 3 * N, tg, ga, dn_acc);
+      if (live) Ops::adj(tr, A, a.M, G + (size_t)ant * 3 * N, tg, ga, dn_acc);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         acc_t v = warp_sum(ga[c]);

@@ -9,10 +9,14 @@ cudaError_t launch_forward_f64(int formalism, const void* tiles, int64_t n_tiles
                                const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
                                cudaStream_t st) {
   FwdArgs a{tiles, n_tiles, ants, n_ant, shape.a_tile, acc, err, FwdGrid{}, M};
-  const int64_t ctas = forward_grid(a, shape, sm_count, sizeof(Acc4D));
-  const int threads = forward_threads(shape.a_tile);
-  if (formalism == C8R_ENDPOINT) return launch_forward_ops<OpsF64<C8R_ENDPOINT>>(a, ctas, threads, st);
-  return launch_forward_ops<OpsF64<C8R_ZHS>>(a, ctas, threads, st);
+  if (formalism == C8R_ENDPOINT) {
+    using O = OpsF64<C8R_ENDPOINT>;
+    const int64_t ctas = forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile), sizeof(Acc4D));
+    return launch_forward_ops<O>(a, ctas, st);
+  }
+  using O = OpsF64<C8R_ZHS>;
+  const int64_t ctas = forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile), sizeof(Acc4D));
+  return launch_forward_ops<O>(a, ctas, st);
 }
 
 cudaError_t launch_arrivals_f64(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,

@@ -9,15 +9,15 @@ cudaError_t launch_forward_mixed(int formalism, const void* tiles, int64_t n_til
                                  const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
                                  cudaStream_t st) {
   FwdArgs a{tiles, n_tiles, ants, n_ant, shape.a_tile, acc, err, FwdGrid{}, M};
-  const int64_t ctas = forward_grid(a, shape, sm_count, sizeof(float4));
-  const int threads = forward_threads(shape.a_tile);
+  auto go = [&](auto ops) {
+    using O = decltype(ops);
+    const int64_t ctas = forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile), sizeof(float4));
+    return launch_forward_ops<O>(a, ctas, st);
+  };
   const bool ex = M.kind == C8R_EXPONENTIAL;
-  if (formalism == C8R_ENDPOINT) {
-    if (ex) return launch_forward_ops<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>>(a, ctas, threads, st);
-    return launch_forward_ops<OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>>(a, ctas, threads, st);
-  }
-  if (ex) return launch_forward_ops<OpsMixed<C8R_ZHS, C8R_EXPONENTIAL>>(a, ctas, threads, st);
-  return launch_forward_ops<OpsMixed<C8R_ZHS, C8R_UNIFORM>>(a, ctas, threads, st);
+  if (formalism == C8R_ENDPOINT)
+    return ex ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>{}) : go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>{});
+  return ex ? go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL>{}) : go(OpsMixed<C8R_ZHS, C8R_UNIFORM>{});
 }
 
 // accumulator [n_ant][n_bins] float4 -> traces [n_ant][3][n_bins] (added or stored)

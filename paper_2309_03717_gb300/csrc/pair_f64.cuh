@@ -62,11 +62,34 @@ __device__ __forceinline__ void endpoint_eval_f64(const double* T, int l, const 
   e.valid = true;
 }
 
+// a track of a staged tile: the FP64 path reads its fields where it needs them
+struct TrackD {
+  const double* T;
+  int l;
+  double q;
+};
+
 template <int FORM>
 struct OpsF64 {
   using acc_t = double;
+  using Track = TrackD;
   static constexpr int kPrec = C8R_FP64;
   static constexpr int kTileBytes = kTileBytesF64;
+  static constexpr int kMinBlocks = 4;
+
+  static __device__ __forceinline__ void load(const void* Tv, int l, const MedParams&, TrackD& t) {
+    t.T = static_cast<const double*>(Tv);
+    t.l = l;
+    t.q = t.T[fd::Q * kTileT + l];
+  }
+  static __device__ __forceinline__ bool live(const TrackD& t) { return t.q != 0.0; }
+  template <class Sink>
+  static __device__ __forceinline__ void pair(const TrackD& t, const AntRec& A, const MedParams& M, Sink& out) {
+    if constexpr (FORM == C8R_ENDPOINT)
+      endpoint(t.T, t.l, A, M, out);
+    else
+      zhs(t.T, t.l, A, M, out);
+  }
 
   template <class Sink>
   static __device__ __forceinline__ void endpoint(const double* T, int l, const AntRec& A, const MedParams& M,
@@ -145,10 +168,11 @@ struct OpsF64 {
       zhs(T, l, A, M, out);
   }
 
-  static __device__ __forceinline__ void adj(const void* Tv, int l, const AntRec& A, const MedParams& M,
+  static __device__ __forceinline__ void adj(const TrackD& tr, const AntRec& A, const MedParams& M,
                                              const double* G, double tg[11], double ga[3], double& dn) {
     static_assert(FORM == C8R_ENDPOINT, "adjoint is defined for the Endpoint formalism");
-    const double* T = static_cast<const double*>(Tv);
+    const double* T = tr.T;
+    const int l = tr.l;
     const double q = TF(fd::Q);
     if (q == 0.0) return;
     const int N = M.n_bins;

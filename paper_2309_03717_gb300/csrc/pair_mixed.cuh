@@ -4,8 +4,11 @@
 // arrival interval are float-float (about 48 significant bits), which keeps the
 // bin of every deposit identical to an FP64 evaluation except within ~1e-7 bin
 // of an edge.  The Doppler factor D = 1 - n beta.rhat is formed without the
-// cancellation of the direct form (see field_mixed), from 1 - n|beta| computed
+// cancellation of the direct form (see field_mixed), from 1 - |beta| computed
 // per track in FP64 by the ingest kernel.
+//
+// A thread loads one track of a staged tile into registers (TrackM) once and
+// then evaluates it against every antenna of the CTA's antenna tile.
 #pragma once
 
 #include "kernels.cuh"
@@ -15,56 +18,85 @@ namespace c8r {
 // track fields of lane l in a field-major tile
 #define TF(f) T[(f) * kTileT + l]
 
+// one track, held in registers while it is evaluated against the antennas
+struct TrackM {
+  float x0, y0, z0, x1, y1, z1;  // FP32-exact endpoints
+  float bx, by, bz, bmag;
+  float amp;                     // q K/dt (Endpoint) or q K_A (t1-t0)/dt (ZHS); 0 = dropped
+  float tau0h, tau0l, tau1h, tau1l, dtauh, dtaul;
+  float E0h, E0l, E1h, E1l, Emh, Eml;
+  float nm1_0, nm1_1, nm1_m;     // n - 1 at start, end, midpoint
+  float om0, om1, om_m;          // 1 - n|beta| at start, end, midpoint
+  // midpoint position and time, float-float
+  float mx, mxl, my, myl, mz, mzl, tmh, tml;
+};
+
+template <int FORM, int KIND>
+__device__ __forceinline__ void load_track_mixed(const float* T, int l, const MedParams& M, TrackM& t) {
+  t.amp = FORM == C8R_ENDPOINT ? TF(fm::AMPE) : (TF(fm::AMPE) == 0.0f ? 0.0f : TF(fm::AMPZ));
+  if (t.amp == 0.0f) return;  // filtered track or padding
+  t.x0 = TF(fm::X0); t.y0 = TF(fm::Y0); t.z0 = TF(fm::Z0);
+  t.x1 = TF(fm::X1); t.y1 = TF(fm::Y1); t.z1 = TF(fm::Z1);
+  t.bx = TF(fm::BX); t.by = TF(fm::BY); t.bz = TF(fm::BZ);
+  t.bmag = TF(fm::BMAG);
+  const float omb = TF(fm::OMB);
+  t.tau0h = TF(fm::TAU0H); t.tau0l = TF(fm::TAU0L);
+  t.tau1h = TF(fm::TAU1H); t.tau1l = TF(fm::TAU1L);
+  t.dtauh = TF(fm::DTAUH); t.dtaul = TF(fm::DTAUL);
+  // n - 1 is formed directly (N0 E, or the uniform n - 1 rounded from FP64): as
+  // (1 + x) - 1 in FP32 it would lose ~6e-8, comparable to D near Cherenkov
+  t.E0h = t.E1h = t.Emh = 1.0f;
+  t.E0l = t.E1l = t.Eml = 0.0f;
+  t.nm1_0 = t.nm1_1 = t.nm1_m = M.nm1f;
+  if (KIND == C8R_EXPONENTIAL) {
+    t.E0h = TF(fm::E0H); t.E0l = TF(fm::E0L);
+    t.E1h = TF(fm::E1H); t.E1l = TF(fm::E1L);
+    t.Emh = TF(fm::EMH); t.Eml = TF(fm::EML);
+    t.nm1_0 = __fmul_rn(M.N0f, t.E0h);
+    t.nm1_1 = __fmul_rn(M.N0f, t.E1h);
+    t.nm1_m = __fmul_rn(M.N0f, t.Emh);
+  }
+  // 1 - n|beta| = (1 - |beta|) - (n - 1)|beta|
+  t.om0 = __fsub_rn(omb, __fmul_rn(t.nm1_0, t.bmag));
+  t.om1 = __fsub_rn(omb, __fmul_rn(t.nm1_1, t.bmag));
+  t.om_m = __fsub_rn(omb, __fmul_rn(t.nm1_m, t.bmag));
+  // midpoint time (t0 + t1)/(2 dt), float-float
+  two_sum(t.tau0h, t.tau1h, t.tmh, t.tml);
+  t.tml = __fadd_rn(t.tml, __fadd_rn(t.tau0l, t.tau1l));
+  t.tmh *= 0.5f;
+  t.tml *= 0.5f;
+  if (FORM == C8R_ZHS) {
+    // midpoint position (x0 + x1)/2, exact in float-float
+    two_sum(t.x0, t.x1, t.mx, t.mxl);
+    two_sum(t.y0, t.y1, t.my, t.myl);
+    two_sum(t.z0, t.z1, t.mz, t.mzl);
+    t.mx *= 0.5f; t.mxl *= 0.5f; t.my *= 0.5f; t.myl *= 0.5f; t.mz *= 0.5f; t.mzl *= 0.5f;
+  }
+}
+
 // geometry shared by the forward and the adjoint Endpoint evaluation
 struct EndpointEvalM {
   GeoM g0, g1, gm;
   FieldM f0, f1, fm;
-  float n0, n1, nm;
-  float E0h, E1h, Emh;
   int branch;     // 0 two endpoints, 1 midpoint
   ff ua, ub;      // arrivals (start/end, or the two linearised midpoint arrivals)
   bool valid;
 };
 
 template <int KIND>
-__device__ __forceinline__ void endpoint_eval_mixed(const float* T, int l, const AntRec& A, const MedParams& M,
+__device__ __forceinline__ void endpoint_eval_mixed(const TrackM& t, const AntRec& A, const MedParams& M,
                                                     EndpointEvalM& e) {
   e.valid = false;
-  const float bx = TF(fm::BX), by = TF(fm::BY), bz = TF(fm::BZ);
-  const float bmag = TF(fm::BMAG), omb = TF(fm::OMB);
-  e.E0h = e.E1h = e.Emh = 1.0f;
-  // n - 1 is formed directly (N0 E, or the uniform n - 1 rounded from FP64): as
-  // (1 + x) - 1 in FP32 it would lose ~6e-8, comparable to D near Cherenkov
-  float nm1_0 = M.nm1f, nm1_1 = M.nm1f;
-  if (KIND == C8R_EXPONENTIAL) {
-    e.E0h = TF(fm::E0H);
-    e.E1h = TF(fm::E1H);
-    nm1_0 = __fmul_rn(M.N0f, e.E0h);
-    nm1_1 = __fmul_rn(M.N0f, e.E1h);
-  }
-  e.n0 = __fadd_rn(1.0f, nm1_0);
-  e.n1 = __fadd_rn(1.0f, nm1_1);
-  // 1 - n|beta| = (1 - |beta|) - (n - 1)|beta|
-  const float om0 = __fsub_rn(omb, __fmul_rn(nm1_0, bmag));
-  const float om1 = __fsub_rn(omb, __fmul_rn(nm1_1, bmag));
-  geo_lite(A, TF(fm::X0), TF(fm::Y0), TF(fm::Z0), 0.f, 0.f, 0.f, e.g0);
-  geo_lite(A, TF(fm::X1), TF(fm::Y1), TF(fm::Z1), 0.f, 0.f, 0.f, e.g1);
+  geo_lite(A, t.x0, t.y0, t.z0, 0.f, 0.f, 0.f, e.g0);
+  geo_lite(A, t.x1, t.y1, t.z1, 0.f, 0.f, 0.f, e.g1);
   if (e.g0.R0 == 0.0f || e.g1.R0 == 0.0f) return;  // emission point on the antenna: outside the domain
-  field_mixed(e.g0, bx, by, bz, bmag, om0, e.n0, e.f0);
-  field_mixed(e.g1, bx, by, bz, bmag, om1, e.n1, e.f1);
+  field_mixed(e.g0, t.bx, t.by, t.bz, t.bmag, t.om0, __fadd_rn(1.0f, t.nm1_0), e.f0);
+  field_mixed(e.g1, t.bx, t.by, t.bz, t.bmag, t.om1, __fadd_rn(1.0f, t.nm1_1), e.f1);
   const bool mid = !(fminf(fabsf(e.f0.D), fabsf(e.f1.D)) >= M.eps_C);
   e.branch = mid ? 1 : 0;
-  float Eml = 0.0f;
   if (mid) {
     // near-Cherenkov: midpoint geometry, arrivals t_m -/+ D_m dt_e/2
-    float nm1_m = M.nm1f;
-    if (KIND == C8R_EXPONENTIAL) {
-      e.Emh = TF(fm::EMH);
-      Eml = TF(fm::EML);
-      nm1_m = __fmul_rn(M.N0f, e.Emh);
-    }
-    e.nm = __fadd_rn(1.0f, nm1_m);
-    midpoint_from_endpoints(e.g0, e.g1, e.f0, e.f1, bmag, __fsub_rn(omb, __fmul_rn(nm1_m, bmag)), e.nm, e.gm, e.fm);
+    midpoint_from_endpoints(e.g0, e.g1, e.f0, e.f1, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), e.gm, e.fm);
     if (e.gm.R0 == 0.0f) return;
   }
   // arrival times: both endpoints, or the midpoint alone (one code path for both
@@ -73,20 +105,10 @@ __device__ __forceinline__ void endpoint_eval_mixed(const float* T, int l, const
 #pragma unroll 1
   for (int j = 0; j < (mid ? 1 : 2); ++j) {
     GeoM g = (j == 0) ? (mid ? e.gm : e.g0) : e.g1;
-    float th, tl, Eh, El;
-    if (mid) {
-      two_sum(TF(fm::TAU0H), TF(fm::TAU1H), th, tl);
-      tl = __fadd_rn(tl, __fadd_rn(TF(fm::TAU0L), TF(fm::TAU1L)));
-      th *= 0.5f;
-      tl *= 0.5f;
-      Eh = e.Emh;
-      El = Eml;
-    } else {
-      th = j == 0 ? TF(fm::TAU0H) : TF(fm::TAU1H);
-      tl = j == 0 ? TF(fm::TAU0L) : TF(fm::TAU1L);
-      Eh = j == 0 ? e.E0h : e.E1h;
-      El = KIND == C8R_EXPONENTIAL ? (j == 0 ? TF(fm::E0L) : TF(fm::E1L)) : 0.0f;
-    }
+    const float th = mid ? t.tmh : (j == 0 ? t.tau0h : t.tau1h);
+    const float tl = mid ? t.tml : (j == 0 ? t.tau0l : t.tau1l);
+    const float Eh = mid ? t.Emh : (j == 0 ? t.E0h : t.E1h);
+    const float El = mid ? t.Eml : (j == 0 ? t.E0l : t.E1l);
     geo_refine(g);
     const ff u = arrival_mixed(M, A, g, th, tl, Eh, El);
     if (j == 0)
@@ -99,15 +121,14 @@ __device__ __forceinline__ void endpoint_eval_mixed(const float* T, int l, const
     e.ub = u1;
   } else {
     float hh, hl;  // D_m (t1 - t0)/(2 dt)
-    two_prod(e.fm.D, TF(fm::DTAUH), hh, hl);
-    hl = __fmaf_rn(e.fm.D, TF(fm::DTAUL), hl);
+    two_prod(e.fm.D, t.dtauh, hh, hl);
+    hl = __fmaf_rn(e.fm.D, t.dtaul, hl);
     hh *= 0.5f;
     hl *= 0.5f;
-    const ff um = u0;
-    two_sum(um.h, -hh, e.ua.h, e.ua.l);
-    e.ua.l = __fadd_rn(e.ua.l, __fsub_rn(um.l, hl));
-    two_sum(um.h, hh, e.ub.h, e.ub.l);
-    e.ub.l = __fadd_rn(e.ub.l, __fadd_rn(um.l, hl));
+    two_sum(u0.h, -hh, e.ua.h, e.ua.l);
+    e.ua.l = __fadd_rn(e.ua.l, __fsub_rn(u0.l, hl));
+    two_sum(u0.h, hh, e.ub.h, e.ub.l);
+    e.ub.l = __fadd_rn(e.ub.l, __fadd_rn(u0.l, hl));
   }
   e.valid = true;
 }
@@ -115,32 +136,38 @@ __device__ __forceinline__ void endpoint_eval_mixed(const float* T, int l, const
 template <int FORM, int KIND>
 struct OpsMixed {
   using acc_t = float;
+  using Track = TrackM;
   static constexpr int kPrec = C8R_MIXED;
   static constexpr int kTileBytes = kTileBytesMixed;
+  // CTAs of 128 threads per SM the register budget is set for
+  static constexpr int kMinBlocks = FORM == C8R_ENDPOINT ? 6 : 8;
+
+  static __device__ __forceinline__ void load(const void* Tv, int l, const MedParams& M, TrackM& t) {
+    load_track_mixed<FORM, KIND>(static_cast<const float*>(Tv), l, M, t);
+  }
+  static __device__ __forceinline__ bool live(const TrackM& t) { return t.amp != 0.0f; }
 
   // -------------------------------------------------------------------------
   // Endpoint (§1; James et al.): +amp V/(D R) at the start's arrival bin and
   // -amp V/(D R) at the end's, amp = q K / dt; midpoint form near Cherenkov.
   // -------------------------------------------------------------------------
   template <class Sink>
-  static __device__ __forceinline__ void endpoint(const float* T, int l, const AntRec& A, const MedParams& M,
-                                                  Sink& out) {
-    const float amp = TF(fm::AMPE);
-    if (amp == 0.0f) return;  // filtered track or padding
+  static __device__ __forceinline__ void endpoint(const TrackM& t, const AntRec& A, const MedParams& M, Sink& out) {
     const int N = M.n_bins;
     EndpointEvalM e;
-    endpoint_eval_mixed<KIND>(T, l, A, M, e);
+    endpoint_eval_mixed<KIND>(t, A, M, e);
     if (!e.valid) return;
     out.rec(e.branch, e.ua, e.ub);
     float fa, fb;
     const int ka = bin_raw(e.ua, N, fa);
     const int kb = bin_raw(e.ub, N, fb);
     const bool ina = ka >= 0 && ka < N, inb = kb >= 0 && kb < N;
+    const float amp = t.amp;
     if (e.branch == 0) {
       const float c0 = __fdividef(amp, e.f0.D * e.g0.R0) * (e.f0.invR * e.f0.invR);
       const float c1 = __fdividef(-amp, e.f1.D * e.g1.R0) * (e.f1.invR * e.f1.invR);
       if (ina && inb && ka == kb) {
-        // both deposits in one bin: add them in registers, one set of atomics
+        // both deposits in one bin: add them in registers, one reduction
         out.dep(ka, c0 * e.f0.V[0] + c1 * e.f1.V[0], c0 * e.f0.V[1] + c1 * e.f1.V[1],
                 c0 * e.f0.V[2] + c1 * e.f1.V[2]);
       } else {
@@ -162,36 +189,19 @@ struct OpsMixed {
   // bin), which needs no division by D and is exact for a one-bin interval.
   // -------------------------------------------------------------------------
   template <class Sink>
-  static __device__ __forceinline__ void zhs(const float* T, int l, const AntRec& A, const MedParams& M, Sink& out) {
-    if (TF(fm::AMPE) == 0.0f) return;
-    const float ampz = TF(fm::AMPZ);
+  static __device__ __forceinline__ void zhs(const TrackM& t, const AntRec& A, const MedParams& M, Sink& out) {
     const int N = M.n_bins;
-    const float bx = TF(fm::BX), by = TF(fm::BY), bz = TF(fm::BZ);
-    const float bmag = TF(fm::BMAG), omb = TF(fm::OMB);
-    float mx, mxl, my, myl, mz, mzl;
-    two_sum(TF(fm::X0), TF(fm::X1), mx, mxl);
-    two_sum(TF(fm::Y0), TF(fm::Y1), my, myl);
-    two_sum(TF(fm::Z0), TF(fm::Z1), mz, mzl);
-    mx *= 0.5f; mxl *= 0.5f; my *= 0.5f; myl *= 0.5f; mz *= 0.5f; mzl *= 0.5f;
     GeoM gm;
-    geo_mixed(A, mx, my, mz, mxl, myl, mzl, gm);
+    geo_lite(A, t.mx, t.my, t.mz, t.mxl, t.myl, t.mzl, gm);
     if (gm.R0 == 0.0f) return;
-    float Emh = 1.0f, Eml = 0.0f, nm1 = M.nm1f;
-    if (KIND == C8R_EXPONENTIAL) {
-      Emh = TF(fm::EMH);
-      Eml = TF(fm::EML);
-      nm1 = __fmul_rn(M.N0f, Emh);
-    }
     FieldM f;
-    field_mixed(gm, bx, by, bz, bmag, __fsub_rn(omb, __fmul_rn(nm1, bmag)), __fadd_rn(1.0f, nm1), f);
-    float th, tl;
-    two_sum(TF(fm::TAU0H), TF(fm::TAU1H), th, tl);
-    tl = __fadd_rn(tl, __fadd_rn(TF(fm::TAU0L), TF(fm::TAU1L)));
-    const ff um = arrival_mixed(M, A, gm, 0.5f * th, 0.5f * tl, Emh, Eml);
+    field_mixed(gm, t.bx, t.by, t.bz, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), f);
+    geo_refine(gm);
+    const ff um = arrival_mixed(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml);
     const float aD = fabsf(f.D);
     float hh, hl;  // |D| (t1 - t0)/(2 dt)
-    two_prod(aD, TF(fm::DTAUH), hh, hl);
-    hl = __fmaf_rn(aD, TF(fm::DTAUL), hl);
+    two_prod(aD, t.dtauh, hh, hl);
+    hl = __fmaf_rn(aD, t.dtaul, hl);
     hh *= 0.5f;
     hl *= 0.5f;
     ff ulo, uhi;
@@ -199,7 +209,7 @@ struct OpsMixed {
     ulo.l = __fadd_rn(ulo.l, __fsub_rn(um.l, hl));
     two_sum(um.h, hh, uhi.h, uhi.l);
     uhi.l = __fadd_rn(uhi.l, __fadd_rn(um.l, hl));
-    const float s = -ampz * (f.invR * f.invR) * f.invR;  // beta_perp = -V
+    const float s = -t.amp * (f.invR * f.invR) * f.invR;  // beta_perp = -V
     const float Mx = s * f.V[0], My = s * f.V[1], Mz = s * f.V[2];
     float flo, fhi;
     const int klo = bin_raw(ulo, N, flo);
@@ -222,47 +232,48 @@ struct OpsMixed {
   }
 
   template <class Sink>
-  static __device__ __forceinline__ void fwd(const void* Tv, int l, const AntRec& A, const MedParams& M, Sink& out) {
-    const float* T = static_cast<const float*>(Tv);
+  static __device__ __forceinline__ void pair(const TrackM& t, const AntRec& A, const MedParams& M, Sink& out) {
     if constexpr (FORM == C8R_ENDPOINT)
-      endpoint(T, l, A, M, out);
+      endpoint(t, A, M, out);
     else
-      zhs(T, l, A, M, out);
+      zhs(t, A, M, out);
+  }
+
+  // one pair from a staged tile (the arrival listing uses this)
+  template <class Sink>
+  static __device__ __forceinline__ void fwd(const void* Tv, int l, const AntRec& A, const MedParams& M, Sink& out) {
+    TrackM t;
+    load(Tv, l, M, t);
+    if (!live(t)) return;
+    pair(t, A, M, out);
   }
 
   // -------------------------------------------------------------------------
   // adjoint of `endpoint` with bins and branch held fixed
   // -------------------------------------------------------------------------
-  static __device__ __forceinline__ void deposit_grad(const GeoM& g, const FieldM& f, float bx, float by, float bz,
-                                                      float n, const float gv[3], float kappa, float dd[3],
-                                                      float db[3], float& dns) {
+  static __device__ __forceinline__ void deposit_grad(const GeoM& g, const FieldM& f, float n, const float gv[3],
+                                                      float kappa, float dd[3], float db[3], float& dns) {
     const float invR = f.invR;
     const float rh[3] = {g.s[0] * invR, g.s[1] * invR, g.s[2] * invR};
     const float inv2 = invR * invR;
     const float V[3] = {f.V[0] * inv2, f.V[1] * inv2, f.V[2] * inv2};
     const float c = f.bd * invR;
     deposit_adjoint<float>(rh, V, c, f.D, g.R0, n, gv, kappa, dd, db, dns);
-    (void)bx;
-    (void)by;
-    (void)bz;
   }
 
-  static __device__ __forceinline__ void adj(const void* Tv, int l, const AntRec& A, const MedParams& M,
-                                             const float* G, float tg[11], float ga[3], float& dn) {
+  static __device__ __forceinline__ void adj(const TrackM& t, const AntRec& A, const MedParams& M, const float* G,
+                                             float tg[11], float ga[3], float& dn) {
     static_assert(FORM == C8R_ENDPOINT, "adjoint is defined for the Endpoint formalism");
-    const float* T = static_cast<const float*>(Tv);
-    const float amp = TF(fm::AMPE);
-    if (amp == 0.0f) return;
     const int N = M.n_bins;
     EndpointEvalM e;
-    endpoint_eval_mixed<KIND>(T, l, A, M, e);
+    endpoint_eval_mixed<KIND>(t, A, M, e);
     if (!e.valid) return;
     float fa, fb;
     const int ka = bin_raw(e.ua, N, fa);
     const int kb = bin_raw(e.ub, N, fb);
     const bool ina = ka >= 0 && ka < N, inb = kb >= 0 && kb < N;
-    const float bx = TF(fm::BX), by = TF(fm::BY), bz = TF(fm::BZ);
     const float dNdz_fac = (KIND == C8R_EXPONENTIAL) ? -M.N0f * M.invH_h : 0.0f;
+    const float amp = t.amp;
     float dd[3], db[3], dns;
     if (e.branch == 0) {
       for (int j = 0; j < 2; ++j) {
@@ -270,9 +281,9 @@ struct OpsMixed {
         if (!in) continue;
         const int k = j == 0 ? ka : kb;
         const float gv[3] = {G[k], G[N + k], G[2 * N + k]};
-        deposit_grad(j == 0 ? e.g0 : e.g1, j == 0 ? e.f0 : e.f1, bx, by, bz, j == 0 ? e.n0 : e.n1, gv,
+        deposit_grad(j == 0 ? e.g0 : e.g1, j == 0 ? e.f0 : e.f1, 1.0f + (j == 0 ? t.nm1_0 : t.nm1_1), gv,
                      j == 0 ? amp : -amp, dd, db, dns);
-        const float E = j == 0 ? e.E0h : e.E1h;
+        const float E = j == 0 ? t.E0h : t.E1h;
         for (int c = 0; c < 3; ++c) {
           tg[3 * j + c] -= dd[c];
           ga[c] += dd[c];
@@ -286,16 +297,16 @@ struct OpsMixed {
     if (ka == kb) return;
     float gv[3];
     for (int c = 0; c < 3; ++c) gv[c] = (ina ? G[c * N + ka] : 0.0f) - (inb ? G[c * N + kb] : 0.0f);
-    deposit_grad(e.gm, e.fm, bx, by, bz, e.nm, gv, amp, dd, db, dns);
+    deposit_grad(e.gm, e.fm, 1.0f + t.nm1_m, gv, amp, dd, db, dns);
     for (int c = 0; c < 3; ++c) {
       tg[c] -= 0.5f * dd[c];
       tg[3 + c] -= 0.5f * dd[c];
       ga[c] += dd[c];
       tg[8 + c] += db[c];
     }
-    tg[2] += 0.5f * dns * dNdz_fac * e.Emh;
-    tg[5] += 0.5f * dns * dNdz_fac * e.Emh;
-    dn += dns * e.Emh;
+    tg[2] += 0.5f * dns * dNdz_fac * t.Emh;
+    tg[5] += 0.5f * dns * dNdz_fac * t.Emh;
+    dn += dns * t.Emh;
   }
 };
 
