@@ -73,7 +73,7 @@ template <class Ops>
 __global__ void __launch_bounds__(kTileT, Ops::kMinBlocks) k_batch(const BatchArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const MedParams& M = a.M;
-  const FwdLayout L = fwd_layout(Ops::kPrec, a.a_tile);
+  const FwdLayout L = fwd_layout(Ops::kPrec, a.a_tile, Ops::kDefers);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar_off);
   AntRec* ant_s = reinterpret_cast<AntRec*>(smem + L.ant_off);
   __shared__ int s_item;
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kTileT, Ops::kMinBlocks) k_batch(const BatchAr
     const WorkItem w = a.items[idx];
     for (int i = tid; i < w.n_here; i += nthr) ant_s[i] = a.ants[w.ant0 + i];
     __syncthreads();
-    if (!stream_range<Ops>(smem, L, bar, ant_s, a.acc + (size_t)w.ant0 * M.n_bins, w.n_here,
+    if (!stream_range<Ops>(smem, L, bar, ant_s, a.acc + (size_t)w.ant0 * M.n_bins * Ops::kAccRows, w.n_here,
                            static_cast<const unsigned char*>(a.tiles), w.t_begin, w.t_end, it, M)) {
       if (tid == 0) atomicExch(a.err, kErrWaitTimeout);
       return;
@@ -110,7 +110,7 @@ using BatchOps = OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>;
 // persistent grid: every CTA that fits on the device at once
 template <class Ops>
 cudaError_t launch_batch_ops(const BatchArgs& a, int sm_count, cudaStream_t st) {
-  const size_t smem = fwd_layout(C8R_MIXED, a.a_tile).total;
+  const size_t smem = fwd_layout(C8R_MIXED, a.a_tile, Ops::kDefers).total;
   auto k = k_batch<Ops>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -272,7 +272,8 @@ int enqueue(c8r_batch* b, const TrackPtrs& tp, float* out, int n_items_limit, cu
   BatchArgs a{b->d_tiles, b->d_items, std::min(b->n_items, n_items_limit), b->d_ants, b->d_acc, b->d_counter,
               b->d_cancel, b->d_err, b->choice.a_tile, b->M};
   e = launch_batch(a, b->formalism, b->sm_count, st);
-  if (e == cudaSuccess && out) e = launch_acc_to_traces(C8R_MIXED, b->d_acc, b->total_ant, b->M.n_bins, out, 1, st);
+  if (e == cudaSuccess && out) e = launch_acc_to_traces(C8R_MIXED, b->d_acc, b->total_ant, b->M.n_bins,
+                                                  acc_rows(C8R_MIXED, b->formalism), out, 1, st);
   if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   return C8R_OK;
 }
@@ -401,7 +402,7 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
     *out = b;
     return C8R_ECUDA;
   }
-  b->acc_bytes = (size_t)b->total_ant * b->M.n_bins * sizeof(float4);
+  b->acc_bytes = (size_t)b->total_ant * b->M.n_bins * sizeof(float4) * acc_rows(C8R_MIXED, b->formalism);
   if (cudaMalloc(&b->d_acc, b->acc_bytes) != cudaSuccess) {
     cudaGetLastError();
     b->d_acc = nullptr;

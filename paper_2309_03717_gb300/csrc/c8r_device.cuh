@@ -359,7 +359,7 @@ __device__ __forceinline__ void field_mixed(const GeoM& g, float bx, float by, f
   if (bd >= 0.0f) {
     const float w2 = __fmaf_rn(wx, wx, __fmaf_rn(wy, wy, __fmul_rn(wz, wz)));
     const float den = __fmul_rn(R, __fmaf_rn(bmag, R, bd));
-    f.D = __fadd_rn(om_nb, __fdiv_rn(__fmul_rn(n, w2), den));
+    f.D = __fadd_rn(om_nb, __fdividef(__fmul_rn(n, w2), den));
   } else {
     f.D = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(n, bd), invR));
   }
@@ -398,7 +398,7 @@ __device__ __forceinline__ void midpoint_from_endpoints(const GeoM& g0, const Ge
   if (bd >= 0.0f) {
     const float w2 = __fmaf_rn(wx, wx, __fmaf_rn(wy, wy, __fmul_rn(wz, wz)));
     const float den = __fmul_rn(gm.R0, __fmaf_rn(bmag, gm.R0, bd));
-    fmid.D = __fadd_rn(om_nb, __fdiv_rn(__fmul_rn(n, w2), den));
+    fmid.D = __fadd_rn(om_nb, __fdividef(__fmul_rn(n, w2), den));
   } else {
     fmid.D = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(n, bd), gm.y));
   }

@@ -24,9 +24,13 @@ struct TrackPtrs {
 size_t tile_bytes(int precision);
 // bytes of one accumulator element (one bin of one antenna: x, y, z, pad)
 inline size_t acc_elem_bytes(int precision) { return precision == C8R_FP64 ? 32 : 16; }
+// accumulator rows per antenna: the mixed ZHS path adds a row of box edges
+inline int acc_rows(int precision, int formalism) { return precision == C8R_MIXED && formalism == C8R_ZHS ? 2 : 1; }
 
-// accumulator [n_ant][n_bins] -> traces [n_ant][3][n_bins]; add != 0 adds into out (FP32 only)
-cudaError_t launch_acc_to_traces(int precision, const void* acc, int n_ant, int n_bins, void* out, int add,
+// accumulator [n_ant][rows][n_bins] -> traces [n_ant][3][n_bins]; with rows == 2
+// the second row (box edges) is integrated over the bins and added; add != 0
+// adds into out (FP32 only)
+cudaError_t launch_acc_to_traces(int precision, const void* acc, int n_ant, int n_bins, int rows, void* out, int add,
                                  cudaStream_t st);
 
 // ingest: filter + derived per-track quantities into tiles; counts kept tracks

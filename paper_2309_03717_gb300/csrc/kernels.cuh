@@ -1,16 +1,21 @@
 // kernels.cuh -- CTA-level loops shared by the FP64 and the mixed-precision
 // translation units.  Each TU supplies an `Ops` class with the per-pair
-// arithmetic (Ops::fwd, Ops::adj) and instantiates the kernels below.
+// arithmetic (load/live/pair_main/pair_deferred, adj) and instantiates the
+// kernels below.
 //
 // Forward (§2 flow, "looped over all antennas"): a CTA owns a tile of antennas
 // and a contiguous range of derived-track tiles.  It streams its range through a
 // two-slot ring of shared-memory tiles filled by TMA bulk copies (cp.async.bulk
-// + mbarrier, bounded waits); for every staged tile each thread evaluates
-// (track, antenna) pairs (warps never straddle antennas) and adds each deposit
-// into the L2-resident accumulator [antenna][bin][x, y, z, 0] with one native
-// vector reduction (atomicAdd on float4; three FP64 reductions in the FP64
-// path).  Shared-memory atomics are not used: FP32 shared atomic adds stall the
-// issuing warp, while the global reductions are fire-and-forget.
+// + mbarrier, bounded waits).  For every staged tile each thread loads one
+// track into registers and evaluates it against every antenna of the tile;
+// pairs whose arithmetic takes a rare branch (Endpoint near the Cherenkov
+// angle) are queued in shared memory and evaluated together after the main
+// pass, so that both branches run in full warps.  Each deposit goes into the
+// L2-resident accumulator [antenna][bin][x, y, z, 0] with one native vector
+// reduction (atomicAdd on float4; three FP64 reductions in the FP64 path); a
+// constant run of bins (ZHS) is added as its two edges into a second row that
+// the fetch integrates.  Shared-memory float atomics are not used: they stall
+// the issuing warp, while the global reductions are fire-and-forget.
 #pragma once
 
 #include <type_traits>
@@ -22,17 +27,19 @@ namespace c8r {
 constexpr int kMaxATile = 32;
 constexpr int kFwdMaxThreads = 512;
 
-// shared memory of a forward CTA: two staged track tiles, two mbarriers and the
-// antenna records of the tile
+// dynamic shared memory of the forward kernels: two staged track tiles, their
+// mbarriers, the antenna tile and (defer) the queue of set-aside pairs, one
+// 16-bit entry per (track, antenna) pair of a tile
 struct FwdLayout {
-  size_t stage_bytes, bar_off, ant_off, total;
+  size_t stage_bytes, bar_off, ant_off, q_off, total;
 };
-__host__ __device__ inline FwdLayout fwd_layout(int precision, int a_tile) {
+__host__ __device__ inline FwdLayout fwd_layout(int precision, int a_tile, bool defer) {
   FwdLayout L;
   L.stage_bytes = precision == C8R_FP64 ? kTileBytesF64 : kTileBytesMixed;
   L.bar_off = 2 * L.stage_bytes;
   L.ant_off = L.bar_off + 128;
-  L.total = L.ant_off + (size_t)a_tile * sizeof(AntRec);
+  L.q_off = L.ant_off + (size_t)a_tile * sizeof(AntRec);
+  L.total = L.q_off + (defer ? (size_t)kTileT * a_tile * sizeof(uint16_t) : 0);
   return L;
 }
 
@@ -110,9 +117,24 @@ template <typename T>
 struct GlobalSink;
 template <>
 struct GlobalSink<float> {
-  float4* row;  // accumulator row of one antenna
+  // accumulator of one antenna: n bins, followed (formalisms that add boxes) by
+  // n bins of box edges, which the fetch integrates over the bins
+  float4* row;
+  int n;
   __device__ __forceinline__ void dep(int k, float x, float y, float z) {
     atomicAdd(row + k, make_float4(x, y, z, 0.0f));
+  }
+  // the same (x, y, z) into every bin k0..k1 (0 <= k0 <= k1 < n): +v at the
+  // box's first bin and -v after its last in the edge row, so a box of any
+  // length costs at most two reductions
+  __device__ __forceinline__ void dep_box(int k0, int k1, float x, float y, float z) {
+    if (k1 - k0 < 2) {
+      dep(k0, x, y, z);
+      if (k1 > k0) dep(k1, x, y, z);
+      return;
+    }
+    atomicAdd(row + n + k0, make_float4(x, y, z, 0.0f));
+    if (k1 + 1 < n) atomicAdd(row + n + k1 + 1, make_float4(-x, -y, -z, 0.0f));
   }
   __device__ __forceinline__ void rec(int, ff, ff) {}
   __device__ __forceinline__ void rec(int, double, double) {}
@@ -120,6 +142,7 @@ struct GlobalSink<float> {
 template <>
 struct GlobalSink<double> {
   Acc4D* row;
+  int n;
   __device__ __forceinline__ void dep(int k, double x, double y, double z) {
     atomicAdd(&row[k].x, x);
     atomicAdd(&row[k].y, y);
@@ -137,6 +160,7 @@ struct ArrivalSink {
   int N;
   __device__ __forceinline__ void dep(int, float, float, float) {}
   __device__ __forceinline__ void dep(int, double, double, double) {}
+  __device__ __forceinline__ void dep_box(int, int, float, float, float) {}
   __device__ __forceinline__ void rec(int b, ff ua, ff ub) {
     float fa, fb;
     int ka = bin_raw(ua, N, fa), kb = bin_raw(ub, N, fb);
@@ -174,14 +198,22 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
   const int N = M.n_bins;
+  const size_t row_stride = (size_t)N * Ops::kAccRows;
   const uint32_t bytes = (uint32_t)L.stage_bytes;
+  // pairs the main pass sets aside (Ops::kDefers): entry = track lane | antenna << 7,
+  // one counter per staging slot
+  uint16_t* queue = reinterpret_cast<uint16_t*>(smem + L.q_off);
+  __shared__ int q_cnt[2];
   if (tid == 0) {
+    q_cnt[0] = 0;
+    q_cnt[1] = 0;
     for (int s = 0; s < 2 && t_begin + s < t_end; ++s) {
       const int st = (int)((it + s) & 1);
       mbar_expect_tx(&bar[st], bytes);
       bulk_g2s(smem + st * L.stage_bytes, src + (t_begin + s) * (int64_t)bytes, bytes, &bar[st]);
     }
   }
+  if (Ops::kDefers) __syncthreads();  // counters zeroed before the first entry is added
   for (int64_t t = t_begin; t < t_end; ++t, ++it) {
     const int st = (int)(it & 1);
     const uint32_t parity = (uint32_t)((it >> 1) & 1);
@@ -194,8 +226,9 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
         if (!Ops::live(tr)) continue;
 #pragma unroll 1
         for (int ant = 0; ant < n_here; ++ant) {
-          GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * N};
-          Ops::pair(tr, ant_s[ant], M, sink);
+          GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * row_stride, N};
+          if (Ops::pair_main(tr, ant_s[ant], M, sink) && Ops::kDefers)
+            queue[atomicAdd(&q_cnt[st], 1)] = (uint16_t)(l | (ant << 7));
         }
       }
     }
@@ -205,6 +238,21 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
         for (int64_t j = it; j < it + 2 && j - it + t < t_end; ++j) mbar_wait_bounded(&bar[j & 1], (uint32_t)((j >> 1) & 1));
       }
       return false;
+    }
+    if (Ops::kDefers) {
+      // the set-aside pairs, evaluated together so that their branch of the
+      // arithmetic runs in full warps; the staged tile is still in place
+      const int nq = q_cnt[st];
+      for (int i = tid; i < nq; i += nthr) {
+        const int e = queue[i];
+        typename Ops::Track tr;
+        Ops::load(smem + st * L.stage_bytes, e & (kTileT - 1), M, tr);
+        const int ant = e >> 7;
+        GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * row_stride, N};
+        Ops::pair_deferred(tr, ant_s[ant], M, sink);
+      }
+      __syncthreads();  // slot st is refilled below; its counter is next used two tiles on
+      if (tid == 0) q_cnt[st] = 0;
     }
     if (tid == 0 && t + 2 < t_end) {
       mbar_expect_tx(&bar[st], bytes);
@@ -219,7 +267,7 @@ __global__ void __launch_bounds__(kTileT, Ops::kMinBlocks) k_forward(const FwdAr
   using acc_t = typename Ops::acc_t;
   using acc4 = typename AccOf<acc_t>::type;
   extern __shared__ __align__(128) unsigned char smem[];
-  const FwdLayout L = fwd_layout(Ops::kPrec, a.a_tile);
+  const FwdLayout L = fwd_layout(Ops::kPrec, a.a_tile, Ops::kDefers);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar_off);
   AntRec* ant_s = reinterpret_cast<AntRec*>(smem + L.ant_off);
   int ant_tile;
@@ -239,7 +287,7 @@ __global__ void __launch_bounds__(kTileT, Ops::kMinBlocks) k_forward(const FwdAr
   }
   __syncthreads();
   int64_t it = 0;
-  acc4* row0 = static_cast<acc4*>(a.acc) + (size_t)ant0 * a.M.n_bins;
+  acc4* row0 = static_cast<acc4*>(a.acc) + (size_t)ant0 * a.M.n_bins * Ops::kAccRows;
   if (!stream_range<Ops>(smem, L, bar, ant_s, row0, n_here, static_cast<const unsigned char*>(a.tiles), t_begin,
                          t_end, it, a.M)) {
     if (tid == 0) atomicExch(a.err, kErrWaitTimeout);
@@ -284,7 +332,7 @@ inline int64_t forward_grid(FwdArgs& a, const FwdShape& shape, int resident, siz
 
 template <class Ops>
 cudaError_t launch_forward_ops(const FwdArgs& a, int64_t ctas, cudaStream_t st) {
-  const size_t smem = fwd_layout(Ops::kPrec, a.a_tile).total;
+  const size_t smem = fwd_layout(Ops::kPrec, a.a_tile, Ops::kDefers).total;
   auto k = k_forward<Ops>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -296,7 +344,7 @@ cudaError_t launch_forward_ops(const FwdArgs& a, int64_t ctas, cudaStream_t st) 
 template <class Ops>
 int forward_blocks_per_sm(int a_tile) {
   int n = 0;
-  const size_t smem = fwd_layout(Ops::kPrec, a_tile).total;
+  const size_t smem = fwd_layout(Ops::kPrec, a_tile, Ops::kDefers).total;
   cudaFuncSetAttribute(k_forward<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward<Ops>, kTileT, smem) != cudaSuccess) n = 1;
   return n < 1 ? 1 : n;

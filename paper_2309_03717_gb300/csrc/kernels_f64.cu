@@ -11,11 +11,13 @@ cudaError_t launch_forward_f64(int formalism, const void* tiles, int64_t n_tiles
   FwdArgs a{tiles, n_tiles, ants, n_ant, shape.a_tile, acc, err, FwdGrid{}, M};
   if (formalism == C8R_ENDPOINT) {
     using O = OpsF64<C8R_ENDPOINT>;
-    const int64_t ctas = forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile), sizeof(Acc4D));
+    const int64_t ctas =
+        forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile), sizeof(Acc4D) * O::kAccRows);
     return launch_forward_ops<O>(a, ctas, st);
   }
   using O = OpsF64<C8R_ZHS>;
-  const int64_t ctas = forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile), sizeof(Acc4D));
+  const int64_t ctas =
+      forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile), sizeof(Acc4D) * O::kAccRows);
   return launch_forward_ops<O>(a, ctas, st);
 }
 

@@ -11,7 +11,8 @@ cudaError_t launch_forward_mixed(int formalism, const void* tiles, int64_t n_til
   FwdArgs a{tiles, n_tiles, ants, n_ant, shape.a_tile, acc, err, FwdGrid{}, M};
   auto go = [&](auto ops) {
     using O = decltype(ops);
-    const int64_t ctas = forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile), sizeof(float4));
+    const int64_t ctas = forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile),
+                                      sizeof(float4) * O::kAccRows);
     return launch_forward_ops<O>(a, ctas, st);
   };
   const bool ex = M.kind == C8R_EXPONENTIAL;
@@ -39,6 +40,62 @@ __global__ void k_acc_to_traces_f32(const float4* acc, int64_t n_ant_bins, int n
   }
 }
 
+// accumulator with a row of box edges [n_ant][2][n_bins] float4 -> traces:
+// out[k] = direct[k] + sum_{j <= k} edge[j].  One CTA per antenna walks the
+// bins in chunks of its size: an inclusive scan of the chunk (FP64, warp
+// shuffles, then the warp totals) plus the carry of the chunks before.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_acc_scan_to_traces(const float4* acc, int n_bins, float* out,
+                                                                      int add) {
+  __shared__ double warp_tot[3][kScanThreads / 32];
+  const int a = blockIdx.x;
+  const float4* direct = acc + (size_t)a * 2 * n_bins;
+  const float4* edge = direct + n_bins;
+  float* o = out + (size_t)a * 3 * n_bins;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double carry[3] = {0.0, 0.0, 0.0};
+  for (int base = 0; base < n_bins; base += blockDim.x) {
+    const int k = base + threadIdx.x;
+    float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < n_bins) e = edge[k];
+    double v[3] = {e.x, e.y, e.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, v[c], d);
+        if (lane >= d) v[c] += u;
+      }
+      if (lane == 31) warp_tot[c][wid] = v[c];
+    }
+    __syncthreads();
+    double tot[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      for (int w = 0; w < nw; ++w) {
+        const double t = warp_tot[c][w];
+        if (w < wid) v[c] += t;
+        tot[c] += t;
+      }
+    }
+    if (k < n_bins) {
+      const float4 d = direct[k];
+      const float r[3] = {(float)((double)d.x + carry[0] + v[0]), (float)((double)d.y + carry[1] + v[1]),
+                          (float)((double)d.z + carry[2] + v[2])};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (add)
+          o[(size_t)c * n_bins + k] += r[c];
+        else
+          o[(size_t)c * n_bins + k] = r[c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) carry[c] += tot[c];
+    __syncthreads();  // warp_tot is rewritten by the next chunk
+  }
+}
+
 __global__ void k_acc_to_traces_f64(const Acc4D* acc, int64_t n_ant_bins, int n_bins, double* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_ant_bins) return;
@@ -51,10 +108,15 @@ __global__ void k_acc_to_traces_f64(const Acc4D* acc, int64_t n_ant_bins, int n_
   o[2 * n_bins] = v.z;
 }
 
-cudaError_t launch_acc_to_traces(int precision, const void* acc, int n_ant, int n_bins, void* out, int add,
+cudaError_t launch_acc_to_traces(int precision, const void* acc, int n_ant, int n_bins, int rows, void* out, int add,
                                  cudaStream_t st) {
   const int64_t n = (int64_t)n_ant * n_bins;
   if (n <= 0) return cudaSuccess;
+  if (rows == 2) {
+    k_acc_scan_to_traces<<<(unsigned)n_ant, kScanThreads, 0, st>>>(static_cast<const float4*>(acc), n_bins,
+                                                                     static_cast<float*>(out), add);
+    return cudaGetLastError();
+  }
   const unsigned blocks = (unsigned)((n + 255) / 256);
   if (precision == C8R_FP64)
     k_acc_to_traces_f64<<<blocks, 256, 0, st>>>(static_cast<const Acc4D*>(acc), n, n_bins, static_cast<double*>(out));

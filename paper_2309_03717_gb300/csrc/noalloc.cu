@@ -51,6 +51,9 @@ struct TraceSink {
     atomicAdd(tr + N + k, y);
     atomicAdd(tr + 2 * N + k, z);
   }
+  __device__ __forceinline__ void dep_box(int k0, int k1, float x, float y, float z) {
+    for (int k = k0; k <= k1; ++k) dep(k, x, y, z);
+  }
   __device__ __forceinline__ void rec(int, ff, ff) {}
   __device__ __forceinline__ void rec(int, double, double) {}
 };
@@ -72,7 +75,7 @@ struct NaArgs {
 template <class Ops>
 __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_forward_noalloc(const NaArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const FwdLayout L = fwd_layout(C8R_MIXED, a.a_tile);
+  const FwdLayout L = fwd_layout(C8R_MIXED, a.a_tile, false);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar_off);
   AntRec* ant_s = reinterpret_cast<AntRec*>(smem + L.ant_off);
   const int N = a.M.n_bins;
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_forward_noalloc(const NaA
 
 template <class Ops>
 cudaError_t launch_na(const NaArgs& a, dim3 grid, cudaStream_t st) {
-  const size_t smem = fwd_layout(C8R_MIXED, a.a_tile).total;
+  const size_t smem = fwd_layout(C8R_MIXED, a.a_tile, false).total;
   auto k = k_forward_noalloc<Ops>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -76,6 +76,8 @@ struct OpsF64 {
   static constexpr int kPrec = C8R_FP64;
   static constexpr int kTileBytes = kTileBytesF64;
   static constexpr int kMinBlocks = 4;
+  static constexpr bool kDefers = false;  // every pair is evaluated in the main pass
+  static constexpr int kAccRows = 1;      // no box deposits
 
   static __device__ __forceinline__ void load(const void* Tv, int l, const MedParams&, TrackD& t) {
     t.T = static_cast<const double*>(Tv);
@@ -90,6 +92,13 @@ struct OpsF64 {
     else
       zhs(t.T, t.l, A, M, out);
   }
+  template <class Sink>
+  static __device__ __forceinline__ bool pair_main(const TrackD& t, const AntRec& A, const MedParams& M, Sink& out) {
+    pair(t, A, M, out);
+    return false;
+  }
+  template <class Sink>
+  static __device__ __forceinline__ void pair_deferred(const TrackD&, const AntRec&, const MedParams&, Sink&) {}
 
   template <class Sink>
   static __device__ __forceinline__ void endpoint(const double* T, int l, const AntRec& A, const MedParams& M,

@@ -83,52 +83,68 @@ struct EndpointEvalM {
   bool valid;
 };
 
+// Endpoint evaluation in three steps, shared by the forward pass (which runs
+// the near-Cherenkov pairs apart from the others) and the adjoint.
+// (1) propagator and field at both endpoints; false when an emission point
+// sits on the antenna (outside the domain of the formula)
+__device__ __forceinline__ bool endpoint_fields(const TrackM& t, const AntRec& A, EndpointEvalM& e) {
+  geo_lite(A, t.x0, t.y0, t.z0, 0.f, 0.f, 0.f, e.g0);
+  geo_lite(A, t.x1, t.y1, t.z1, 0.f, 0.f, 0.f, e.g1);
+  if (e.g0.R0 == 0.0f || e.g1.R0 == 0.0f) return false;
+  field_mixed(e.g0, t.bx, t.by, t.bz, t.bmag, t.om0, __fadd_rn(1.0f, t.nm1_0), e.f0);
+  field_mixed(e.g1, t.bx, t.by, t.bz, t.bmag, t.om1, __fadd_rn(1.0f, t.nm1_1), e.f1);
+  return true;
+}
+
+// the near-Cherenkov test: min(|D_start|, |D_end|) < eps_C
+__device__ __forceinline__ bool endpoint_near_cherenkov(const EndpointEvalM& e, const MedParams& M) {
+  return !(fminf(fabsf(e.f0.D), fabsf(e.f1.D)) >= M.eps_C);
+}
+
+// (2a) arrival positions of the two endpoints
+template <int KIND>
+__device__ __forceinline__ void endpoint_arrivals(const TrackM& t, const AntRec& A, const MedParams& M,
+                                                  EndpointEvalM& e) {
+  GeoM g0 = e.g0, g1 = e.g1;
+  geo_refine(g0);
+  geo_refine(g1);
+  e.ua = arrival_mixed(M, A, g0, t.tau0h, t.tau0l, t.E0h, t.E0l);
+  e.ub = arrival_mixed(M, A, g1, t.tau1h, t.tau1l, t.E1h, t.E1l);
+  e.branch = 0;
+}
+
+// (2b) near-Cherenkov: midpoint geometry and the linearised arrivals
+// t_m -/+ D_m (t1 - t0)/2; false when the midpoint sits on the antenna
+template <int KIND>
+__device__ __forceinline__ bool endpoint_midpoint(const TrackM& t, const AntRec& A, const MedParams& M,
+                                                  EndpointEvalM& e) {
+  midpoint_from_endpoints(e.g0, e.g1, e.f0, e.f1, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), e.gm, e.fm);
+  if (e.gm.R0 == 0.0f) return false;
+  GeoM g = e.gm;
+  geo_refine(g);
+  const ff u0 = arrival_mixed(M, A, g, t.tmh, t.tml, t.Emh, t.Eml);
+  float hh, hl;  // D_m (t1 - t0)/(2 dt)
+  two_prod(e.fm.D, t.dtauh, hh, hl);
+  hl = __fmaf_rn(e.fm.D, t.dtaul, hl);
+  hh *= 0.5f;
+  hl *= 0.5f;
+  two_sum(u0.h, -hh, e.ua.h, e.ua.l);
+  e.ua.l = __fadd_rn(e.ua.l, __fsub_rn(u0.l, hl));
+  two_sum(u0.h, hh, e.ub.h, e.ub.l);
+  e.ub.l = __fadd_rn(e.ub.l, __fadd_rn(u0.l, hl));
+  e.branch = 1;
+  return true;
+}
+
 template <int KIND>
 __device__ __forceinline__ void endpoint_eval_mixed(const TrackM& t, const AntRec& A, const MedParams& M,
                                                     EndpointEvalM& e) {
   e.valid = false;
-  geo_lite(A, t.x0, t.y0, t.z0, 0.f, 0.f, 0.f, e.g0);
-  geo_lite(A, t.x1, t.y1, t.z1, 0.f, 0.f, 0.f, e.g1);
-  if (e.g0.R0 == 0.0f || e.g1.R0 == 0.0f) return;  // emission point on the antenna: outside the domain
-  field_mixed(e.g0, t.bx, t.by, t.bz, t.bmag, t.om0, __fadd_rn(1.0f, t.nm1_0), e.f0);
-  field_mixed(e.g1, t.bx, t.by, t.bz, t.bmag, t.om1, __fadd_rn(1.0f, t.nm1_1), e.f1);
-  const bool mid = !(fminf(fabsf(e.f0.D), fabsf(e.f1.D)) >= M.eps_C);
-  e.branch = mid ? 1 : 0;
-  if (mid) {
-    // near-Cherenkov: midpoint geometry, arrivals t_m -/+ D_m dt_e/2
-    midpoint_from_endpoints(e.g0, e.g1, e.f0, e.f1, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), e.gm, e.fm);
-    if (e.gm.R0 == 0.0f) return;
-  }
-  // arrival times: both endpoints, or the midpoint alone (one code path for both
-  // branches, so a warp mixing them does not run two copies of it)
-  ff u0 = {0.0f, 0.0f}, u1 = {0.0f, 0.0f};
-#pragma unroll 1
-  for (int j = 0; j < (mid ? 1 : 2); ++j) {
-    GeoM g = (j == 0) ? (mid ? e.gm : e.g0) : e.g1;
-    const float th = mid ? t.tmh : (j == 0 ? t.tau0h : t.tau1h);
-    const float tl = mid ? t.tml : (j == 0 ? t.tau0l : t.tau1l);
-    const float Eh = mid ? t.Emh : (j == 0 ? t.E0h : t.E1h);
-    const float El = mid ? t.Eml : (j == 0 ? t.E0l : t.E1l);
-    geo_refine(g);
-    const ff u = arrival_mixed(M, A, g, th, tl, Eh, El);
-    if (j == 0)
-      u0 = u;
-    else
-      u1 = u;
-  }
-  if (!mid) {
-    e.ua = u0;
-    e.ub = u1;
+  if (!endpoint_fields(t, A, e)) return;
+  if (endpoint_near_cherenkov(e, M)) {
+    if (!endpoint_midpoint<KIND>(t, A, M, e)) return;
   } else {
-    float hh, hl;  // D_m (t1 - t0)/(2 dt)
-    two_prod(e.fm.D, t.dtauh, hh, hl);
-    hl = __fmaf_rn(e.fm.D, t.dtaul, hl);
-    hh *= 0.5f;
-    hl *= 0.5f;
-    two_sum(u0.h, -hh, e.ua.h, e.ua.l);
-    e.ua.l = __fadd_rn(e.ua.l, __fsub_rn(u0.l, hl));
-    two_sum(u0.h, hh, e.ub.h, e.ub.l);
-    e.ub.l = __fadd_rn(e.ub.l, __fadd_rn(u0.l, hl));
+    endpoint_arrivals<KIND>(t, A, M, e);
   }
   e.valid = true;
 }
@@ -141,6 +157,11 @@ struct OpsMixed {
   static constexpr int kTileBytes = kTileBytesMixed;
   // CTAs of 128 threads per SM the register budget is set for
   static constexpr int kMinBlocks = FORM == C8R_ENDPOINT ? 6 : 8;
+  // Endpoint: the near-Cherenkov pairs (a minority, spread over most warps)
+  // are set aside by the main pass and evaluated together afterwards
+  static constexpr bool kDefers = FORM == C8R_ENDPOINT;
+  // ZHS: a second accumulator row holds the edges of box deposits
+  static constexpr int kAccRows = FORM == C8R_ZHS ? 2 : 1;
 
   static __device__ __forceinline__ void load(const void* Tv, int l, const MedParams& M, TrackM& t) {
     load_track_mixed<FORM, KIND>(static_cast<const float*>(Tv), l, M, t);
@@ -151,12 +172,12 @@ struct OpsMixed {
   // Endpoint (§1; James et al.): +amp V/(D R) at the start's arrival bin and
   // -amp V/(D R) at the end's, amp = q K / dt; midpoint form near Cherenkov.
   // -------------------------------------------------------------------------
+  // The deposits of an evaluated pair; the evaluation is split between
+  // pair_main and pair_deferred below.
   template <class Sink>
-  static __device__ __forceinline__ void endpoint(const TrackM& t, const AntRec& A, const MedParams& M, Sink& out) {
+  static __device__ __forceinline__ void endpoint_deposit(const TrackM& t, const EndpointEvalM& e,
+                                                          const MedParams& M, Sink& out) {
     const int N = M.n_bins;
-    EndpointEvalM e;
-    endpoint_eval_mixed<KIND>(t, A, M, e);
-    if (!e.valid) return;
     out.rec(e.branch, e.ua, e.ub);
     float fa, fb;
     const int ka = bin_raw(e.ua, N, fa);
@@ -220,23 +241,54 @@ struct OpsMixed {
       return;
     }
     const float invW = __fdividef(1.0f, 2.0f * hh);  // 1 / interval length in bins
-    const int kb = klo < 0 ? 0 : klo;
-    const int ke = khi > N - 1 ? N - 1 : khi;
-    for (int k = kb; k <= ke; ++k) {
-      float o = 1.0f;
-      if (k == klo) o = 1.0f - flo;
-      if (k == khi) o = fhi;
-      const float w = o * invW;
-      if (w > 0.0f) out.dep(k, Mx * w, My * w, Mz * w);
+    // partly covered first and last bins
+    if (klo >= 0 && klo < N) {
+      const float w = (1.0f - flo) * invW;
+      if (w > 0.0f) out.dep(klo, Mx * w, My * w, Mz * w);
+    }
+    if (khi >= 0 && khi < N) {
+      const float w = fhi * invW;
+      if (w > 0.0f) out.dep(khi, Mx * w, My * w, Mz * w);
+    }
+    // the whole bins in between (inside the window) all receive M / W
+    const int kb = klo + 1 < 0 ? 0 : klo + 1;
+    const int ke = khi - 1 > N - 1 ? N - 1 : khi - 1;
+    if (kb <= ke) out.dep_box(kb, ke, Mx * invW, My * invW, Mz * invW);
+  }
+
+  // main pass: every pair except (Endpoint) the near-Cherenkov ones, for which
+  // it deposits nothing and returns true
+  template <class Sink>
+  static __device__ __forceinline__ bool pair_main(const TrackM& t, const AntRec& A, const MedParams& M, Sink& out) {
+    if constexpr (FORM == C8R_ENDPOINT) {
+      EndpointEvalM e;
+      if (!endpoint_fields(t, A, e)) return false;
+      if (endpoint_near_cherenkov(e, M)) return true;
+      endpoint_arrivals<KIND>(t, A, M, e);
+      endpoint_deposit(t, e, M, out);
+      return false;
+    } else {
+      zhs(t, A, M, out);
+      return false;
     }
   }
 
+  // a pair set aside by the main pass (Endpoint near the Cherenkov angle)
+  template <class Sink>
+  static __device__ __forceinline__ void pair_deferred(const TrackM& t, const AntRec& A, const MedParams& M,
+                                                       Sink& out) {
+    if constexpr (FORM == C8R_ENDPOINT) {
+      EndpointEvalM e;
+      if (!endpoint_fields(t, A, e)) return;
+      if (!endpoint_midpoint<KIND>(t, A, M, e)) return;
+      endpoint_deposit(t, e, M, out);
+    }
+  }
+
+  // one pair, complete
   template <class Sink>
   static __device__ __forceinline__ void pair(const TrackM& t, const AntRec& A, const MedParams& M, Sink& out) {
-    if constexpr (FORM == C8R_ENDPOINT)
-      endpoint(t, A, M, out);
-    else
-      zhs(t, A, M, out);
+    if (pair_main(t, A, M, out)) pair_deferred(t, A, M, out);
   }
 
   // one pair from a staged tile (the arrival listing uses this)
