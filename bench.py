@@ -42,7 +42,11 @@ FP32_LANES_PER_SM = 128
 # formula (two endpoints: propagator, Doppler factor, arrival bin, field vector
 # and amplitude): 56 arithmetic + 6 special-function operations
 ALG_OPS_PER_ENDPOINT_PAIR = 62
-SHARED_ATOMICS_PER_ENDPOINT_PAIR = 6
+# DRAM bytes (read + write) per pair of the Endpoint forward kernel: one ncu
+# capture of a 4e6-track x 160-antenna launch (6.4e8 pairs) read 407.7 MB and
+# wrote 5.4 MB; the traffic is the staged track tiles, so it scales with the
+# pairs at a fixed antenna count.  Set to None when the kernel changes.
+DRAM_BYTES_PER_ENDPOINT_PAIR = 413.1e6 / 6.4e8
 
 
 def parse():
@@ -305,7 +309,10 @@ def main():
                             + prof_z["ingest_launches"]),
         "roofline": {"bound": "alu", "kernel": "k_forward<OpsMixed<Endpoint, exponential>>",
                      "achieved": achieved, "peak": peak_alu, "unit": "Gop/s (FP32 lane ops)",
-                     "frac": achieved / peak_alu, "traffic": None,
+                     "frac": achieved / peak_alu,
+                     "traffic": (DRAM_BYTES_PER_ENDPOINT_PAIR * pairs_per_launch
+                                 if DRAM_BYTES_PER_ENDPOINT_PAIR and A == 160 else None),
+                     "traffic_note": "DRAM bytes per launch: ncu capture of a 4e6-track launch, scaled by pairs",
                      "peak_source": f"152 SMs x 128 FP32 lanes x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
                                     f"({pk_src} max SM clock)",
                      "ops_per_pair": ALG_OPS_PER_ENDPOINT_PAIR, "kernel_ms": kernel_ms,

@@ -32,6 +32,9 @@ void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, d
   M.eps_C = (float)eps_C;
   const double kc = 1.0 / (kCns * dt_ns);
   split(kc, M.kc_h, M.kc_l);
+  split(1.0 / dt_ns, M.idt_h, M.idt_l);
+  M.ampE = (float)(kKendpoint / (dt_ns * 1e-9));
+  M.kzhs = (float)kKzhs;
   if (kind == C8R_UNIFORM) {
     M.n = n_or_N0;
     M.N0 = 0.0;

@@ -87,6 +87,9 @@ struct MedParams {
   float cN_h, cN_l;      // exponential: N0 H /(c dt)
   float invH_h, invH_l;  // 1/H
   float N0f, nf;         // N0 and n as floats
+  float idt_h, idt_l;    // 1/dt (per ns)
+  float ampE;            // K/dt of the Endpoint amplitude (per unit charge), FP64 rounded once
+  float kzhs;            // K_A of the ZHS amplitude
   float nm1f;            // uniform: n - 1 formed in FP64, then rounded (never (1 + x) - 1 in FP32)
   float eps_C;           // near-Cherenkov threshold
 };

@@ -32,7 +32,8 @@ __device__ __forceinline__ void load_track(const TrackPtrs& t, int64_t i, double
 }
 
 // track filter: q != 0, all fields finite, t1 > t0, |x1 - x0| > 0, 0 < |beta| < 1
-__device__ __forceinline__ bool track_kept(const double v[12]) {
+// (in FP64, as the definition reads); b = |beta| when kept
+__device__ __forceinline__ bool track_kept(const double v[12], double& b) {
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < 12; ++k) ok = ok && isfinite(v[k]);
@@ -41,8 +42,24 @@ __device__ __forceinline__ bool track_kept(const double v[12]) {
   if (!(v[7] > v[6])) return false;
   double lx = v[3] - v[0], ly = v[4] - v[1], lz = v[5] - v[2];
   if (!(lx * lx + ly * ly + lz * lz > 0.0)) return false;
-  double b = sqrt(v[8] * v[8] + v[9] * v[9] + v[10] * v[10]);
+  b = sqrt(v[8] * v[8] + v[9] * v[9] + v[10] * v[10]);
   return b > 0.0 && b < 1.0;
+}
+
+// float x float-float -> float-float, renormalised (relative error ~2^-47)
+__device__ __forceinline__ void mul_f_ff(float a, float bh, float bl, float& h, float& l) {
+  float p, e;
+  two_prod(a, bh, p, e);
+  e = __fmaf_rn(a, bl, e);
+  h = __fadd_rn(p, e);
+  l = __fsub_rn(e, __fsub_rn(h, p));
+}
+
+// exp(-z/H) of an endpoint given E = exp(-z_ref/H) of a nearby point, x = -(z - z_ref)/H:
+// E (1 + x + x^2/2 + ... + x^5/120), truncation below 2^-60 for |x| < 1e-3
+__device__ __forceinline__ double exp_near(double E, double x) {
+  const double p = 1.0 + x * (1.0 + x * (0.5 + x * (1.0 / 6.0 + x * (1.0 / 24.0 + x * (1.0 / 120.0)))));
+  return E * p;
 }
 
 __device__ __forceinline__ void split(double x, float& h, float& l) {
@@ -67,25 +84,46 @@ __global__ void __launch_bounds__(256) k_ingest_mixed(TrackPtrs t, Map map, int6
     if (src >= 0) {
       double v[12];
       load_track<Tin>(t, src, v, true);
-      keep = track_kept(v);
+      double b = 0.0;
+      keep = track_kept(v, b);
       if (keep) {
-        double b = sqrt(v[8] * v[8] + v[9] * v[9] + v[10] * v[10]);
-        double dt = M.dt_ns;
-        double dtau = (v[7] - v[6]) / dt;
-        out[fm::X0] = (float)v[0]; out[fm::Y0] = (float)v[1]; out[fm::Z0] = (float)v[2];
-        out[fm::X1] = (float)v[3]; out[fm::Y1] = (float)v[4]; out[fm::Z1] = (float)v[5];
-        out[fm::BX] = (float)v[8]; out[fm::BY] = (float)v[9]; out[fm::BZ] = (float)v[10];
-        out[fm::AMPE] = (float)(v[11] * kKendpoint / (dt * 1e-9));
-        out[fm::AMPZ] = (float)(v[11] * kKzhs * dtau);
+        // the inputs are FP32 values here: the per-track quantities are formed in
+        // float-float on the FP32 pipe, FP64 (slow on this part) only for |beta|,
+        // 1 - |beta| and exp(-z/H)
+        float f[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) f[k] = (float)v[k];
+        out[fm::X0] = f[0]; out[fm::Y0] = f[1]; out[fm::Z0] = f[2];
+        out[fm::X1] = f[3]; out[fm::Y1] = f[4]; out[fm::Z1] = f[5];
+        out[fm::BX] = f[8]; out[fm::BY] = f[9]; out[fm::BZ] = f[10];
+        // tau = t/dt, (t1 - t0)/dt = (exact difference) x 1/dt
+        mul_f_ff(f[6], M.idt_h, M.idt_l, out[fm::TAU0H], out[fm::TAU0L]);
+        mul_f_ff(f[7], M.idt_h, M.idt_l, out[fm::TAU1H], out[fm::TAU1L]);
+        float dh, dl;
+        two_sum(f[7], -f[6], dh, dl);
+        float ph, pl;
+        mul_f_ff(dh, M.idt_h, M.idt_l, ph, pl);
+        pl = __fmaf_rn(dl, M.idt_h, pl);
+        out[fm::DTAUH] = __fadd_rn(ph, pl);
+        out[fm::DTAUL] = __fsub_rn(pl, __fsub_rn(out[fm::DTAUH], ph));
+        out[fm::AMPE] = __fmul_rn(f[11], M.ampE);
+        out[fm::AMPZ] = __fmul_rn(__fmul_rn(f[11], M.kzhs), out[fm::DTAUH]);
         out[fm::BMAG] = (float)b;
         out[fm::OMB] = (float)(1.0 - b);
-        split(v[6] / dt, out[fm::TAU0H], out[fm::TAU0L]);
-        split(v[7] / dt, out[fm::TAU1H], out[fm::TAU1L]);
-        split(dtau, out[fm::DTAUH], out[fm::DTAUL]);
         if (M.kind == C8R_EXPONENTIAL) {
-          split(exp(-v[2] * M.invH), out[fm::E0H], out[fm::E0L]);
-          split(exp(-v[5] * M.invH), out[fm::E1H], out[fm::E1L]);
-          split(exp(-0.5 * (v[2] + v[5]) * M.invH), out[fm::EMH], out[fm::EML]);
+          const double E0 = exp(-v[2] * M.invH);
+          const double x = -(v[5] - v[2]) * M.invH;
+          double E1, Em;
+          if (fabs(x) < 1e-3) {
+            E1 = exp_near(E0, x);
+            Em = exp_near(E0, 0.5 * x);
+          } else {
+            E1 = exp(-v[5] * M.invH);
+            Em = exp(-0.5 * (v[2] + v[5]) * M.invH);
+          }
+          split(E0, out[fm::E0H], out[fm::E0L]);
+          split(E1, out[fm::E1H], out[fm::E1L]);
+          split(Em, out[fm::EMH], out[fm::EML]);
         } else {
           out[fm::E0H] = out[fm::E1H] = out[fm::EMH] = 1.0f;
         }
@@ -113,7 +151,8 @@ __global__ void __launch_bounds__(256) k_ingest_f64(TrackPtrs t, Map map, int64_
     if (src >= 0) {
       double v[12];
       load_track<Tin>(t, src, v, false);
-      keep = track_kept(v);
+      double b;
+      keep = track_kept(v, b);
       if (keep) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) out[fd::X0 + k] = v[k];
