@@ -377,6 +377,44 @@ __device__ __forceinline__ void field_mixed(const GeoM& g, float bx, float by, f
   f.w[2] = wz;
 }
 
+// D = 1 - n (beta . d)/R in float-float, for a refined geometry (R = R0 + R1)
+// and n - 1 given directly.  Its absolute error (~1e-10, set by n - 1 in FP32)
+// is what the arrival interval ends u_m -/+ |D| (t1 - t0)/(2 dt) need: the
+// half-width reaches ~10^2 bins, so D must be good to ~1e-9 absolute, which the
+// FP32 form of field_mixed (good to ~1e-7 relative) is not for |D| of order 1.
+__device__ __forceinline__ ff doppler_ff(const GeoM& g, float bx, float by, float bz, float nm1) {
+  // beta . d with d = s + e exact: exact products of the high parts, summed
+  // with TwoSum; the low parts and the rounding errors in FP32
+  float p0, q0, p1, q1, p2, q2;
+  two_prod(bx, g.s[0], p0, q0);
+  two_prod(by, g.s[1], p1, q1);
+  two_prod(bz, g.s[2], p2, q2);
+  float S1, E1, S2, E2;
+  two_sum(p0, p1, S1, E1);
+  two_sum(S1, p2, S2, E2);
+  const float be = __fmaf_rn(bx, g.e[0], __fmaf_rn(by, g.e[1], __fmul_rn(bz, g.e[2])));
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2, E1)), __fadd_rn(E2, be));
+  // q = (beta . d)/R: FP32 quotient, then one correction from the exact residual
+  const float qh = __fmul_rn(S2, g.y);
+  float ph, pl;
+  two_prod(qh, g.R0, ph, pl);
+  const float r = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(S2, ph), pl), lo), __fmul_rn(qh, g.R1));
+  const float ql = __fmul_rn(r, g.y);
+  // n q = q + (n - 1) q, then D = 1 - n q
+  float nh, nl;
+  two_sum(qh, __fmul_rn(nm1, qh), nh, nl);
+  nl = __fadd_rn(nl, ql);
+  float dh, dl;
+  two_sum(1.0f, -nh, dh, dl);
+  dl = __fsub_rn(dl, nl);
+  // renormalise, so that the sign of D is the sign of D.h (near D = 0 the high
+  // part alone can be 0 or of the other sign)
+  ff D;
+  D.h = __fadd_rn(dh, dl);
+  D.l = __fsub_rn(dl, __fsub_rn(D.h, dh));
+  return D;
+}
+
 // the same field quantities at the midpoint of a track, from those of its two
 // endpoints: d_m = (d0 + d1)/2 exactly (float-float), and w = d x beta and
 // beta.d are linear in d, so w_m = (w0 + w1)/2, (beta.d)_m = (bd0 + bd1)/2

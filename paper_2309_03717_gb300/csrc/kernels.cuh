@@ -381,20 +381,45 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+constexpr int kBwdThreads = 256;
+constexpr int kBwdAntBlock = 16;  // antennas between two passes over the set-aside pairs
+
+// dynamic shared memory of k_backward: antenna gradients [n_ant][3] + dN0, and
+// (Ops::kDefers) the CTA's track gradients [11][kBwdThreads] and the queue of
+// set-aside pairs (track slot | antenna within the block << 8)
 template <class Ops>
-__global__ void __launch_bounds__(256) k_backward(const BwdArgs a) {
+size_t bwd_smem_bytes(int n_ant) {
+  using acc_t = typename Ops::acc_t;
+  size_t b = sizeof(acc_t) * ((3 * (size_t)n_ant + 1 + 3) / 4 * 4);
+  if (Ops::kDefers) b += sizeof(acc_t) * 11 * kBwdThreads + sizeof(uint16_t) * kBwdThreads * kBwdAntBlock;
+  return b;
+}
+
+// Adjoint: one thread per track, looping over all antennas; track gradients
+// stay in registers, antenna gradients are warp-reduced into shared memory.
+// Pairs set aside by Ops::adj_main (Endpoint near the Cherenkov angle) are
+// evaluated together after every kBwdAntBlock antennas, in full warps; their
+// track gradients go through shared memory.
+template <class Ops>
+__global__ void __launch_bounds__(kBwdThreads) k_backward(const BwdArgs a) {
   using acc_t = typename Ops::acc_t;
   extern __shared__ __align__(16) unsigned char smem_b[];
   acc_t* sg = reinterpret_cast<acc_t*>(smem_b);  // [n_ant][3] + dN0
+  acc_t* tg_s = sg + (3 * a.n_ant + 1 + 3) / 4 * 4;
+  uint16_t* queue = reinterpret_cast<uint16_t*>(tg_s + 11 * kBwdThreads);
+  __shared__ int q_n;
   const int tid = threadIdx.x;
   for (int k = tid; k < 3 * a.n_ant + 1; k += blockDim.x) sg[k] = acc_t(0);
+  if (tid == 0) q_n = 0;
   __syncthreads();
   const int N = a.M.n_bins;
   const acc_t* G = static_cast<const acc_t*>(a.G);
   acc_t dn_acc = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t n_pad = (a.n + 31) / 32 * 32;  // whole warps stay together for the reductions
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < n_pad; i += stride) {
+  // the loop bounds are uniform over the CTA (barriers inside); whole warps
+  // stay together for the reductions
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += stride) {
+    const int64_t i = base + tid;
     const bool valid = i < a.n;
     const unsigned char* T = static_cast<const unsigned char*>(a.tiles) +
                              ((valid ? i : 0) / kTileT) * (int64_t)Ops::kTileBytes;
@@ -402,17 +427,51 @@ __global__ void __launch_bounds__(256) k_backward(const BwdArgs a) {
     acc_t tg[11];
 #pragma unroll
     for (int k = 0; k < 11; ++k) tg[k] = acc_t(0);
+    if (Ops::kDefers) {
+#pragma unroll
+      for (int k = 0; k < 11; ++k) tg_s[k * kBwdThreads + tid] = acc_t(0);
+    }
     typename Ops::Track tr;
     Ops::load(T, l, a.M, tr);
     const bool live = valid && Ops::live(tr);
-    for (int ant = 0; ant < a.n_ant; ++ant) {
-      const AntRec A = a.ants[ant];
-      acc_t ga[3] = {0, 0, 0};
-      if (live) Ops::adj(tr, A, a.M, G + (size_t)ant * 3 * N, tg, ga, dn_acc);
+    for (int ant0 = 0; ant0 < a.n_ant; ant0 += kBwdAntBlock) {
+      const int ant_end = min(ant0 + kBwdAntBlock, a.n_ant);
+      for (int ant = ant0; ant < ant_end; ++ant) {
+        const AntRec A = a.ants[ant];
+        acc_t ga[3] = {0, 0, 0};
+        if (live && Ops::adj_main(tr, A, a.M, G + (size_t)ant * 3 * N, tg, ga, dn_acc) && Ops::kDefers)
+          queue[atomicAdd(&q_n, 1)] = (uint16_t)(tid | ((ant - ant0) << 8));
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        acc_t v = warp_sum(ga[c]);
-        if ((tid & 31) == 0 && v != acc_t(0)) atomicAdd(&sg[3 * ant + c], v);
+        for (int c = 0; c < 3; ++c) {
+          acc_t v = warp_sum(ga[c]);
+          if ((tid & 31) == 0 && v != acc_t(0)) atomicAdd(&sg[3 * ant + c], v);
+        }
+      }
+      if (Ops::kDefers) {
+        __syncthreads();  // queue complete (and the track-gradient slots zeroed)
+        const int nq = q_n;
+        for (int q = tid; q < nq; q += blockDim.x) {
+          const int e = queue[q];
+          const int slot = e & 0xff, ant = ant0 + (e >> 8);
+          const int64_t j = base + slot;
+          typename Ops::Track tj;
+          Ops::load(static_cast<const unsigned char*>(a.tiles) + (j / kTileT) * (int64_t)Ops::kTileBytes,
+                    (int)(j % kTileT), a.M, tj);
+          acc_t tgl[11];
+#pragma unroll
+          for (int k = 0; k < 11; ++k) tgl[k] = acc_t(0);
+          acc_t gal[3] = {0, 0, 0};
+          Ops::adj_deferred(tj, a.ants[ant], a.M, G + (size_t)ant * 3 * N, tgl, gal, dn_acc);
+#pragma unroll
+          for (int k = 0; k < 11; ++k)
+            if (tgl[k] != acc_t(0)) atomicAdd(&tg_s[k * kBwdThreads + slot], tgl[k]);
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            if (gal[c] != acc_t(0)) atomicAdd(&sg[3 * ant + c], gal[c]);
+        }
+        __syncthreads();  // every thread has read q_n
+        if (tid == 0) q_n = 0;
+        __syncthreads();  // reset visible before the next entries
       }
     }
     if (valid) {
@@ -420,7 +479,7 @@ __global__ void __launch_bounds__(256) k_backward(const BwdArgs a) {
                       (acc_t*)a.out.z1, (acc_t*)a.out.t0, (acc_t*)a.out.t1, (acc_t*)a.out.bx, (acc_t*)a.out.by,
                       (acc_t*)a.out.bz};
 #pragma unroll
-      for (int k = 0; k < 11; ++k) o[k][i] += tg[k];
+      for (int k = 0; k < 11; ++k) o[k][i] += tg[k] + (Ops::kDefers ? tg_s[k * kBwdThreads + tid] : acc_t(0));
     }
   }
   acc_t d = warp_sum(dn_acc);

@@ -32,13 +32,14 @@ cudaError_t launch_arrivals_f64(int formalism, const void* tiles, int64_t n, con
 }
 
 cudaError_t launch_backward_f64(const BwdArgs& a, int blocks, cudaStream_t st) {
-  const size_t smem = sizeof(double) * (3 * (size_t)a.n_ant + 1);
-  auto k = k_backward<OpsF64<C8R_ENDPOINT>>;
+  using O = OpsF64<C8R_ENDPOINT>;
+  const size_t smem = bwd_smem_bytes<O>(a.n_ant);
+  auto k = k_backward<O>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k<<<blocks, 256, smem, st>>>(a);
+  k<<<blocks, kBwdThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -149,18 +149,19 @@ cudaError_t launch_arrivals_mixed(int formalism, const void* tiles, int64_t n, c
 }
 
 cudaError_t launch_backward_mixed(const BwdArgs& a, int blocks, cudaStream_t st) {
-  const size_t smem = sizeof(float) * (3 * (size_t)a.n_ant + 1);
-  const bool ex = a.M.kind == C8R_EXPONENTIAL;
-  if (ex) {
-    auto k = k_backward<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<blocks, 256, smem, st>>>(a);
-  } else {
-    auto k = k_backward<OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<blocks, 256, smem, st>>>(a);
-  }
-  return cudaGetLastError();
+  auto go = [&](auto ops) {
+    using O = decltype(ops);
+    const size_t smem = bwd_smem_bytes<O>(a.n_ant);
+    auto k = k_backward<O>;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    k<<<blocks, kBwdThreads, smem, st>>>(a);
+    return cudaGetLastError();
+  };
+  if (a.M.kind == C8R_EXPONENTIAL) return go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>{});
+  return go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>{});
 }
 
 }  // namespace c8r

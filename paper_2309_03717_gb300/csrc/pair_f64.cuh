@@ -177,6 +177,13 @@ struct OpsF64 {
       zhs(T, l, A, M, out);
   }
 
+  static __device__ __forceinline__ bool adj_main(const TrackD& tr, const AntRec& A, const MedParams& M,
+                                                  const double* G, double tg[11], double ga[3], double& dn) {
+    adj(tr, A, M, G, tg, ga, dn);
+    return false;
+  }
+  static __device__ __forceinline__ void adj_deferred(const TrackD&, const AntRec&, const MedParams&, const double*,
+                                                      double*, double*, double&) {}
   static __device__ __forceinline__ void adj(const TrackD& tr, const AntRec& A, const MedParams& M,
                                              const double* G, double tg[11], double ga[3], double& dn) {
     static_assert(FORM == C8R_ENDPOINT, "adjoint is defined for the Endpoint formalism");

@@ -123,9 +123,13 @@ __device__ __forceinline__ bool endpoint_midpoint(const TrackM& t, const AntRec&
   GeoM g = e.gm;
   geo_refine(g);
   const ff u0 = arrival_mixed(M, A, g, t.tmh, t.tml, t.Emh, t.Eml);
-  float hh, hl;  // D_m (t1 - t0)/(2 dt)
-  two_prod(e.fm.D, t.dtauh, hh, hl);
-  hl = __fmaf_rn(e.fm.D, t.dtaul, hl);
+  const ff Dm = doppler_ff(g, t.bx, t.by, t.bz, t.nm1_m);
+  // the amplitude's 1/D_m, too, from the float-float D: here |D_m| can be far
+  // below the FP32 form's absolute accuracy
+  e.fm.D = __fadd_rn(Dm.h, Dm.l);
+  float hh, hl;  // D_m (t1 - t0)/(2 dt), float-float
+  two_prod(Dm.h, t.dtauh, hh, hl);
+  hl = __fmaf_rn(Dm.h, t.dtaul, __fmaf_rn(Dm.l, t.dtauh, hl));
   hh *= 0.5f;
   hl *= 0.5f;
   two_sum(u0.h, -hh, e.ua.h, e.ua.l);
@@ -219,10 +223,14 @@ struct OpsMixed {
     field_mixed(gm, t.bx, t.by, t.bz, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), f);
     geo_refine(gm);
     const ff um = arrival_mixed(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml);
-    const float aD = fabsf(f.D);
-    float hh, hl;  // |D| (t1 - t0)/(2 dt)
-    two_prod(aD, t.dtauh, hh, hl);
-    hl = __fmaf_rn(aD, t.dtaul, hl);
+    ff aD = doppler_ff(gm, t.bx, t.by, t.bz, t.nm1_m);
+    if (aD.h < 0.0f) {
+      aD.h = -aD.h;
+      aD.l = -aD.l;
+    }
+    float hh, hl;  // |D| (t1 - t0)/(2 dt), float-float
+    two_prod(aD.h, t.dtauh, hh, hl);
+    hl = __fmaf_rn(aD.h, t.dtaul, __fmaf_rn(aD.l, t.dtauh, hl));
     hh *= 0.5f;
     hl *= 0.5f;
     ff ulo, uhi;
@@ -313,13 +321,34 @@ struct OpsMixed {
     deposit_adjoint<float>(rh, V, c, f.D, g.R0, n, gv, kappa, dd, db, dns);
   }
 
+  // adjoint main pass: every pair except the near-Cherenkov ones, for which it
+  // adds nothing and returns true
+  static __device__ __forceinline__ bool adj_main(const TrackM& t, const AntRec& A, const MedParams& M,
+                                                  const float* G, float tg[11], float ga[3], float& dn) {
+    static_assert(FORM == C8R_ENDPOINT, "adjoint is defined for the Endpoint formalism");
+    EndpointEvalM e;
+    if (!endpoint_fields(t, A, e)) return false;
+    if (endpoint_near_cherenkov(e, M)) return true;
+    endpoint_arrivals<KIND>(t, A, M, e);
+    adj_deposits(t, e, M, G, tg, ga, dn);
+    return false;
+  }
+  static __device__ __forceinline__ void adj_deferred(const TrackM& t, const AntRec& A, const MedParams& M,
+                                                      const float* G, float tg[11], float ga[3], float& dn) {
+    EndpointEvalM e;
+    if (!endpoint_fields(t, A, e)) return;
+    if (!endpoint_midpoint<KIND>(t, A, M, e)) return;
+    adj_deposits(t, e, M, G, tg, ga, dn);
+  }
   static __device__ __forceinline__ void adj(const TrackM& t, const AntRec& A, const MedParams& M, const float* G,
                                              float tg[11], float ga[3], float& dn) {
-    static_assert(FORM == C8R_ENDPOINT, "adjoint is defined for the Endpoint formalism");
+    if (adj_main(t, A, M, G, tg, ga, dn)) adj_deferred(t, A, M, G, tg, ga, dn);
+  }
+
+  // gradients of the deposits of an evaluated pair
+  static __device__ __forceinline__ void adj_deposits(const TrackM& t, const EndpointEvalM& e, const MedParams& M,
+                                                      const float* G, float tg[11], float ga[3], float& dn) {
     const int N = M.n_bins;
-    EndpointEvalM e;
-    endpoint_eval_mixed<KIND>(t, A, M, e);
-    if (!e.valid) return;
     float fa, fb;
     const int ka = bin_raw(e.ua, N, fa);
     const int kb = bin_raw(e.ub, N, fb);

@@ -1,0 +1,73 @@
+"""Parity at full size, in the launch configuration bench.py times.
+
+The 2e7-track shower (exponential atmosphere, 160-antenna star, 4096 x 0.2 ns)
+goes through the default launch shape for both formalisms in mixed precision;
+the inclined 1024-antenna workload (8192 x 0.1 ns) streams 8e6 tracks in its
+4e6-track chunks.  The CUDA path computes every antenna; the oracle, which
+cannot, evaluates all tracks for a sample of antennas, one antenna at a time.
+Bar: the mixed-precision relative L2 of 1e-4 on each sampled antenna.
+
+As in the smaller parity tests, the tracks with an Endpoint deposit within
+1e-6 bin of an edge at a sampled antenna (a few hundred of the 2e7) are left
+out of the input: either bin is correct for them, and at this size one of them
+moves ~2e-4 of a trace, because a trace is ~1e3 times smaller than the sum of
+the magnitudes of its deposits.  The bin test at smaller sizes covers them."""
+import numpy as np
+import pytest
+
+from _util import built_lib, drop_tracks, edge_ambiguous, oracle_arrivals, oracle_traces, rel_l2, to_device
+from paper_2309_03717_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    built_lib()
+
+
+def sampled_check(w, tracks, formalisms, sample, chunk=0):
+    from paper_2309_03717_gb300.c8r import RadioProcess
+    amb = np.zeros(len(tracks["x0"]), dtype=bool)
+    for a in sample:
+        _, u = oracle_arrivals(tracks, w["ant_xyz"][a:a + 1], w["t_start_ns"][a:a + 1], w["n_bins"], w["dt_ns"],
+                               w["medium"], "endpoint")
+        amb |= edge_ambiguous(u, 1e-6).reshape(len(amb), -1).any(axis=1)
+    assert amb.mean() < 1e-4
+    tracks = drop_tracks(tracks, ~amb)
+    dev = to_device(tracks)
+    for formalism in formalisms:
+        p = RadioProcess(w["medium"], w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], formalism, "mixed")
+        if chunk:
+            p.set_launch_shape(0, 0, chunk)
+        p.push(dev)
+        got = p.traces().cpu().numpy()
+        kept = p.stats()["tracks_kept"]
+        p.close()
+        for a in sample:
+            ref, okept = oracle_traces(tracks, w["ant_xyz"][a:a + 1], w["t_start_ns"][a:a + 1], w["n_bins"],
+                                       w["dt_ns"], w["medium"], formalism)
+            assert okept == kept
+            assert np.abs(ref).max() > 0
+            err = rel_l2(got[a:a + 1], ref)
+            assert err <= 1e-4, f"{formalism} antenna {a}: relative L2 {err:.3e}"
+
+
+def test_shower_2e7_tracks_star_160_antennas():
+    w = synth.workload(1)
+    assert w["n_tracks"] == 20_000_000 and len(w["ant_xyz"]) == 160
+    tracks = synth.workload_tracks(w)
+    # innermost, a middle radius and the outermost antenna, on different arms
+    sample = [0, 8 * 10 + 3, 159]
+    sampled_check(w, tracks, ("endpoint", "zhs"), sample)
+
+
+def test_inclined_1024_antennas_streamed_in_4e6_track_chunks():
+    w = synth.workload(2, n_tracks=8_000_000)
+    assert len(w["ant_xyz"]) == 1024 and w["n_bins"] == 8192 and w["chunk"] == 4_000_000
+    tracks = synth.workload_tracks(w)
+    sample = [0, 527, 1023]
+    sampled_check(w, tracks, ("endpoint",), sample, chunk=w["chunk"])

@@ -56,6 +56,13 @@ CASES = [
     (1, 20011, 160, "zhs", "mixed", 1e-4),
     (0, 20011, 16, "endpoint", "mixed", 1e-4),
     (0, 20011, 16, "zhs", "mixed", 1e-4),
+    # inclined (60 deg) shower, 32 x 32 grid, 8192 x 0.1 ns
+    (2, 6007, 64, "endpoint", "fp64", 1e-9),
+    (2, 6007, 64, "zhs", "fp64", 1e-9),
+    (2, 20011, 256, "endpoint", "mixed", 1e-4),
+    (2, 20011, 256, "zhs", "mixed", 1e-4),
+    # differentiable workload: star 8 x 8, 2048 x 0.2 ns
+    (4, 20011, 64, "endpoint", "mixed", 1e-4),
 ]
 
 
