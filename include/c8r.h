@@ -181,7 +181,9 @@ int c8r_reset(c8r_ctx* ctx, void* cuda_stream);
  * [n_ant][3]) and dL/dN0 into *out_dN0 (DEVICE FP64 scalar; for a uniform medium
  * the derivative with respect to n - 1).  Bin indices and the near-Cherenkov
  * branch are held fixed, so the time derivatives are zero.  The per-pair geometry
- * is recomputed, not stored.  EINVAL for a ZHS context or mismatched dtypes. */
+ * is recomputed, not stored.  The first call allocates a bin-major copy of
+ * grad_traces inside the context (ENOMEM if that fails).  EINVAL for a ZHS
+ * context or mismatched dtypes. */
 int c8r_backward(c8r_ctx* ctx, const c8r_tracks* tracks, int64_t n, const void* grad_traces,
                  const c8r_track_grads* out_tracks, double* out_ant_grad, double* out_dN0, void* cuda_stream);
 

@@ -98,6 +98,7 @@ struct c8r_ctx {
   void* d_acc = nullptr;     // accumulator [n_ant][n_bins][x, y, z, pad]
   size_t acc_bytes = 0;
   void* d_stage = nullptr;   // [n_ant][3][n_bins] staging for copies to host
+  void* d_gbm = nullptr;     // backward: dL/dtraces, bin-major [n_ant][n_bins] accumulator elements
   size_t trace_bytes = 0;
   // scratch: derived-track tiles for one chunk
   void* d_tiles = nullptr;
@@ -148,6 +149,8 @@ void free_antenna_state(c8r_ctx* c) {
   if (c->d_ants) cudaFree(c->d_ants);
   if (c->d_acc) cudaFree(c->d_acc);
   if (c->d_stage) cudaFree(c->d_stage);
+  if (c->d_gbm) cudaFree(c->d_gbm);
+  c->d_gbm = nullptr;
   c->d_ants = nullptr;
   c->d_acc = nullptr;
   c->d_stage = nullptr;
@@ -550,6 +553,18 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
   const int64_t chunk = n < c->chunk_tracks ? n : c->chunk_tracks;
   if ((r = ensure_tiles(c, chunk)) != C8R_OK) return r;
   const size_t es = want == C8R_F64 ? 8 : 4;
+  if (!c->d_gbm) {
+    cudaError_t e = cudaMalloc(&c->d_gbm, (size_t)c->n_ant * c->n_bins * acc_elem_bytes(c->precision));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->d_gbm = nullptr;
+      return fail(c, C8R_ENOMEM, "backward gradient buffer");
+    }
+  }
+  {
+    cudaError_t e = launch_traces_to_bin_major(c->precision, grad_traces, c->n_ant, c->n_bins, c->d_gbm, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "gradient layout");
+  }
   for (int64_t off = 0; off < n; off += chunk) {
     const int64_t m = (n - off) < chunk ? (n - off) : chunk;
     cudaError_t e = launch_ingest(c->precision, offset_tracks(t, off), m, c->d_tiles, c->M, nullptr, st);
@@ -557,7 +572,7 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
     c8r_track_grads o = *out;
     void** og[11] = {&o.x0, &o.y0, &o.z0, &o.x1, &o.y1, &o.z1, &o.t0, &o.t1, &o.bx, &o.by, &o.bz};
     for (int k = 0; k < 11; ++k) *og[k] = static_cast<char*>(*og[k]) + off * es;
-    BwdArgs ba{c->d_tiles, m, c->d_ants, c->n_ant, grad_traces, o, ant_grad, dN0, c->M};
+    BwdArgs ba{c->d_tiles, m, c->d_ants, c->n_ant, c->d_gbm, o, ant_grad, dN0, c->M};
     int64_t want_blocks = (m + 255) / 256;
     const int blocks = (int)(want_blocks < 8LL * c->sm_count ? want_blocks : 8LL * c->sm_count);
     e = (c->precision == C8R_FP64) ? launch_backward_f64(ba, blocks, st) : launch_backward_mixed(ba, blocks, st);

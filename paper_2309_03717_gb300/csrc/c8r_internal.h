@@ -33,6 +33,10 @@ inline int acc_rows(int precision, int formalism) { return precision == C8R_MIXE
 cudaError_t launch_acc_to_traces(int precision, const void* acc, int n_ant, int n_bins, int rows, void* out, int add,
                                  cudaStream_t st);
 
+// dL/dtraces [n_ant][3][n_bins] -> bin-major [n_ant][n_bins] accumulator elements
+cudaError_t launch_traces_to_bin_major(int precision, const void* g, int n_ant, int n_bins, void* out,
+                                       cudaStream_t st);
+
 // ingest: filter + derived per-track quantities into tiles; counts kept tracks
 // into *kept unless kept is NULL
 cudaError_t launch_ingest(int precision, const TrackPtrs& t, int64_t n, void* tiles, const MedParams& M,

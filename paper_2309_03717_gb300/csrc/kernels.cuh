@@ -94,7 +94,7 @@ struct BwdArgs {
   int64_t n;          // tracks
   const AntRec* ants;
   int n_ant;
-  const void* G;      // dL/dtraces [n_ant][3][n_bins]
+  const void* G;      // dL/dtraces, bin-major [n_ant][n_bins] of (x, y, z, 0) accumulator elements
   c8r_track_grads out;
   double* ant_grad;   // [n_ant][3]
   double* dN0;
@@ -401,7 +401,7 @@ size_t bwd_smem_bytes(int n_ant) {
 // evaluated together after every kBwdAntBlock antennas, in full warps; their
 // track gradients go through shared memory.
 template <class Ops>
-__global__ void __launch_bounds__(kBwdThreads) k_backward(const BwdArgs a) {
+__global__ void __launch_bounds__(kBwdThreads, Ops::kBwdMinBlocks) k_backward(const BwdArgs a) {
   using acc_t = typename Ops::acc_t;
   extern __shared__ __align__(16) unsigned char smem_b[];
   acc_t* sg = reinterpret_cast<acc_t*>(smem_b);  // [n_ant][3] + dN0
@@ -413,7 +413,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const BwdArgs a) {
   if (tid == 0) q_n = 0;
   __syncthreads();
   const int N = a.M.n_bins;
-  const acc_t* G = static_cast<const acc_t*>(a.G);
+  using acc4 = typename AccOf<acc_t>::type;
+  const acc4* G = static_cast<const acc4*>(a.G);
   acc_t dn_acc = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // the loop bounds are uniform over the CTA (barriers inside); whole warps
@@ -439,7 +440,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const BwdArgs a) {
       for (int ant = ant0; ant < ant_end; ++ant) {
         const AntRec A = a.ants[ant];
         acc_t ga[3] = {0, 0, 0};
-        if (live && Ops::adj_main(tr, A, a.M, G + (size_t)ant * 3 * N, tg, ga, dn_acc) && Ops::kDefers)
+        if (live && Ops::adj_main(tr, A, a.M, G + (size_t)ant * N, tg, ga, dn_acc) && Ops::kDefers)
           queue[atomicAdd(&q_n, 1)] = (uint16_t)(tid | ((ant - ant0) << 8));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const BwdArgs a) {
 #pragma unroll
           for (int k = 0; k < 11; ++k) tgl[k] = acc_t(0);
           acc_t gal[3] = {0, 0, 0};
-          Ops::adj_deferred(tj, a.ants[ant], a.M, G + (size_t)ant * 3 * N, tgl, gal, dn_acc);
+          Ops::adj_deferred(tj, a.ants[ant], a.M, G + (size_t)ant * N, tgl, gal, dn_acc);
 #pragma unroll
           for (int k = 0; k < 11; ++k)
             if (tgl[k] != acc_t(0)) atomicAdd(&tg_s[k * kBwdThreads + slot], tgl[k]);

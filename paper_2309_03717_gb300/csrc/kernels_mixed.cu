@@ -126,6 +126,37 @@ cudaError_t launch_acc_to_traces(int precision, const void* acc, int n_ant, int 
   return cudaGetLastError();
 }
 
+// traces [n_ant][3][n_bins] (float or double) -> bin-major [n_ant][n_bins] of
+// (x, y, z, 0), the layout the adjoint gathers one bin of from
+template <typename T, typename T4>
+__global__ void k_traces_to_bin_major(const T* g, int64_t n_ant_bins, int n_bins, T4* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_ant_bins) return;
+  const int64_t a = i / n_bins;
+  const int k = (int)(i - a * n_bins);
+  const T* s = g + a * 3 * n_bins + k;
+  T4 v;
+  v.x = s[0];
+  v.y = s[n_bins];
+  v.z = s[2 * (size_t)n_bins];
+  v.w = T(0);
+  out[i] = v;
+}
+
+cudaError_t launch_traces_to_bin_major(int precision, const void* g, int n_ant, int n_bins, void* out,
+                                       cudaStream_t st) {
+  const int64_t n = (int64_t)n_ant * n_bins;
+  if (n <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (precision == C8R_FP64)
+    k_traces_to_bin_major<double, Acc4D><<<blocks, 256, 0, st>>>(static_cast<const double*>(g), n, n_bins,
+                                                                 static_cast<Acc4D*>(out));
+  else
+    k_traces_to_bin_major<float, float4><<<blocks, 256, 0, st>>>(static_cast<const float*>(g), n, n_bins,
+                                                                 static_cast<float4*>(out));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_arrivals_mixed(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,
                                   const MedParams& M, int32_t* branch, int32_t* bin, float* frac, cudaStream_t st) {
   const unsigned blocks = (unsigned)((n * (int64_t)n_ant + 255) / 256);

@@ -77,6 +77,7 @@ struct OpsF64 {
   static constexpr int kTileBytes = kTileBytesF64;
   static constexpr int kMinBlocks = 4;
   static constexpr bool kDefers = false;  // every pair is evaluated in the main pass
+  static constexpr int kBwdMinBlocks = 1;
   static constexpr int kAccRows = 1;      // no box deposits
 
   static __device__ __forceinline__ void load(const void* Tv, int l, const MedParams&, TrackD& t) {
@@ -178,14 +179,14 @@ struct OpsF64 {
   }
 
   static __device__ __forceinline__ bool adj_main(const TrackD& tr, const AntRec& A, const MedParams& M,
-                                                  const double* G, double tg[11], double ga[3], double& dn) {
+                                                  const Acc4D* G, double tg[11], double ga[3], double& dn) {
     adj(tr, A, M, G, tg, ga, dn);
     return false;
   }
-  static __device__ __forceinline__ void adj_deferred(const TrackD&, const AntRec&, const MedParams&, const double*,
+  static __device__ __forceinline__ void adj_deferred(const TrackD&, const AntRec&, const MedParams&, const Acc4D*,
                                                       double*, double*, double&) {}
   static __device__ __forceinline__ void adj(const TrackD& tr, const AntRec& A, const MedParams& M,
-                                             const double* G, double tg[11], double ga[3], double& dn) {
+                                             const Acc4D* G, double tg[11], double ga[3], double& dn) {
     static_assert(FORM == C8R_ENDPOINT, "adjoint is defined for the Endpoint formalism");
     const double* T = tr.T;
     const int l = tr.l;
@@ -207,7 +208,7 @@ struct OpsF64 {
         const bool in = j == 0 ? ina : inb;
         if (!in) continue;
         const int k = (int)(j == 0 ? ka : kb);
-        const double gv[3] = {G[k], G[N + k], G[2 * N + k]};
+        const double gv[3] = {G[k].x, G[k].y, G[k].z};
         const GeoD& g = j == 0 ? e.g0 : e.g1;
         const double* V = j == 0 ? e.V0 : e.V1;
         const double c = b[0] * g.rh[0] + b[1] * g.rh[1] + b[2] * g.rh[2];
@@ -231,7 +232,7 @@ struct OpsF64 {
     if (ka == kb) return;
     double gv[3];
     for (int cc = 0; cc < 3; ++cc)
-      gv[cc] = (ina ? G[cc * N + (int)ka] : 0.0) - (inb ? G[cc * N + (int)kb] : 0.0);
+      gv[cc] = (ina ? (&G[(int)ka].x)[cc] : 0.0) - (inb ? (&G[(int)kb].x)[cc] : 0.0);
     const double c = b[0] * e.gm.rh[0] + b[1] * e.gm.rh[1] + b[2] * e.gm.rh[2];
     deposit_adjoint<double>(e.gm.rh, e.Vm, c, e.Dm, e.gm.R, e.gm.n_src, gv, K / dt_s, dd, db, dns);
     for (int cc = 0; cc < 3; ++cc) {

@@ -164,6 +164,7 @@ struct OpsMixed {
   // Endpoint: the near-Cherenkov pairs (a minority, spread over most warps)
   // are set aside by the main pass and evaluated together afterwards
   static constexpr bool kDefers = FORM == C8R_ENDPOINT;
+  static constexpr int kBwdMinBlocks = 3;  // adjoint CTAs (256 threads) per SM the registers are set for
   // ZHS: a second accumulator row holds the edges of box deposits
   static constexpr int kAccRows = FORM == C8R_ZHS ? 2 : 1;
 
@@ -324,7 +325,7 @@ struct OpsMixed {
   // adjoint main pass: every pair except the near-Cherenkov ones, for which it
   // adds nothing and returns true
   static __device__ __forceinline__ bool adj_main(const TrackM& t, const AntRec& A, const MedParams& M,
-                                                  const float* G, float tg[11], float ga[3], float& dn) {
+                                                  const float4* G, float tg[11], float ga[3], float& dn) {
     static_assert(FORM == C8R_ENDPOINT, "adjoint is defined for the Endpoint formalism");
     EndpointEvalM e;
     if (!endpoint_fields(t, A, e)) return false;
@@ -334,20 +335,20 @@ struct OpsMixed {
     return false;
   }
   static __device__ __forceinline__ void adj_deferred(const TrackM& t, const AntRec& A, const MedParams& M,
-                                                      const float* G, float tg[11], float ga[3], float& dn) {
+                                                      const float4* G, float tg[11], float ga[3], float& dn) {
     EndpointEvalM e;
     if (!endpoint_fields(t, A, e)) return;
     if (!endpoint_midpoint<KIND>(t, A, M, e)) return;
     adj_deposits(t, e, M, G, tg, ga, dn);
   }
-  static __device__ __forceinline__ void adj(const TrackM& t, const AntRec& A, const MedParams& M, const float* G,
+  static __device__ __forceinline__ void adj(const TrackM& t, const AntRec& A, const MedParams& M, const float4* G,
                                              float tg[11], float ga[3], float& dn) {
     if (adj_main(t, A, M, G, tg, ga, dn)) adj_deferred(t, A, M, G, tg, ga, dn);
   }
 
   // gradients of the deposits of an evaluated pair
   static __device__ __forceinline__ void adj_deposits(const TrackM& t, const EndpointEvalM& e, const MedParams& M,
-                                                      const float* G, float tg[11], float ga[3], float& dn) {
+                                                      const float4* G, float tg[11], float ga[3], float& dn) {
     const int N = M.n_bins;
     float fa, fb;
     const int ka = bin_raw(e.ua, N, fa);
@@ -361,7 +362,8 @@ struct OpsMixed {
         const bool in = j == 0 ? ina : inb;
         if (!in) continue;
         const int k = j == 0 ? ka : kb;
-        const float gv[3] = {G[k], G[N + k], G[2 * N + k]};
+        const float4 g4 = G[k];
+        const float gv[3] = {g4.x, g4.y, g4.z};
         deposit_grad(j == 0 ? e.g0 : e.g1, j == 0 ? e.f0 : e.f1, 1.0f + (j == 0 ? t.nm1_0 : t.nm1_1), gv,
                      j == 0 ? amp : -amp, dd, db, dns);
         const float E = j == 0 ? t.E0h : t.E1h;
@@ -377,7 +379,11 @@ struct OpsMixed {
     }
     if (ka == kb) return;
     float gv[3];
-    for (int c = 0; c < 3; ++c) gv[c] = (ina ? G[c * N + ka] : 0.0f) - (inb ? G[c * N + kb] : 0.0f);
+    const float4 ga4 = ina ? G[ka] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 gb4 = inb ? G[kb] : make_float4(0.f, 0.f, 0.f, 0.f);
+    gv[0] = ga4.x - gb4.x;
+    gv[1] = ga4.y - gb4.y;
+    gv[2] = ga4.z - gb4.z;
     deposit_grad(e.gm, e.fm, 1.0f + t.nm1_m, gv, amp, dd, db, dns);
     for (int c = 0; c < 3; ++c) {
       tg[c] -= 0.5f * dd[c];
