@@ -140,6 +140,72 @@ def to_dev(tracks, torch, pinned=False):
     return out
 
 
+_CPU_TRACKS = None
+
+
+def _cpu_init(n_tracks, seed, zenith):
+    """Worker set-up (untimed): the same seeded track sample in every process."""
+    global _CPU_TRACKS
+    import oracle
+    from paper_2309_03717_gb300 import synth
+    _CPU_TRACKS = oracle.tracks_from_ns(synth.make_tracks(n_tracks, seed, zenith, np.float32))
+
+
+def _cpu_part(job):
+    import oracle
+    ant, t_start_s, n_bins, dt_s, medium, formalism = job
+    oracle.forward(_CPU_TRACKS, ant, t_start_s, n_bins, dt_s, medium, formalism)
+    return len(ant)
+
+
+class OraclePool:
+    """The oracle as it stands in one process per host core, each taking a
+    contiguous slice of the antennas (the paper's antenna-bunch split).  The
+    workers are spawned (never forked) and set up their track sample untimed."""
+
+    def __init__(self, w, n_tracks, formalisms):
+        import multiprocessing as mp
+        import oracle
+        oracle.build()
+        self.w, self.n_tracks, self.formalisms = w, n_tracks, formalisms
+        A = len(w["ant_xyz"])
+        self.P = P = max(1, min(os.cpu_count() or 1, A))
+        bounds = np.linspace(0, A, P + 1).astype(int)
+        self.jobs = [(np.ascontiguousarray(w["ant_xyz"][bounds[i]:bounds[i + 1]]),
+                      w["t_start_ns"][bounds[i]:bounds[i + 1]] * 1e-9, w["n_bins"], w["dt_ns"] * 1e-9, w["medium"],
+                      oracle.ENDPOINT if f == "endpoint" else oracle.ZHS)
+                     for f in formalisms for i in range(P)]
+        self.pool = mp.get_context("spawn").Pool(P, initializer=_cpu_init,
+                                                 initargs=(n_tracks, w["seed"] + 17, w["zenith"]))
+        self.pool.map(_cpu_part, [(j[0][:1], j[1][:1], 16, j[3], j[4], j[5]) for j in self.jobs[:P]])  # warm-up
+
+    def run(self):
+        """One timed pass over the sample: returns (pairs/s, seconds)."""
+        t0 = time.perf_counter()
+        self.pool.map(_cpu_part, self.jobs, chunksize=1)
+        dt = time.perf_counter() - t0
+        return self.n_tracks * len(self.w["ant_xyz"]) * len(self.formalisms) / dt, dt
+
+    def describe(self, dt):
+        A = len(self.w["ant_xyz"])
+        pairs = self.n_tracks * A * len(self.formalisms)
+        return (f"{self.n_tracks} tracks x {A} antennas x {len(self.formalisms)} formalisms ({pairs:.3g} pairs, "
+                f"{dt:.2f} s wall, FP64 C oracle, {self.P} processes each on 1/{self.P} of the antennas)")
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline_all_cores(w, n_tracks, formalisms):
+    op = OraclePool(w, n_tracks, formalisms)
+    try:
+        v, dt = op.run()
+        return {"value": v, "unit": "pairs/s", "cores": op.P, "kind": "oracle", "sample": op.describe(dt)}
+    finally:
+        op.close()
+
+
 def cpu_baseline(w, n_tracks, formalisms):
     """The FP64 oracle as it stands, single-threaded, on a sample of the workload."""
     import oracle
@@ -159,24 +225,26 @@ def cpu_baseline(w, n_tracks, formalisms):
 
 
 def run_reference(args):
-    """Reference arm: the oracle, timed on the host cores on bounded samples."""
+    """Reference arm: the oracle, timed on all host cores on bounded samples."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_2309_03717_gb300 import synth
-    import oracle
-    oracle.build()
     w = synth.workload(1)
-    n = args.cpu_sample_tracks
-    for _ in range(args.warmup):
-        cpu_baseline(w, max(n // 10, 100), ("endpoint", "zhs"))
-    vals = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(w, n, ("endpoint", "zhs")))
-    elapsed = time.perf_counter() - t0
-    v = sum(x["value"] for x in vals) / len(vals)
+    n = 10 * args.cpu_sample_tracks
+    op = OraclePool(w, n, ("endpoint", "zhs"))
+    try:
+        for _ in range(args.warmup):
+            op.run()
+        vals = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            vals.append(op.run())
+        elapsed = time.perf_counter() - t0
+    finally:
+        op.close()
     pairs_per_step = 2 * n * len(w["ant_xyz"])
+    v = pairs_per_step * args.steps / sum(dt for _, dt in vals)
     line = {
         "impl": "reference", "metric": "track-antenna pairs/sec (Endpoint, ZHS) on 1 GB300; backward/forward time ratio",
         "value": v, "unit": "pairs/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
@@ -184,7 +252,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "shower 2e7 tracks (sampled), star 8x20 antennas, exp. atmosphere, 4096 x 0.2 ns",
                    "sample_tracks_per_step": n, "pairs_per_step": pairs_per_step},
-        "cpu_baseline": {"value": v, "kind": "oracle", "cores": 1, "sample": vals[0]["sample"]},
+        "cpu_baseline": {"value": v, "kind": "oracle", "cores": op.P, "sample": op.describe(vals[0][1])},
         "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -330,7 +398,9 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_extras:
         result["extras"] = extras(torch, c8r, synth, w)
-        result["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_tracks, ("endpoint", "zhs"))
+        single = cpu_baseline(w, args.cpu_sample_tracks, ("endpoint", "zhs"))
+        result["cpu_baseline"] = cpu_baseline_all_cores(w, 10 * args.cpu_sample_tracks, ("endpoint", "zhs"))
+        result["cpu_baseline"]["single_core"] = {k: single[k] for k in ("value", "cores", "sample")}
     if rank == 0:
         print(json.dumps(result))
     if world > 1:
@@ -393,7 +463,96 @@ def extras(torch, c8r, synth, w):
     out["bwd_fwd_ratio"] = times["bwd"] / times["fwd"]
     out["diff_workload"] = "1e6 tracks x star 8x8, 2048 x 0.2 ns, exponential atmosphere, Endpoint mixed"
     p.close()
+    del d4, tg, g
+
+    # large inclined array: 60 deg shower, 32 x 32 grid (1024 antennas), 8192 x 0.1 ns,
+    # tracks streamed through the context in 4e6-track chunks (a sample of 8e6 tracks)
+    w2 = synth.workload(2, n_tracks=8_000_000)
+    d2 = {k: torch.from_numpy(v).cuda() for k, v in synth.workload_tracks(w2).items()}
+    p = c8r.RadioProcess(w2["medium"], w2["ant_xyz"], w2["t_start_ns"], w2["n_bins"], w2["dt_ns"], "endpoint", "mixed")
+    p.set_launch_shape(0, 0, w2["chunk"])
+    o2 = torch.empty((len(w2["ant_xyz"]), 3, w2["n_bins"]), dtype=torch.float32, device="cuda")
+
+    def step2():
+        p.reset()
+        p.push(d2)
+        p.traces(out=o2)
+
+    step2()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        step2()
+    e1.record()
+    torch.cuda.synchronize()
+    out["inclined_pairs_per_s"] = 3 * 8_000_000 * len(w2["ant_xyz"]) / (e0.elapsed_time(e1) * 1e-3)
+    out["inclined_workload"] = ("8e6 tracks (2 chunks of 4e6) x 32x32 grid, 60 deg, 8192 x 0.1 ns, exponential "
+                                "atmosphere, Endpoint mixed")
+    p.close()
+    del d2, o2
+
+    # batched uneven showers: one persistent graph-captured launch against one
+    # launch per shower (64 showers; track counts scaled by 0.1 to bound the
+    # input generation time, and by 0.01 for showers small enough that
+    # per-launch costs show)
+    for scale, tag in ((0.1, "batched"), (0.01, "batched_small")):
+        r = batched_vs_separate(torch, c8r, synth, scale)
+        out[f"{tag}_pairs_per_s"] = r["batched"]
+        out[f"{tag}_separate_launches_pairs_per_s"] = r["separate"]
+        out[f"{tag}_workload"] = r["workload"]
     return out
+
+
+def batched_vs_separate(torch, c8r, synth, scale):
+    showers = synth.batched_workload(64, track_scale=scale)
+    trs = [synth.make_tracks(sh["n_tracks"], sh["seed"], sh["zenith"]) for sh in showers]
+    cat = {f: torch.from_numpy(np.concatenate([t[f] for t in trs])).cuda() for f in synth.FIELDS}
+    pairs = float(sum(sh["n_tracks"] * len(sh["ant_xyz"]) for sh in showers))
+    b = c8r.Batch(showers, synth.AIR_EXPONENTIAL, 4096, 0.2, "endpoint")
+    bo = b.new_output()
+    for _ in range(2):
+        bo.zero_()
+        b.run(cat, bo, use_graph=True)
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        bo.zero_()
+        b.run(cat, bo, use_graph=True)
+    e1.record()
+    b.sync()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 3
+    b.close()
+    procs = []
+    off = 0
+    for sh in showers:
+        n = sh["n_tracks"]
+        sub = {f: cat[f][off:off + n] for f in synth.FIELDS}
+        off += n
+        pr = c8r.RadioProcess(synth.AIR_EXPONENTIAL, sh["ant_xyz"], sh["t_start_ns"], 4096, 0.2, "endpoint", "mixed")
+        procs.append((pr, sub, torch.empty((len(sh["ant_xyz"]), 3, 4096), dtype=torch.float32, device="cuda")))
+
+    def separate():
+        for pr, sub, o in procs:
+            pr.reset()
+            pr.push(sub)
+            pr.traces(out=o)
+
+    separate()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(3):
+        separate()
+    e1.record()
+    torch.cuda.synchronize()
+    t_sep = e0.elapsed_time(e1) / 3
+    for pr, _, _ in procs:
+        pr.close()
+    return {"batched": pairs / (t_batch * 1e-3), "separate": pairs / (t_sep * 1e-3),
+            "workload": (f"64 showers, {int(sum(sh['n_tracks'] for sh in showers)):.3g} tracks, {pairs:.3g} pairs, "
+                         f"antennas 16-512, zenith 0-65 deg, Endpoint mixed")}
 
 
 if __name__ == "__main__":

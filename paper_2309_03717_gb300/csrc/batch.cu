@@ -107,29 +107,43 @@ __global__ void __launch_bounds__(kTileT, Ops::kMinBlocks) k_batch(const BatchAr
 
 using BatchOps = OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>;
 
+// resident CTAs per SM of the batch kernel for antenna tiles of a_tile
+template <class Ops>
+int batch_blocks_per_sm(int a_tile) {
+  const size_t smem = fwd_layout(C8R_MIXED, a_tile, Ops::kDefers).total;
+  auto k = k_batch<Ops>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTileT, smem) != cudaSuccess) return 1;
+  return per_sm < 1 ? 1 : per_sm;
+}
+
 // persistent grid: every CTA that fits on the device at once
 template <class Ops>
 cudaError_t launch_batch_ops(const BatchArgs& a, int sm_count, cudaStream_t st) {
   const size_t smem = fwd_layout(C8R_MIXED, a.a_tile, Ops::kDefers).total;
   auto k = k_batch<Ops>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTileT, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  const int per_sm = batch_blocks_per_sm<Ops>(a.a_tile);
   k<<<sm_count * per_sm, kTileT, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch(const BatchArgs& a, int formalism, int grid, cudaStream_t st) {
-  const bool ex = a.M.kind == C8R_EXPONENTIAL;
-  if (formalism == C8R_ENDPOINT) {
-    if (ex) return launch_batch_ops<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>>(a, grid, st);
-    return launch_batch_ops<OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>>(a, grid, st);
-  }
-  if (ex) return launch_batch_ops<OpsMixed<C8R_ZHS, C8R_EXPONENTIAL>>(a, grid, st);
-  return launch_batch_ops<OpsMixed<C8R_ZHS, C8R_UNIFORM>>(a, grid, st);
+template <class F>
+auto with_batch_ops(int formalism, int kind, F f) {
+  const bool ex = kind == C8R_EXPONENTIAL;
+  if (formalism == C8R_ENDPOINT)
+    return ex ? f(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>{}) : f(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>{});
+  return ex ? f(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL>{}) : f(OpsMixed<C8R_ZHS, C8R_UNIFORM>{});
+}
+
+cudaError_t launch_batch(const BatchArgs& a, int formalism, int sm_count, cudaStream_t st) {
+  return with_batch_ops(formalism, a.M.kind,
+                        [&](auto ops) { return launch_batch_ops<decltype(ops)>(a, sm_count, st); });
+}
+
+int batch_resident(int formalism, int kind, int a_tile, int sm_count) {
+  return sm_count *
+         with_batch_ops(formalism, kind, [&](auto ops) { return batch_blocks_per_sm<decltype(ops)>(a_tile); });
 }
 
 // ---------------------------------------------------------------------------
@@ -253,34 +267,52 @@ int upload_items(c8r_batch* b, const std::vector<WorkItem>& v) {
   return C8R_OK;
 }
 
-// tiles per item giving about `waves` items per SM for tile width a_tile
+// tiles per item giving about `waves` items per resident CTA for tile width a_tile
 int64_t tpi_for(const c8r_batch* b, int a_tile, int waves) {
   const double pair_units = (double)b->total_pairs / (kTileT * (double)a_tile);
-  int64_t t = (int64_t)(pair_units / ((double)waves * b->sm_count));
+  const int resident = batch_resident(b->formalism, b->M.kind, a_tile, b->sm_count);
+  int64_t t = (int64_t)(pair_units / ((double)waves * resident));
   return std::max<int64_t>(t, 8);
+}
+
+// zero the accumulator and ingest the tracks
+int enqueue_ingest(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
+  BatchMap map{b->d_tile_off, b->d_track_off, b->d_n_tracks, b->n_showers};
+  cudaError_t e = cudaMemsetAsync(b->d_acc, 0, b->acc_bytes, st);
+  if (e == cudaSuccess)
+    e = launch_ingest_map(C8R_MIXED, tp, map, b->total_tiles * kTileT, b->d_tiles, b->M, nullptr, st);
+  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch ingest: ") + cudaGetErrorString(e));
+  return C8R_OK;
+}
+
+// run the persistent kernel over the first n_items_limit items of the work list
+int enqueue_kernel(c8r_batch* b, int n_items_limit, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch counter: ") + cudaGetErrorString(e));
+  BatchArgs a{b->d_tiles, b->d_items, std::min(b->n_items, n_items_limit), b->d_ants, b->d_acc, b->d_counter,
+              b->d_cancel, b->d_err, b->choice.a_tile, b->M};
+  e = launch_batch(a, b->formalism, b->sm_count, st);
+  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  return C8R_OK;
 }
 
 // zero the accumulator, ingest, run the persistent kernel over the first
 // n_items_limit items, and (out != NULL) add the accumulator into out
 int enqueue(c8r_batch* b, const TrackPtrs& tp, float* out, int n_items_limit, cudaStream_t st) {
-  BatchMap map{b->d_tile_off, b->d_track_off, b->d_n_tracks, b->n_showers};
-  cudaError_t e = cudaMemsetAsync(b->d_acc, 0, b->acc_bytes, st);
-  if (e == cudaSuccess)
-    e = launch_ingest_map(C8R_MIXED, tp, map, b->total_tiles * kTileT, b->d_tiles, b->M, nullptr, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
-  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch ingest: ") + cudaGetErrorString(e));
-  BatchArgs a{b->d_tiles, b->d_items, std::min(b->n_items, n_items_limit), b->d_ants, b->d_acc, b->d_counter,
-              b->d_cancel, b->d_err, b->choice.a_tile, b->M};
-  e = launch_batch(a, b->formalism, b->sm_count, st);
-  if (e == cudaSuccess && out) e = launch_acc_to_traces(C8R_MIXED, b->d_acc, b->total_ant, b->M.n_bins,
-                                                  acc_rows(C8R_MIXED, b->formalism), out, 1, st);
-  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  int r = enqueue_ingest(b, tp, st);
+  if (r == C8R_OK) r = enqueue_kernel(b, n_items_limit, st);
+  if (r != C8R_OK) return r;
+  if (out) {
+    cudaError_t e = launch_acc_to_traces(C8R_MIXED, b->d_acc, b->total_ant, b->M.n_bins,
+                                         acc_rows(C8R_MIXED, b->formalism), out, 1, st);
+    if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch fetch: ") + cudaGetErrorString(e));
+  }
   return C8R_OK;
 }
 
 int autotune(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
   char keybuf[160];
-  std::snprintf(keybuf, sizeof keybuf, "batch:N%d:f%d:m%d:sm%d:P%lld", b->M.n_bins, b->formalism, b->M.kind,
+  std::snprintf(keybuf, sizeof keybuf, "batch2:N%d:f%d:m%d:sm%d:P%lld", b->M.n_bins, b->formalism, b->M.kind,
                 b->sm_count, (long long)(b->total_pairs >> 26));
   const std::string key = keybuf;
   TuneChoice best{};
@@ -290,23 +322,31 @@ int autotune(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
     return upload_items(b, make_items(b, best.a_tile, best.tiles_per_item));
   }
   std::vector<TuneChoice> cands;
-  for (int at : {4, 8, 16})
+  for (int at : {8, 16, 32})
     for (int waves : {4, 8, 16}) cands.push_back({at, tpi_for(b, at, waves)});
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   double best_rate = -1.0;
+  // the tracks are ingested once; each candidate's kernel is timed alone on the
+  // leading items of its work list (largest showers first) that carry a quarter
+  // of the pairs, but at least four items per resident CTA
+  int r = enqueue_ingest(b, tp, st);
+  if (r != C8R_OK) return r;
   for (const TuneChoice& c : cands) {
     b->choice = c;
     std::vector<WorkItem> v = make_items(b, c.a_tile, c.tiles_per_item);
-    // subsample: the first items of the sorted list (a mix of shower sizes)
-    const int lim = std::min<int>((int)v.size(), 4 * b->sm_count);
+    const int min_items = 4 * batch_resident(b->formalism, b->M.kind, c.a_tile, b->sm_count);
+    int lim = 0;
     double pairs = 0;
-    for (int i = 0; i < lim; ++i) pairs += (double)(v[i].t_end - v[i].t_begin) * kTileT * v[i].n_here;
-    int r = upload_items(b, v);
+    while (lim < (int)v.size() && (pairs < 0.25 * (double)b->total_pairs || lim < min_items)) {
+      pairs += (double)(v[lim].t_end - v[lim].t_begin) * kTileT * v[lim].n_here;
+      ++lim;
+    }
+    r = upload_items(b, v);
     if (r != C8R_OK) return r;
     cudaEventRecord(e0, st);
-    r = enqueue(b, tp, nullptr, lim, st);
+    r = enqueue_kernel(b, lim, st);
     if (r != C8R_OK) return r;
     cudaEventRecord(e1, st);
     if (cudaEventSynchronize(e1) != cudaSuccess) return bfail(b, C8R_ECUDA, "autotuner timing failed");
