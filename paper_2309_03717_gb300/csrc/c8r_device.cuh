@@ -112,6 +112,11 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
   p = __fmul_rn(a, b);
   e = __fmaf_rn(a, b, -p);
 }
+// Dekker's Fast2Sum: exact when the exponent of a is at least that of b
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
 
 // ---------------------------------------------------------------------------
 // TMA bulk copies and mbarriers (inline PTX, sm_90+ forms valid on sm_103a)
@@ -230,6 +235,20 @@ __device__ __forceinline__ void geo_lite(const AntRec& A, float pxh, float pyh, 
 
 // R = |d| in float-float: the three exact squares are summed with TwoSum, then
 // one Newton step corrects the FP32 estimate R0 (its square is formed exactly)
+// the same for an FP32-exact point (no low part)
+__device__ __forceinline__ void geo_lite(const AntRec& A, float px, float py, float pz, GeoM& g) {
+  two_sum(A.xh, -px, g.s[0], g.e[0]);
+  two_sum(A.yh, -py, g.s[1], g.e[1]);
+  two_sum(A.zh, -pz, g.s[2], g.e[2]);
+  g.e[0] = __fadd_rn(g.e[0], A.xl);
+  g.e[1] = __fadd_rn(g.e[1], A.yl);
+  g.e[2] = __fadd_rn(g.e[2], A.zl);
+  const float S = __fmaf_rn(g.s[0], g.s[0], __fmaf_rn(g.s[1], g.s[1], __fmul_rn(g.s[2], g.s[2])));
+  g.y = rsqrtf(S);
+  g.R0 = __fmul_rn(S, g.y);
+  g.R1 = 0.0f;
+}
+
 __device__ __forceinline__ void geo_refine(GeoM& g) {
   float p0, q0, p1, q1, p2, q2;
   two_prod(g.s[0], g.s[0], p0, q0);
@@ -297,7 +316,7 @@ __device__ __forceinline__ ff arrival_mixed(const MedParams& M, const AntRec& A,
     two_prod(w, M.cN_h, v, ve);
     ve = __fmaf_rn(w, M.cN_l, __fmaf_rn(we, M.cN_h, ve));
     float p2, pe2;
-    two_sum(p, v, p2, pe2);
+    fast_two_sum(p, v, p2, pe2);  // |v| = (n_avg - 1)|p| < |p|
     p = p2;
     pe = __fadd_rn(pe, __fadd_rn(pe2, ve));
   }

@@ -227,7 +227,7 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
 #pragma unroll 1
         for (int ant = 0; ant < n_here; ++ant) {
           GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * row_stride, N};
-          if (Ops::pair_main(tr, ant_s[ant], M, sink) && Ops::kDefers)
+          if (Ops::pair_main(tr, Ops::load_ant(ant_s + ant), M, sink) && Ops::kDefers)
             queue[atomicAdd(&q_cnt[st], 1)] = (uint16_t)(l | (ant << 7));
         }
       }
@@ -249,7 +249,7 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
         Ops::load(smem + st * L.stage_bytes, e & (kTileT - 1), M, tr);
         const int ant = e >> 7;
         GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * row_stride, N};
-        Ops::pair_deferred(tr, ant_s[ant], M, sink);
+        Ops::pair_deferred(tr, Ops::load_ant(ant_s + ant), M, sink);
       }
       __syncthreads();  // slot st is refilled below; its counter is next used two tiles on
       if (tid == 0) q_cnt[st] = 0;

@@ -80,6 +80,8 @@ struct OpsF64 {
   static constexpr int kBwdMinBlocks = 1;
   static constexpr int kAccRows = 1;      // no box deposits
 
+  static __device__ __forceinline__ AntRec load_ant(const AntRec* p) { return *p; }
+
   static __device__ __forceinline__ void load(const void* Tv, int l, const MedParams&, TrackD& t) {
     t.T = static_cast<const double*>(Tv);
     t.l = l;

@@ -88,8 +88,8 @@ struct EndpointEvalM {
 // (1) propagator and field at both endpoints; false when an emission point
 // sits on the antenna (outside the domain of the formula)
 __device__ __forceinline__ bool endpoint_fields(const TrackM& t, const AntRec& A, EndpointEvalM& e) {
-  geo_lite(A, t.x0, t.y0, t.z0, 0.f, 0.f, 0.f, e.g0);
-  geo_lite(A, t.x1, t.y1, t.z1, 0.f, 0.f, 0.f, e.g1);
+  geo_lite(A, t.x0, t.y0, t.z0, e.g0);
+  geo_lite(A, t.x1, t.y1, t.z1, e.g1);
   if (e.g0.R0 == 0.0f || e.g1.R0 == 0.0f) return false;
   field_mixed(e.g0, t.bx, t.by, t.bz, t.bmag, t.om0, __fadd_rn(1.0f, t.nm1_0), e.f0);
   field_mixed(e.g1, t.bx, t.by, t.bz, t.bmag, t.om1, __fadd_rn(1.0f, t.nm1_1), e.f1);
@@ -167,6 +167,17 @@ struct OpsMixed {
   static constexpr int kBwdMinBlocks = 3;  // adjoint CTAs (256 threads) per SM the registers are set for
   // ZHS: a second accumulator row holds the edges of box deposits
   static constexpr int kAccRows = FORM == C8R_ZHS ? 2 : 1;
+
+  // the float-float part of an antenna record, as three 16-byte shared-memory loads
+  static __device__ __forceinline__ AntRec load_ant(const AntRec* p) {
+    const float4* f = reinterpret_cast<const float4*>(&p->xh);
+    const float4 a = f[0], b = f[1], c = f[2];
+    AntRec r;
+    r.xh = a.x; r.yh = a.y; r.zh = a.z; r.xl = a.w;
+    r.yl = b.x; r.zl = b.y; r.tauh = b.z; r.taul = b.w;
+    r.Eah = c.x; r.Eal = c.y;
+    return r;
+  }
 
   static __device__ __forceinline__ void load(const void* Tv, int l, const MedParams& M, TrackM& t) {
     load_track_mixed<FORM, KIND>(static_cast<const float*>(Tv), l, M, t);
