@@ -43,10 +43,10 @@ FP32_LANES_PER_SM = 128
 # and amplitude): 56 arithmetic + 6 special-function operations
 ALG_OPS_PER_ENDPOINT_PAIR = 62
 # DRAM bytes (read + write) per pair of the Endpoint forward kernel: one ncu
-# capture of a 4e6-track x 160-antenna launch (6.4e8 pairs) read 407.7 MB and
-# wrote 5.4 MB; the traffic is the staged track tiles, so it scales with the
+# capture of a 4e6-track x 160-antenna launch (6.4e8 pairs) read 407.6 MB and
+# wrote 5.3 MB; the traffic is the staged track tiles, so it scales with the
 # pairs at a fixed antenna count.  Set to None when the kernel changes.
-DRAM_BYTES_PER_ENDPOINT_PAIR = 413.1e6 / 6.4e8
+DRAM_BYTES_PER_ENDPOINT_PAIR = 412.9e6 / 6.4e8
 
 
 def parse():
