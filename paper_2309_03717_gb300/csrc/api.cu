@@ -572,10 +572,10 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
     c8r_track_grads o = *out;
     void** og[11] = {&o.x0, &o.y0, &o.z0, &o.x1, &o.y1, &o.z1, &o.t0, &o.t1, &o.bx, &o.by, &o.bz};
     for (int k = 0; k < 11; ++k) *og[k] = static_cast<char*>(*og[k]) + off * es;
-    BwdArgs ba{c->d_tiles, m, c->d_ants, c->n_ant, c->d_gbm, o, ant_grad, dN0, c->M};
-    int64_t want_blocks = (m + 255) / 256;
-    const int blocks = (int)(want_blocks < 8LL * c->sm_count ? want_blocks : 8LL * c->sm_count);
-    e = (c->precision == C8R_FP64) ? launch_backward_f64(ba, blocks, st) : launch_backward_mixed(ba, blocks, st);
+    BwdArgs ba{c->d_tiles, m, (m + kTileT - 1) / kTileT, c->d_ants, c->n_ant, c->shape.a_tile, c->d_gbm, o,
+               ant_grad, dN0, c->d_err, FwdGrid{}, c->M};
+    e = (c->precision == C8R_FP64) ? launch_backward_f64(ba, c->shape, c->sm_count, st)
+                                   : launch_backward_mixed(ba, c->shape, c->sm_count, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "backward launch");
   }
   return C8R_OK;

@@ -55,8 +55,8 @@ cudaError_t launch_arrivals_f64(int formalism, const void* tiles, int64_t n, con
                                 const MedParams& M, int32_t* branch, int32_t* bin, float* frac, cudaStream_t st);
 cudaError_t launch_arrivals_mixed(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,
                                   const MedParams& M, int32_t* branch, int32_t* bin, float* frac, cudaStream_t st);
-cudaError_t launch_backward_f64(const BwdArgs& a, int blocks, cudaStream_t st);
-cudaError_t launch_backward_mixed(const BwdArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_backward_f64(BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st);
+cudaError_t launch_backward_mixed(BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st);
 
 // helpers shared by the context and the batch runner
 void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, double dt_ns, double eps_C);

@@ -92,12 +92,16 @@ struct FwdArgs {
 struct BwdArgs {
   const void* tiles;
   int64_t n;          // tracks
+  int64_t n_tiles;    // derived tiles holding them
   const AntRec* ants;
   int n_ant;
+  int a_tile;
   const void* G;      // dL/dtraces, bin-major [n_ant][n_bins] of (x, y, z, 0) accumulator elements
   c8r_track_grads out;
   double* ant_grad;   // [n_ant][3]
   double* dN0;
+  int* err;
+  FwdGrid g;          // set by the launcher
   MedParams M;
 };
 
@@ -381,114 +385,145 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-constexpr int kBwdThreads = 256;
-constexpr int kBwdAntBlock = 16;  // antennas between two passes over the set-aside pairs
-
-// dynamic shared memory of k_backward: antenna gradients [n_ant][3] + dN0, and
-// (Ops::kDefers) the CTA's track gradients [11][kBwdThreads] and the queue of
-// set-aside pairs (track slot | antenna within the block << 8)
-template <class Ops>
-size_t bwd_smem_bytes(int n_ant) {
-  using acc_t = typename Ops::acc_t;
-  size_t b = sizeof(acc_t) * ((3 * (size_t)n_ant + 1 + 3) / 4 * 4);
-  if (Ops::kDefers) b += sizeof(acc_t) * 11 * kBwdThreads + sizeof(uint16_t) * kBwdThreads * kBwdAntBlock;
-  return b;
+// Adjoint, laid out like the forward pass: a CTA owns an antenna tile and a
+// range of derived-track tiles streamed through the TMA ring; each thread holds
+// one track of the staged tile and walks the tile's antennas, keeping the
+// track's 11 gradients in registers and adding them to the output with one
+// reduction per gradient and antenna tile.  Antenna gradients are warp-reduced
+// into shared memory and added to the FP64 output once per CTA.  Pairs set
+// aside by Ops::adj_main (Endpoint near the Cherenkov angle) are evaluated
+// together after the main pass over each tile, in full warps.
+template <typename T>
+__device__ __forceinline__ void add_track_grads(const c8r_track_grads& out, int64_t i, const T tg[11]) {
+  T* o[11] = {(T*)out.x0, (T*)out.y0, (T*)out.z0, (T*)out.x1, (T*)out.y1, (T*)out.z1,
+              (T*)out.t0, (T*)out.t1, (T*)out.bx, (T*)out.by, (T*)out.bz};
+#pragma unroll
+  for (int k = 0; k < 11; ++k)
+    if (tg[k] != T(0)) atomicAdd(o[k] + i, tg[k]);
 }
 
-// Adjoint: one thread per track, looping over all antennas; track gradients
-// stay in registers, antenna gradients are warp-reduced into shared memory.
-// Pairs set aside by Ops::adj_main (Endpoint near the Cherenkov angle) are
-// evaluated together after every kBwdAntBlock antennas, in full warps; their
-// track gradients go through shared memory.
 template <class Ops>
-__global__ void __launch_bounds__(kBwdThreads, Ops::kBwdMinBlocks) k_backward(const BwdArgs a) {
+__global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const BwdArgs a) {
   using acc_t = typename Ops::acc_t;
-  extern __shared__ __align__(16) unsigned char smem_b[];
-  acc_t* sg = reinterpret_cast<acc_t*>(smem_b);  // [n_ant][3] + dN0
-  acc_t* tg_s = sg + (3 * a.n_ant + 1 + 3) / 4 * 4;
-  uint16_t* queue = reinterpret_cast<uint16_t*>(tg_s + 11 * kBwdThreads);
-  __shared__ int q_n;
-  const int tid = threadIdx.x;
-  for (int k = tid; k < 3 * a.n_ant + 1; k += blockDim.x) sg[k] = acc_t(0);
-  if (tid == 0) q_n = 0;
-  __syncthreads();
-  const int N = a.M.n_bins;
   using acc4 = typename AccOf<acc_t>::type;
-  const acc4* G = static_cast<const acc4*>(a.G);
-  acc_t dn_acc = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // the loop bounds are uniform over the CTA (barriers inside); whole warps
-  // stay together for the reductions
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += stride) {
-    const int64_t i = base + tid;
-    const bool valid = i < a.n;
-    const unsigned char* T = static_cast<const unsigned char*>(a.tiles) +
-                             ((valid ? i : 0) / kTileT) * (int64_t)Ops::kTileBytes;
-    const int l = (int)((valid ? i : 0) % kTileT);
-    acc_t tg[11];
-#pragma unroll
-    for (int k = 0; k < 11; ++k) tg[k] = acc_t(0);
-    if (Ops::kDefers) {
-#pragma unroll
-      for (int k = 0; k < 11; ++k) tg_s[k * kBwdThreads + tid] = acc_t(0);
+  extern __shared__ __align__(128) unsigned char smem[];
+  const MedParams& M = a.M;
+  const FwdLayout L = fwd_layout(Ops::kPrec, a.a_tile, Ops::kDefers);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+  AntRec* ant_s = reinterpret_cast<AntRec*>(smem + L.ant_off);
+  uint16_t* queue = reinterpret_cast<uint16_t*>(smem + L.q_off);
+  __shared__ acc_t sg[3 * kMaxATile + 1];  // antenna gradients of the tile, then dN0
+  __shared__ int q_cnt[2];
+  int ant_tile;
+  int64_t range;
+  a.g.decode(blockIdx.x, ant_tile, range);
+  const int ant0 = ant_tile * a.a_tile;
+  const int n_here = min(a.a_tile, a.n_ant - ant0);
+  const int64_t t_begin = range * a.g.tiles_per_range;
+  const int64_t t_end = min(t_begin + a.g.tiles_per_range, a.n_tiles);
+  if (t_begin >= t_end || n_here <= 0) return;  // uniform over the CTA
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int N = M.n_bins;
+  const acc4* G = static_cast<const acc4*>(a.G) + (size_t)ant0 * N;
+  for (int i = tid; i < n_here; i += nthr) ant_s[i] = a.ants[ant0 + i];
+  for (int i = tid; i < 3 * n_here + 1; i += nthr) sg[i] = acc_t(0);
+  const uint32_t bytes = (uint32_t)L.stage_bytes;
+  const unsigned char* src = static_cast<const unsigned char*>(a.tiles);
+  if (tid == 0) {
+    q_cnt[0] = 0;
+    q_cnt[1] = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+    for (int s = 0; s < 2 && t_begin + s < t_end; ++s) {
+      mbar_expect_tx(&bar[s], bytes);
+      bulk_g2s(smem + s * L.stage_bytes, src + (t_begin + s) * (int64_t)bytes, bytes, &bar[s]);
     }
-    typename Ops::Track tr;
-    Ops::load(T, l, a.M, tr);
-    const bool live = valid && Ops::live(tr);
-    for (int ant0 = 0; ant0 < a.n_ant; ant0 += kBwdAntBlock) {
-      const int ant_end = min(ant0 + kBwdAntBlock, a.n_ant);
-      for (int ant = ant0; ant < ant_end; ++ant) {
-        const AntRec A = a.ants[ant];
+  }
+  __syncthreads();
+  acc_t dn_acc = 0;
+  int64_t it = 0;
+  for (int64_t t = t_begin; t < t_end; ++t, ++it) {
+    const int st = (int)(it & 1);
+    const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((it >> 1) & 1));
+    const unsigned char* stage = smem + st * L.stage_bytes;
+    // every lane walks the antennas (dead slots included) so the warp reductions see all 32
+    for (int l = tid; l < kTileT; l += nthr) {
+      const int64_t i = t * kTileT + l;
+      typename Ops::Track tr;
+      Ops::load(stage, l, M, tr);
+      const bool live = ok && i < a.n && Ops::live(tr);
+      acc_t tg[11];
+#pragma unroll
+      for (int k = 0; k < 11; ++k) tg[k] = acc_t(0);
+#pragma unroll 1
+      for (int ant = 0; ant < n_here; ++ant) {
         acc_t ga[3] = {0, 0, 0};
-        if (live && Ops::adj_main(tr, A, a.M, G + (size_t)ant * N, tg, ga, dn_acc) && Ops::kDefers)
-          queue[atomicAdd(&q_n, 1)] = (uint16_t)(tid | ((ant - ant0) << 8));
+        if (live && Ops::adj_main(tr, Ops::load_ant(ant_s + ant), M, G + (size_t)ant * N, tg, ga, dn_acc) &&
+            Ops::kDefers)
+          queue[atomicAdd(&q_cnt[st], 1)] = (uint16_t)(l | (ant << 7));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          acc_t v = warp_sum(ga[c]);
+          const acc_t v = warp_sum(ga[c]);
           if ((tid & 31) == 0 && v != acc_t(0)) atomicAdd(&sg[3 * ant + c], v);
         }
       }
-      if (Ops::kDefers) {
-        __syncthreads();  // queue complete (and the track-gradient slots zeroed)
-        const int nq = q_n;
-        for (int q = tid; q < nq; q += blockDim.x) {
-          const int e = queue[q];
-          const int slot = e & 0xff, ant = ant0 + (e >> 8);
-          const int64_t j = base + slot;
-          typename Ops::Track tj;
-          Ops::load(static_cast<const unsigned char*>(a.tiles) + (j / kTileT) * (int64_t)Ops::kTileBytes,
-                    (int)(j % kTileT), a.M, tj);
-          acc_t tgl[11];
-#pragma unroll
-          for (int k = 0; k < 11; ++k) tgl[k] = acc_t(0);
-          acc_t gal[3] = {0, 0, 0};
-          Ops::adj_deferred(tj, a.ants[ant], a.M, G + (size_t)ant * N, tgl, gal, dn_acc);
-#pragma unroll
-          for (int k = 0; k < 11; ++k)
-            if (tgl[k] != acc_t(0)) atomicAdd(&tg_s[k * kBwdThreads + slot], tgl[k]);
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            if (gal[c] != acc_t(0)) atomicAdd(&sg[3 * ant + c], gal[c]);
-        }
-        __syncthreads();  // every thread has read q_n
-        if (tid == 0) q_n = 0;
-        __syncthreads();  // reset visible before the next entries
-      }
+      if (live) add_track_grads<acc_t>(a.out, i, tg);
     }
-    if (valid) {
-      acc_t* o[11] = {(acc_t*)a.out.x0, (acc_t*)a.out.y0, (acc_t*)a.out.z0, (acc_t*)a.out.x1, (acc_t*)a.out.y1,
-                      (acc_t*)a.out.z1, (acc_t*)a.out.t0, (acc_t*)a.out.t1, (acc_t*)a.out.bx, (acc_t*)a.out.by,
-                      (acc_t*)a.out.bz};
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicExch(a.err, kErrWaitTimeout);
+        for (int64_t j = it; j < it + 2 && j - it + t < t_end; ++j) mbar_wait_bounded(&bar[j & 1], (uint32_t)((j >> 1) & 1));
+      }
+      return;
+    }
+    if (Ops::kDefers) {
+      const int nq = q_cnt[st];
+      for (int q = tid; q < nq; q += nthr) {
+        const int e = queue[q];
+        const int l = e & (kTileT - 1), ant = e >> 7;
+        typename Ops::Track tr;
+        Ops::load(stage, l, M, tr);
+        acc_t tg[11];
 #pragma unroll
-      for (int k = 0; k < 11; ++k) o[k][i] += tg[k] + (Ops::kDefers ? tg_s[k * kBwdThreads + tid] : acc_t(0));
+        for (int k = 0; k < 11; ++k) tg[k] = acc_t(0);
+        acc_t ga[3] = {0, 0, 0};
+        Ops::adj_deferred(tr, Ops::load_ant(ant_s + ant), M, G + (size_t)ant * N, tg, ga, dn_acc);
+        add_track_grads<acc_t>(a.out, t * kTileT + l, tg);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (ga[c] != acc_t(0)) atomicAdd(&sg[3 * ant + c], ga[c]);
+      }
+      __syncthreads();  // slot st is refilled below; its counter is next used two tiles on
+      if (tid == 0) q_cnt[st] = 0;
+    }
+    if (tid == 0 && t + 2 < t_end) {
+      mbar_expect_tx(&bar[st], bytes);
+      bulk_g2s(smem + st * L.stage_bytes, src + (t + 2) * (int64_t)bytes, bytes, &bar[st]);
     }
   }
-  acc_t d = warp_sum(dn_acc);
-  if ((tid & 31) == 0 && d != acc_t(0)) atomicAdd(&sg[3 * a.n_ant], d);
+  const acc_t d = warp_sum(dn_acc);
+  if ((tid & 31) == 0 && d != acc_t(0)) atomicAdd(&sg[3 * n_here], d);
   __syncthreads();
-  for (int k = tid; k < 3 * a.n_ant; k += blockDim.x)
-    if (sg[k] != acc_t(0)) atomicAdd(&a.ant_grad[k], (double)sg[k]);
-  if (tid == 0 && sg[3 * a.n_ant] != acc_t(0)) atomicAdd(a.dN0, (double)sg[3 * a.n_ant]);
+  for (int k = tid; k < 3 * n_here; k += nthr)
+    if (sg[k] != acc_t(0)) atomicAdd(&a.ant_grad[3 * (size_t)ant0 + k], (double)sg[k]);
+  if (tid == 0 && sg[3 * n_here] != acc_t(0)) atomicAdd(a.dN0, (double)sg[3 * n_here]);
+}
+
+template <class Ops>
+cudaError_t launch_backward_ops(BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st) {
+  const size_t smem = fwd_layout(Ops::kPrec, a.a_tile, Ops::kDefers).total;
+  auto k = k_backward<Ops>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTileT, smem);
+  if (e != cudaSuccess) return e;
+  FwdArgs f{a.tiles, a.n_tiles, a.ants, a.n_ant, a.a_tile, nullptr, a.err, FwdGrid{}, a.M};
+  const int64_t ctas = forward_grid(f, shape, sm_count * (per_sm < 1 ? 1 : per_sm), sizeof(typename AccOf<typename Ops::acc_t>::type));
+  a.g = f.g;
+  k<<<(unsigned)ctas, kTileT, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 // gradient of one deposit l = kappa (g.V)/(D R) with respect to d = x_a - x_e,

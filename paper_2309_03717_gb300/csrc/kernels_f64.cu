@@ -31,16 +31,8 @@ cudaError_t launch_arrivals_f64(int formalism, const void* tiles, int64_t n, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_backward_f64(const BwdArgs& a, int blocks, cudaStream_t st) {
-  using O = OpsF64<C8R_ENDPOINT>;
-  const size_t smem = bwd_smem_bytes<O>(a.n_ant);
-  auto k = k_backward<O>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  k<<<blocks, kBwdThreads, smem, st>>>(a);
-  return cudaGetLastError();
+cudaError_t launch_backward_f64(BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st) {
+  return launch_backward_ops<OpsF64<C8R_ENDPOINT>>(a, shape, sm_count, st);
 }
 
 }  // namespace c8r

@@ -179,20 +179,10 @@ cudaError_t launch_arrivals_mixed(int formalism, const void* tiles, int64_t n, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_backward_mixed(const BwdArgs& a, int blocks, cudaStream_t st) {
-  auto go = [&](auto ops) {
-    using O = decltype(ops);
-    const size_t smem = bwd_smem_bytes<O>(a.n_ant);
-    auto k = k_backward<O>;
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    k<<<blocks, kBwdThreads, smem, st>>>(a);
-    return cudaGetLastError();
-  };
-  if (a.M.kind == C8R_EXPONENTIAL) return go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>{});
-  return go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>{});
+cudaError_t launch_backward_mixed(BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st) {
+  if (a.M.kind == C8R_EXPONENTIAL)
+    return launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>>(a, shape, sm_count, st);
+  return launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>>(a, shape, sm_count, st);
 }
 
 }  // namespace c8r

@@ -77,7 +77,7 @@ struct OpsF64 {
   static constexpr int kTileBytes = kTileBytesF64;
   static constexpr int kMinBlocks = 4;
   static constexpr bool kDefers = false;  // every pair is evaluated in the main pass
-  static constexpr int kBwdMinBlocks = 1;
+  static constexpr int kBwdMinBlocks = 2;
   static constexpr int kAccRows = 1;      // no box deposits
 
   static __device__ __forceinline__ AntRec load_ant(const AntRec* p) { return *p; }

@@ -164,7 +164,7 @@ struct OpsMixed {
   // Endpoint: the near-Cherenkov pairs (a minority, spread over most warps)
   // are set aside by the main pass and evaluated together afterwards
   static constexpr bool kDefers = FORM == C8R_ENDPOINT;
-  static constexpr int kBwdMinBlocks = 3;  // adjoint CTAs (256 threads) per SM the registers are set for
+  static constexpr int kBwdMinBlocks = 6;  // adjoint CTAs (128 threads) per SM the registers are set for
   // ZHS: a second accumulator row holds the edges of box deposits
   static constexpr int kAccRows = FORM == C8R_ZHS ? 2 : 1;
 
