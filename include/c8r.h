@@ -174,16 +174,18 @@ int c8r_fetch_traces(c8r_ctx* ctx, void* dst, int dst_is_device, int reset, void
 /* Zero the accumulated traces and the statistics. */
 int c8r_reset(c8r_ctx* ctx, void* cuda_stream);
 
-/* Adjoint of c8r_push_tracks for the Endpoint formalism (not in the paper; a
- * hand-written reverse pass).  Given the same tracks and grad_traces = dL/dtraces
+/* Adjoint of c8r_push_tracks (not in the paper; a hand-written reverse pass),
+ * for both formalisms.  Given the same tracks and grad_traces = dL/dtraces
  * (DEVICE, layout and element type of c8r_fetch_traces), ACCUMULATES dL/d(track
- * inputs) into out_tracks, dL/d(antenna positions) into out_ant_grad (DEVICE FP64
- * [n_ant][3]) and dL/dN0 into *out_dN0 (DEVICE FP64 scalar; for a uniform medium
- * the derivative with respect to n - 1).  Bin indices and the near-Cherenkov
- * branch are held fixed, so the time derivatives are zero.  The per-pair geometry
- * is recomputed, not stored.  The first call allocates a bin-major copy of
- * grad_traces inside the context (ENOMEM if that fails).  EINVAL for a ZHS
- * context or mismatched dtypes. */
+ * inputs) into out_tracks (times per ns), dL/d(antenna positions) into
+ * out_ant_grad (DEVICE FP64 [n_ant][3]) and dL/dN0 into *out_dN0 (DEVICE FP64
+ * scalar; for a uniform medium the derivative with respect to n - 1).  Bin
+ * indices and the near-Cherenkov branch are held fixed: the Endpoint deposits
+ * then do not depend on the times (zero time gradients), while the ZHS deposits
+ * do, through the fractions of the arrival interval in its first and last bin.
+ * The per-pair geometry is recomputed, not stored.  The first call allocates a
+ * bin-major copy of grad_traces (and, for ZHS, its running sums over the bins)
+ * inside the context (ENOMEM if that fails).  EINVAL for mismatched dtypes. */
 int c8r_backward(c8r_ctx* ctx, const c8r_tracks* tracks, int64_t n, const void* grad_traces,
                  const c8r_track_grads* out_tracks, double* out_ant_grad, double* out_dN0, void* cuda_stream);
 

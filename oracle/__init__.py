@@ -78,6 +78,10 @@ def _load():
         lib.oracle_backward.argtypes = [P(_Tracks), ctypes.c_int64, P(_Antennas), P(_Medium), ctypes.c_double,
                                         P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
                                         P(ctypes.c_double)]
+        lib.oracle_backward_zhs.restype = None
+        lib.oracle_backward_zhs.argtypes = [P(_Tracks), ctypes.c_int64, P(_Antennas), P(_Medium),
+                                            P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+                                            P(ctypes.c_double)]
         lib.oracle_propagate.restype = None
         lib.oracle_propagate.argtypes = [P(_Medium), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double)]
         lib.oracle_filter.restype = ctypes.c_int64
@@ -139,8 +143,8 @@ def arrivals(tracks, ant_xyz, t_ref, n_bins, dt, medium, formalism=ENDPOINT, eps
     return br, u
 
 
-def backward(tracks, ant_xyz, t_ref, n_bins, dt, medium, grad_traces, eps_C=1e-3):
-    """Endpoint adjoint: (track_grad [n, 11], ant_grad [n_ant, 3], dN0)."""
+def backward(tracks, ant_xyz, t_ref, n_bins, dt, medium, grad_traces, eps_C=1e-3, formalism=ENDPOINT):
+    """Adjoint of forward(): (track_grad [n, 11], ant_grad [n_ant, 3], dN0)."""
     lib = _load()
     p = _Pack(tracks, ant_xyz, t_ref, n_bins, dt, medium)
     G = np.ascontiguousarray(grad_traces, dtype=np.float64)
@@ -149,8 +153,12 @@ def backward(tracks, ant_xyz, t_ref, n_bins, dt, medium, grad_traces, eps_C=1e-3
     tg = np.zeros((p.n, 11), dtype=np.float64)
     ag = np.zeros((len(p.xyz), 3), dtype=np.float64)
     dn = np.zeros(1, dtype=np.float64)
-    lib.oracle_backward(ctypes.byref(p.T), p.n, ctypes.byref(p.A), ctypes.byref(p.M), float(eps_C), _dptr(G),
-                        _dptr(tg), _dptr(ag), _dptr(dn))
+    if formalism == ZHS:
+        lib.oracle_backward_zhs(ctypes.byref(p.T), p.n, ctypes.byref(p.A), ctypes.byref(p.M), _dptr(G), _dptr(tg),
+                                _dptr(ag), _dptr(dn))
+    else:
+        lib.oracle_backward(ctypes.byref(p.T), p.n, ctypes.byref(p.A), ctypes.byref(p.M), float(eps_C), _dptr(G),
+                            _dptr(tg), _dptr(ag), _dptr(dn))
     return tg, ag, float(dn[0])
 
 

@@ -37,6 +37,10 @@
  *  G  adjoint (Endpoint): gradient of a scalar loss whose derivative with respect
  *     to the traces is given, with every bin index and branch decision held
  *     fixed (the traces are piecewise constant in the times).
+ *  GZ adjoint (ZHS): the same with the bins of the two interval ends held fixed;
+ *     the fractions of the interval that fall in its first and last bin vary
+ *     with the interval ends, so the ZHS traces are piecewise linear in the
+ *     arrival time and the times get non-zero gradients.
  *
  * Parity unpinned: the value eps_C = 1e-3 itself (any value gives a consistent
  * result; the tests pin the branch's formula, not the threshold), and the choice
@@ -413,6 +417,143 @@ void oracle_backward(const or_tracks* T, int64_t n, const or_antennas* A, const 
       }
       /* d/dt0 and d/dt1 stay zero: with bins held fixed the deposits do not
          depend on the times (reading G). */
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* reading GZ: reverse-mode gradient of the ZHS traces.  Per pair, with the   */
+/* midpoint path (d = x_a - x_m, R, rhat, c = beta.rhat, D = 1 - n_src c,     */
+/* beta_perp = beta - c rhat) the deposit into bin k is A w_k, with          */
+/*   A   = K_A beta_perp dt_e / (R dt)           (the one-bin deposit),       */
+/*   w_k = |[t_lo, t_hi] & bin k| / (t_hi - t_lo)  (1 for a one-bin interval), */
+/*   t_lo, t_hi = tau -/+ |D| dt_e / 2,  tau = (t_m - t_ref) + n_avg R / c.   */
+/* With S = sum_k w_k G_k, g_lo/g_hi = A.G at the first/last bin (0 outside  */
+/* the window) and W = t_hi - t_lo, for a multi-bin interval                 */
+/*   dL/dtau  = (g_hi - g_lo) / W,  dL/dhalf = (g_hi + g_lo - 2 A.S) / W,     */
+/* and both vanish for a one-bin interval (w = 1).  The rest is the chain     */
+/* rule through A, |D|, tau and the path (n_avg R = R + F, F the             */
+/* refractivity part of the optical path).                                   */
+static void refractive_part(const or_medium* m, const double xm[3], const double xa[3], double R, double* F,
+                            double* dF_dR, double* dF_dzm, double* dF_dza, double* dF_dN0) {
+  if (m->kind == OR_UNIFORM) {
+    *F = (m->n - 1.0) * R;
+    *dF_dR = m->n - 1.0;
+    *dF_dzm = *dF_dza = 0.0;
+    *dF_dN0 = R; /* d/d(n - 1) */
+    return;
+  }
+  /* F = N0 E_m R rho(x), rho(x) = (1 - exp(-x))/x, x = (z_a - z_m)/H; rho' = (exp(-x) - rho)/x */
+  double E = exp(-xm[2] / m->H);
+  double x = (xa[2] - xm[2]) / m->H;
+  double rho, drho;
+  if (fabs(x) < 1e-3) {
+    rho = 1.0 - x / 2.0 + x * x / 6.0 - x * x * x / 24.0;
+    drho = -0.5 + x / 3.0 - x * x / 8.0 + x * x * x / 30.0;
+  } else {
+    rho = -expm1(-x) / x;
+    drho = (exp(-x) - rho) / x;
+  }
+  *F = m->N0 * E * R * rho;
+  *dF_dR = m->N0 * E * rho;
+  *dF_dzm = -m->N0 * R * E * (rho + drho) / m->H;
+  *dF_dza = m->N0 * R * E * drho / m->H;
+  *dF_dN0 = E * R * rho;
+}
+
+/* G: dL/dtraces [n_ant][3][n_bins].  Outputs are ACCUMULATED, as for
+   oracle_backward (track_grad [n][11], ant_grad [n_ant][3], dN0). */
+void oracle_backward_zhs(const or_tracks* T, int64_t n, const or_antennas* A, const or_medium* m, const double* G,
+                         double* track_grad, double* ant_grad, double* dN0) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (!track_kept(T, i)) continue;
+    double x0[3], x1[3], xm[3], beta[3];
+    track_points(T, i, x0, x1, xm, beta);
+    double KA = K_zhs(T->q[i]);
+    double t0 = T->t0[i], t1 = T->t1[i], dte = t1 - t0, tm = 0.5 * (t0 + t1);
+    double* tg = track_grad + 11 * i;
+    for (int a = 0; a < A->n_ant; ++a) {
+      const double* xa = A->xyz + 3 * (int64_t)a;
+      const double* G_a = G + (int64_t)a * 3 * A->n_bins;
+      double dt = A->dt, t_ref = A->t_ref[a];
+      int nb = A->n_bins;
+      or_path pm;
+      propagate(m, xm, xa, &pm);
+      double c = dot3(beta, pm.rh);
+      double D = 1.0 - pm.n_src * c;
+      double bperp[3], Av[3];
+      for (int k = 0; k < 3; ++k) {
+        bperp[k] = beta[k] - c * pm.rh[k];
+        Av[k] = KA * bperp[k] * dte / (pm.R * dt);
+      }
+      double tau = (tm - t_ref) + pm.n_avg * pm.R / OR_C_LIGHT;
+      double half = fabs(D) * dte / 2.0;
+      double t_lo = tau - half, t_hi = tau + half;
+      int64_t k_lo = (int64_t)floor(t_lo / dt), k_hi = (int64_t)floor(t_hi / dt);
+      /* S = sum_k w_k G_k over the bins inside the window */
+      double S[3] = {0.0, 0.0, 0.0}, g[3];
+      double dL_dtau = 0.0, dL_dhalf = 0.0;
+      if (k_lo == k_hi) {
+        gather_g(G_a, nb, k_lo, S);
+      } else {
+        double W = t_hi - t_lo;
+        int64_t kb = k_lo < 0 ? 0 : k_lo, ke = k_hi > nb - 1 ? nb - 1 : k_hi;
+        for (int64_t k = kb; k <= ke; ++k) {
+          double o = fmin(t_hi, (double)(k + 1) * dt) - fmax(t_lo, (double)k * dt);
+          if (o <= 0.0) continue;
+          gather_g(G_a, nb, k, g);
+          for (int q = 0; q < 3; ++q) S[q] += (o / W) * g[q];
+        }
+        gather_g(G_a, nb, k_lo, g);
+        double g_lo = dot3(Av, g);
+        gather_g(G_a, nb, k_hi, g);
+        double g_hi = dot3(Av, g);
+        double AS = dot3(Av, S);
+        dL_dtau = (g_hi - g_lo) / W;
+        dL_dhalf = (g_hi + g_lo - 2.0 * AS) / W;
+      }
+      double AS = dot3(Av, S);
+      if (AS == 0.0 && dL_dtau == 0.0 && dL_dhalf == 0.0) continue;
+      /* through A = K_A beta_perp dt_e / (R dt) */
+      double sb[3], dL_dbeta[3], dL_drh[3];
+      for (int k = 0; k < 3; ++k) sb[k] = KA * dte / (pm.R * dt) * S[k];
+      double sbr = dot3(sb, pm.rh);
+      for (int k = 0; k < 3; ++k) {
+        dL_dbeta[k] = sb[k] - sbr * pm.rh[k];
+        dL_drh[k] = -c * sb[k] - sbr * beta[k];
+      }
+      double dL_ddte = AS / dte;
+      double dL_dR = -AS / pm.R;
+      /* through half = |D| dt_e / 2 */
+      double sgn = D < 0.0 ? -1.0 : 1.0;
+      double dL_dD = dL_dhalf * sgn * dte / 2.0;
+      dL_ddte += dL_dhalf * fabs(D) / 2.0;
+      /* D = 1 - n_src c */
+      double dL_dnsrc = -c * dL_dD;
+      for (int k = 0; k < 3; ++k) {
+        dL_dbeta[k] += -pm.n_src * pm.rh[k] * dL_dD;
+        dL_drh[k] += -pm.n_src * beta[k] * dL_dD;
+      }
+      /* tau = (t_m - t_ref) + (R + F) / c */
+      double F, dF_dR, dF_dzm, dF_dza, dF_dN0;
+      refractive_part(m, xm, xa, pm.R, &F, &dF_dR, &dF_dzm, &dF_dza, &dF_dN0);
+      double dL_dopt = dL_dtau / OR_C_LIGHT;
+      dL_dR += dL_dopt * (1.0 + dF_dR);
+      double dL_dzm = dL_dopt * dF_dzm + dL_dnsrc * pm.dn_src_dze;
+      double dL_dza = dL_dopt * dF_dza;
+      *dN0 += dL_dopt * dF_dN0 + dL_dnsrc * pm.dn_src_dN0;
+      /* rhat = d/R, d = x_a - x_m */
+      double rdr = dot3(dL_drh, pm.rh), dL_dd[3];
+      for (int k = 0; k < 3; ++k) dL_dd[k] = (dL_drh[k] - rdr * pm.rh[k]) / pm.R + dL_dR * pm.rh[k];
+      for (int k = 0; k < 3; ++k) {
+        double dm = -dL_dd[k] + (k == 2 ? dL_dzm : 0.0);
+        tg[k] += 0.5 * dm;
+        tg[3 + k] += 0.5 * dm;
+        tg[8 + k] += dL_dbeta[k];
+        ant_grad[3 * a + k] += dL_dd[k] + (k == 2 ? dL_dza : 0.0);
+      }
+      tg[6] += 0.5 * dL_dtau - dL_ddte;
+      tg[7] += 0.5 * dL_dtau + dL_ddte;
     }
   }
 }

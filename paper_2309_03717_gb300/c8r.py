@@ -351,10 +351,10 @@ class RadioTraces(torch.autograd.Function):
     """traces = RadioTraces.apply(process, N0_ref, *track_tensors, ant_xyz_tensor)
 
     Forward pushes the tracks through ``process`` (reset first) and returns its
-    traces.  Backward runs the library's Endpoint adjoint and returns gradients
-    for the twelve track tensors (zero for q), for N0 (a 0-d tensor standing for
-    the refractivity; its value is the one the process was configured with) and
-    for the antenna positions [n_ant, 3]."""
+    traces.  Backward runs the library's adjoint (Endpoint or ZHS, the process's
+    formalism) and returns gradients for the twelve track tensors (zero for q),
+    for N0 (a 0-d tensor standing for the refractivity; its value is the one the
+    process was configured with) and for the antenna positions [n_ant, 3]."""
 
     @staticmethod
     def forward(ctx, process: RadioProcess, N0, *args):

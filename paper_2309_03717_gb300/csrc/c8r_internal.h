@@ -55,8 +55,12 @@ cudaError_t launch_arrivals_f64(int formalism, const void* tiles, int64_t n, con
                                 const MedParams& M, int32_t* branch, int32_t* bin, float* frac, cudaStream_t st);
 cudaError_t launch_arrivals_mixed(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,
                                   const MedParams& M, int32_t* branch, int32_t* bin, float* frac, cudaStream_t st);
-cudaError_t launch_backward_f64(BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st);
-cudaError_t launch_backward_mixed(BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st);
+cudaError_t launch_backward_f64(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st);
+cudaError_t launch_backward_mixed(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st);
+// running sums over the bins of a bin-major gradient (FP64): [n_ant][n_bins + 1]
+struct Acc4D;
+cudaError_t launch_bin_running_sums(int precision, const void* g, int n_ant, int n_bins, Acc4D* out,
+                                    cudaStream_t st);
 
 // helpers shared by the context and the batch runner
 void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, double dt_ns, double eps_C);

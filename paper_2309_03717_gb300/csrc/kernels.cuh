@@ -97,6 +97,7 @@ struct BwdArgs {
   int n_ant;
   int a_tile;
   const void* G;      // dL/dtraces, bin-major [n_ant][n_bins] of (x, y, z, 0) accumulator elements
+  const Acc4D* Gp;    // ZHS: running sums of G over the bins, [n_ant][n_bins + 1] (entry k: bins < k)
   c8r_track_grads out;
   double* ant_grad;   // [n_ant][3]
   double* dN0;
@@ -385,6 +386,45 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Refractivity part F = (n_avg - 1) R of the optical path R + F and its
+// derivatives (reading M; the ZHS adjoint needs them, the Endpoint deposits do
+// not depend on the arrival time).  Exponential medium: F = N0 E_m R rho(x),
+// rho(x) = (1 - exp(-x))/x, x = (z_a - z_m)/H, rho' = (exp(-x) - rho)/x; both
+// by their series for |x| < 1e-3.  Uniform medium: F = (n - 1) R, and "N0"
+// stands for n - 1.
+template <typename T>
+struct RefrGrad {
+  T dF_dR, dF_dzm, dF_dza, dF_dN0, dn_dzm, dn_dN0;
+};
+template <typename T>
+__device__ __forceinline__ RefrGrad<T> refraction_grad(int kind, T R, T x, T E, T N0, T invH, T nm1) {
+  RefrGrad<T> g;
+  if (kind == C8R_UNIFORM) {
+    g.dF_dR = nm1;
+    g.dF_dzm = g.dF_dza = T(0);
+    g.dF_dN0 = R;
+    g.dn_dzm = T(0);
+    g.dn_dN0 = T(1);
+    return g;
+  }
+  T rho, drho;
+  if (fabs(x) < T(1e-3)) {
+    rho = T(1) + x * (T(-0.5) + x * (T(1) / T(6) + x * (T(-1) / T(24))));
+    drho = T(-0.5) + x * (T(1) / T(3) + x * (T(-1) / T(8) + x * (T(1) / T(30))));
+  } else {
+    const T em = exp(-x);
+    rho = (T(1) - em) / x;
+    drho = (em - rho) / x;
+  }
+  g.dF_dR = N0 * E * rho;
+  g.dF_dzm = -N0 * R * E * (rho + drho) * invH;
+  g.dF_dza = N0 * R * E * drho * invH;
+  g.dF_dN0 = E * R * rho;
+  g.dn_dzm = -N0 * E * invH;
+  g.dn_dN0 = E;
+  return g;
+}
+
 // Adjoint, laid out like the forward pass: a CTA owns an antenna tile and a
 // range of derived-track tiles streamed through the TMA ring; each thread holds
 // one track of the staged tile and walks the tile's antennas, keeping the
@@ -425,6 +465,7 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int N = M.n_bins;
   const acc4* G = static_cast<const acc4*>(a.G) + (size_t)ant0 * N;
+  const Acc4D* Gp = a.Gp ? a.Gp + (size_t)ant0 * (N + 1) : nullptr;
   for (int i = tid; i < n_here; i += nthr) ant_s[i] = a.ants[ant0 + i];
   for (int i = tid; i < 3 * n_here + 1; i += nthr) sg[i] = acc_t(0);
   const uint32_t bytes = (uint32_t)L.stage_bytes;
@@ -459,7 +500,8 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
 #pragma unroll 1
       for (int ant = 0; ant < n_here; ++ant) {
         acc_t ga[3] = {0, 0, 0};
-        if (live && Ops::adj_main(tr, Ops::load_ant(ant_s + ant), M, G + (size_t)ant * N, tg, ga, dn_acc) &&
+        const Acc4D* Gp_a = Gp ? Gp + (size_t)ant * (N + 1) : nullptr;
+        if (live && Ops::adj_main(tr, Ops::load_ant(ant_s + ant), M, G + (size_t)ant * N, Gp_a, tg, ga, dn_acc) &&
             Ops::kDefers)
           queue[atomicAdd(&q_cnt[st], 1)] = (uint16_t)(l | (ant << 7));
 #pragma unroll
@@ -488,7 +530,8 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
 #pragma unroll
         for (int k = 0; k < 11; ++k) tg[k] = acc_t(0);
         acc_t ga[3] = {0, 0, 0};
-        Ops::adj_deferred(tr, Ops::load_ant(ant_s + ant), M, G + (size_t)ant * N, tg, ga, dn_acc);
+        Ops::adj_deferred(tr, Ops::load_ant(ant_s + ant), M, G + (size_t)ant * N,
+                          Gp ? Gp + (size_t)ant * (N + 1) : nullptr, tg, ga, dn_acc);
         add_track_grads<acc_t>(a.out, t * kTileT + l, tg);
 #pragma unroll
         for (int c = 0; c < 3; ++c)

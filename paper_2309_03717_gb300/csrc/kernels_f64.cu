@@ -31,7 +31,8 @@ cudaError_t launch_arrivals_f64(int formalism, const void* tiles, int64_t n, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_backward_f64(BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st) {
+cudaError_t launch_backward_f64(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st) {
+  if (formalism == C8R_ZHS) return launch_backward_ops<OpsF64<C8R_ZHS>>(a, shape, sm_count, st);
   return launch_backward_ops<OpsF64<C8R_ENDPOINT>>(a, shape, sm_count, st);
 }
 

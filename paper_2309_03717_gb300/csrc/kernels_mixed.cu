@@ -157,6 +157,62 @@ cudaError_t launch_traces_to_bin_major(int precision, const void* g, int n_ant, 
   return cudaGetLastError();
 }
 
+// running sums over the bins of a bin-major gradient, in FP64:
+// out[a][k] = sum_{j < k} g[a][j], k = 0 .. n_bins (one CTA per antenna)
+template <typename T4>
+__global__ void __launch_bounds__(kScanThreads) k_bin_running_sums(const T4* g, int n_bins, Acc4D* out) {
+  __shared__ double warp_tot[3][kScanThreads / 32];
+  const int a = blockIdx.x;
+  const T4* row = g + (size_t)a * n_bins;
+  Acc4D* o = out + (size_t)a * (n_bins + 1);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double carry[3] = {0.0, 0.0, 0.0};
+  if (threadIdx.x == 0) o[0] = Acc4D{0.0, 0.0, 0.0, 0.0};
+  for (int base = 0; base < n_bins; base += blockDim.x) {
+    const int k = base + threadIdx.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (k < n_bins) {
+      const T4 e = row[k];
+      v[0] = e.x;
+      v[1] = e.y;
+      v[2] = e.z;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, v[c], d);
+        if (lane >= d) v[c] += u;
+      }
+      if (lane == 31) warp_tot[c][wid] = v[c];
+    }
+    __syncthreads();
+    double tot[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      for (int w = 0; w < nw; ++w) {
+        const double t = warp_tot[c][w];
+        if (w < wid) v[c] += t;
+        tot[c] += t;
+      }
+    }
+    if (k < n_bins) o[k + 1] = Acc4D{carry[0] + v[0], carry[1] + v[1], carry[2] + v[2], 0.0};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) carry[c] += tot[c];
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_bin_running_sums(int precision, const void* g, int n_ant, int n_bins, Acc4D* out,
+                                    cudaStream_t st) {
+  if (n_ant <= 0 || n_bins <= 0) return cudaSuccess;
+  if (precision == C8R_FP64)
+    k_bin_running_sums<Acc4D><<<(unsigned)n_ant, kScanThreads, 0, st>>>(static_cast<const Acc4D*>(g), n_bins, out);
+  else
+    k_bin_running_sums<float4><<<(unsigned)n_ant, kScanThreads, 0, st>>>(static_cast<const float4*>(g), n_bins, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_arrivals_mixed(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,
                                   const MedParams& M, int32_t* branch, int32_t* bin, float* frac, cudaStream_t st) {
   const unsigned blocks = (unsigned)((n * (int64_t)n_ant + 255) / 256);
@@ -179,10 +235,14 @@ cudaError_t launch_arrivals_mixed(int formalism, const void* tiles, int64_t n, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_backward_mixed(BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st) {
-  if (a.M.kind == C8R_EXPONENTIAL)
-    return launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>>(a, shape, sm_count, st);
-  return launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>>(a, shape, sm_count, st);
+cudaError_t launch_backward_mixed(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count,
+                                  cudaStream_t st) {
+  const bool ex = a.M.kind == C8R_EXPONENTIAL;
+  if (formalism == C8R_ZHS)
+    return ex ? launch_backward_ops<OpsMixed<C8R_ZHS, C8R_EXPONENTIAL>>(a, shape, sm_count, st)
+              : launch_backward_ops<OpsMixed<C8R_ZHS, C8R_UNIFORM>>(a, shape, sm_count, st);
+  return ex ? launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>>(a, shape, sm_count, st)
+            : launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>>(a, shape, sm_count, st);
 }
 
 }  // namespace c8r

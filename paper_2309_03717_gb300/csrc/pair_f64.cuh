@@ -181,12 +181,113 @@ struct OpsF64 {
   }
 
   static __device__ __forceinline__ bool adj_main(const TrackD& tr, const AntRec& A, const MedParams& M,
-                                                  const Acc4D* G, double tg[11], double ga[3], double& dn) {
-    adj(tr, A, M, G, tg, ga, dn);
+                                                  const Acc4D* G, const Acc4D* Gp, double tg[11], double ga[3],
+                                                  double& dn) {
+    if constexpr (FORM == C8R_ZHS)
+      adj_zhs(tr, A, M, G, Gp, tg, ga, dn);
+    else
+      adj(tr, A, M, G, tg, ga, dn);
     return false;
   }
   static __device__ __forceinline__ void adj_deferred(const TrackD&, const AntRec&, const MedParams&, const Acc4D*,
-                                                      double*, double*, double&) {}
+                                                      const Acc4D*, double*, double*, double&) {}
+
+  // ZHS adjoint (bins of the interval ends held fixed; see the mixed path for
+  // the formulas): in FP64, times in ns, positions in m
+  static __device__ __forceinline__ void adj_zhs(const TrackD& tr, const AntRec& A, const MedParams& M,
+                                                 const Acc4D* G, const Acc4D*, double tg[11], double ga[3],
+                                                 double& dn) {
+    const double* T = tr.T;
+    const int l = tr.l;
+    const double q = TF(fd::Q);
+    if (q == 0.0) return;
+    const int N = M.n_bins;
+    const double b[3] = {TF(fd::BX), TF(fd::BY), TF(fd::BZ)};
+    const double x0 = TF(fd::X0), y0 = TF(fd::Y0), z0 = TF(fd::Z0);
+    const double x1 = TF(fd::X1), y1 = TF(fd::Y1), z1 = TF(fd::Z1);
+    const double t0 = TF(fd::T0), t1 = TF(fd::T1);
+    const double Em = TF(fd::EM);
+    GeoD gm;
+    geo_f64(M, A, 0.5 * (x0 + x1), 0.5 * (y0 + y1), 0.5 * (z0 + z1), Em, gm);
+    if (gm.R == 0.0) return;
+    const double c = b[0] * gm.rh[0] + b[1] * gm.rh[1] + b[2] * gm.rh[2];
+    const double Dm = 1.0 - gm.n_src * c;
+    const double dte = t1 - t0;
+    const double tm = 0.5 * (t0 + t1);
+    const double tarr_rel = (tm - A.t_ref) + gm.n_avg * gm.R * M.inv_c_ns;
+    const double half = fabs(Dm) * dte / 2.0;
+    const double dt = M.dt_ns;
+    const double u_lo = (tarr_rel - half) / dt, u_hi = (tarr_rel + half) / dt;
+    const double k_lo = floor(u_lo), k_hi = floor(u_hi);
+    const double KA = q * kKzhs;
+    double Av[3];
+    for (int k = 0; k < 3; ++k) Av[k] = KA * (b[k] - c * gm.rh[k]) * dte / (gm.R * dt);
+    double S[3] = {0.0, 0.0, 0.0};
+    double dLdu = 0.0, dLdh = 0.0;  // per bin of u, per bin of h = half/dt
+    if (k_lo == k_hi) {
+      if (!(k_lo >= 0.0 && k_lo < (double)N)) return;
+      const Acc4D g = G[(int)k_lo];
+      S[0] = g.x; S[1] = g.y; S[2] = g.z;
+    } else {
+      // S = sum of (overlap / width) G over the bins of the interval inside the
+      // window, bin by bin (the FP64 path does not use the running sums)
+      const double W = u_hi - u_lo;
+      const bool inlo = k_lo >= 0.0 && k_lo < (double)N, inhi = k_hi >= 0.0 && k_hi < (double)N;
+      const Acc4D zero{0.0, 0.0, 0.0, 0.0};
+      const Acc4D glo = inlo ? G[(int)k_lo] : zero, ghi = inhi ? G[(int)k_hi] : zero;
+      const double kb = fmax(k_lo, 0.0), ke = fmin(k_hi, (double)(N - 1));
+      for (double kd = kb; kd <= ke; kd += 1.0) {
+        const double o = fmin(u_hi, kd + 1.0) - fmax(u_lo, kd);
+        if (o <= 0.0) continue;
+        const Acc4D g = G[(int)kd];
+        S[0] += (o / W) * g.x;
+        S[1] += (o / W) * g.y;
+        S[2] += (o / W) * g.z;
+      }
+      const double g_lo = Av[0] * glo.x + Av[1] * glo.y + Av[2] * glo.z;
+      const double g_hi = Av[0] * ghi.x + Av[1] * ghi.y + Av[2] * ghi.z;
+      const double AS = Av[0] * S[0] + Av[1] * S[1] + Av[2] * S[2];
+      dLdu = (g_hi - g_lo) / W;
+      dLdh = (g_hi + g_lo - 2.0 * AS) / W;
+    }
+    const double AS = Av[0] * S[0] + Av[1] * S[1] + Av[2] * S[2];
+    const double ka = KA * dte / (gm.R * dt);
+    double sb[3], dLdb[3], dLdr[3];
+    for (int k = 0; k < 3; ++k) sb[k] = ka * S[k];
+    const double sbr = sb[0] * gm.rh[0] + sb[1] * gm.rh[1] + sb[2] * gm.rh[2];
+    for (int k = 0; k < 3; ++k) {
+      dLdb[k] = sb[k] - sbr * gm.rh[k];
+      dLdr[k] = -c * sb[k] - sbr * b[k];
+    }
+    // dte enters A and h = |D| dte / (2 dt); u_m = tau_m - tau_a + n_avg R / (c dt)
+    double dLd_dte = AS / dte + dLdh * fabs(Dm) / (2.0 * dt);
+    double dLdR = -AS / gm.R;
+    const double dLdD = dLdh * (Dm < 0.0 ? -1.0 : 1.0) * dte / (2.0 * dt);
+    const double dLdn = -c * dLdD;
+    for (int k = 0; k < 3; ++k) {
+      dLdb[k] -= gm.n_src * gm.rh[k] * dLdD;
+      dLdr[k] -= gm.n_src * b[k] * dLdD;
+    }
+    const RefrGrad<double> rg =
+        refraction_grad<double>(M.kind, gm.R, gm.d[2] * M.invH, Em, M.N0, M.invH, M.n - 1.0);
+    const double dLdopt = dLdu * M.inv_c_ns / dt;
+    dLdR += dLdopt * (1.0 + rg.dF_dR);
+    const double dLdzm = dLdopt * rg.dF_dzm + dLdn * rg.dn_dzm;
+    const double dLdza = dLdopt * rg.dF_dza;
+    dn += dLdopt * rg.dF_dN0 + dLdn * rg.dn_dN0;
+    const double rdr = dLdr[0] * gm.rh[0] + dLdr[1] * gm.rh[1] + dLdr[2] * gm.rh[2];
+    for (int k = 0; k < 3; ++k) {
+      const double dd = (dLdr[k] - rdr * gm.rh[k]) / gm.R + dLdR * gm.rh[k];
+      const double dm = -dd + (k == 2 ? dLdzm : 0.0);
+      tg[k] += 0.5 * dm;
+      tg[3 + k] += 0.5 * dm;
+      tg[8 + k] += dLdb[k];
+      ga[k] += dd + (k == 2 ? dLdza : 0.0);
+    }
+    tg[6] += 0.5 * dLdu / dt - dLd_dte;
+    tg[7] += 0.5 * dLdu / dt + dLd_dte;
+  }
+
   static __device__ __forceinline__ void adj(const TrackD& tr, const AntRec& A, const MedParams& M,
                                              const Acc4D* G, double tg[11], double ga[3], double& dn) {
     static_assert(FORM == C8R_ENDPOINT, "adjoint is defined for the Endpoint formalism");

@@ -333,28 +333,161 @@ struct OpsMixed {
     deposit_adjoint<float>(rh, V, c, f.D, g.R0, n, gv, kappa, dd, db, dns);
   }
 
-  // adjoint main pass: every pair except the near-Cherenkov ones, for which it
-  // adds nothing and returns true
+  // adjoint main pass: every pair except (Endpoint) the near-Cherenkov ones, for
+  // which it adds nothing and returns true
   static __device__ __forceinline__ bool adj_main(const TrackM& t, const AntRec& A, const MedParams& M,
-                                                  const float4* G, float tg[11], float ga[3], float& dn) {
-    static_assert(FORM == C8R_ENDPOINT, "adjoint is defined for the Endpoint formalism");
-    EndpointEvalM e;
-    if (!endpoint_fields(t, A, e)) return false;
-    if (endpoint_near_cherenkov(e, M)) return true;
-    endpoint_arrivals<KIND>(t, A, M, e);
-    adj_deposits(t, e, M, G, tg, ga, dn);
-    return false;
+                                                  const float4* G, const Acc4D* Gp, float tg[11], float ga[3],
+                                                  float& dn) {
+    if constexpr (FORM == C8R_ZHS) {
+      adj_zhs(t, A, M, G, Gp, tg, ga, dn);
+      return false;
+    } else {
+      EndpointEvalM e;
+      if (!endpoint_fields(t, A, e)) return false;
+      if (endpoint_near_cherenkov(e, M)) return true;
+      endpoint_arrivals<KIND>(t, A, M, e);
+      adj_deposits(t, e, M, G, tg, ga, dn);
+      return false;
+    }
   }
   static __device__ __forceinline__ void adj_deferred(const TrackM& t, const AntRec& A, const MedParams& M,
-                                                      const float4* G, float tg[11], float ga[3], float& dn) {
-    EndpointEvalM e;
-    if (!endpoint_fields(t, A, e)) return;
-    if (!endpoint_midpoint<KIND>(t, A, M, e)) return;
-    adj_deposits(t, e, M, G, tg, ga, dn);
+                                                      const float4* G, const Acc4D*, float tg[11], float ga[3],
+                                                      float& dn) {
+    if constexpr (FORM == C8R_ENDPOINT) {
+      EndpointEvalM e;
+      if (!endpoint_fields(t, A, e)) return;
+      if (!endpoint_midpoint<KIND>(t, A, M, e)) return;
+      adj_deposits(t, e, M, G, tg, ga, dn);
+    }
   }
   static __device__ __forceinline__ void adj(const TrackM& t, const AntRec& A, const MedParams& M, const float4* G,
-                                             float tg[11], float ga[3], float& dn) {
-    if (adj_main(t, A, M, G, tg, ga, dn)) adj_deferred(t, A, M, G, tg, ga, dn);
+                                             const Acc4D* Gp, float tg[11], float ga[3], float& dn) {
+    if (adj_main(t, A, M, G, Gp, tg, ga, dn)) adj_deferred(t, A, M, G, Gp, tg, ga, dn);
+  }
+
+  // ZHS adjoint (bins of the interval ends held fixed): the forward arithmetic
+  // of `zhs`, then the chain rule through the one-bin deposit A = amp beta_perp/R
+  // (amp = q K_A (t1 - t0)/dt) and the weights of [u_m - h, u_m + h] over its
+  // bins: with S = sum_k w_k G_k, g_lo/g_hi = A.G at the first/last bin and W =
+  // 2h, dL/du_m = (g_hi - g_lo)/W and dL/dh = (g_hi + g_lo - 2 A.S)/W (both 0
+  // for a one-bin interval).  The sum of G over the whole bins in between comes
+  // from the running sums Gp.  Times in ns, positions in m.
+  static __device__ __forceinline__ void adj_zhs(const TrackM& t, const AntRec& A, const MedParams& M,
+                                                 const float4* G, const Acc4D* Gp, float tg[11], float ga[3],
+                                                 float& dn) {
+    const int N = M.n_bins;
+    GeoM gm;
+    geo_lite(A, t.mx, t.my, t.mz, t.mxl, t.myl, t.mzl, gm);
+    if (gm.R0 == 0.0f) return;
+    FieldM f;
+    field_mixed(gm, t.bx, t.by, t.bz, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), f);
+    geo_refine(gm);
+    const ff um = arrival_mixed(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml);
+    ff aD = doppler_ff(gm, t.bx, t.by, t.bz, t.nm1_m);
+    const float sgn = aD.h < 0.0f ? -1.0f : 1.0f;
+    if (aD.h < 0.0f) {
+      aD.h = -aD.h;
+      aD.l = -aD.l;
+    }
+    float hh, hl;
+    two_prod(aD.h, t.dtauh, hh, hl);
+    hl = __fmaf_rn(aD.h, t.dtaul, __fmaf_rn(aD.l, t.dtauh, hl));
+    hh *= 0.5f;
+    hl *= 0.5f;
+    ff ulo, uhi;
+    two_sum(um.h, -hh, ulo.h, ulo.l);
+    ulo.l = __fadd_rn(ulo.l, __fsub_rn(um.l, hl));
+    two_sum(um.h, hh, uhi.h, uhi.l);
+    uhi.l = __fadd_rn(uhi.l, __fadd_rn(um.l, hl));
+    float flo, fhi;
+    const int klo = bin_raw(ulo, N, flo);
+    const int khi = bin_raw(uhi, N, fhi);
+    const float invR = f.invR;
+    const float rh[3] = {gm.s[0] * invR, gm.s[1] * invR, gm.s[2] * invR};
+    const float b[3] = {t.bx, t.by, t.bz};
+    const float c = f.bd * invR;
+    const float Av[3] = {t.amp * (b[0] - c * rh[0]) * invR, t.amp * (b[1] - c * rh[1]) * invR,
+                         t.amp * (b[2] - c * rh[2]) * invR};
+    float S[3];
+    float dLdu = 0.0f, dLdh = 0.0f;
+    if (klo == khi) {
+      if (klo < 0 || klo >= N) return;
+      const float4 g = G[klo];
+      S[0] = g.x; S[1] = g.y; S[2] = g.z;
+    } else {
+      const float invW = __fdividef(1.0f, 2.0f * hh);
+      const bool inlo = klo >= 0 && klo < N, inhi = khi >= 0 && khi < N;
+      const float4 glo = inlo ? G[klo] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 ghi = inhi ? G[khi] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float wlo = (1.0f - flo) * invW, whi = fhi * invW;
+      double ix = 0.0, iy = 0.0, iz = 0.0;  // G summed over the whole bins between
+      const int kb = klo + 1 < 0 ? 0 : klo + 1;
+      const int ke = khi - 1 > N - 1 ? N - 1 : khi - 1;
+      if (kb <= ke) {
+        const Acc4D p1 = Gp[ke + 1], p0 = Gp[kb];
+        ix = p1.x - p0.x;
+        iy = p1.y - p0.y;
+        iz = p1.z - p0.z;
+      }
+      S[0] = wlo * glo.x + invW * (float)ix + whi * ghi.x;
+      S[1] = wlo * glo.y + invW * (float)iy + whi * ghi.y;
+      S[2] = wlo * glo.z + invW * (float)iz + whi * ghi.z;
+      const float g_lo = Av[0] * glo.x + Av[1] * glo.y + Av[2] * glo.z;
+      const float g_hi = Av[0] * ghi.x + Av[1] * ghi.y + Av[2] * ghi.z;
+      const float AS = Av[0] * S[0] + Av[1] * S[1] + Av[2] * S[2];
+      dLdu = (g_hi - g_lo) * invW;
+      dLdh = (g_hi + g_lo - 2.0f * AS) * invW;
+    }
+    const float AS = Av[0] * S[0] + Av[1] * S[1] + Av[2] * S[2];
+    // through A
+    const float ka = t.amp * invR;
+    const float sb[3] = {ka * S[0], ka * S[1], ka * S[2]};
+    const float sbr = sb[0] * rh[0] + sb[1] * rh[1] + sb[2] * rh[2];
+    float dLdb[3], dLdr[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      dLdb[k] = sb[k] - sbr * rh[k];
+      dLdr[k] = -c * sb[k] - sbr * b[k];
+    }
+    const float dtau = t.dtauh;  // (t1 - t0)/dt
+    float dLd_dtau = __fdividef(AS, dtau);
+    float dLdR = -AS * invR;
+    // through h = |D| dtau / 2
+    const float absD = aD.h;
+    const float dLdD = dLdh * sgn * 0.5f * dtau;
+    dLd_dtau += dLdh * 0.5f * absD;
+    // D = 1 - n c
+    const float n = 1.0f + t.nm1_m;
+    const float dLdn = -c * dLdD;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      dLdb[k] -= n * rh[k] * dLdD;
+      dLdr[k] -= n * b[k] * dLdD;
+    }
+    // u_m = tau_m - tau_a + (R + F) / (c dt)
+    const float R = gm.R0;
+    const RefrGrad<float> rg = refraction_grad<float>(KIND, R, gm.s[2] * M.invH_h, t.Emh, M.N0f, M.invH_h, M.nm1f);
+    const float dLdopt = dLdu * M.kc_h;
+    dLdR += dLdopt * (1.0f + rg.dF_dR);
+    const float dLdzm = dLdopt * rg.dF_dzm + dLdn * rg.dn_dzm;
+    const float dLdza = dLdopt * rg.dF_dza;
+    dn += dLdopt * rg.dF_dN0 + dLdn * rg.dn_dN0;
+    // rhat = d/R, d = x_a - x_m
+    const float rdr = dLdr[0] * rh[0] + dLdr[1] * rh[1] + dLdr[2] * rh[2];
+    float dLdd[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dLdd[k] = (dLdr[k] - rdr * rh[k]) * invR + dLdR * rh[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float dm = -dLdd[k] + (k == 2 ? dLdzm : 0.0f);
+      tg[k] += 0.5f * dm;
+      tg[3 + k] += 0.5f * dm;
+      tg[8 + k] += dLdb[k];
+      ga[k] += dLdd[k] + (k == 2 ? dLdza : 0.0f);
+    }
+    const float idt = (float)(1.0 / M.dt_ns);
+    tg[6] += (0.5f * dLdu - dLd_dtau) * idt;
+    tg[7] += (0.5f * dLdu + dLd_dtau) * idt;
   }
 
   // gradients of the deposits of an evaluated pair

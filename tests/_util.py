@@ -110,6 +110,13 @@ def drop_tracks(tracks, keep_mask):
     return {f: np.ascontiguousarray(tracks[f][keep_mask]) for f in FIELDS}
 
 
+def unambiguous(tracks, ant, t_start_ns, n_bins, dt_ns, medium, formalism, tol=1e-6):
+    """Tracks none of whose arrival positions (Endpoint deposits, ZHS interval
+    ends) lies within tol bin of a bin edge."""
+    _, u = oracle_arrivals(tracks, ant, t_start_ns, n_bins, dt_ns, medium, formalism)
+    return ~edge_ambiguous(u, tol).any(axis=-1).any(axis=-1)
+
+
 def endpoint_unambiguous(tracks, ant, t_start_ns, n_bins, dt_ns, medium, tol=1e-6, eps_C=1e-3):
     """Tracks whose Endpoint deposits are all away from bin edges and whose branch
     decision is away from the threshold (so the trace is a continuous function of

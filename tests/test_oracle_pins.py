@@ -512,6 +512,80 @@ def test_adjoint_matches_central_differences(medium):
     assert checked > 5 * skipped
 
 
+def _loss_zhs(tr, ant, t_ref, medium, G, dt, N):
+    out, _ = oracle.forward(tr, ant, t_ref, N, dt, medium, oracle.ZHS)
+    return float((out * G).sum())
+
+
+@pytest.mark.parametrize("medium", [EXP_AIR, UNIFORM_AIR])
+def test_zhs_adjoint_matches_central_differences(medium):
+    """Reading GZ: with the bins of the interval ends held fixed the ZHS traces are
+    smooth in every input, times included; central differences that keep those
+    bins pin every component of the hand-written gradient."""
+    tr = random_tracks(5, 37, spread_deg=6.0)
+    ant = ground_antennas([40.0, 200.0], [0.0, 130.0])
+    dt, N = 0.2e-9, 4096
+    t_ref = t_ref_for(ant)
+    rng = np.random.default_rng(3)
+    out, _ = oracle.forward(tr, ant, t_ref, N, dt, medium, oracle.ZHS)
+    G = rng.normal(size=out.shape) * (np.abs(out) > 0)
+    G += 0.1 * rng.normal(size=out.shape)
+    tg, ag, dN = oracle.backward(tr, ant, t_ref, N, dt, medium, G, formalism=oracle.ZHS)
+    br0, u0 = oracle.arrivals(tr, ant, t_ref, N, dt, medium, oracle.ZHS)
+    assert (br0 == 3).any()  # multi-bin intervals: the weights vary with the times
+
+    def same_bins(t2, a2=ant, m2=medium):
+        br, u = oracle.arrivals(t2, a2, t_ref, N, dt, m2, oracle.ZHS)
+        return np.array_equal(br, br0) and np.array_equal(np.floor(u), np.floor(u0))
+
+    l1 = float(np.abs(out * G).sum())
+    gs = {"pos": np.abs(np.concatenate([tg[:, :6].ravel(), ag.ravel()])).max(), "t": np.abs(tg[:, 6:8]).max(),
+          "beta": np.abs(tg[:, 8:]).max()}
+    assert gs["t"] > 0  # the times do get gradients
+
+    def close(fd, adj, h, kind):
+        return abs(fd - adj) <= 1e-5 * abs(adj) + 1e-7 * gs[kind] + 100 * 2.2e-16 * l1 / h
+
+    checked = skipped = 0
+    names = ["x0", "y0", "z0", "x1", "y1", "z1", "t0", "t1", "bx", "by", "bz"]
+    for i in range(len(tr["x0"])):
+        for j, f in enumerate(names):
+            v = tr[f][i]
+            h = 1e-6 * max(abs(v), 1e-3) if f[0] != "t" else 1e-6 * 1e-9
+            tp, tm = dict(tr), dict(tr)
+            tp[f] = tr[f].copy(); tp[f][i] = v + h
+            tm[f] = tr[f].copy(); tm[f][i] = v - h
+            if not (same_bins(tp) and same_bins(tm)):
+                skipped += 1
+                continue
+            fd = (_loss_zhs(tp, ant, t_ref, medium, G, dt, N) - _loss_zhs(tm, ant, t_ref, medium, G, dt, N)) / (2 * h)
+            kind = {"t": "t", "b": "beta"}.get(f[0], "pos")
+            assert close(fd, tg[i, j], h, kind), (i, f, fd, tg[i, j])
+            checked += 1
+    for a in range(len(ant)):
+        for k in range(3):
+            h = 1e-6 * max(np.linalg.norm(ant[a]), 1.0)
+            ap, am = ant.copy(), ant.copy()
+            ap[a, k] += h
+            am[a, k] -= h
+            if not (same_bins(tr, ap) and same_bins(tr, am)):
+                skipped += 1
+                continue
+            fd = (_loss_zhs(tr, ap, t_ref, medium, G, dt, N) - _loss_zhs(tr, am, t_ref, medium, G, dt, N)) / (2 * h)
+            assert close(fd, ag[a, k], h, "pos"), (a, k, fd, ag[a, k])
+            checked += 1
+    key = "N0" if medium["kind"] == "exponential" else "n"
+    h = 1e-6 * (medium[key] if key == "N0" else medium["n"] - 1)
+    mp_, mm_ = dict(medium), dict(medium)
+    mp_[key] += h
+    mm_[key] -= h
+    if same_bins(tr, ant, mp_) and same_bins(tr, ant, mm_):
+        fd = (_loss_zhs(tr, ant, t_ref, mp_, G, dt, N) - _loss_zhs(tr, ant, t_ref, mm_, G, dt, N)) / (2 * h)
+        assert abs(fd - dN) <= 1e-5 * abs(dN) + 100 * 2.2e-16 * l1 / h, (fd, dN)
+        checked += 1
+    assert checked > 5 * skipped
+
+
 def test_abs_mode_bounds_the_signed_traces():
     """MODE_ABS sums |deposit|: it bounds |trace| bin by bin and equals it where a
     bin holds a single deposit."""
