@@ -420,6 +420,8 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_extras:
         result["extras"] = extras(torch, c8r, synth, w)
+        # the metric's second part: adjoint / forward time on the differentiable workload
+        result["bwd_fwd_ratio"] = result["extras"]["bwd_fwd_ratio"]
         single = cpu_baseline(w, args.cpu_sample_tracks, ("endpoint", "zhs"))
         result["cpu_baseline"] = cpu_baseline_all_cores(w, 10 * args.cpu_sample_tracks, ("endpoint", "zhs"))
         result["cpu_baseline"]["single_core"] = {k: single[k] for k in ("value", "cores", "sample")}
@@ -450,42 +452,19 @@ def extras(torch, c8r, synth, w):
         out[f"fp64_{f}_pairs_per_s"] = 2 * n64 * A / (e0.elapsed_time(e1) * 1e-3)
         p.close()
     del d64
-    # adjoint / forward on the differentiable workload (1e6 tracks x 64 antennas, 2048 bins)
+    # adjoint / forward on the differentiable workload (1e6 tracks x 64 antennas,
+    # 2048 bins): the Endpoint adjoint the workload names, and the ZHS one
     w4 = synth.workload(4)
     tr4 = synth.workload_tracks(w4)
     d4 = {k: torch.from_numpy(v).cuda() for k, v in tr4.items()}
-    p = c8r.RadioProcess(w4["medium"], w4["ant_xyz"], w4["t_start_ns"], w4["n_bins"], w4["dt_ns"], "endpoint", "mixed")
-    n4 = tr4["x0"].size
-    g = torch.randn((len(w4["ant_xyz"]), 3, w4["n_bins"]), device="cuda")
-    tg = {f: torch.zeros(n4, dtype=torch.float32, device="cuda") for f in c8r.GRAD_FIELDS}
-    ag = torch.zeros((len(w4["ant_xyz"]), 3), dtype=torch.float64, device="cuda")
-    dn = torch.zeros(1, dtype=torch.float64, device="cuda")
-
-    def fwd():
-        p.reset()
-        p.push(d4)
-
-    def bwd():
-        c8r.c8r_backward(p.ctx, d4, g, tg, ag, dn)
-
-    for fn in (fwd, bwd):
-        fn()
-    torch.cuda.synchronize()
-    times = {}
-    for name, fn in (("fwd", fwd), ("bwd", bwd)):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(3):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        times[name] = e0.elapsed_time(e1) / 3
-    out["diff_fwd_ms"] = times["fwd"]
-    out["diff_bwd_ms"] = times["bwd"]
-    out["bwd_fwd_ratio"] = times["bwd"] / times["fwd"]
-    out["diff_workload"] = "1e6 tracks x star 8x8, 2048 x 0.2 ns, exponential atmosphere, Endpoint mixed"
-    p.close()
-    del d4, tg, g
+    for f, tag in (("endpoint", "diff"), ("zhs", "diff_zhs")):
+        fwd_ms, bwd_ms = adjoint_timing(torch, c8r, w4, d4, f)
+        out[f"{tag}_fwd_ms"] = fwd_ms
+        out[f"{tag}_bwd_ms"] = bwd_ms
+        out[f"{tag}_bwd_fwd_ratio"] = bwd_ms / fwd_ms
+    out["bwd_fwd_ratio"] = out["diff_bwd_fwd_ratio"]
+    out["diff_workload"] = "1e6 tracks x star 8x8, 2048 x 0.2 ns, exponential atmosphere, mixed precision"
+    del d4
 
     # large inclined array: 60 deg shower, 32 x 32 grid (1024 antennas), 8192 x 0.1 ns,
     # tracks streamed through the context in 4e6-track chunks (a sample of 8e6 tracks)
@@ -524,6 +503,38 @@ def extras(torch, c8r, synth, w):
         out[f"{tag}_separate_launches_pairs_per_s"] = r["separate"]
         out[f"{tag}_workload"] = r["workload"]
     return out
+
+
+def adjoint_timing(torch, c8r, w4, d4, formalism):
+    """(forward ms, adjoint ms) per pass; both include their ingest."""
+    p = c8r.RadioProcess(w4["medium"], w4["ant_xyz"], w4["t_start_ns"], w4["n_bins"], w4["dt_ns"], formalism, "mixed")
+    n4 = d4["x0"].numel()
+    g = torch.randn((len(w4["ant_xyz"]), 3, w4["n_bins"]), device="cuda")
+    tg = {f: torch.zeros(n4, dtype=torch.float32, device="cuda") for f in c8r.GRAD_FIELDS}
+    ag = torch.zeros((len(w4["ant_xyz"]), 3), dtype=torch.float64, device="cuda")
+    dn = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def fwd():
+        p.reset()
+        p.push(d4)
+
+    def bwd():
+        c8r.c8r_backward(p.ctx, d4, g, tg, ag, dn)
+
+    for fn in (fwd, bwd):
+        fn()
+    torch.cuda.synchronize()
+    times = {}
+    for name, fn in (("fwd", fwd), ("bwd", bwd)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / 3
+    p.close()
+    return times["fwd"], times["bwd"]
 
 
 def batched_vs_separate(torch, c8r, synth, scale):
