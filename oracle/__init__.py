@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-UNIFORM, EXPONENTIAL = 0, 1
+UNIFORM, EXPONENTIAL, EXPONENTIAL_SPHERICAL = 0, 1, 2
 ENDPOINT, ZHS = 0, 1
 MODE_NORMAL, MODE_FORCE_MIDPOINT, MODE_ZHS_EDGE_SAMPLED, MODE_ABS = 0, 1, 2, 3
 FIELDS = ("x0", "y0", "z0", "x1", "y1", "z1", "t0", "t1", "bx", "by", "bz", "q")
@@ -37,7 +37,18 @@ class _Tracks(ctypes.Structure):
 
 
 class _Medium(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_double), ("N0", ctypes.c_double), ("H", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_double), ("N0", ctypes.c_double), ("H", ctypes.c_double),
+                ("R_E", ctypes.c_double)]
+
+
+def _medium_struct(medium):
+    """medium dict: kind "uniform" (n), "exponential" (N0, H) or
+    "exponential_spherical" (N0, H, R_E)."""
+    kind = medium["kind"]
+    k = {UNIFORM: UNIFORM, "uniform": UNIFORM, EXPONENTIAL: EXPONENTIAL, "exponential": EXPONENTIAL,
+         EXPONENTIAL_SPHERICAL: EXPONENTIAL_SPHERICAL, "exponential_spherical": EXPONENTIAL_SPHERICAL}[kind]
+    return _Medium(k, float(medium.get("n", 1.0)), float(medium.get("N0", 0.0)), float(medium.get("H", 1.0)),
+                   float(medium.get("R_E", 0.0)))
 
 
 class _Antennas(ctypes.Structure):
@@ -110,8 +121,7 @@ class _Pack:
             raise ValueError("antenna position / start time counts differ")
         self.A = _Antennas(_dptr(self.xyz), _dptr(self.t_ref), len(self.xyz), int(n_bins), float(dt))
         kind = medium["kind"]
-        self.M = _Medium(EXPONENTIAL if kind in (EXPONENTIAL, "exponential") else UNIFORM,
-                         float(medium.get("n", 1.0)), float(medium.get("N0", 0.0)), float(medium.get("H", 1.0)))
+        self.M = _medium_struct(medium)
 
 
 def tracks_from_ns(tracks: dict) -> dict:
@@ -144,9 +154,12 @@ def arrivals(tracks, ant_xyz, t_ref, n_bins, dt, medium, formalism=ENDPOINT, eps
 
 
 def backward(tracks, ant_xyz, t_ref, n_bins, dt, medium, grad_traces, eps_C=1e-3, formalism=ENDPOINT):
-    """Adjoint of forward(): (track_grad [n, 11], ant_grad [n_ant, 3], dN0)."""
+    """Adjoint of forward(): (track_grad [n, 11], ant_grad [n_ant, 3], dN0).
+    Not defined for the spherical-Earth atmosphere."""
     lib = _load()
     p = _Pack(tracks, ant_xyz, t_ref, n_bins, dt, medium)
+    if p.M.kind == EXPONENTIAL_SPHERICAL:
+        raise ValueError("the adjoint is not defined for the spherical-Earth atmosphere")
     G = np.ascontiguousarray(grad_traces, dtype=np.float64)
     if G.shape != (len(p.xyz), 3, int(n_bins)):
         raise ValueError("grad_traces shape")
@@ -165,9 +178,7 @@ def backward(tracks, ant_xyz, t_ref, n_bins, dt, medium, grad_traces, eps_C=1e-3
 def propagate(medium, x_e, x_a):
     """(R, n_src, n_avg, delay_s) of the straight path x_e -> x_a."""
     lib = _load()
-    kind = medium["kind"]
-    M = _Medium(EXPONENTIAL if kind in (EXPONENTIAL, "exponential") else UNIFORM,
-                float(medium.get("n", 1.0)), float(medium.get("N0", 0.0)), float(medium.get("H", 1.0)))
+    M = _medium_struct(medium)
     xe = np.ascontiguousarray(x_e, dtype=np.float64)
     xa = np.ascontiguousarray(x_a, dtype=np.float64)
     out = np.zeros(4)

@@ -23,6 +23,11 @@
  *     n(z) = 1 + N0 exp(-z/H), n_src = n(z_e), n_avg = path average of n(z),
  *     evaluated in the expm1 form that is exact for every dz; arrival time
  *     t_arr = t_e + n_avg R / c.  The Doppler factor uses n_src.
+ *  MS the exponential atmosphere over a spherical Earth (the straight path is
+ *     kept; only the altitude is measured from the sphere): centre (0, 0, -R_E),
+ *     h(x) = |x - centre| - R_E, n(x) = 1 + N0 exp(-h(x)/H); n_avg R is the
+ *     integral of n along the path, by composite 8-point Gauss-Legendre
+ *     quadrature (64 panels).
  *  T  binning: bin k of antenna a covers [t_ref + k dt, t_ref + (k+1) dt); a
  *     deposit with k outside [0, N) is dropped.
  *  E  Endpoint: at the start (sign +1) and the end (sign -1) of the track a
@@ -56,7 +61,7 @@
 #define OR_QE 1.602176634e-19           /* C                          */
 #define OR_PI 3.14159265358979323846
 
-enum { OR_UNIFORM = 0, OR_EXPONENTIAL = 1 };
+enum { OR_UNIFORM = 0, OR_EXPONENTIAL = 1, OR_EXPONENTIAL_SPHERICAL = 2 };
 enum { OR_ENDPOINT = 0, OR_ZHS = 1 };
 /* oracle-only evaluation modes used by the tests: the identity tests force the
    Endpoint midpoint form or sample the ZHS potential at bin edges; MODE_ABS
@@ -72,10 +77,11 @@ typedef struct {
 } or_tracks;
 
 typedef struct {
-  int kind;        /* OR_UNIFORM or OR_EXPONENTIAL                          */
+  int kind;        /* OR_UNIFORM, OR_EXPONENTIAL or OR_EXPONENTIAL_SPHERICAL */
   double n;        /* uniform: refractive index                             */
   double N0;       /* exponential: refractivity at z = 0                    */
   double H;        /* exponential: scale height, m                          */
+  double R_E;      /* spherical: Earth radius, m                            */
 } or_medium;
 
 typedef struct {
@@ -131,10 +137,44 @@ typedef struct {
   double n_src, n_avg, dn_src_dN0, dn_src_dze;
 } or_path;
 
+/* reading MS: altitude above the sphere, without the cancellation of |x - c| - R_E */
+static double sphere_altitude(const or_medium* m, const double x[3]) {
+  double zr = x[2] + m->R_E;
+  double r = sqrt(x[0] * x[0] + x[1] * x[1] + zr * zr);
+  return (x[0] * x[0] + x[1] * x[1] + x[2] * (x[2] + 2.0 * m->R_E)) / (r + m->R_E);
+}
+
+/* integral of N0 exp(-h/H) along the straight path xe -> xe + R rhat */
+static double sphere_refractive_path(const or_medium* m, const double xe[3], const double rh[3], double R) {
+  static const double xg[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+  static const double wg[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+  const int panels = 64;
+  double sum = 0.0, hw = 0.5 * R / panels;
+  for (int pn = 0; pn < panels; ++pn) {
+    double mid = (pn + 0.5) * (R / panels);
+    for (int j = 0; j < 4; ++j) {
+      for (int sg = -1; sg <= 1; sg += 2) {
+        double sdist = mid + sg * hw * xg[j], x[3];
+        for (int c = 0; c < 3; ++c) x[c] = xe[c] + sdist * rh[c];
+        sum += wg[j] * hw * m->N0 * exp(-sphere_altitude(m, x) / m->H);
+      }
+    }
+  }
+  return sum;
+}
+
 static void propagate(const or_medium* m, const double xe[3], const double xa[3], or_path* p) {
   for (int c = 0; c < 3; ++c) p->d[c] = xa[c] - xe[c];
   p->R = sqrt(p->d[0] * p->d[0] + p->d[1] * p->d[1] + p->d[2] * p->d[2]);
   for (int c = 0; c < 3; ++c) p->rh[c] = p->d[c] / p->R;
+  if (m->kind == OR_EXPONENTIAL_SPHERICAL) {
+    double E = exp(-sphere_altitude(m, xe) / m->H);
+    p->n_src = 1.0 + m->N0 * E;
+    p->n_avg = 1.0 + sphere_refractive_path(m, xe, p->rh, p->R) / p->R;
+    p->dn_src_dN0 = E;
+    p->dn_src_dze = NAN; /* the adjoint is not defined for this medium */
+    return;
+  }
   medium_indices(m, xe[2], xa[2], &p->n_src, &p->n_avg, &p->dn_src_dN0, &p->dn_src_dze);
 }
 

@@ -433,6 +433,80 @@ def test_exponential_path_average_continuous_at_equal_altitude():
 
 
 # ---------------------------------------------------------------------------
+# reading MS: the exponential atmosphere over a spherical Earth
+# ---------------------------------------------------------------------------
+SPH_AIR = dict(kind="exponential_spherical", N0=3.25e-4, H=8000.0, R_E=6371e3)
+
+
+def _sphere_h(x, R_E):
+    x = [mp.mpf(float(v)) for v in x]
+    return mp.sqrt(x[0] ** 2 + x[1] ** 2 + (x[2] + R_E) ** 2) - R_E
+
+
+def test_spherical_emission_index_closed_form():
+    mp.mp.dps = 40
+    for xe in ([0.0, 0.0, 4000.0], [10000.0, 0.0, 0.0], [15000.0, -7000.0, 2500.0]):
+        h = _sphere_h(xe, mp.mpf(SPH_AIR["R_E"]))
+        n_src = 1 + mp.mpf(SPH_AIR["N0"]) * mp.exp(-h / SPH_AIR["H"])
+        got = oracle.propagate(SPH_AIR, xe, [0.0, 0.0, 0.0])[1]
+        assert abs(got - float(n_src)) <= 1e-15 * float(n_src)
+
+
+def test_spherical_path_integral_against_mpmath_quadrature():
+    mp.mp.dps = 30
+    R_E, N0, H = mp.mpf(SPH_AIR["R_E"]), mp.mpf(SPH_AIR["N0"]), mp.mpf(SPH_AIR["H"])
+    for xe, xa in (([9000.0, 3000.0, 5000.0], [120.0, -40.0, 0.0]), ([-20000.0, 500.0, 9000.0], [300.0, 800.0, 10.0])):
+        d = [mp.mpf(b) - mp.mpf(a) for a, b in zip(xe, xa)]
+        R = mp.sqrt(sum(v * v for v in d))
+
+        def f(s):
+            x = [mp.mpf(xe[k]) + s * d[k] / R for k in range(3)]
+            return N0 * mp.exp(-(mp.sqrt(x[0] ** 2 + x[1] ** 2 + (x[2] + R_E) ** 2) - R_E) / H)
+
+        F = mp.quad(f, [0, R / 2, R])
+        got = oracle.propagate(SPH_AIR, xe, xa)
+        assert got[0] == pytest.approx(float(R), rel=1e-15)
+        assert (got[2] - 1.0) * got[0] == pytest.approx(float(F), rel=1e-12)
+
+
+def test_spherical_radial_path_equals_flat_closed_form():
+    """Along a vertical line through the sphere's centre the altitude is z itself,
+    so the spherical path integral equals the flat closed form."""
+    flat = dict(kind="exponential", N0=SPH_AIR["N0"], H=SPH_AIR["H"])
+    for ze, za in ((500.0, 0.0), (4000.0, 0.0), (9000.0, 1200.0), (100.0, 3000.0)):
+        a = oracle.propagate(flat, [0.0, 0.0, ze], [0.0, 0.0, za])
+        b = oracle.propagate(SPH_AIR, [0.0, 0.0, ze], [0.0, 0.0, za])
+        assert b[2] - 1.0 == pytest.approx(a[2] - 1.0, rel=1e-13)
+        assert b[1] == pytest.approx(a[1], rel=1e-15)
+
+
+def test_spherical_reduces_to_flat_for_a_large_radius():
+    flat = dict(kind="exponential", N0=SPH_AIR["N0"], H=SPH_AIR["H"])
+    big = dict(SPH_AIR, R_E=1e13)
+    for xe, xa in (([9000.0, 3000.0, 5000.0], [120.0, -40.0, 0.0]), ([-20000.0, 500.0, 9000.0], [300.0, 800.0, 10.0])):
+        a = oracle.propagate(flat, xe, xa)
+        b = oracle.propagate(big, xe, xa)
+        c = oracle.propagate(SPH_AIR, xe, xa)
+        assert abs(b[2] - a[2]) <= 1e-9 * (a[2] - 1.0)
+        assert abs(c[2] - a[2]) > 1e-5 * (a[2] - 1.0)  # at the real radius the curvature shows
+
+
+def test_spherical_path_integral_symmetric_and_additive():
+    xa, xb = np.array([-15000.0, 4000.0, 8000.0]), np.array([200.0, -100.0, 0.0])
+    fwd = oracle.propagate(SPH_AIR, xa, xb)
+    rev = oracle.propagate(SPH_AIR, xb, xa)
+    assert rev[2] == pytest.approx(fwd[2], rel=1e-15)
+    F = (fwd[2] - 1.0) * fwd[0]
+    for lam in (0.2, 0.5, 0.77):
+        xm = xa + lam * (xb - xa)
+        p1 = oracle.propagate(SPH_AIR, xa, xm)
+        p2 = oracle.propagate(SPH_AIR, xm, xb)
+        # the quadrature is good to ~1e-13 (pinned against mpmath above); a sum of
+        # two adds their errors
+        assert (p1[2] - 1.0) * p1[0] + (p2[2] - 1.0) * p2[0] == pytest.approx(F, rel=2e-12)
+
+
+# ---------------------------------------------------------------------------
 # adjoint vs central finite differences
 # ---------------------------------------------------------------------------
 def _loss(tr, ant, t_ref, medium, G, dt, N):
