@@ -47,6 +47,7 @@ extern "C" {
 /* medium kinds (straight-line propagator, §4 listing) */
 #define C8R_UNIFORM 0      /* n constant                                              */
 #define C8R_EXPONENTIAL 1  /* n(z) = 1 + N0 exp(-z / H), z = altitude in metres         */
+#define C8R_EXPONENTIAL_SPHERICAL 2 /* the same over a spherical Earth (c8r_set_medium_spherical) */
 
 /* formalisms (§1) */
 #define C8R_ENDPOINT 0
@@ -121,6 +122,18 @@ const char* c8r_last_error(const c8r_ctx* ctx);
  * May be called before or after c8r_set_antennas; traces already accumulated
  * are kept.  EINVAL on non-finite or out-of-range values. */
 int c8r_set_medium(c8r_ctx* ctx, int kind, double n_or_N0, double scale_height_m);
+
+/* The exponential medium over a spherical Earth (an Earth-curvature option of the
+ * straight-line propagator; the paper notes that the propagator's complexity sets
+ * the cost of the step, §2): the Earth's centre is at (0, 0, -earth_radius_m),
+ * the altitude of a point x is h(x) = |x - centre| - earth_radius_m and
+ * n(x) = 1 + N0 exp(-h(x) / H).  The path stays straight; the travel time uses
+ * the integral of n along it (the flat-atmosphere closed form plus an 8-point
+ * Gauss-Legendre quadrature of the curvature correction), the Doppler factor
+ * n at the emission point.  The adjoint (c8r_backward), the batched launch and
+ * c8r_traces_noalloc do not take this medium (EINVAL).  EINVAL unless N0 >= 0,
+ * H > 0 and earth_radius_m > 0 are finite.  Sets kind C8R_EXPONENTIAL_SPHERICAL. */
+int c8r_set_medium_spherical(c8r_ctx* ctx, double N0, double scale_height_m, double earth_radius_m);
 
 /* Antenna collection ("detector", §2, §4 make_radio_process_*).  pos_xyz: HOST
  * array [n_ant][3] of antenna positions (m); t_start_ns: HOST array [n_ant] of the

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libc8r.so")
 
 C8R_OK = 0
 C8R_EINVAL, C8R_ENOMEM, C8R_ECUDA, C8R_ECANCELLED, C8R_ETOOBIG, C8R_ESTATE = -1, -2, -3, -4, -5, -6
-C8R_UNIFORM, C8R_EXPONENTIAL = 0, 1
+C8R_UNIFORM, C8R_EXPONENTIAL, C8R_EXPONENTIAL_SPHERICAL = 0, 1, 2
 C8R_ENDPOINT, C8R_ZHS = 0, 1
 C8R_FP64, C8R_MIXED = 0, 1
 C8R_F32, C8R_F64 = 0, 1
@@ -76,6 +76,7 @@ _SIGNATURES = [
     ("c8r_destroy", None, [_P]),
     ("c8r_last_error", ctypes.c_char_p, [_P]),
     ("c8r_set_medium", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+    ("c8r_set_medium_spherical", ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     ("c8r_set_antennas", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
                                         ctypes.c_int, ctypes.c_int]),
@@ -186,6 +187,10 @@ def c8r_set_medium(ctx, kind, n_or_N0, scale_height_m=1.0):
     return _check(ctx, load().c8r_set_medium(ctx, int(kind), float(n_or_N0), float(scale_height_m)))
 
 
+def c8r_set_medium_spherical(ctx, N0, scale_height_m, earth_radius_m):
+    return _check(ctx, load().c8r_set_medium_spherical(ctx, float(N0), float(scale_height_m), float(earth_radius_m)))
+
+
 def c8r_set_antennas(ctx, pos_xyz, t_start_ns, n_bins, dt_ns, formalism, precision):
     pos = np.ascontiguousarray(pos_xyz, dtype=np.float64).reshape(-1, 3)
     ts = np.ascontiguousarray(t_start_ns, dtype=np.float64).reshape(-1)
@@ -280,7 +285,7 @@ def c8r_measure_peaks(device: int = 0):
 # ---------------------------------------------------------------------------
 # paper-level convenience objects
 # ---------------------------------------------------------------------------
-_MEDIUM = {"uniform": C8R_UNIFORM, "exponential": C8R_EXPONENTIAL}
+_MEDIUM = {"uniform": C8R_UNIFORM, "exponential": C8R_EXPONENTIAL, "exponential_spherical": C8R_EXPONENTIAL_SPHERICAL}
 _FORMALISM = {"endpoint": C8R_ENDPOINT, "coreas": C8R_ENDPOINT, "zhs": C8R_ZHS}
 _PRECISION = {"fp64": C8R_FP64, "mixed": C8R_MIXED}
 
@@ -304,6 +309,8 @@ class RadioProcess:
         kind = _MEDIUM[medium["kind"]]
         if kind == C8R_UNIFORM:
             c8r_set_medium(self.ctx, kind, medium["n"], 1.0)
+        elif kind == C8R_EXPONENTIAL_SPHERICAL:
+            c8r_set_medium_spherical(self.ctx, medium["N0"], medium["H"], medium["R_E"])
         else:
             c8r_set_medium(self.ctx, kind, medium["N0"], medium["H"])
         c8r_set_antennas(self.ctx, ant_xyz, t_start_ns, n_bins, dt_ns, _FORMALISM[formalism], _PRECISION[precision])

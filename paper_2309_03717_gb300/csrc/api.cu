@@ -18,7 +18,8 @@ namespace c8r {
 
 static thread_local std::string g_create_error;
 
-void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, double dt_ns, double eps_C) {
+void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, double dt_ns, double eps_C,
+                 double earth_radius) {
   std::memset(&M, 0, sizeof(M));
   auto split = [](double x, float& h, float& l) {
     h = (float)x;
@@ -52,6 +53,8 @@ void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, d
     split(1.0 / H, M.invH_h, M.invH_l);
     M.N0f = (float)n_or_N0;
     M.nf = 1.0f;
+    M.R_E = earth_radius;
+    M.RE_f = (float)earth_radius;
   }
 }
 
@@ -65,7 +68,7 @@ void fill_antenna(AntRec& r, double x, double y, double z, double t_ref_ns, cons
   r.y = y;
   r.z = z;
   r.t_ref = t_ref_ns;
-  r.Ea = (M.kind == C8R_EXPONENTIAL) ? std::exp(-z / M.H) : 1.0;
+  r.Ea = (M.kind != C8R_UNIFORM) ? std::exp(-z / M.H) : 1.0;  // flat: the sphere's part comes per pair
   split(x, r.xh, r.xl);
   split(y, r.yh, r.yl);
   split(z, r.zh, r.zl);
@@ -87,7 +90,7 @@ struct c8r_ctx {
   // medium
   bool medium_set = false;
   int med_kind = C8R_UNIFORM;
-  double med_a = 1.0, med_H = 1.0;
+  double med_a = 1.0, med_H = 1.0, med_RE = 0.0;
   double eps_C = 1e-3;
   // antennas
   bool ants_set = false;
@@ -137,7 +140,7 @@ bool finite_all(const double* p, size_t n) {
 
 int rebuild_tables(c8r_ctx* c) {
   if (!c->ants_set) return C8R_OK;
-  fill_medium(c->M, c->med_kind, c->med_a, c->med_H, c->n_bins, c->dt_ns, c->eps_C);
+  fill_medium(c->M, c->med_kind, c->med_a, c->med_H, c->n_bins, c->dt_ns, c->eps_C, c->med_RE);
   std::vector<AntRec> recs(c->n_ant);
   for (int a = 0; a < c->n_ant; ++a)
     fill_antenna(recs[a], c->pos[3 * a], c->pos[3 * a + 1], c->pos[3 * a + 2], c->t_start[a], c->M);
@@ -282,6 +285,8 @@ int c8r_set_medium(c8r_ctx* c, int kind, double n_or_N0, double H) {
   } else if (kind == C8R_EXPONENTIAL) {
     if (!std::isfinite(n_or_N0) || n_or_N0 < 0.0) return fail(c, C8R_EINVAL, "exponential medium needs finite N0 >= 0");
     if (!std::isfinite(H) || !(H > 0.0)) return fail(c, C8R_EINVAL, "exponential medium needs finite H > 0");
+  } else if (kind == C8R_EXPONENTIAL_SPHERICAL) {
+    return fail(c, C8R_EINVAL, "the spherical-Earth medium is set with c8r_set_medium_spherical");
   } else {
     return fail(c, C8R_EINVAL, "unknown medium kind");
   }
@@ -289,6 +294,21 @@ int c8r_set_medium(c8r_ctx* c, int kind, double n_or_N0, double H) {
   c->med_kind = kind;
   c->med_a = n_or_N0;
   c->med_H = H;
+  c->med_RE = 0.0;
+  c->medium_set = true;
+  return rebuild_tables(c);
+}
+
+int c8r_set_medium_spherical(c8r_ctx* c, double N0, double H, double RE) {
+  if (!c) return C8R_EINVAL;
+  if (!std::isfinite(N0) || N0 < 0.0) return fail(c, C8R_EINVAL, "spherical medium needs finite N0 >= 0");
+  if (!std::isfinite(H) || !(H > 0.0)) return fail(c, C8R_EINVAL, "spherical medium needs finite H > 0");
+  if (!std::isfinite(RE) || !(RE > 0.0)) return fail(c, C8R_EINVAL, "spherical medium needs a finite Earth radius > 0");
+  cudaSetDevice(c->device);
+  c->med_kind = C8R_EXPONENTIAL_SPHERICAL;
+  c->med_a = N0;
+  c->med_H = H;
+  c->med_RE = RE;
   c->medium_set = true;
   return rebuild_tables(c);
 }
@@ -542,6 +562,8 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
   int r = ready(c);
   if (r != C8R_OK) return r;
   if ((r = check_tracks(c, t, n)) != C8R_OK) return r;
+  if (c->med_kind == C8R_EXPONENTIAL_SPHERICAL)
+    return fail(c, C8R_EINVAL, "c8r_backward does not take the spherical-Earth medium");
   if (!grad_traces || !out || !ant_grad || !dN0) return fail(c, C8R_EINVAL, "NULL gradient pointer");
   const int want = c->precision == C8R_FP64 ? C8R_F64 : C8R_F32;
   if (out->dtype != want) return fail(c, C8R_EINVAL, "out_tracks.dtype must match the context precision");

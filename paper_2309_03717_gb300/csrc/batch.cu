@@ -385,6 +385,7 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
     return bad(C8R_EINVAL, "batch descriptor incomplete");
   if (d->n_bins < 1 || !(d->dt_ns > 0.0)) return bad(C8R_EINVAL, "n_bins / dt_ns");
   if (d->formalism != C8R_ENDPOINT && d->formalism != C8R_ZHS) return bad(C8R_EINVAL, "formalism");
+  if (kind != C8R_UNIFORM && kind != C8R_EXPONENTIAL) return bad(C8R_EINVAL, "medium kind (uniform or exponential)");
   if (kind == C8R_UNIFORM ? !(n_or_N0 > 0.0) : !(n_or_N0 >= 0.0 && H > 0.0)) return bad(C8R_EINVAL, "medium");
   if (d->n_bins > (1 << 24)) return bad(C8R_ETOOBIG, "n_bins exceeds 2^24");
   if (cudaSetDevice(device) != cudaSuccess) return bad(C8R_EINVAL, "device");

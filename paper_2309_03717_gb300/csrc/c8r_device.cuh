@@ -78,6 +78,7 @@ struct MedParams {
   int n_bins;
   double n;              // uniform index
   double N0, H, invH;    // exponential
+  double R_E;            // spherical: Earth radius (m)
   double dt_ns;
   double inv_c_ns;       // 1 / c in ns/m
   double eps_Cd;         // near-Cherenkov threshold (FP64 path)
@@ -91,6 +92,7 @@ struct MedParams {
   float ampE;            // K/dt of the Endpoint amplitude (per unit charge), FP64 rounded once
   float kzhs;            // K_A of the ZHS amplitude
   float nm1f;            // uniform: n - 1 formed in FP64, then rounded (never (1 + x) - 1 in FP32)
+  float RE_f;            // spherical: Earth radius (m)
   float eps_C;           // near-Cherenkov threshold
 };
 
@@ -173,6 +175,49 @@ struct GeoD {
   double d[3], R, rh[3], n_src, n_avg;
 };
 
+// ---------------------------------------------------------------------------
+// exponential atmosphere over a spherical Earth (centre (0, 0, -R_E)): the
+// altitude excess of a point over the flat altitude z,
+//   delta = h - z = |x - centre| - R_E - z = rho^2 / (|x - centre| + z + R_E),
+// written without the cancellation of the first form.  The optical path is the
+// flat closed form plus the integral along the straight path of
+// N0 exp(-z/H) (exp(-delta/H) - 1), by 8-point Gauss-Legendre quadrature (nodes
+// sigma_j on [0, 1] from the emission point, weights w_j summing to 1).
+// ---------------------------------------------------------------------------
+constexpr int kSphNodes = 8;
+__device__ __constant__ const double kSphSigma[kSphNodes] = {
+    0.019855071751231856, 0.10166676129318664, 0.2372337950418355, 0.4082826787521751,
+    0.5917173212478249,   0.7627662049581645,  0.8983332387068134, 0.9801449282487681};
+__device__ __constant__ const double kSphWeight[kSphNodes] = {
+    0.05061426814518813, 0.11119051722668724, 0.15685332293894363, 0.18134189168918100,
+    0.18134189168918100, 0.15685332293894363, 0.11119051722668724, 0.05061426814518813};
+
+template <typename T>
+__device__ __forceinline__ T sphere_excess(T x, T y, T z, T R_E) {
+  const T rho2 = x * x + y * y;
+  const T zr = z + R_E;
+  return rho2 / (sqrt(rho2 + zr * zr) + zr);
+}
+// exp(-x) - 1 for x >= 0 without cancellation
+template <typename T>
+__device__ __forceinline__ T exp_m1_neg(T x) {
+  if (x < T(0.1)) return -x * (T(1) + x * (T(-0.5) + x * (T(1) / T(6) + x * (T(-1) / T(24) + x * (T(1) / T(120))))));
+  return exp(-x) - T(1);
+}
+// the curvature part of the optical path from x_e to the antenna a, d = a - x_e
+template <typename T>
+__device__ __forceinline__ T sphere_path_correction(T ax, T ay, T az, T dx, T dy, T dz, T R, T N0, T invH, T R_E) {
+  T sum = T(0);
+#pragma unroll
+  for (int j = 0; j < kSphNodes; ++j) {
+    const T f = T(1) - T(kSphSigma[j]);  // the node at x_e + sigma d = a - (1 - sigma) d
+    const T x = ax - f * dx, y = ay - f * dy, z = az - f * dz;
+    const T ex = sphere_excess(x, y, z, R_E);
+    sum += T(kSphWeight[j]) * exp(-z * invH) * exp_m1_neg(ex * invH);
+  }
+  return N0 * R * sum;
+}
+
 // straight emission path x_e -> antenna (propagator, §2): distance, direction,
 // source index and path-averaged index of the medium
 __device__ __forceinline__ void geo_f64(const MedParams& M, const AntRec& A, double xe, double ye, double ze,
@@ -200,6 +245,11 @@ __device__ __forceinline__ void geo_f64(const MedParams& M, const AntRec& A, dou
     else
       ratio = Ee * (1.0 + x * (-0.5 + x * (1.0 / 6.0 + x * (-1.0 / 24.0 + x * (1.0 / 120.0)))));
     g.n_avg = 1.0 + M.N0 * ratio;
+    if (M.kind == C8R_EXPONENTIAL_SPHERICAL) {
+      g.n_src = 1.0 + M.N0 * Ee * exp(-sphere_excess(xe, ye, ze, M.R_E) * M.invH);
+      g.n_avg += sphere_path_correction<double>(A.x, A.y, A.z, g.d[0], g.d[1], g.d[2], g.R, M.N0, M.invH, M.R_E) /
+                 g.R;
+    }
   }
 }
 
@@ -273,17 +323,20 @@ __device__ __forceinline__ void geo_mixed(const AntRec& A, float pxh, float pyh,
 
 // arrival position u = (t_e - t_ref)/dt + n_avg R / (c dt) in bins, float-float.
 // tau_e = t_e/dt and the antenna's tau = t_ref/dt come in float-float.
+// KIND: the medium kind (a template argument, so each kernel carries only its own
+// medium's arithmetic; it equals M.kind)
+template <int KIND>
 __device__ __forceinline__ ff arrival_mixed(const MedParams& M, const AntRec& A, const GeoM& g, float tauh, float taul,
                                             float Eeh, float Eel) {
   float ts, te;
   two_sum(tauh, -A.tauh, ts, te);
   te = __fadd_rn(te, __fsub_rn(taul, A.taul));
-  float sh = (M.kind == C8R_UNIFORM) ? M.s_h : M.kc_h;
-  float sl = (M.kind == C8R_UNIFORM) ? M.s_l : M.kc_l;
+  float sh = (KIND == C8R_UNIFORM) ? M.s_h : M.kc_h;
+  float sl = (KIND == C8R_UNIFORM) ? M.s_l : M.kc_l;
   float p, pe;
   two_prod(g.R0, sh, p, pe);
   pe = __fmaf_rn(g.R0, sl, __fmaf_rn(g.R1, sh, pe));
-  if (M.kind == C8R_EXPONENTIAL) {
+  if constexpr (KIND != C8R_UNIFORM) {
     // refractivity term (n_avg - 1) R/(c dt) = N0 H/(c dt) * (E_e - E_a)/dz * R
     float q0, q1;
     float dzh = g.s[2], dzl = g.e[2];
@@ -319,6 +372,15 @@ __device__ __forceinline__ ff arrival_mixed(const MedParams& M, const AntRec& A,
     fast_two_sum(p, v, p2, pe2);  // |v| = (n_avg - 1)|p| < |p|
     p = p2;
     pe = __fadd_rn(pe, __fadd_rn(pe2, ve));
+    if constexpr (KIND == C8R_EXPONENTIAL_SPHERICAL) {
+      // curvature correction (~1e-3 of the refractivity term, FP32 is enough)
+      const float cs = __fmul_rn(
+          sphere_path_correction<float>(A.xh, A.yh, A.zh, g.s[0], g.s[1], g.s[2], g.R0, M.N0f, M.invH_h, M.RE_f),
+          M.kc_h);
+      fast_two_sum(p, cs, p2, pe2);
+      p = p2;
+      pe = __fadd_rn(pe, pe2);
+    }
   }
   float uh, ue;
   two_sum(ts, p, uh, ue);

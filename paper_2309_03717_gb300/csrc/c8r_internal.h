@@ -63,7 +63,8 @@ cudaError_t launch_bin_running_sums(int precision, const void* g, int n_ant, int
                                     cudaStream_t st);
 
 // helpers shared by the context and the batch runner
-void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, double dt_ns, double eps_C);
+void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, double dt_ns, double eps_C,
+                 double earth_radius = 0.0);
 void fill_antenna(AntRec& r, double x, double y, double z, double t_ref_ns, const MedParams& M);
 
 }  // namespace c8r

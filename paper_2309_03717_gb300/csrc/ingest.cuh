@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256) k_ingest_mixed(TrackPtrs t, Map map, int6
         const float bmag = sqrtf((float)S);
         out[fm::BMAG] = bmag;
         out[fm::OMB] = __fdiv_rn((float)__dsub_rn(1.0, S), __fadd_rn(1.0f, bmag));
-        if (M.kind == C8R_EXPONENTIAL) {
+        if (M.kind != C8R_UNIFORM) {  // flat exp(-z/H); the sphere's part comes per pair
           exp_alt(f[2], 0.0f, M, out[fm::E0H], out[fm::E0L]);
           exp_alt(f[5], 0.0f, M, out[fm::E1H], out[fm::E1L]);
           float zmh, zml;  // (z0 + z1)/2, exact
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) k_ingest_f64(TrackPtrs t, Map map, int64_
         out[fd::Q] = v[11];
         out[fd::T0] = v[6];
         out[fd::T1] = v[7];
-        if (M.kind == C8R_EXPONENTIAL) {
+        if (M.kind != C8R_UNIFORM) {
           out[fd::E0] = exp(-v[2] * M.invH);
           out[fd::E1] = exp(-v[5] * M.invH);
           out[fd::EM] = exp(-(0.5 * (v[2] + v[5])) * M.invH);

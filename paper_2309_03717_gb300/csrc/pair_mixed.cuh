@@ -48,13 +48,20 @@ __device__ __forceinline__ void load_track_mixed(const float* T, int l, const Me
   t.E0h = t.E1h = t.Emh = 1.0f;
   t.E0l = t.E1l = t.Eml = 0.0f;
   t.nm1_0 = t.nm1_1 = t.nm1_m = M.nm1f;
-  if (KIND == C8R_EXPONENTIAL) {
+  if (KIND != C8R_UNIFORM) {
     t.E0h = TF(fm::E0H); t.E0l = TF(fm::E0L);
     t.E1h = TF(fm::E1H); t.E1l = TF(fm::E1L);
     t.Emh = TF(fm::EMH); t.Eml = TF(fm::EML);
     t.nm1_0 = __fmul_rn(M.N0f, t.E0h);
     t.nm1_1 = __fmul_rn(M.N0f, t.E1h);
     t.nm1_m = __fmul_rn(M.N0f, t.Emh);
+  }
+  if (KIND == C8R_EXPONENTIAL_SPHERICAL) {
+    // n - 1 at the points over the sphere: the flat N0 exp(-z/H) times exp(-delta/H)
+    t.nm1_0 = __fmul_rn(t.nm1_0, expf(-sphere_excess(t.x0, t.y0, t.z0, M.RE_f) * M.invH_h));
+    t.nm1_1 = __fmul_rn(t.nm1_1, expf(-sphere_excess(t.x1, t.y1, t.z1, M.RE_f) * M.invH_h));
+    t.nm1_m = __fmul_rn(t.nm1_m, expf(-sphere_excess(0.5f * (t.x0 + t.x1), 0.5f * (t.y0 + t.y1),
+                                                     0.5f * (t.z0 + t.z1), M.RE_f) * M.invH_h));
   }
   // 1 - n|beta| = (1 - |beta|) - (n - 1)|beta|
   t.om0 = __fsub_rn(omb, __fmul_rn(t.nm1_0, t.bmag));
@@ -108,8 +115,8 @@ __device__ __forceinline__ void endpoint_arrivals(const TrackM& t, const AntRec&
   GeoM g0 = e.g0, g1 = e.g1;
   geo_refine(g0);
   geo_refine(g1);
-  e.ua = arrival_mixed(M, A, g0, t.tau0h, t.tau0l, t.E0h, t.E0l);
-  e.ub = arrival_mixed(M, A, g1, t.tau1h, t.tau1l, t.E1h, t.E1l);
+  e.ua = arrival_mixed<KIND>(M, A, g0, t.tau0h, t.tau0l, t.E0h, t.E0l);
+  e.ub = arrival_mixed<KIND>(M, A, g1, t.tau1h, t.tau1l, t.E1h, t.E1l);
   e.branch = 0;
 }
 
@@ -122,7 +129,7 @@ __device__ __forceinline__ bool endpoint_midpoint(const TrackM& t, const AntRec&
   if (e.gm.R0 == 0.0f) return false;
   GeoM g = e.gm;
   geo_refine(g);
-  const ff u0 = arrival_mixed(M, A, g, t.tmh, t.tml, t.Emh, t.Eml);
+  const ff u0 = arrival_mixed<KIND>(M, A, g, t.tmh, t.tml, t.Emh, t.Eml);
   const ff Dm = doppler_ff(g, t.bx, t.by, t.bz, t.nm1_m);
   // the amplitude's 1/D_m, too, from the float-float D: here |D_m| can be far
   // below the FP32 form's absolute accuracy
@@ -234,7 +241,7 @@ struct OpsMixed {
     FieldM f;
     field_mixed(gm, t.bx, t.by, t.bz, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), f);
     geo_refine(gm);
-    const ff um = arrival_mixed(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml);
+    const ff um = arrival_mixed<KIND>(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml);
     ff aD = doppler_ff(gm, t.bx, t.by, t.bz, t.nm1_m);
     if (aD.h < 0.0f) {
       aD.h = -aD.h;
@@ -382,7 +389,7 @@ struct OpsMixed {
     FieldM f;
     field_mixed(gm, t.bx, t.by, t.bz, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), f);
     geo_refine(gm);
-    const ff um = arrival_mixed(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml);
+    const ff um = arrival_mixed<KIND>(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml);
     ff aD = doppler_ff(gm, t.bx, t.by, t.bz, t.nm1_m);
     const float sgn = aD.h < 0.0f ? -1.0f : 1.0f;
     if (aD.h < 0.0f) {

@@ -37,6 +37,8 @@ FIELDS = ("x0", "y0", "z0", "x1", "y1", "z1", "t0", "t1", "bx", "by", "bz", "q")
 
 AIR_UNIFORM = {"kind": "uniform", "n": 1.000292}
 AIR_EXPONENTIAL = {"kind": "exponential", "N0": 3.25e-4, "H": 8000.0}
+# the same atmosphere over a spherical Earth (mean radius 6371 km)
+AIR_SPHERICAL = {"kind": "exponential_spherical", "N0": 3.25e-4, "H": 8000.0, "R_E": 6.371e6}
 
 
 def _rot_y(theta):

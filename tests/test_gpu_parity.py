@@ -89,6 +89,35 @@ def test_traces_match_oracle(cfg, n, n_ant, formalism, precision, tol):
     assert n_cmp > 0.99 * obr.size
 
 
+@pytest.mark.parametrize("cfg,n,n_ant", [(2, 2003, 64), (1, 2003, 40)])
+@pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_spherical_earth_matches_oracle(cfg, n, n_ant, formalism, precision, tol):
+    """The exponential atmosphere over a spherical Earth: the curvature part of
+    the optical path (quadrature on the GPU, composite quadrature in the oracle)
+    and of the source index, on the inclined shower where it matters most."""
+    w = synth.workload(cfg, n_tracks=n, n_ant=n_ant)
+    w["medium"] = dict(synth.AIR_SPHERICAL)
+    if precision == "mixed":
+        w["dtype"] = np.float32
+    tracks = synth.workload_tracks(w)
+    if formalism == "endpoint":
+        keep = endpoint_unambiguous(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"])
+        tracks = drop_tracks(tracks, keep)
+    ref, kept = oracle_traces(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], formalism)
+    flat, _ = oracle_traces(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], synth.AIR_EXPONENTIAL,
+                            formalism)
+    if cfg == 2:  # the inclined shower's emission points lie tens of km out: the curvature shows
+        assert rel_l2(flat, ref) > 10 * tol
+    gpu, arr, st = run(w, tracks, formalism, precision)
+    assert st["tracks_kept"] == kept
+    err = rel_l2(gpu, ref)
+    assert err <= tol, f"relative L2 {err:.3e} > {tol:.0e}"
+    obr, ou = oracle_arrivals(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], formalism)
+    n_cmp, _ = compare_bins(arr[0], arr[1], arr[2], obr, ou, w["n_bins"])
+    assert n_cmp > 0.99 * obr.size
+
+
 @pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_invariant_to_launch_shape(formalism, precision):
