@@ -491,6 +491,20 @@ def extras(torch, c8r, synth, w):
     out["inclined_workload"] = ("8e6 tracks (2 chunks of 4e6) x 32x32 grid, 60 deg, 8192 x 0.1 ns, exponential "
                                 "atmosphere, Endpoint mixed")
     p.close()
+    # the same with the atmosphere over a spherical Earth (curvature quadrature per pair)
+    for f in ("endpoint", "zhs"):
+        p = c8r.RadioProcess(synth.AIR_SPHERICAL, w2["ant_xyz"], w2["t_start_ns"], w2["n_bins"], w2["dt_ns"], f,
+                             "mixed")
+        p.set_launch_shape(0, 0, w2["chunk"])
+        step2()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(3):
+            step2()
+        e1.record()
+        torch.cuda.synchronize()
+        out[f"inclined_spherical_{f}_pairs_per_s"] = 3 * 8_000_000 * len(w2["ant_xyz"]) / (e0.elapsed_time(e1) * 1e-3)
+        p.close()
     del d2, o2
 
     # batched uneven showers: one persistent graph-captured launch against one
