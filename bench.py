@@ -47,6 +47,12 @@ ALG_OPS_PER_ENDPOINT_PAIR = 62
 # wrote 5.3 MB; the traffic is the staged track tiles, so it scales with the
 # pairs at a fixed antenna count.  Set to None when the kernel changes.
 DRAM_BYTES_PER_ENDPOINT_PAIR = 412.9e6 / 6.4e8
+# The same capture: warp instructions issued per pair and the share of issue
+# slots busy (smsp__issue_active) -- the bound the kernel actually meets, since
+# the float-float arrival time makes its instruction count ~8x the plain
+# formula's.  Set to None when the kernel changes.
+ENDPOINT_WARP_INST_PER_PAIR = 1.0905501354e10 / 6.4e8
+ENDPOINT_ISSUE_ACTIVE_NCU = 0.864
 
 
 def parse():
@@ -403,6 +409,12 @@ def main():
                      "traffic": (DRAM_BYTES_PER_ENDPOINT_PAIR * pairs_per_launch
                                  if DRAM_BYTES_PER_ENDPOINT_PAIR and A == 160 else None),
                      "traffic_note": "DRAM bytes per launch: ncu capture of a 4e6-track launch, scaled by pairs",
+                     "issue": ({"warp_inst_per_pair_ncu": ENDPOINT_WARP_INST_PER_PAIR,
+                                "achieved_warp_inst_per_s": ENDPOINT_WARP_INST_PER_PAIR * pairs_per_launch
+                                / (kernel_ms * 1e-3),
+                                "peak_warp_inst_per_s": SM_COUNT * 4 * pk.get("sm_max_mhz", 2070.0) * 1e6,
+                                "issue_slots_busy_ncu": ENDPOINT_ISSUE_ACTIVE_NCU}
+                               if ENDPOINT_WARP_INST_PER_PAIR else None),
                      "peak_source": f"152 SMs x 128 FP32 lanes x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
                                     f"({pk_src} max SM clock)",
                      "ops_per_pair": ALG_OPS_PER_ENDPOINT_PAIR, "kernel_ms": kernel_ms,
