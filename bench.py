@@ -517,7 +517,37 @@ def extras(torch, c8r, synth, w):
         torch.cuda.synchronize()
         out[f"inclined_spherical_{f}_pairs_per_s"] = 3 * 8_000_000 * len(w2["ant_xyz"]) / (e0.elapsed_time(e1) * 1e-3)
         p.close()
-    del d2, o2
+    del d2
+    # the whole inclined shower: 1e8 tracks generated on the device by the
+    # counter-based generator, 4e6 at a time, each chunk pushed as it is made
+    n_full, chunk = 100_000_000, w2["chunk"]
+    p = c8r.RadioProcess(w2["medium"], w2["ant_xyz"], w2["t_start_ns"], w2["n_bins"], w2["dt_ns"], "endpoint", "mixed")
+    p.set_launch_shape(0, 0, chunk)
+
+    def full_pass(n):
+        p.reset()
+        for first in range(0, n, chunk):
+            p.push(c8r.c8r_generate_tracks(2309, first, min(chunk, n - first), 60.0))
+        p.traces(out=o2)
+
+    full_pass(chunk)
+    torch.cuda.synchronize()
+    e0.record()
+    full_pass(n_full)
+    e1.record()
+    torch.cuda.synchronize()
+    out["inclined_full_generated_pairs_per_s"] = n_full * len(w2["ant_xyz"]) / (e0.elapsed_time(e1) * 1e-3)
+    out["inclined_full_generated_s"] = e0.elapsed_time(e1) * 1e-3
+    e0.record()
+    for first in range(0, n_full, chunk):
+        c8r.c8r_generate_tracks(2309, first, chunk, 60.0)
+    e1.record()
+    torch.cuda.synchronize()
+    out["generate_tracks_per_s"] = n_full / (e0.elapsed_time(e1) * 1e-3)
+    out["inclined_full_workload"] = ("1e8 tracks generated on the device in 25 chunks of 4e6 x 32x32 grid, 60 deg, "
+                                     "8192 x 0.1 ns, exponential atmosphere, Endpoint mixed")
+    p.close()
+    del o2
 
     # batched uneven showers: one persistent graph-captured launch against one
     # launch per shower (64 showers; track counts scaled by 0.1 to bound the

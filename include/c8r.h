@@ -96,6 +96,16 @@ typedef struct {
   int64_t pairs;         /* kept tracks x antennas evaluated                         */
 } c8r_stats_t;
 
+/* Writable DEVICE arrays for c8r_generate_tracks, one per track field. */
+typedef struct {
+  int32_t dtype; /* must be C8R_F32 */
+  void *x0, *y0, *z0;
+  void *x1, *y1, *z1;
+  void *t0, *t1;
+  void *bx, *by, *bz;
+  void *q;
+} c8r_tracks_out;
+
 /* ---- lifecycle ------------------------------------------------------------ */
 
 /* Create a context on CUDA device `device`.  *out is NULL on failure.
@@ -302,6 +312,23 @@ int c8r_batch_sync(c8r_batch* b, void* cuda_stream);
 int c8r_traces_noalloc(const c8r_tracks* tracks, int64_t n, int32_t n_ant, const double* pos_xyz,
                        const double* t_start_ns, int32_t n_bins, double dt_ns, int formalism, int medium_kind,
                        double n_or_N0, double scale_height_m, float* out_traces, void* cuda_stream);
+
+/* ---- synthetic showers generated on the device --------------------------------- */
+
+/* Writes tracks first .. first+n-1 of the counter-based synthetic shower `seed`
+ * into out (DEVICE FP32 arrays of length n), enqueued on cuda_stream.  The
+ * shower is the one the tests and the benchmark use: start height
+ * N(4 km, 1.5 km) truncated to [0.5, 10] km, lateral offset Exp(30 m) at a
+ * uniform azimuth, direction -z tilted by N(0, 5 deg) about x and y, length
+ * U[0.5, 5] m, gamma log-uniform in [10, 1e4], charge -1 (55 %) or +1, start
+ * time (10 km - h)/c; the whole shower is rotated about y by zenith_deg.  Track g
+ * is drawn from its own Philox4x32-10 blocks, counter (g, block, tag) and key
+ * seed, so chunks of a shower can be generated independently (a stream of tracks
+ * without a host-to-device copy; the paper's workload is a full shower, §6).
+ * Not in the paper.  EINVAL on NULL arrays, n < 0, first < 0, a non-finite
+ * zenith or dtype other than C8R_F32; ECUDA if the launch fails. */
+int c8r_generate_tracks(uint64_t seed, int64_t first, int64_t n, double zenith_deg, const c8r_tracks_out* out,
+                        void* cuda_stream);
 
 /* ---- device peaks microbenchmark ----------------------------------------------- */
 

@@ -2,8 +2,8 @@
 
 Each translation unit under csrc/ is compiled in parallel to an object file in
 ``_build/`` and the objects are linked into ``_build/libc8r.so`` (CUDA runtime
-linked statically).  The FP64 kernel unit is compiled with ``--fmad=false`` so
-its arithmetic rounds exactly as written.  A rebuild happens only when a source
+linked statically).  The FP64 kernel unit and the track generator are compiled
+with ``--fmad=false`` so their arithmetic rounds exactly as written.  A rebuild happens only when a source
 or header is newer than the library.
 """
 from __future__ import annotations
@@ -22,7 +22,7 @@ LIB = os.path.join(BUILD, "libc8r.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "--expt-relaxed-constexpr"]
-PER_FILE = {"kernels_f64.cu": ["--fmad=false"]}
+PER_FILE = {"kernels_f64.cu": ["--fmad=false"], "generate.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:

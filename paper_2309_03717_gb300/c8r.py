@@ -100,6 +100,8 @@ _SIGNATURES = [
     ("c8r_batch_set_cancel", ctypes.c_int, [_P, ctypes.c_int]),
     ("c8r_batch_sync", ctypes.c_int, [_P, _P]),
     ("c8r_measure_peaks", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    ("c8r_generate_tracks", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                           ctypes.POINTER(c8r_tracks), _P]),
     ("c8r_traces_noalloc", ctypes.c_int, [ctypes.POINTER(c8r_tracks), ctypes.c_int64, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                           ctypes.c_int32, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -280,6 +282,19 @@ def c8r_measure_peaks(device: int = 0):
         raise C8RError(rc, "peaks microbenchmark failed")
     keys = ("ffma_per_s", "dfma_per_s", "rsqrt_per_s", "shared_atomic_f32_per_s", "shared_atomic_f64_per_s")
     return dict(zip(keys, list(out)))
+
+
+def c8r_generate_tracks(seed: int, first: int, n: int, zenith_deg: float = 0.0, stream=None, device=None):
+    """Tracks first .. first+n-1 of the counter-based synthetic shower `seed`,
+    generated on the device: a dict of FP32 CUDA tensors (the host twin is
+    synth.make_tracks_counter)."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    out = {f: torch.empty(int(n), dtype=torch.float32, device=dev) for f in TRACK_FIELDS}
+    s = c8r_tracks(C8R_F32, *[_ptr(out[f]) for f in TRACK_FIELDS])  # same layout as c8r_tracks_out
+    rc = load().c8r_generate_tracks(int(seed), int(first), int(n), float(zenith_deg), ctypes.byref(s), _stream(stream))
+    if rc < 0:
+        raise C8RError(rc, "c8r_generate_tracks failed")
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -225,3 +225,99 @@ def batched_workload(n_showers: int = 64, seed: int = 1003, track_scale: float =
                         t_start_ns=trace_start_ns(ant, zen), seed=seed * 1000 + s,
                         medium=dict(AIR_EXPONENTIAL), n_bins=4096, dt_ns=0.2, dtype=np.float32))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Counter-based shower generator: the same distributions as make_tracks, with
+# every track drawn from its own Philox4x32-10 blocks (Salmon, Moraes, Dror &
+# Shaw, SC'11), so any range of tracks of a shower can be generated on its own
+# and on the device (c8r_generate_tracks) with the same values.  All transforms
+# are FP64 with one rounding per operation, in the order written here.
+# ---------------------------------------------------------------------------
+_PHILOX_M0, _PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+_PHILOX_W0, _PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
+PHILOX_TAG = 0x63387237  # fourth counter word of every block
+H_ATTEMPTS = 16          # rejection attempts for the start height
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Vectorised Philox4x32-10 (uint64 arrays holding 32-bit words)."""
+    c0, c1, c2, c3 = (np.asarray(v, dtype=np.uint64) for v in (c0, c1, c2, c3))
+    k0 = np.asarray(k0, dtype=np.uint64) + np.zeros_like(c0)
+    k1 = np.asarray(k1, dtype=np.uint64) + np.zeros_like(c0)
+    mask = np.uint64(0xFFFFFFFF)
+    for _ in range(10):
+        p0 = np.uint64(_PHILOX_M0) * c0
+        p1 = np.uint64(_PHILOX_M1) * c2
+        c0, c1, c2, c3 = (p1 >> np.uint64(32)) ^ c1 ^ k0, p1 & mask, (p0 >> np.uint64(32)) ^ c3 ^ k1, p0 & mask
+        k0 = (k0 + np.uint64(_PHILOX_W0)) & mask
+        k1 = (k1 + np.uint64(_PHILOX_W1)) & mask
+    return c0, c1, c2, c3
+
+
+def _u01(w):
+    return (w.astype(np.float64) + 0.5) * (1.0 / 4294967296.0)
+
+
+def make_tracks_counter(first: int, n: int, seed: int, zenith_deg: float = 0.0) -> dict:
+    """Tracks first .. first+n-1 of the counter-based synthetic shower `seed`
+    (FP32 SoA).  Block b of track g is philox(counter = (g lo, g hi, b, tag),
+    key = (seed lo, seed hi)); U(w) = (w + 1/2) / 2^32.
+      block 0: r = -30 ln U, phi = 2 pi U, L = 0.5 + 4.5 U, gamma = exp(ln 10 + ln(1e3) U);
+      block 1: q = -1 if U < 0.55 else +1; two Box-Muller normals of 5 deg: ax, ay;
+      blocks 2 .. 17: start height h = 4000 + 1500 N(0,1), the first in [500, 10000]
+      (4000 if none); then the geometry of make_tracks."""
+    g = np.arange(first, first + n, dtype=np.uint64)
+    lo, hi = g & np.uint64(0xFFFFFFFF), g >> np.uint64(32)
+    k0, k1 = np.uint64(seed & 0xFFFFFFFF), np.uint64((seed >> 32) & 0xFFFFFFFF)
+
+    def block(b):
+        return philox4x32_10(lo, hi, np.full(n, b, dtype=np.uint64), np.full(n, PHILOX_TAG, dtype=np.uint64), k0, k1)
+
+    w = block(0)
+    r = -30.0 * np.log(_u01(w[0]))
+    phi = (2.0 * math.pi) * _u01(w[1])
+    L = 0.5 + 4.5 * _u01(w[2])
+    gamma = np.exp(math.log(10.0) + (math.log(1e4) - math.log(10.0)) * _u01(w[3]))
+    w = block(1)
+    q = np.where(_u01(w[0]) < 0.55, -1.0, 1.0)
+    rad = np.sqrt(-2.0 * np.log(_u01(w[1])))
+    ang = (2.0 * math.pi) * _u01(w[2])
+    sig = 5.0 * math.pi / 180.0
+    ax = sig * (rad * np.cos(ang))
+    ay = sig * (rad * np.sin(ang))
+    h = np.full(n, 4000.0)
+    done = np.zeros(n, dtype=bool)
+    for j in range(H_ATTEMPTS):
+        w = block(2 + j)
+        z = np.sqrt(-2.0 * np.log(_u01(w[0]))) * np.cos((2.0 * math.pi) * _u01(w[1]))
+        hj = 4000.0 + 1500.0 * z
+        take = ~done & (hj >= 500.0) & (hj <= 10000.0)
+        h = np.where(take, hj, h)
+        done |= take
+    ux = -(np.cos(ax) * np.sin(ay))
+    uy = np.sin(ax)
+    uz = -(np.cos(ax) * np.cos(ay))
+    un = np.sqrt((ux * ux + uy * uy) + uz * uz)
+    ux, uy, uz = ux / un, uy / un, uz / un
+    x, y, zz = r * np.cos(phi), r * np.sin(phi), h
+    if zenith_deg:
+        c, s = math.cos(math.radians(zenith_deg)), math.sin(math.radians(zenith_deg))
+        x, zz = c * x + s * zz, c * zz - s * x
+        ux, uz = c * ux + s * uz, c * uz - s * ux
+    bmag = np.sqrt(1.0 - 1.0 / (gamma * gamma))
+    b = [(ux * bmag).astype(np.float32), (uy * bmag).astype(np.float32), (uz * bmag).astype(np.float32)]
+    for _ in range(64):
+        b2 = (b[0].astype(np.float64) * b[0] + b[1].astype(np.float64) * b[1]) + b[2].astype(np.float64) * b[2]
+        bad = b2 >= 1.0
+        if not bad.any():
+            break
+        for k in range(3):
+            b[k] = np.where(bad, (b[k].astype(np.float64) * (1.0 - 2e-7)).astype(np.float32), b[k])
+    b2 = (b[0].astype(np.float64) * b[0] + b[1].astype(np.float64) * b[1]) + b[2].astype(np.float64) * b[2]
+    t0 = (10000.0 - h) / C_M_PER_NS
+    t1 = t0 + L / (np.sqrt(b2) * C_M_PER_NS)
+    f32 = np.float32
+    return {"x0": x.astype(f32), "y0": y.astype(f32), "z0": zz.astype(f32),
+            "x1": (x + ux * L).astype(f32), "y1": (y + uy * L).astype(f32), "z1": (zz + uz * L).astype(f32),
+            "t0": t0.astype(f32), "t1": t1.astype(f32), "bx": b[0], "by": b[1], "bz": b[2], "q": q.astype(f32)}
