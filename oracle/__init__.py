@@ -28,6 +28,7 @@ _lib = None
 UNIFORM, EXPONENTIAL, EXPONENTIAL_SPHERICAL = 0, 1, 2
 ENDPOINT, ZHS = 0, 1
 MODE_NORMAL, MODE_FORCE_MIDPOINT, MODE_ZHS_EDGE_SAMPLED, MODE_ABS = 0, 1, 2, 3
+DEPOSIT_BIN, DEPOSIT_LINEAR = 0, 1
 FIELDS = ("x0", "y0", "z0", "x1", "y1", "z1", "t0", "t1", "bx", "by", "bz", "q")
 C_LIGHT = 299792458.0
 
@@ -81,16 +82,16 @@ def _load():
         P = ctypes.POINTER
         lib.oracle_forward.restype = ctypes.c_int64
         lib.oracle_forward.argtypes = [P(_Tracks), ctypes.c_int64, P(_Antennas), P(_Medium), ctypes.c_int,
-                                       ctypes.c_double, ctypes.c_int, P(ctypes.c_double)]
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]
         lib.oracle_arrivals.restype = None
         lib.oracle_arrivals.argtypes = [P(_Tracks), ctypes.c_int64, P(_Antennas), P(_Medium), ctypes.c_int,
                                         ctypes.c_double, P(ctypes.c_int32), P(ctypes.c_double)]
         lib.oracle_backward.restype = None
         lib.oracle_backward.argtypes = [P(_Tracks), ctypes.c_int64, P(_Antennas), P(_Medium), ctypes.c_double,
-                                        P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+                                        ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
                                         P(ctypes.c_double)]
         lib.oracle_backward_zhs.restype = None
-        lib.oracle_backward_zhs.argtypes = [P(_Tracks), ctypes.c_int64, P(_Antennas), P(_Medium),
+        lib.oracle_backward_zhs.argtypes = [P(_Tracks), ctypes.c_int64, P(_Antennas), P(_Medium), ctypes.c_int,
                                             P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
                                             P(ctypes.c_double)]
         lib.oracle_propagate.restype = None
@@ -132,13 +133,16 @@ def tracks_from_ns(tracks: dict) -> dict:
     return out
 
 
-def forward(tracks, ant_xyz, t_ref, n_bins, dt, medium, formalism=ENDPOINT, eps_C=1e-3, mode=MODE_NORMAL):
-    """Traces [n_ant, 3, n_bins] (V/m for Endpoint, V s/m for ZHS) and the kept-track count."""
+def forward(tracks, ant_xyz, t_ref, n_bins, dt, medium, formalism=ENDPOINT, eps_C=1e-3, mode=MODE_NORMAL,
+            deposit=DEPOSIT_BIN):
+    """Traces [n_ant, 3, n_bins] (V/m for Endpoint, V s/m for ZHS) and the kept-track count.
+    deposit: DEPOSIT_BIN (each deposit in its arrival bin) or DEPOSIT_LINEAR
+    (spread over one bin width centred on the arrival)."""
     lib = _load()
     p = _Pack(tracks, ant_xyz, t_ref, n_bins, dt, medium)
     out = np.zeros((len(p.xyz), 3, int(n_bins)), dtype=np.float64)
     kept = lib.oracle_forward(ctypes.byref(p.T), p.n, ctypes.byref(p.A), ctypes.byref(p.M), int(formalism),
-                              float(eps_C), int(mode), _dptr(out))
+                              float(eps_C), int(mode), int(deposit), _dptr(out))
     return out, int(kept)
 
 
@@ -153,7 +157,8 @@ def arrivals(tracks, ant_xyz, t_ref, n_bins, dt, medium, formalism=ENDPOINT, eps
     return br, u
 
 
-def backward(tracks, ant_xyz, t_ref, n_bins, dt, medium, grad_traces, eps_C=1e-3, formalism=ENDPOINT):
+def backward(tracks, ant_xyz, t_ref, n_bins, dt, medium, grad_traces, eps_C=1e-3, formalism=ENDPOINT,
+             deposit=DEPOSIT_BIN):
     """Adjoint of forward(): (track_grad [n, 11], ant_grad [n_ant, 3], dN0).
     Not defined for the spherical-Earth atmosphere."""
     lib = _load()
@@ -167,11 +172,11 @@ def backward(tracks, ant_xyz, t_ref, n_bins, dt, medium, grad_traces, eps_C=1e-3
     ag = np.zeros((len(p.xyz), 3), dtype=np.float64)
     dn = np.zeros(1, dtype=np.float64)
     if formalism == ZHS:
-        lib.oracle_backward_zhs(ctypes.byref(p.T), p.n, ctypes.byref(p.A), ctypes.byref(p.M), _dptr(G), _dptr(tg),
-                                _dptr(ag), _dptr(dn))
+        lib.oracle_backward_zhs(ctypes.byref(p.T), p.n, ctypes.byref(p.A), ctypes.byref(p.M), int(deposit), _dptr(G),
+                                _dptr(tg), _dptr(ag), _dptr(dn))
     else:
-        lib.oracle_backward(ctypes.byref(p.T), p.n, ctypes.byref(p.A), ctypes.byref(p.M), float(eps_C), _dptr(G),
-                            _dptr(tg), _dptr(ag), _dptr(dn))
+        lib.oracle_backward(ctypes.byref(p.T), p.n, ctypes.byref(p.A), ctypes.byref(p.M), float(eps_C),
+                            int(deposit), _dptr(G), _dptr(tg), _dptr(ag), _dptr(dn))
     return tg, ag, float(dn[0])
 
 

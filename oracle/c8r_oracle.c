@@ -46,6 +46,20 @@
  *     the fractions of the interval that fall in its first and last bin vary
  *     with the interval ends, so the ZHS traces are piecewise linear in the
  *     arrival time and the times get non-zero gradients.
+ *  LD linear (two-bin) deposit, an alternative to T for both formalisms: a
+ *     deposit arriving at u (in bins from the window start) is spread evenly
+ *     over one bin width centred on u, so bin k receives the fraction
+ *     |[u - 1/2, u + 1/2] & [k, k + 1)| of it (bins floor(u - 1/2) and the next;
+ *     the weight is the tent max(0, 1 - |u - (k + 1/2)|)).  ZHS: the bin weights
+ *     are that tent averaged over the arrival interval; when the interval lies
+ *     between two consecutive bin centres the tents are linear over it and the
+ *     average is the tent at the interval's middle (no division by D).
+ *     Endpoint near Cherenkov (C): the two linearised arrivals +/- K V/(D R dt)
+ *     are spread the same way; when they lie between the same two bin centres
+ *     J - 1/2 and J + 1/2 the result is the exact limit K V dt_e/(R dt^2) into
+ *     bin J - 1 and its negative into bin J (no division by D).  The traces are
+ *     then continuous in the arrival times, which gives the times informative
+ *     gradients; the adjoints hold the bins of the deposits fixed.
  *
  * Parity unpinned: the value eps_C = 1e-3 itself (any value gives a consistent
  * result; the tests pin the branch's formula, not the threshold), and the choice
@@ -68,6 +82,8 @@ enum { OR_ENDPOINT = 0, OR_ZHS = 1 };
    accumulates |deposit| per component (the magnitude of the summed terms, the
    scale of the rounding error of any evaluation of the sum) */
 enum { OR_MODE_NORMAL = 0, OR_MODE_FORCE_MIDPOINT = 1, OR_MODE_ZHS_EDGE_SAMPLED = 2, OR_MODE_ABS = 3 };
+/* deposit shapes: reading T (one bin) or reading LD (spread over one bin width) */
+enum { OR_DEPOSIT_BIN = 0, OR_DEPOSIT_LINEAR = 1 };
 
 typedef struct {
   const double *x0, *y0, *z0, *x1, *y1, *z1; /* m                          */
@@ -192,6 +208,33 @@ static void deposit(double* trace_a, int n_bins, int64_t k, const double v[3], d
   for (int c = 0; c < 3; ++c) trace_a[(int64_t)c * n_bins + k] += g_abs_mode ? fabs(scale * v[c]) : scale * v[c];
 }
 
+/* reading LD: the share of a deposit arriving at u that falls in bin k */
+static double lin_weight(double u, int64_t k) {
+  double lo = fmax(u - 0.5, (double)k), hi = fmin(u + 0.5, (double)(k + 1));
+  return hi > lo ? hi - lo : 0.0;
+}
+
+static void deposit_linear(double* trace_a, int n_bins, double u, const double v[3], double scale) {
+  int64_t k0 = (int64_t)floor(u - 0.5);
+  for (int64_t k = k0; k <= k0 + 1; ++k) {
+    double w = lin_weight(u, k);
+    if (w > 0.0) deposit(trace_a, n_bins, k, v, scale * w);
+  }
+}
+
+/* integral over [a, b] of lin_weight(u, k) du: the tent is linear between its
+   knots k - 1/2, k + 1/2, k + 3/2, so each piece contributes its length times the
+   tent at the piece's middle */
+static double lin_weight_integral(double a, double b, int64_t k) {
+  double knot[3] = {(double)k - 0.5, (double)k + 0.5, (double)k + 1.5};
+  double sum = 0.0;
+  for (int p = 0; p < 2; ++p) {
+    double lo = fmax(a, knot[p]), hi = fmin(b, knot[p + 1]);
+    if (hi > lo) sum += (hi - lo) * lin_weight(0.5 * (lo + hi), k);
+  }
+  return sum;
+}
+
 static double K_endpoint(double q) { return q * OR_QE / (4.0 * OR_PI * OR_EPS0 * OR_C_LIGHT); }
 static double K_zhs(double q) {
   double mu0 = 1.0 / (OR_EPS0 * OR_C_LIGHT * OR_C_LIGHT);
@@ -222,7 +265,7 @@ typedef struct {
 } or_pair_info;
 
 static or_pair_info endpoint_pair(const or_tracks* T, int64_t i, const double xa[3], double t_ref, double dt,
-                                  int n_bins, const or_medium* m, double eps_C, int mode, double* trace_a) {
+                                  int n_bins, const or_medium* m, double eps_C, int mode, int lin, double* trace_a) {
   double x0[3], x1[3], xm[3], beta[3];
   track_points(T, i, x0, x1, xm, beta);
   double K = K_endpoint(T->q[i]);
@@ -238,7 +281,12 @@ static or_pair_info endpoint_pair(const or_tracks* T, int64_t i, const double xa
     double u0 = arrival_in_bins(&p0, t0, t_ref, dt);
     double u1 = arrival_in_bins(&p1, t1, t_ref, dt);
     double V[3];
-    if (trace_a) {
+    if (trace_a && lin) {
+      endpoint_vector(beta, p0.rh, V);
+      deposit_linear(trace_a, n_bins, u0, V, +K / (D0 * p0.R * dt));
+      endpoint_vector(beta, p1.rh, V);
+      deposit_linear(trace_a, n_bins, u1, V, -K / (D1 * p1.R * dt));
+    } else if (trace_a) {
       endpoint_vector(beta, p0.rh, V);
       deposit(trace_a, n_bins, (int64_t)floor(u0), V, +K / (D0 * p0.R * dt));
       endpoint_vector(beta, p1.rh, V);
@@ -256,19 +304,34 @@ static or_pair_info endpoint_pair(const or_tracks* T, int64_t i, const double xa
   double ua = (tarr_rel - Dm * dte / 2.0) / dt; /* arrival of the start */
   double ub = (tarr_rel + Dm * dte / 2.0) / dt; /* arrival of the end   */
   int64_t ka = (int64_t)floor(ua), kb = (int64_t)floor(ub);
-  if (trace_a && ka != kb) {
-    double V[3];
-    endpoint_vector(beta, pm.rh, V);
+  info.branch = 1; info.u_a = ua; info.u_b = ub;
+  if (!trace_a) return info;
+  double V[3];
+  endpoint_vector(beta, pm.rh, V);
+  if (lin) {
+    int64_t Ja = (int64_t)floor(ua + 0.5), Jb = (int64_t)floor(ub + 0.5);
+    if (Ja == Jb) {
+      /* both between the bin centres Ja - 1/2 and Ja + 1/2: the exact limit */
+      double B = K * dte / (pm.R * dt * dt);
+      deposit(trace_a, n_bins, Ja - 1, V, +B);
+      deposit(trace_a, n_bins, Ja, V, -B);
+    } else {
+      double amp = K / (Dm * pm.R * dt);
+      deposit_linear(trace_a, n_bins, ua, V, +amp);
+      deposit_linear(trace_a, n_bins, ub, V, -amp);
+    }
+    return info;
+  }
+  if (ka != kb) {
     double amp = K / (Dm * pm.R * dt);
     deposit(trace_a, n_bins, ka, V, +amp);
     deposit(trace_a, n_bins, kb, V, -amp);
   }
-  info.branch = 1; info.u_a = ua; info.u_b = ub;
   return info;
 }
 
 static or_pair_info zhs_pair(const or_tracks* T, int64_t i, const double xa[3], double t_ref, double dt, int n_bins,
-                             const or_medium* m, int mode, double* trace_a) {
+                             const or_medium* m, int mode, int lin, double* trace_a) {
   double x0[3], x1[3], xm[3], beta[3];
   track_points(T, i, x0, x1, xm, beta);
   double KA = K_zhs(T->q[i]);
@@ -300,6 +363,23 @@ static or_pair_info zhs_pair(const or_tracks* T, int64_t i, const double xa[3], 
     }
     return info;
   }
+  if (lin) {
+    /* reading LD: the tent weights averaged over [u_lo, u_hi] */
+    info.branch = (k_lo == k_hi) ? 2 : 3;
+    if (!trace_a) return info;
+    double A1 = KA * dte / (pm.R * dt); /* the whole interval's deposit */
+    if (floor(u_lo + 0.5) == floor(u_hi + 0.5)) {
+      deposit_linear(trace_a, n_bins, 0.5 * (u_lo + u_hi), bperp, A1);
+      return info;
+    }
+    double W = u_hi - u_lo;
+    for (int64_t k = (int64_t)floor(u_lo - 0.5); k <= (int64_t)floor(u_hi + 0.5); ++k) {
+      if (k < 0 || k >= n_bins) continue;
+      double w = lin_weight_integral(u_lo, u_hi, k) / W;
+      if (w > 0.0) deposit(trace_a, n_bins, k, bperp, A1 * w);
+    }
+    return info;
+  }
   if (k_lo == k_hi) {
     info.branch = 2;
     if (trace_a) deposit(trace_a, n_bins, k_lo, bperp, KA * dte / (pm.R * dt));
@@ -323,7 +403,8 @@ static or_pair_info zhs_pair(const or_tracks* T, int64_t i, const double xa[3], 
 /* Forward: traces[a][c][k] (row-major [n_ant][3][n_bins]) are ACCUMULATED.  */
 /* Returns the number of tracks kept by the filter.                          */
 int64_t oracle_forward(const or_tracks* T, int64_t n, const or_antennas* A, const or_medium* m, int formalism,
-                       double eps_C, int mode, double* traces) {
+                       double eps_C, int mode, int deposit_kind, double* traces) {
+  int lin = deposit_kind == OR_DEPOSIT_LINEAR;
   int64_t kept = 0;
   g_abs_mode = (mode == OR_MODE_ABS);
   if (g_abs_mode) mode = OR_MODE_NORMAL;
@@ -334,9 +415,9 @@ int64_t oracle_forward(const or_tracks* T, int64_t n, const or_antennas* A, cons
       const double* xa = A->xyz + 3 * (int64_t)a;
       double* tr = traces + (int64_t)a * 3 * A->n_bins;
       if (formalism == OR_ENDPOINT)
-        endpoint_pair(T, i, xa, A->t_ref[a], A->dt, A->n_bins, m, eps_C, mode, tr);
+        endpoint_pair(T, i, xa, A->t_ref[a], A->dt, A->n_bins, m, eps_C, mode, lin, tr);
       else
-        zhs_pair(T, i, xa, A->t_ref[a], A->dt, A->n_bins, m, mode, tr);
+        zhs_pair(T, i, xa, A->t_ref[a], A->dt, A->n_bins, m, mode, lin, tr);
     }
   }
   g_abs_mode = 0;
@@ -355,13 +436,60 @@ void oracle_arrivals(const or_tracks* T, int64_t n, const or_antennas* A, const 
       if (!keep) { branch[j] = -1; u[2 * j] = u[2 * j + 1] = 0.0; continue; }
       const double* xa = A->xyz + 3 * (int64_t)a;
       or_pair_info info = (formalism == OR_ENDPOINT)
-                              ? endpoint_pair(T, i, xa, A->t_ref[a], A->dt, A->n_bins, m, eps_C, OR_MODE_NORMAL, 0)
-                              : zhs_pair(T, i, xa, A->t_ref[a], A->dt, A->n_bins, m, OR_MODE_NORMAL, 0);
+                              ? endpoint_pair(T, i, xa, A->t_ref[a], A->dt, A->n_bins, m, eps_C, OR_MODE_NORMAL, 0, 0)
+                              : zhs_pair(T, i, xa, A->t_ref[a], A->dt, A->n_bins, m, OR_MODE_NORMAL, 0, 0);
       branch[j] = info.branch;
       u[2 * j] = info.u_a;
       u[2 * j + 1] = info.u_b;
     }
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* the refractivity part F of the optical path n_avg R = R + F from x_e to    */
+/* x_a (reading M), with its derivatives                                      */
+static void refractive_part(const or_medium* m, const double xm[3], const double xa[3], double R, double* F,
+                            double* dF_dR, double* dF_dzm, double* dF_dza, double* dF_dN0) {
+  if (m->kind == OR_UNIFORM) {
+    *F = (m->n - 1.0) * R;
+    *dF_dR = m->n - 1.0;
+    *dF_dzm = *dF_dza = 0.0;
+    *dF_dN0 = R; /* d/d(n - 1) */
+    return;
+  }
+  /* F = N0 E_m R rho(x), rho(x) = (1 - exp(-x))/x, x = (z_a - z_m)/H; rho' = (exp(-x) - rho)/x */
+  double E = exp(-xm[2] / m->H);
+  double x = (xa[2] - xm[2]) / m->H;
+  double rho, drho;
+  if (fabs(x) < 1e-3) {
+    rho = 1.0 - x / 2.0 + x * x / 6.0 - x * x * x / 24.0;
+    drho = -0.5 + x / 3.0 - x * x / 8.0 + x * x * x / 30.0;
+  } else {
+    rho = -expm1(-x) / x;
+    drho = (exp(-x) - rho) / x;
+  }
+  *F = m->N0 * E * R * rho;
+  *dF_dR = m->N0 * E * rho;
+  *dF_dzm = -m->N0 * R * E * (rho + drho) / m->H;
+  *dF_dza = m->N0 * R * E * drho / m->H;
+  *dF_dN0 = E * R * rho;
+}
+
+/* chain rule through an arrival time t_e + (R + F)/c: adds dL/dx_e and dL/dx_a
+   (into gxe, gxa) and dL/dN0 for a given dL/dt_arr (dL/dt_e is dL/dt_arr) */
+static void arrival_adjoint(const or_medium* m, const double xe[3], const double xa[3], const or_path* p,
+                            double dL_dtarr, double gxe[3], double gxa[3], double* dN0) {
+  double F, dF_dR, dF_dze, dF_dza, dF_dN0;
+  refractive_part(m, xe, xa, p->R, &F, &dF_dR, &dF_dze, &dF_dza, &dF_dN0);
+  double g = dL_dtarr / OR_C_LIGHT;
+  double dR = g * (1.0 + dF_dR);
+  for (int k = 0; k < 3; ++k) {
+    gxe[k] -= dR * p->rh[k];
+    gxa[k] += dR * p->rh[k];
+  }
+  gxe[2] += g * dF_dze;
+  gxa[2] += g * dF_dza;
+  *dN0 += g * dF_dN0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -392,11 +520,29 @@ static void gather_g(const double* G_a, int n_bins, int64_t k, double g[3]) {
   for (int c = 0; c < 3; ++c) g[c] = (k >= 0 && k < n_bins) ? G_a[(int64_t)c * n_bins + k] : 0.0;
 }
 
+/* reading LD: the combination of dL/dtrace that a unit deposit arriving at u
+   sees, and its rate of change with u (the deposit slides from bin k0 to k0 + 1) */
+static void gather_lin(const double* G_a, int n_bins, double u, double g[3], double slope[3]) {
+  int64_t k0 = (int64_t)floor(u - 0.5);
+  double w0 = lin_weight(u, k0), w1 = lin_weight(u, k0 + 1), g0[3], g1[3];
+  gather_g(G_a, n_bins, k0, g0);
+  gather_g(G_a, n_bins, k0 + 1, g1);
+  for (int c = 0; c < 3; ++c) {
+    g[c] = w0 * g0[c] + w1 * g1[c];
+    slope[c] = g1[c] - g0[c];
+  }
+}
+
 /* G: dL/dtraces [n_ant][3][n_bins].  Outputs are ACCUMULATED:
    track_grad[i][11] = d/d{x0,y0,z0,x1,y1,z1,t0,t1,bx,by,bz}, ant_grad[a][3],
-   *dN0 = d/dN0 (exponential) or d/d(n-1) (uniform). */
+   *dN0 = d/dN0 (exponential) or d/d(n-1) (uniform).  With the linear deposit
+   (reading LD) the deposits also slide with their arrival times u: a deposit
+   l(g) = kappa (g.V)/(D R) at u adds dL/du = l(G_{k0+1} - G_{k0}), which the
+   chain rule takes through the arrival time (arrival_adjoint) and, near
+   Cherenkov, through u_a, u_b = tau -/+ D dt_e/(2 dt). */
 void oracle_backward(const or_tracks* T, int64_t n, const or_antennas* A, const or_medium* m, double eps_C,
-                     const double* G, double* track_grad, double* ant_grad, double* dN0) {
+                     int deposit_kind, const double* G, double* track_grad, double* ant_grad, double* dN0) {
+  int lin = deposit_kind == OR_DEPOSIT_LINEAR;
   for (int64_t i = 0; i < n; ++i) {
     if (!track_kept(T, i)) continue;
     double x0[3], x1[3], xm[3], beta[3];
@@ -418,8 +564,11 @@ void oracle_backward(const or_tracks* T, int64_t n, const or_antennas* A, const 
         const or_path* ps[2] = {&p0, &p1};
         double ts[2] = {t0, t1};
         for (int j = 0; j < 2; ++j) {
-          double u = arrival_in_bins(ps[j], ts[j], t_ref, dt);
-          gather_g(G_a, A->n_bins, (int64_t)floor(u), g);
+          double u = arrival_in_bins(ps[j], ts[j], t_ref, dt), slope[3];
+          if (lin)
+            gather_lin(G_a, A->n_bins, u, g, slope);
+          else
+            gather_g(G_a, A->n_bins, (int64_t)floor(u), g);
           double kappa = (j == 0 ? +K : -K) / dt;
           deposit_adjoint(ps[j], beta, g, kappa, gd, gb, &gn);
           for (int k = 0; k < 3; ++k) {
@@ -429,7 +578,95 @@ void oracle_backward(const or_tracks* T, int64_t n, const or_antennas* A, const 
           }
           tg[3 * j + 2] += gn * ps[j]->dn_src_dze;
           *dN0 += gn * ps[j]->dn_src_dN0;
+          if (lin) {
+            double V[3], gxe[3] = {0.0, 0.0, 0.0};
+            endpoint_vector(beta, ps[j]->rh, V);
+            double Dj = j == 0 ? D0 : D1;
+            double dL_du = kappa * dot3(slope, V) / (Dj * ps[j]->R);
+            arrival_adjoint(m, j == 0 ? x0 : x1, xa, ps[j], dL_du / dt, gxe, ant_grad + 3 * a, dN0);
+            for (int k = 0; k < 3; ++k) tg[3 * j + k] += gxe[k];
+            tg[6 + j] += dL_du / dt;
+          }
         }
+      } else if (lin) {
+        /* reading LD near Cherenkov */
+        or_path pm;
+        propagate(m, xm, xa, &pm);
+        double c = dot3(beta, pm.rh);
+        double Dm = 1.0 - pm.n_src * c;
+        double tm = 0.5 * (t0 + t1);
+        double tarr_rel = (tm - t_ref) + pm.n_avg * pm.R / OR_C_LIGHT;
+        double ua = (tarr_rel - Dm * dte / 2.0) / dt;
+        double ub = (tarr_rel + Dm * dte / 2.0) / dt;
+        double V[3], ga[3], gbv[3];
+        endpoint_vector(beta, pm.rh, V);
+        int64_t Ja = (int64_t)floor(ua + 0.5), Jb = (int64_t)floor(ub + 0.5);
+        if (Ja == Jb) {
+          /* l = kappa (g.V)/R with kappa = K dt_e/dt^2 and g = G_{J-1} - G_J: the
+             deposit adjoint with D = 1 (n = 0), plus dl/d dt_e = l/dt_e */
+          gather_g(G_a, A->n_bins, Ja - 1, ga);
+          gather_g(G_a, A->n_bins, Ja, gbv);
+          for (int k = 0; k < 3; ++k) g[k] = ga[k] - gbv[k];
+          or_path pz = pm;
+          pz.n_src = 0.0;
+          double kap = K * dte / (dt * dt);
+          deposit_adjoint(&pz, beta, g, kap, gd, gb, &gn);
+          for (int k = 0; k < 3; ++k) {
+            tg[k] -= 0.5 * gd[k];
+            tg[3 + k] -= 0.5 * gd[k];
+            ant_grad[3 * a + k] += gd[k];
+            tg[8 + k] += gb[k];
+          }
+          double l = kap * dot3(g, V) / pm.R;
+          tg[6] -= l / dte;
+          tg[7] += l / dte;
+          continue;
+        }
+        double sa[3], sb[3];
+        gather_lin(G_a, A->n_bins, ua, ga, sa);
+        gather_lin(G_a, A->n_bins, ub, gbv, sb);
+        for (int k = 0; k < 3; ++k) g[k] = ga[k] - gbv[k];
+        deposit_adjoint(&pm, beta, g, K / dt, gd, gb, &gn);
+        for (int k = 0; k < 3; ++k) {
+          tg[k] -= 0.5 * gd[k];
+          tg[3 + k] -= 0.5 * gd[k];
+          ant_grad[3 * a + k] += gd[k];
+          tg[8 + k] += gb[k];
+        }
+        tg[2] += 0.5 * gn * pm.dn_src_dze;
+        tg[5] += 0.5 * gn * pm.dn_src_dze;
+        *dN0 += gn * pm.dn_src_dN0;
+        /* the arrivals slide the deposits +/- amp V, amp = K/(D R dt) */
+        double amp = K / (Dm * pm.R * dt);
+        double dL_dua = amp * dot3(sa, V), dL_dub = -amp * dot3(sb, V);
+        double dL_dtau = (dL_dua + dL_dub) / dt; /* per second of tarr_rel */
+        double dL_dD = (dL_dub - dL_dua) * dte / (2.0 * dt);
+        double dL_ddte = (dL_dub - dL_dua) * Dm / (2.0 * dt);
+        /* D = 1 - n_src (beta.rhat), rhat = d/R, d = x_a - x_m */
+        double dL_drh[3];
+        for (int k = 0; k < 3; ++k) {
+          tg[8 + k] -= pm.n_src * pm.rh[k] * dL_dD;
+          dL_drh[k] = -pm.n_src * beta[k] * dL_dD;
+        }
+        double rdr = dot3(dL_drh, pm.rh);
+        for (int k = 0; k < 3; ++k) {
+          double dd = (dL_drh[k] - rdr * pm.rh[k]) / pm.R;
+          tg[k] -= 0.5 * dd;
+          tg[3 + k] -= 0.5 * dd;
+          ant_grad[3 * a + k] += dd;
+        }
+        double dL_dn = -c * dL_dD;
+        tg[2] += 0.5 * dL_dn * pm.dn_src_dze;
+        tg[5] += 0.5 * dL_dn * pm.dn_src_dze;
+        *dN0 += dL_dn * pm.dn_src_dN0;
+        double gxm[3] = {0.0, 0.0, 0.0};
+        arrival_adjoint(m, xm, xa, &pm, dL_dtau, gxm, ant_grad + 3 * a, dN0);
+        for (int k = 0; k < 3; ++k) {
+          tg[k] += 0.5 * gxm[k];
+          tg[3 + k] += 0.5 * gxm[k];
+        }
+        tg[6] += 0.5 * dL_dtau - dL_ddte;
+        tg[7] += 0.5 * dL_dtau + dL_ddte;
       } else {
         or_path pm;
         propagate(m, xm, xa, &pm);
@@ -455,8 +692,8 @@ void oracle_backward(const or_tracks* T, int64_t n, const or_antennas* A, const 
         tg[5] += 0.5 * gn * pm.dn_src_dze;
         *dN0 += gn * pm.dn_src_dN0;
       }
-      /* d/dt0 and d/dt1 stay zero: with bins held fixed the deposits do not
-         depend on the times (reading G). */
+      /* with the one-bin deposit d/dt0 and d/dt1 stay zero: with bins held
+         fixed the deposits do not depend on the times (reading G). */
     }
   }
 }
@@ -474,37 +711,15 @@ void oracle_backward(const or_tracks* T, int64_t n, const or_antennas* A, const 
 /* and both vanish for a one-bin interval (w = 1).  The rest is the chain     */
 /* rule through A, |D|, tau and the path (n_avg R = R + F, F the             */
 /* refractivity part of the optical path).                                   */
-static void refractive_part(const or_medium* m, const double xm[3], const double xa[3], double R, double* F,
-                            double* dF_dR, double* dF_dzm, double* dF_dza, double* dF_dN0) {
-  if (m->kind == OR_UNIFORM) {
-    *F = (m->n - 1.0) * R;
-    *dF_dR = m->n - 1.0;
-    *dF_dzm = *dF_dza = 0.0;
-    *dF_dN0 = R; /* d/d(n - 1) */
-    return;
-  }
-  /* F = N0 E_m R rho(x), rho(x) = (1 - exp(-x))/x, x = (z_a - z_m)/H; rho' = (exp(-x) - rho)/x */
-  double E = exp(-xm[2] / m->H);
-  double x = (xa[2] - xm[2]) / m->H;
-  double rho, drho;
-  if (fabs(x) < 1e-3) {
-    rho = 1.0 - x / 2.0 + x * x / 6.0 - x * x * x / 24.0;
-    drho = -0.5 + x / 3.0 - x * x / 8.0 + x * x * x / 30.0;
-  } else {
-    rho = -expm1(-x) / x;
-    drho = (exp(-x) - rho) / x;
-  }
-  *F = m->N0 * E * R * rho;
-  *dF_dR = m->N0 * E * rho;
-  *dF_dzm = -m->N0 * R * E * (rho + drho) / m->H;
-  *dF_dza = m->N0 * R * E * drho / m->H;
-  *dF_dN0 = E * R * rho;
-}
-
+/* With the linear deposit (reading LD) w_k is the tent of bin k averaged over */
+/* the interval; S and the two formulas keep their form, with g_lo, g_hi the */
+/* tent-weighted A.G at the interval ends, and for an interval between two   */
+/* consecutive bin centres dL/dtau = A.(G_{k0+1} - G_{k0})/dt, dL/dhalf = 0.  */
 /* G: dL/dtraces [n_ant][3][n_bins].  Outputs are ACCUMULATED, as for
    oracle_backward (track_grad [n][11], ant_grad [n_ant][3], dN0). */
-void oracle_backward_zhs(const or_tracks* T, int64_t n, const or_antennas* A, const or_medium* m, const double* G,
-                         double* track_grad, double* ant_grad, double* dN0) {
+void oracle_backward_zhs(const or_tracks* T, int64_t n, const or_antennas* A, const or_medium* m, int deposit_kind,
+                         const double* G, double* track_grad, double* ant_grad, double* dN0) {
+  int lin = deposit_kind == OR_DEPOSIT_LINEAR;
   for (int64_t i = 0; i < n; ++i) {
     if (!track_kept(T, i)) continue;
     double x0[3], x1[3], xm[3], beta[3];
@@ -533,7 +748,26 @@ void oracle_backward_zhs(const or_tracks* T, int64_t n, const or_antennas* A, co
       /* S = sum_k w_k G_k over the bins inside the window */
       double S[3] = {0.0, 0.0, 0.0}, g[3];
       double dL_dtau = 0.0, dL_dhalf = 0.0;
-      if (k_lo == k_hi) {
+      double u_lo = t_lo / dt, u_hi = t_hi / dt;
+      if (lin && floor(u_lo + 0.5) == floor(u_hi + 0.5)) {
+        double slope[3];
+        gather_lin(G_a, nb, 0.5 * (u_lo + u_hi), S, slope);
+        dL_dtau = dot3(Av, slope) / dt;
+      } else if (lin) {
+        double W = t_hi - t_lo, Wb = u_hi - u_lo, slope[3];
+        for (int64_t k = (int64_t)floor(u_lo - 0.5); k <= (int64_t)floor(u_hi + 0.5); ++k) {
+          double w = lin_weight_integral(u_lo, u_hi, k) / Wb;
+          gather_g(G_a, nb, k, g);
+          for (int q = 0; q < 3; ++q) S[q] += w * g[q];
+        }
+        gather_lin(G_a, nb, u_lo, g, slope);
+        double g_lo = dot3(Av, g);
+        gather_lin(G_a, nb, u_hi, g, slope);
+        double g_hi = dot3(Av, g);
+        double AS = dot3(Av, S);
+        dL_dtau = (g_hi - g_lo) / W;
+        dL_dhalf = (g_hi + g_lo - 2.0 * AS) / W;
+      } else if (k_lo == k_hi) {
         gather_g(G_a, nb, k_lo, S);
       } else {
         double W = t_hi - t_lo;
