@@ -62,6 +62,10 @@ extern "C" {
 #define C8R_F32 0
 #define C8R_F64 1
 
+/* deposit shapes (c8r_set_deposit) */
+#define C8R_DEPOSIT_BIN 0     /* each deposit in the bin of its arrival time (default)    */
+#define C8R_DEPOSIT_LINEAR 1  /* spread over one bin width centred on the arrival time    */
+
 typedef struct c8r_ctx c8r_ctx;
 
 /* Particle tracks in structure-of-arrays form: twelve DEVICE arrays of one
@@ -163,6 +167,21 @@ int c8r_set_antennas(c8r_ctx* ctx, int32_t n_ant, const double* pos_xyz, const d
  * the track midpoint with linearised arrival times.  EINVAL unless 0 < eps < 1. */
 int c8r_set_cherenkov_threshold(c8r_ctx* ctx, double eps_C);
 
+/* Shape of every deposit (not in the paper; it leaves the binning open).
+ * C8R_DEPOSIT_BIN (default): a deposit lands in the bin of its arrival time.
+ * C8R_DEPOSIT_LINEAR: a deposit arriving at u bins from the window start is
+ * spread evenly over [u - 1/2, u + 1/2], i.e. bins floor(u - 1/2) and the next
+ * receive 1 - f and f of it, f = u - 1/2 - floor(u - 1/2).  ZHS intervals are
+ * spread the same way (the weights are averaged over the interval); an Endpoint
+ * pair near the Cherenkov angle whose two linearised arrivals lie between the
+ * same two bin centres J - 1/2 and J + 1/2 deposits the exact limit
+ * K (t1 - t0) V/(R dt^2) into bin J - 1 and its negative into bin J.  The traces
+ * are then continuous in the arrival times, so c8r_backward gives the times
+ * informative gradients.  Applies to the tracks pushed (and the adjoints run)
+ * after the call; the batch runner and c8r_traces_noalloc use the one-bin
+ * deposit.  EINVAL for another value. */
+int c8r_set_deposit(c8r_ctx* ctx, int deposit);
+
 /* Launch shape of the forward kernels: antennas per CTA (1..32; each thread
  * holds one track of a staged tile and evaluates it against all of them) and
  * the target number of waves per launch, a wave being every CTA the device
@@ -203,9 +222,12 @@ int c8r_reset(c8r_ctx* ctx, void* cuda_stream);
  * inputs) into out_tracks (times per ns), dL/d(antenna positions) into
  * out_ant_grad (DEVICE FP64 [n_ant][3]) and dL/dN0 into *out_dN0 (DEVICE FP64
  * scalar; for a uniform medium the derivative with respect to n - 1).  Bin
- * indices and the near-Cherenkov branch are held fixed: the Endpoint deposits
- * then do not depend on the times (zero time gradients), while the ZHS deposits
- * do, through the fractions of the arrival interval in its first and last bin.
+ * indices and the near-Cherenkov branch are held fixed: with the one-bin
+ * deposit the Endpoint deposits then do not depend on the times (zero time
+ * gradients), while the ZHS deposits do, through the fractions of the arrival
+ * interval in its first and last bin; with the linear deposit
+ * (c8r_set_deposit) every deposit slides between its two bins with its arrival
+ * time, so both formalisms give the times informative gradients.
  * The per-pair geometry is recomputed, not stored.  The first call allocates a
  * bin-major copy of grad_traces (and, for ZHS, its running sums over the bins)
  * inside the context (ENOMEM if that fails).  EINVAL for mismatched dtypes. */

@@ -2,7 +2,7 @@
 
 Each translation unit under csrc/ is compiled in parallel to an object file in
 ``_build/`` and the objects are linked into ``_build/libc8r.so`` (CUDA runtime
-linked statically).  The FP64 kernel unit and the track generator are compiled
+linked statically).  The FP64 kernel units and the track generator are compiled
 with ``--fmad=false`` so their arithmetic rounds exactly as written.  A rebuild happens only when a source
 or header is newer than the library.
 """
@@ -22,7 +22,7 @@ LIB = os.path.join(BUILD, "libc8r.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "--expt-relaxed-constexpr"]
-PER_FILE = {"kernels_f64.cu": ["--fmad=false"], "generate.cu": ["--fmad=false"]}
+PER_FILE = {"kernels_f64.cu": ["--fmad=false"], "kernels_f64_lin.cu": ["--fmad=false"], "generate.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:

@@ -29,6 +29,7 @@ C8R_UNIFORM, C8R_EXPONENTIAL, C8R_EXPONENTIAL_SPHERICAL = 0, 1, 2
 C8R_ENDPOINT, C8R_ZHS = 0, 1
 C8R_FP64, C8R_MIXED = 0, 1
 C8R_F32, C8R_F64 = 0, 1
+C8R_DEPOSIT_BIN, C8R_DEPOSIT_LINEAR = 0, 1
 
 TRACK_FIELDS = ("x0", "y0", "z0", "x1", "y1", "z1", "t0", "t1", "bx", "by", "bz", "q")
 GRAD_FIELDS = TRACK_FIELDS[:-1]
@@ -81,6 +82,7 @@ _SIGNATURES = [
                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
                                         ctypes.c_int, ctypes.c_int]),
     ("c8r_set_cherenkov_threshold", ctypes.c_int, [_P, ctypes.c_double]),
+    ("c8r_set_deposit", ctypes.c_int, [_P, ctypes.c_int]),
     ("c8r_set_launch_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64]),
     ("c8r_push_tracks", ctypes.c_int, [_P, ctypes.POINTER(c8r_tracks), ctypes.c_int64, _P]),
     ("c8r_fetch_traces", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P]),
@@ -207,6 +209,10 @@ def c8r_set_cherenkov_threshold(ctx, eps_C):
     return _check(ctx, load().c8r_set_cherenkov_threshold(ctx, float(eps_C)))
 
 
+def c8r_set_deposit(ctx, deposit):
+    return _check(ctx, load().c8r_set_deposit(ctx, int(deposit)))
+
+
 def c8r_set_launch_shape(ctx, a_tile=0, waves=0, chunk_tracks=0):
     return _check(ctx, load().c8r_set_launch_shape(ctx, int(a_tile), int(waves), int(chunk_tracks)))
 
@@ -303,16 +309,18 @@ def c8r_generate_tracks(seed: int, first: int, n: int, zenith_deg: float = 0.0, 
 _MEDIUM = {"uniform": C8R_UNIFORM, "exponential": C8R_EXPONENTIAL, "exponential_spherical": C8R_EXPONENTIAL_SPHERICAL}
 _FORMALISM = {"endpoint": C8R_ENDPOINT, "coreas": C8R_ENDPOINT, "zhs": C8R_ZHS}
 _PRECISION = {"fp64": C8R_FP64, "mixed": C8R_MIXED}
+_DEPOSIT = {"bin": C8R_DEPOSIT_BIN, "linear": C8R_DEPOSIT_LINEAR}
 
 
 class RadioProcess:
     """One radio process (§2): a medium for the straight-line propagator, an
     antenna collection and one formalism.  ``push`` hands it tracks; ``traces``
     returns the accumulated [n_ant, 3, n_bins] traces (float64 for precision
-    'fp64', float32 for 'mixed')."""
+    'fp64', float32 for 'mixed').  ``deposit`` is 'bin' (each deposit in its
+    arrival bin) or 'linear' (spread over one bin width centred on the arrival)."""
 
     def __init__(self, medium: dict, ant_xyz, t_start_ns, n_bins: int, dt_ns: float, formalism="endpoint",
-                 precision="mixed", device: int | None = None, eps_C: float | None = None):
+                 precision="mixed", device: int | None = None, eps_C: float | None = None, deposit="bin"):
         if device is None:
             device = torch.cuda.current_device()
         self.device = torch.device("cuda", device)
@@ -331,6 +339,8 @@ class RadioProcess:
         c8r_set_antennas(self.ctx, ant_xyz, t_start_ns, n_bins, dt_ns, _FORMALISM[formalism], _PRECISION[precision])
         if eps_C is not None:
             c8r_set_cherenkov_threshold(self.ctx, eps_C)
+        c8r_set_deposit(self.ctx, _DEPOSIT[deposit])
+        self.deposit = deposit
 
     @property
     def trace_dtype(self):

@@ -92,6 +92,7 @@ struct c8r_ctx {
   int med_kind = C8R_UNIFORM;
   double med_a = 1.0, med_H = 1.0, med_RE = 0.0;
   double eps_C = 1e-3;
+  int deposit = C8R_DEPOSIT_BIN;
   // antennas
   bool ants_set = false;
   int n_ant = 0, n_bins = 0, formalism = C8R_ENDPOINT, precision = C8R_MIXED;
@@ -321,6 +322,14 @@ int c8r_set_cherenkov_threshold(c8r_ctx* c, double eps) {
   return rebuild_tables(c);
 }
 
+int c8r_set_deposit(c8r_ctx* c, int deposit) {
+  if (!c) return C8R_EINVAL;
+  if (deposit != C8R_DEPOSIT_BIN && deposit != C8R_DEPOSIT_LINEAR)
+    return fail(c, C8R_EINVAL, "deposit must be C8R_DEPOSIT_BIN or C8R_DEPOSIT_LINEAR");
+  c->deposit = deposit;
+  return C8R_OK;
+}
+
 int c8r_set_antennas(c8r_ctx* c, int32_t n_ant, const double* pos, const double* t_start, int32_t n_bins,
                      double dt_ns, int formalism, int precision) {
   if (!c) return C8R_EINVAL;
@@ -391,6 +400,7 @@ int c8r_push_tracks(c8r_ctx* c, const c8r_tracks* t, int64_t n, void* stream) {
   c->last_stream = st;
   const int64_t chunk = n < c->chunk_tracks ? n : c->chunk_tracks;
   if ((r = ensure_tiles(c, chunk)) != C8R_OK) return r;
+  const bool lin = c->deposit == C8R_DEPOSIT_LINEAR;
   for (int64_t off = 0; off < n; off += chunk) {
     const int64_t m = (n - off) < chunk ? (n - off) : chunk;
     TrackPtrs p = offset_tracks(t, off);
@@ -406,10 +416,10 @@ int c8r_push_tracks(c8r_ctx* c, const c8r_tracks* t, int64_t n, void* stream) {
     if (c->profiling) cudaEventRecord(e1, st);
     const int64_t n_tiles = (m + kTileT - 1) / kTileT;
     e = (c->precision == C8R_FP64)
-            ? launch_forward_f64(c->formalism, c->d_tiles, n_tiles, c->d_ants, c->n_ant, c->M, c->d_acc, c->shape,
-                                 c->sm_count, c->d_err, st)
-            : launch_forward_mixed(c->formalism, c->d_tiles, n_tiles, c->d_ants, c->n_ant, c->M, c->d_acc, c->shape,
-                                   c->sm_count, c->d_err, st);
+            ? launch_forward_f64(c->formalism, lin, c->d_tiles, n_tiles, c->d_ants, c->n_ant, c->M, c->d_acc,
+                                 c->shape, c->sm_count, c->d_err, st)
+            : launch_forward_mixed(c->formalism, lin, c->d_tiles, n_tiles, c->d_ants, c->n_ant, c->M, c->d_acc,
+                                   c->shape, c->sm_count, c->d_err, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "forward launch");
     if (c->profiling) {
       cudaEventRecord(e2, st);
@@ -568,6 +578,7 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
   const int want = c->precision == C8R_FP64 ? C8R_F64 : C8R_F32;
   if (out->dtype != want) return fail(c, C8R_EINVAL, "out_tracks.dtype must match the context precision");
   if (n == 0) return C8R_OK;
+  const bool lin = c->deposit == C8R_DEPOSIT_LINEAR;
   void* g[11] = {out->x0, out->y0, out->z0, out->x1, out->y1, out->z1, out->t0, out->t1, out->bx, out->by, out->bz};
   for (int k = 0; k < 11; ++k)
     if (!g[k]) return fail(c, C8R_EINVAL, "a gradient array pointer is NULL");
@@ -608,8 +619,8 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
     for (int k = 0; k < 11; ++k) *og[k] = static_cast<char*>(*og[k]) + off * es;
     BwdArgs ba{c->d_tiles, m, (m + kTileT - 1) / kTileT, c->d_ants, c->n_ant, c->shape.a_tile, c->d_gbm,
                c->formalism == C8R_ZHS ? c->d_gpre : nullptr, o, ant_grad, dN0, c->d_err, FwdGrid{}, c->M};
-    e = (c->precision == C8R_FP64) ? launch_backward_f64(c->formalism, ba, c->shape, c->sm_count, st)
-                                   : launch_backward_mixed(c->formalism, ba, c->shape, c->sm_count, st);
+    e = (c->precision == C8R_FP64) ? launch_backward_f64(c->formalism, lin, ba, c->shape, c->sm_count, st)
+                                   : launch_backward_mixed(c->formalism, lin, ba, c->shape, c->sm_count, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "backward launch");
   }
   return C8R_OK;

@@ -44,19 +44,31 @@ cudaError_t launch_ingest(int precision, const TrackPtrs& t, int64_t n, void* ti
 
 struct BwdArgs;
 
-// per-precision launchers (kernels_f64.cu / kernels_mixed.cu)
-cudaError_t launch_forward_f64(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants, int n_ant,
-                               const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
+// per-precision launchers (kernels_f64.cu / kernels_mixed.cu); `lin` selects
+// the linear (two-bin) deposit, whose kernels live in kernels_*_lin.cu
+cudaError_t launch_forward_f64(int formalism, bool lin, const void* tiles, int64_t n_tiles, const AntRec* ants,
+                               int n_ant, const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
                                cudaStream_t st);
-cudaError_t launch_forward_mixed(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants, int n_ant,
-                                 const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
-                                 cudaStream_t st);
+cudaError_t launch_forward_mixed(int formalism, bool lin, const void* tiles, int64_t n_tiles, const AntRec* ants,
+                                 int n_ant, const MedParams& M, void* acc, const FwdShape& shape, int sm_count,
+                                 int* err, cudaStream_t st);
+cudaError_t launch_forward_f64_lin(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants, int n_ant,
+                                   const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
+                                   cudaStream_t st);
+cudaError_t launch_forward_mixed_lin(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants,
+                                     int n_ant, const MedParams& M, void* acc, const FwdShape& shape, int sm_count,
+                                     int* err, cudaStream_t st);
 cudaError_t launch_arrivals_f64(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,
                                 const MedParams& M, int32_t* branch, int32_t* bin, float* frac, cudaStream_t st);
 cudaError_t launch_arrivals_mixed(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,
                                   const MedParams& M, int32_t* branch, int32_t* bin, float* frac, cudaStream_t st);
-cudaError_t launch_backward_f64(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st);
-cudaError_t launch_backward_mixed(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st);
+cudaError_t launch_backward_f64(int formalism, bool lin, BwdArgs& a, const FwdShape& shape, int sm_count,
+                                cudaStream_t st);
+cudaError_t launch_backward_mixed(int formalism, bool lin, BwdArgs& a, const FwdShape& shape, int sm_count,
+                                  cudaStream_t st);
+cudaError_t launch_backward_f64_lin(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st);
+cudaError_t launch_backward_mixed_lin(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count,
+                                      cudaStream_t st);
 // running sums over the bins of a bin-major gradient (FP64): [n_ant][n_bins + 1]
 struct Acc4D;
 cudaError_t launch_bin_running_sums(int precision, const void* g, int n_ant, int n_bins, Acc4D* out,

@@ -5,20 +5,11 @@
 
 namespace c8r {
 
-cudaError_t launch_forward_f64(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants, int n_ant,
-                               const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
+cudaError_t launch_forward_f64(int formalism, bool lin, const void* tiles, int64_t n_tiles, const AntRec* ants,
+                               int n_ant, const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
                                cudaStream_t st) {
-  FwdArgs a{tiles, n_tiles, ants, n_ant, shape.a_tile, acc, err, FwdGrid{}, M};
-  if (formalism == C8R_ENDPOINT) {
-    using O = OpsF64<C8R_ENDPOINT>;
-    const int64_t ctas =
-        forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile), sizeof(Acc4D) * O::kAccRows);
-    return launch_forward_ops<O>(a, ctas, st);
-  }
-  using O = OpsF64<C8R_ZHS>;
-  const int64_t ctas =
-      forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile), sizeof(Acc4D) * O::kAccRows);
-  return launch_forward_ops<O>(a, ctas, st);
+  if (lin) return launch_forward_f64_lin(formalism, tiles, n_tiles, ants, n_ant, M, acc, shape, sm_count, err, st);
+  return forward_f64<false>(formalism, tiles, n_tiles, ants, n_ant, M, acc, shape, sm_count, err, st);
 }
 
 cudaError_t launch_arrivals_f64(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,
@@ -31,9 +22,10 @@ cudaError_t launch_arrivals_f64(int formalism, const void* tiles, int64_t n, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_backward_f64(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st) {
-  if (formalism == C8R_ZHS) return launch_backward_ops<OpsF64<C8R_ZHS>>(a, shape, sm_count, st);
-  return launch_backward_ops<OpsF64<C8R_ENDPOINT>>(a, shape, sm_count, st);
+cudaError_t launch_backward_f64(int formalism, bool lin, BwdArgs& a, const FwdShape& shape, int sm_count,
+                                cudaStream_t st) {
+  if (lin) return launch_backward_f64_lin(formalism, a, shape, sm_count, st);
+  return backward_f64<false>(formalism, a, shape, sm_count, st);
 }
 
 }  // namespace c8r

@@ -5,23 +5,11 @@
 
 namespace c8r {
 
-cudaError_t launch_forward_mixed(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants, int n_ant,
-                                 const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
-                                 cudaStream_t st) {
-  FwdArgs a{tiles, n_tiles, ants, n_ant, shape.a_tile, acc, err, FwdGrid{}, M};
-  auto go = [&](auto ops) {
-    using O = decltype(ops);
-    const int64_t ctas = forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile),
-                                      sizeof(float4) * O::kAccRows);
-    return launch_forward_ops<O>(a, ctas, st);
-  };
-  const bool ex = M.kind == C8R_EXPONENTIAL;
-  if (M.kind == C8R_EXPONENTIAL_SPHERICAL)
-    return formalism == C8R_ENDPOINT ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL_SPHERICAL>{})
-                                     : go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL_SPHERICAL>{});
-  if (formalism == C8R_ENDPOINT)
-    return ex ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>{}) : go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>{});
-  return ex ? go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL>{}) : go(OpsMixed<C8R_ZHS, C8R_UNIFORM>{});
+cudaError_t launch_forward_mixed(int formalism, bool lin, const void* tiles, int64_t n_tiles, const AntRec* ants,
+                                 int n_ant, const MedParams& M, void* acc, const FwdShape& shape, int sm_count,
+                                 int* err, cudaStream_t st) {
+  if (lin) return launch_forward_mixed_lin(formalism, tiles, n_tiles, ants, n_ant, M, acc, shape, sm_count, err, st);
+  return forward_mixed<false>(formalism, tiles, n_tiles, ants, n_ant, M, acc, shape, sm_count, err, st);
 }
 
 // accumulator [n_ant][n_bins] float4 -> traces [n_ant][3][n_bins] (added or stored)
@@ -247,14 +235,10 @@ cudaError_t launch_arrivals_mixed(int formalism, const void* tiles, int64_t n, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_backward_mixed(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count,
+cudaError_t launch_backward_mixed(int formalism, bool lin, BwdArgs& a, const FwdShape& shape, int sm_count,
                                   cudaStream_t st) {
-  const bool ex = a.M.kind == C8R_EXPONENTIAL;
-  if (formalism == C8R_ZHS)
-    return ex ? launch_backward_ops<OpsMixed<C8R_ZHS, C8R_EXPONENTIAL>>(a, shape, sm_count, st)
-              : launch_backward_ops<OpsMixed<C8R_ZHS, C8R_UNIFORM>>(a, shape, sm_count, st);
-  return ex ? launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>>(a, shape, sm_count, st)
-            : launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>>(a, shape, sm_count, st);
+  if (lin) return launch_backward_mixed_lin(formalism, a, shape, sm_count, st);
+  return backward_mixed<false>(formalism, a, shape, sm_count, st);
 }
 
 }  // namespace c8r

@@ -62,6 +62,50 @@ __device__ __forceinline__ void endpoint_eval_f64(const double* T, int l, const 
   e.valid = true;
 }
 
+// Linear (two-bin) deposit (reading LD), in FP64: a deposit arriving at u
+// covers [u - 1/2, u + 1/2]; bin k0 = floor(u - 1/2) receives
+// (k0 + 1) - (u - 1/2) of it and bin k0 + 1 receives (u + 1/2) - (k0 + 1).
+template <class Sink>
+__device__ __forceinline__ void dep_lin_f64(Sink& out, int N, double u, double x, double y, double z) {
+  const double k0 = floor(u - 0.5);
+  const double w0 = (k0 + 1.0) - (u - 0.5), w1 = (u + 0.5) - (k0 + 1.0);
+  if (k0 >= 0.0 && k0 < (double)N && w0 > 0.0) out.dep((int)k0, x * w0, y * w0, z * w0);
+  if (k0 + 1.0 >= 0.0 && k0 + 1.0 < (double)N && w1 > 0.0) out.dep((int)k0 + 1, x * w1, y * w1, z * w1);
+}
+
+// the share of bin k of a deposit arriving at u (the tent max(0, 1 - |u - k - 1/2|))
+__device__ __forceinline__ double lin_share_f64(double u, double k) {
+  const double lo = fmax(u - 0.5, k), hi = fmin(u + 0.5, k + 1.0);
+  return hi > lo ? hi - lo : 0.0;
+}
+
+// integral of that share over u in [a, b]: the tent is linear between its knots
+// k - 1/2, k + 1/2, k + 3/2, so each piece is its length times the tent at its
+// middle
+__device__ __forceinline__ double lin_share_integral_f64(double a, double b, double k) {
+  double sum = 0.0;
+  for (int p = 0; p < 2; ++p) {
+    const double lo = fmax(a, k - 0.5 + p), hi = fmin(b, k + 0.5 + p);
+    if (hi > lo) sum += (hi - lo) * lin_share_f64(0.5 * (lo + hi), k);
+  }
+  return sum;
+}
+
+// dL/dtrace seen by a unit deposit at u, and its rate of change with u
+__device__ __forceinline__ void gather_lin_f64(const Acc4D* G, int N, double u, double g[3], double slope[3]) {
+  const double k0 = floor(u - 0.5);
+  const double w0 = (k0 + 1.0) - (u - 0.5), w1 = (u + 0.5) - (k0 + 1.0);
+  const Acc4D zero{0.0, 0.0, 0.0, 0.0};
+  const Acc4D g0 = (k0 >= 0.0 && k0 < (double)N) ? G[(int)k0] : zero;
+  const Acc4D g1 = (k0 + 1.0 >= 0.0 && k0 + 1.0 < (double)N) ? G[(int)k0 + 1] : zero;
+  g[0] = w0 * g0.x + w1 * g1.x;
+  g[1] = w0 * g0.y + w1 * g1.y;
+  g[2] = w0 * g0.z + w1 * g1.z;
+  slope[0] = g1.x - g0.x;
+  slope[1] = g1.y - g0.y;
+  slope[2] = g1.z - g0.z;
+}
+
 // a track of a staged tile: the FP64 path reads its fields where it needs them
 struct TrackD {
   const double* T;
@@ -69,7 +113,7 @@ struct TrackD {
   double q;
 };
 
-template <int FORM>
+template <int FORM, bool LIN = false>
 struct OpsF64 {
   using acc_t = double;
   using Track = TrackD;
@@ -115,6 +159,29 @@ struct OpsF64 {
     out.rec(e.branch, e.ua, e.ub);
     const double K = q * kKendpoint;
     const double dt_s = M.dt_ns * 1e-9;
+    if constexpr (LIN) {
+      // reading LD
+      if (e.branch == 0) {
+        const double s0 = +K / (e.D0 * e.g0.R * dt_s);
+        const double s1 = -K / (e.D1 * e.g1.R * dt_s);
+        dep_lin_f64(out, N, e.ua, s0 * e.V0[0], s0 * e.V0[1], s0 * e.V0[2]);
+        dep_lin_f64(out, N, e.ub, s1 * e.V1[0], s1 * e.V1[1], s1 * e.V1[2]);
+        return;
+      }
+      const double Ja = floor(e.ua + 0.5), Jb = floor(e.ub + 0.5);
+      if (Ja == Jb) {
+        // both arrivals in one cell: the exact limit K (dt_e/dt) V/(R dt) into
+        // bin J - 1 and its negative into bin J
+        const double B = K * ((TF(fd::T1) - TF(fd::T0)) / M.dt_ns) / (e.gm.R * dt_s);
+        if (Ja - 1.0 >= 0.0 && Ja - 1.0 < (double)N) out.dep((int)Ja - 1, B * e.Vm[0], B * e.Vm[1], B * e.Vm[2]);
+        if (Ja >= 0.0 && Ja < (double)N) out.dep((int)Ja, -B * e.Vm[0], -B * e.Vm[1], -B * e.Vm[2]);
+        return;
+      }
+      const double s = K / (e.Dm * e.gm.R * dt_s);
+      dep_lin_f64(out, N, e.ua, s * e.Vm[0], s * e.Vm[1], s * e.Vm[2]);
+      dep_lin_f64(out, N, e.ub, -s * e.Vm[0], -s * e.Vm[1], -s * e.Vm[2]);
+      return;
+    }
     const double ka = floor(e.ua), kb = floor(e.ub);
     const bool ina = ka >= 0.0 && ka < (double)N, inb = kb >= 0.0 && kb < (double)N;
     if (e.branch == 0) {
@@ -156,6 +223,21 @@ struct OpsF64 {
     const double k_lo = floor(u_lo), k_hi = floor(u_hi);
     out.rec(k_lo == k_hi ? 2 : 3, u_lo, u_hi);
     if (!(u_lo < (double)N + 1.0 && u_hi > -1.0)) return;
+    if constexpr (LIN) {
+      // reading LD: the tent weights averaged over [u_lo, u_hi]
+      const double A1 = KA * dte / (gm.R * dt);
+      if (floor(u_lo + 0.5) == floor(u_hi + 0.5)) {
+        dep_lin_f64(out, N, 0.5 * (u_lo + u_hi), A1 * bp[0], A1 * bp[1], A1 * bp[2]);
+        return;
+      }
+      const double W = u_hi - u_lo;
+      const double kb = fmax(floor(u_lo - 0.5), 0.0), ke = fmin(floor(u_hi + 0.5), (double)(N - 1));
+      for (double kd = kb; kd <= ke; kd += 1.0) {
+        const double w = lin_share_integral_f64(u_lo, u_hi, kd) / W;
+        if (w > 0.0) out.dep((int)kd, A1 * w * bp[0], A1 * w * bp[1], A1 * w * bp[2]);
+      }
+      return;
+    }
     if (k_lo == k_hi) {
       const double s = KA * dte / (gm.R * dt);
       if (k_lo >= 0.0 && k_lo < (double)N) out.dep((int)k_lo, s * bp[0], s * bp[1], s * bp[2]);
@@ -224,7 +306,33 @@ struct OpsF64 {
     for (int k = 0; k < 3; ++k) Av[k] = KA * (b[k] - c * gm.rh[k]) * dte / (gm.R * dt);
     double S[3] = {0.0, 0.0, 0.0};
     double dLdu = 0.0, dLdh = 0.0;  // per bin of u, per bin of h = half/dt
-    if (k_lo == k_hi) {
+    if constexpr (LIN) {
+      // reading LD: S = sum_k w_k G_k with the tent weights averaged over the
+      // interval; the interval-end values p = A.(G seen by a deposit at the end)
+      double sl[3];
+      if (floor(u_lo + 0.5) == floor(u_hi + 0.5)) {
+        gather_lin_f64(G, N, 0.5 * (u_lo + u_hi), S, sl);
+        dLdu = Av[0] * sl[0] + Av[1] * sl[1] + Av[2] * sl[2];
+      } else {
+        const double W = u_hi - u_lo;
+        const double kb = fmax(floor(u_lo - 0.5), 0.0), ke = fmin(floor(u_hi + 0.5), (double)(N - 1));
+        for (double kd = kb; kd <= ke; kd += 1.0) {
+          const double w = lin_share_integral_f64(u_lo, u_hi, kd) / W;
+          const Acc4D g = G[(int)kd];
+          S[0] += w * g.x;
+          S[1] += w * g.y;
+          S[2] += w * g.z;
+        }
+        double glo[3], ghi[3];
+        gather_lin_f64(G, N, u_lo, glo, sl);
+        gather_lin_f64(G, N, u_hi, ghi, sl);
+        const double p_lo = Av[0] * glo[0] + Av[1] * glo[1] + Av[2] * glo[2];
+        const double p_hi = Av[0] * ghi[0] + Av[1] * ghi[1] + Av[2] * ghi[2];
+        const double AS = Av[0] * S[0] + Av[1] * S[1] + Av[2] * S[2];
+        dLdu = (p_hi - p_lo) / W;
+        dLdh = (p_hi + p_lo - 2.0 * AS) / W;
+      }
+    } else if (k_lo == k_hi) {
       if (!(k_lo >= 0.0 && k_lo < (double)N)) return;
       const Acc4D g = G[(int)k_lo];
       S[0] = g.x; S[1] = g.y; S[2] = g.z;
@@ -288,6 +396,133 @@ struct OpsF64 {
     tg[7] += 0.5 * dLdu / dt + dLd_dte;
   }
 
+  // chain rule through an arrival position u = (t_e - t_a)/dt + n_avg R/(c dt)
+  // of the emission point at d = x_a - x_e (refractivity factor E): adds dL/dx_e
+  // x w_e to pos0 (and pos1), dL/dx_a and dL/dN0 (the caller adds dL/dt_e)
+  static __device__ __forceinline__ void arrival_grad(const GeoD& g, double E, const MedParams& M, double dLdu,
+                                                      double* pos0, double* pos1, double w_e, double ga[3],
+                                                      double& dn) {
+    const RefrGrad<double> rg = refraction_grad<double>(M.kind, g.R, g.d[2] * M.invH, E, M.N0, M.invH, M.n - 1.0);
+    const double dLdopt = dLdu * M.inv_c_ns / M.dt_ns;
+    const double dLdR = dLdopt * (1.0 + rg.dF_dR);
+    for (int k = 0; k < 3; ++k) {
+      const double v = dLdR * g.rh[k];
+      ga[k] += v;
+      pos0[k] -= w_e * v;
+      if (pos1) pos1[k] -= w_e * v;
+    }
+    pos0[2] += w_e * dLdopt * rg.dF_dzm;
+    if (pos1) pos1[2] += w_e * dLdopt * rg.dF_dzm;
+    ga[2] += dLdopt * rg.dF_dza;
+    dn += dLdopt * rg.dF_dN0;
+  }
+
+  // Endpoint adjoint with the linear deposit (reading LD): the amplitude against
+  // the spread of dL/dtrace each deposit sees, plus the slide of the deposits with
+  // their arrivals (dL/du = l(G_{k0+1} - G_{k0})), through the arrival times and,
+  // near Cherenkov, through u_a, u_b = u_m -/+ D dt_e/(2 dt).  Times in ns.
+  static __device__ __forceinline__ void adj_lin(const double* T, int l, const EndpointEvalD& e, const double b[3],
+                                                 double K, double dt_s, const MedParams& M, const Acc4D* G,
+                                                 double tg[11], double ga[3], double& dn) {
+    const int N = M.n_bins;
+    const double dt = M.dt_ns;
+    double dd[3], db[3], dns, gv[3], sl[3];
+    if (e.branch == 0) {
+      for (int j = 0; j < 2; ++j) {
+        const GeoD& g = j == 0 ? e.g0 : e.g1;
+        const double* V = j == 0 ? e.V0 : e.V1;
+        const double D = j == 0 ? e.D0 : e.D1;
+        const double E = j == 0 ? e.E0 : e.E1;
+        const double kap = (j == 0 ? K : -K) / dt_s;
+        gather_lin_f64(G, N, j == 0 ? e.ua : e.ub, gv, sl);
+        const double c = b[0] * g.rh[0] + b[1] * g.rh[1] + b[2] * g.rh[2];
+        deposit_adjoint<double>(g.rh, V, c, D, g.R, g.n_src, gv, kap, dd, db, dns);
+        const RefrGrad<double> rg =
+            refraction_grad<double>(M.kind, g.R, g.d[2] * M.invH, E, M.N0, M.invH, M.n - 1.0);
+        for (int cc = 0; cc < 3; ++cc) {
+          tg[3 * j + cc] -= dd[cc];
+          ga[cc] += dd[cc];
+          tg[8 + cc] += db[cc];
+        }
+        tg[3 * j + 2] += dns * rg.dn_dzm;
+        dn += dns * rg.dn_dN0;
+        const double dLdu = kap * (V[0] * sl[0] + V[1] * sl[1] + V[2] * sl[2]) / (D * g.R);
+        arrival_grad(g, E, M, dLdu, tg + 3 * j, nullptr, 1.0, ga, dn);
+        tg[6 + j] += dLdu / dt;
+      }
+      return;
+    }
+    const GeoD& g = e.gm;
+    const double c = b[0] * g.rh[0] + b[1] * g.rh[1] + b[2] * g.rh[2];
+    const double dte = TF(fd::T1) - TF(fd::T0);
+    const double Ja = floor(e.ua + 0.5), Jb = floor(e.ub + 0.5);
+    if (Ja == Jb) {
+      // l = kap (g.V)/R, kap = K (dt_e/dt)/dt_s, g = G_{J-1} - G_J: the deposit
+      // adjoint with D = 1 and n = 0, and dl/d dt_e = l/dt_e
+      const Acc4D zero{0.0, 0.0, 0.0, 0.0};
+      const Acc4D g0 = (Ja - 1.0 >= 0.0 && Ja - 1.0 < (double)N) ? G[(int)Ja - 1] : zero;
+      const Acc4D g1 = (Ja >= 0.0 && Ja < (double)N) ? G[(int)Ja] : zero;
+      gv[0] = g0.x - g1.x;
+      gv[1] = g0.y - g1.y;
+      gv[2] = g0.z - g1.z;
+      const double kap = K * (dte / dt) / dt_s;
+      deposit_adjoint<double>(g.rh, e.Vm, c, 1.0, g.R, 0.0, gv, kap, dd, db, dns);
+      for (int cc = 0; cc < 3; ++cc) {
+        tg[cc] -= 0.5 * dd[cc];
+        tg[3 + cc] -= 0.5 * dd[cc];
+        ga[cc] += dd[cc];
+        tg[8 + cc] += db[cc];
+      }
+      const double lv = kap * (gv[0] * e.Vm[0] + gv[1] * e.Vm[1] + gv[2] * e.Vm[2]) / g.R;
+      tg[6] -= lv / dte;
+      tg[7] += lv / dte;
+      return;
+    }
+    double gav[3], gbv[3], sla[3], slb[3];
+    gather_lin_f64(G, N, e.ua, gav, sla);
+    gather_lin_f64(G, N, e.ub, gbv, slb);
+    for (int cc = 0; cc < 3; ++cc) gv[cc] = gav[cc] - gbv[cc];
+    deposit_adjoint<double>(g.rh, e.Vm, c, e.Dm, g.R, g.n_src, gv, K / dt_s, dd, db, dns);
+    const RefrGrad<double> rg = refraction_grad<double>(M.kind, g.R, g.d[2] * M.invH, e.Em, M.N0, M.invH, M.n - 1.0);
+    for (int cc = 0; cc < 3; ++cc) {
+      tg[cc] -= 0.5 * dd[cc];
+      tg[3 + cc] -= 0.5 * dd[cc];
+      ga[cc] += dd[cc];
+      tg[8 + cc] += db[cc];
+    }
+    tg[2] += 0.5 * dns * rg.dn_dzm;
+    tg[5] += 0.5 * dns * rg.dn_dzm;
+    dn += dns * rg.dn_dN0;
+    // the slide of the two spread deposits +/- s V, s = K/(D R dt_s)
+    const double sm = K / (e.Dm * g.R * dt_s);
+    const double dLdua = sm * (e.Vm[0] * sla[0] + e.Vm[1] * sla[1] + e.Vm[2] * sla[2]);
+    const double dLdub = -sm * (e.Vm[0] * slb[0] + e.Vm[1] * slb[1] + e.Vm[2] * slb[2]);
+    const double dLdum = dLdua + dLdub;
+    const double dtau = dte / dt;
+    const double dLdD = (dLdub - dLdua) * dtau / 2.0;
+    const double dLd_dtau = (dLdub - dLdua) * e.Dm / 2.0;
+    // D = 1 - n_src (beta.rhat), rhat = d/R, d = x_a - x_m
+    double dLdr[3];
+    for (int k = 0; k < 3; ++k) {
+      tg[8 + k] -= g.n_src * g.rh[k] * dLdD;
+      dLdr[k] = -g.n_src * b[k] * dLdD;
+    }
+    const double rdr = dLdr[0] * g.rh[0] + dLdr[1] * g.rh[1] + dLdr[2] * g.rh[2];
+    for (int k = 0; k < 3; ++k) {
+      const double v = (dLdr[k] - rdr * g.rh[k]) / g.R;
+      tg[k] -= 0.5 * v;
+      tg[3 + k] -= 0.5 * v;
+      ga[k] += v;
+    }
+    const double dLdn = -c * dLdD;
+    tg[2] += 0.5 * dLdn * rg.dn_dzm;
+    tg[5] += 0.5 * dLdn * rg.dn_dzm;
+    dn += dLdn * rg.dn_dN0;
+    arrival_grad(g, e.Em, M, dLdum, tg, tg + 3, 0.5, ga, dn);
+    tg[6] += (0.5 * dLdum - dLd_dtau) / dt;
+    tg[7] += (0.5 * dLdum + dLd_dtau) / dt;
+  }
+
   static __device__ __forceinline__ void adj(const TrackD& tr, const AntRec& A, const MedParams& M,
                                              const Acc4D* G, double tg[11], double ga[3], double& dn) {
     static_assert(FORM == C8R_ENDPOINT, "adjoint is defined for the Endpoint formalism");
@@ -302,6 +537,10 @@ struct OpsF64 {
     const double b[3] = {TF(fd::BX), TF(fd::BY), TF(fd::BZ)};
     const double K = q * kKendpoint;
     const double dt_s = M.dt_ns * 1e-9;
+    if constexpr (LIN) {
+      adj_lin(T, l, e, b, K, dt_s, M, G, tg, ga, dn);
+      return;
+    }
     const double ka = floor(e.ua), kb = floor(e.ub);
     const bool ina = ka >= 0.0 && ka < (double)N, inb = kb >= 0.0 && kb < (double)N;
     const bool expo = M.kind == C8R_EXPONENTIAL;
@@ -355,5 +594,26 @@ struct OpsF64 {
 };
 
 #undef TF
+
+// forward and adjoint launches for one deposit shape
+template <bool LIN>
+cudaError_t forward_f64(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants, int n_ant,
+                        const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
+                        cudaStream_t st) {
+  FwdArgs a{tiles, n_tiles, ants, n_ant, shape.a_tile, acc, err, FwdGrid{}, M};
+  auto go = [&](auto ops) {
+    using O = decltype(ops);
+    const int64_t ctas =
+        forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile), sizeof(Acc4D) * O::kAccRows);
+    return launch_forward_ops<O>(a, ctas, st);
+  };
+  return formalism == C8R_ENDPOINT ? go(OpsF64<C8R_ENDPOINT, LIN>{}) : go(OpsF64<C8R_ZHS, LIN>{});
+}
+
+template <bool LIN>
+cudaError_t backward_f64(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st) {
+  if (formalism == C8R_ZHS) return launch_backward_ops<OpsF64<C8R_ZHS, LIN>>(a, shape, sm_count, st);
+  return launch_backward_ops<OpsF64<C8R_ENDPOINT, LIN>>(a, shape, sm_count, st);
+}
 
 }  // namespace c8r

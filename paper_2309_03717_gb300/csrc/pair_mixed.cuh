@@ -160,7 +160,56 @@ __device__ __forceinline__ void endpoint_eval_mixed(const TrackM& t, const AntRe
   e.valid = true;
 }
 
-template <int FORM, int KIND>
+// Linear (two-bin) deposit (reading LD): a deposit arriving at u is spread over
+// [u - 1/2, u + 1/2].  With J = floor(u + 1/2) (the "cell" between the bin
+// centres J - 1/2 and J + 1/2) and s = u + 1/2 - J, bins J - 1 and J receive
+// 1 - s and s of it.  Cells outside [0, N] touch no bin of the window; bin_raw
+// clamps them to -1 or N + 1.
+__device__ __forceinline__ int lin_cell(ff u, int N, float& s) {
+  ff v;
+  two_sum(u.h, 0.5f, v.h, v.l);
+  v.l = __fadd_rn(v.l, u.l);
+  return bin_raw(v, N + 1, s);
+}
+
+// ZHS with the linear deposit, an interval [u_lo, u_hi] over more than one cell:
+// the tent weights averaged over it, for the bins around its two ends (per unit
+// of the whole interval's deposit); every bin strictly between them receives
+// 1/W.  First cell: bins J_lo - 1 and J_lo get (1 - s_lo)^2/2 and
+// (1 - s_lo^2)/2; last cell: J_hi - 1 and J_hi get s_hi (1 - s_hi/2) and
+// s_hi^2/2; every whole cell in between gives 1/2 to each of its two bins.
+struct LinEnds {
+  int k[4];
+  float w[4];
+  int n;
+};
+__device__ __forceinline__ LinEnds lin_ends(int Jlo, float slo, int Jhi, float shi, float invW) {
+  const float a = 1.0f - slo;
+  const float lo0 = 0.5f * a * a, lo1 = 0.5f * (1.0f - slo * slo);
+  const float hi0 = shi * (1.0f - 0.5f * shi), hi1 = 0.5f * shi * shi;
+  LinEnds z;
+  z.k[0] = Jlo - 1;
+  z.w[0] = lo0 * invW;
+  z.k[1] = Jlo;
+  if (Jhi == Jlo + 1) {
+    z.w[1] = (lo1 + hi0) * invW;
+    z.k[2] = Jhi;
+    z.w[2] = hi1 * invW;
+    z.k[3] = -1;
+    z.w[3] = 0.0f;
+    z.n = 3;
+  } else {
+    z.w[1] = (lo1 + 0.5f) * invW;
+    z.k[2] = Jhi - 1;
+    z.w[2] = (hi0 + 0.5f) * invW;
+    z.k[3] = Jhi;
+    z.w[3] = hi1 * invW;
+    z.n = 4;
+  }
+  return z;
+}
+
+template <int FORM, int KIND, bool LIN = false>
 struct OpsMixed {
   using acc_t = float;
   using Track = TrackM;
@@ -171,7 +220,9 @@ struct OpsMixed {
   // Endpoint: the near-Cherenkov pairs (a minority, spread over most warps)
   // are set aside by the main pass and evaluated together afterwards
   static constexpr bool kDefers = FORM == C8R_ENDPOINT;
-  static constexpr int kBwdMinBlocks = 6;  // adjoint CTAs (128 threads) per SM the registers are set for
+  // adjoint CTAs (128 threads) per SM the registers are set for (the linear
+  // Endpoint adjoint carries the slide of each deposit as well)
+  static constexpr int kBwdMinBlocks = (LIN && FORM == C8R_ENDPOINT) ? 4 : 6;
   // ZHS: a second accumulator row holds the edges of box deposits
   static constexpr int kAccRows = FORM == C8R_ZHS ? 2 : 1;
 
@@ -197,9 +248,64 @@ struct OpsMixed {
   // -------------------------------------------------------------------------
   // The deposits of an evaluated pair; the evaluation is split between
   // pair_main and pair_deferred below.
+  // a deposit (x, y, z) arriving in cell J at s, spread over bins J - 1 and J
+  template <class Sink>
+  static __device__ __forceinline__ void dep_lin(Sink& out, int N, int J, float s, float x, float y, float z) {
+    const float r = 1.0f - s;
+    if (J >= 1 && J - 1 < N) out.dep(J - 1, x * r, y * r, z * r);
+    if (J >= 0 && J < N) out.dep(J, x * s, y * s, z * s);
+  }
+
+  // Endpoint deposits spread over two bins each (reading LD).  Near Cherenkov,
+  // when both linearised arrivals lie in one cell J, the two spread deposits
+  // +/- amp V/(D R) combine to the exact amp (dt_e/dt) V/R into bin J - 1 and
+  // its negative into bin J, with no division by D.
+  template <class Sink>
+  static __device__ __forceinline__ void endpoint_deposit_lin(const TrackM& t, const EndpointEvalM& e,
+                                                              const MedParams& M, Sink& out) {
+    const int N = M.n_bins;
+    out.rec(e.branch, e.ua, e.ub);
+    float sa, sb;
+    const int Ja = lin_cell(e.ua, N, sa);
+    const int Jb = lin_cell(e.ub, N, sb);
+    const float amp = t.amp;
+    if (e.branch == 0) {
+      const float c0 = __fdividef(amp, e.f0.D * e.g0.R0) * (e.f0.invR * e.f0.invR);
+      const float c1 = __fdividef(-amp, e.f1.D * e.g1.R0) * (e.f1.invR * e.f1.invR);
+      if (Ja == Jb) {
+        // both in one cell: add them in registers, two reductions
+        const float a0 = c0 * (1.0f - sa), b0 = c1 * (1.0f - sb), a1 = c0 * sa, b1 = c1 * sb;
+        if (Ja >= 1 && Ja - 1 < N)
+          out.dep(Ja - 1, a0 * e.f0.V[0] + b0 * e.f1.V[0], a0 * e.f0.V[1] + b0 * e.f1.V[1],
+                  a0 * e.f0.V[2] + b0 * e.f1.V[2]);
+        if (Ja >= 0 && Ja < N)
+          out.dep(Ja, a1 * e.f0.V[0] + b1 * e.f1.V[0], a1 * e.f0.V[1] + b1 * e.f1.V[1],
+                  a1 * e.f0.V[2] + b1 * e.f1.V[2]);
+      } else {
+        dep_lin(out, N, Ja, sa, c0 * e.f0.V[0], c0 * e.f0.V[1], c0 * e.f0.V[2]);
+        dep_lin(out, N, Jb, sb, c1 * e.f1.V[0], c1 * e.f1.V[1], c1 * e.f1.V[2]);
+      }
+      return;
+    }
+    const float i2 = e.fm.invR * e.fm.invR;
+    if (Ja == Jb) {
+      const float c = amp * t.dtauh * (i2 * e.fm.invR);
+      if (Ja >= 1 && Ja - 1 < N) out.dep(Ja - 1, c * e.fm.V[0], c * e.fm.V[1], c * e.fm.V[2]);
+      if (Ja >= 0 && Ja < N) out.dep(Ja, -c * e.fm.V[0], -c * e.fm.V[1], -c * e.fm.V[2]);
+      return;
+    }
+    const float c = __fdividef(amp, e.fm.D * e.gm.R0) * i2;
+    dep_lin(out, N, Ja, sa, c * e.fm.V[0], c * e.fm.V[1], c * e.fm.V[2]);
+    dep_lin(out, N, Jb, sb, -c * e.fm.V[0], -c * e.fm.V[1], -c * e.fm.V[2]);
+  }
+
   template <class Sink>
   static __device__ __forceinline__ void endpoint_deposit(const TrackM& t, const EndpointEvalM& e,
                                                           const MedParams& M, Sink& out) {
+    if constexpr (LIN) {
+      endpoint_deposit_lin(t, e, M, out);
+      return;
+    }
     const int N = M.n_bins;
     out.rec(e.branch, e.ua, e.ub);
     float fa, fb;
@@ -263,6 +369,26 @@ struct OpsMixed {
     const int klo = bin_raw(ulo, N, flo);
     const int khi = bin_raw(uhi, N, fhi);
     out.rec(klo == khi ? 2 : 3, ulo, uhi);
+    if constexpr (LIN) {
+      // reading LD: the tent weights averaged over the interval
+      float slo, shi;
+      const int Jlo = lin_cell(ulo, N, slo);
+      const int Jhi = lin_cell(uhi, N, shi);
+      if (Jlo == Jhi) {
+        // inside one cell the tents are linear: the tent at the middle
+        dep_lin(out, N, Jlo, 0.5f * (slo + shi), Mx, My, Mz);
+        return;
+      }
+      const float invW = __fdividef(1.0f, 2.0f * hh);
+      const LinEnds z = lin_ends(Jlo, slo, Jhi, shi, invW);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < z.n && z.k[i] >= 0 && z.k[i] < N) out.dep(z.k[i], Mx * z.w[i], My * z.w[i], Mz * z.w[i]);
+      const int kb = Jlo + 1 < 0 ? 0 : Jlo + 1;
+      const int ke = Jhi - 2 > N - 1 ? N - 1 : Jhi - 2;
+      if (kb <= ke) out.dep_box(kb, ke, Mx * invW, My * invW, Mz * invW);
+      return;
+    }
     if (klo == khi) {
       if (klo >= 0 && klo < N) out.dep(klo, Mx, My, Mz);
       return;
@@ -330,14 +456,58 @@ struct OpsMixed {
   // -------------------------------------------------------------------------
   // adjoint of `endpoint` with bins and branch held fixed
   // -------------------------------------------------------------------------
-  static __device__ __forceinline__ void deposit_grad(const GeoM& g, const FieldM& f, float n, const float gv[3],
-                                                      float kappa, float dd[3], float db[3], float& dns) {
+  static __device__ __forceinline__ void deposit_grad(const GeoM& g, const FieldM& f, float D, float n,
+                                                      const float gv[3], float kappa, float dd[3], float db[3],
+                                                      float& dns) {
     const float invR = f.invR;
     const float rh[3] = {g.s[0] * invR, g.s[1] * invR, g.s[2] * invR};
     const float inv2 = invR * invR;
     const float V[3] = {f.V[0] * inv2, f.V[1] * inv2, f.V[2] * inv2};
     const float c = f.bd * invR;
-    deposit_adjoint<float>(rh, V, c, f.D, g.R0, n, gv, kappa, dd, db, dns);
+    deposit_adjoint<float>(rh, V, c, D, g.R0, n, gv, kappa, dd, db, dns);
+  }
+  static __device__ __forceinline__ void deposit_grad(const GeoM& g, const FieldM& f, float n, const float gv[3],
+                                                      float kappa, float dd[3], float db[3], float& dns) {
+    deposit_grad(g, f, f.D, n, gv, kappa, dd, db, dns);
+  }
+
+  // dL/dtrace seen by a unit deposit in cell J at s (reading LD), and its rate of
+  // change with the arrival (bins outside the window read 0)
+  static __device__ __forceinline__ void gather_lin(const float4* G, int N, int J, float s, float gv[3],
+                                                    float slope[3]) {
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 g0 = (J >= 1 && J - 1 < N) ? G[J - 1] : z4;
+    const float4 g1 = (J >= 0 && J < N) ? G[J] : z4;
+    const float r = 1.0f - s;
+    gv[0] = r * g0.x + s * g1.x;
+    gv[1] = r * g0.y + s * g1.y;
+    gv[2] = r * g0.z + s * g1.z;
+    slope[0] = g1.x - g0.x;
+    slope[1] = g1.y - g0.y;
+    slope[2] = g1.z - g0.z;
+  }
+
+  // chain rule through an arrival position u = (t_e - t_a)/dt + (R + F)/(c dt)
+  // of the emission point at d = x_a - x_e (refractivity factor E): adds
+  // dL/dx_e x w_e (w_e = 1, or 1/2 to each endpoint for the midpoint), dL/dx_a,
+  // dL/dN0; the caller adds dL/dt_e
+  static __device__ __forceinline__ void arrival_grad(const GeoM& g, float invR, float E, const MedParams& M,
+                                                      float dLdu, float* tg_pos0, float* tg_pos1, float w_e,
+                                                      float ga[3], float& dn) {
+    const RefrGrad<float> rg = refraction_grad<float>(KIND, g.R0, g.s[2] * M.invH_h, E, M.N0f, M.invH_h, M.nm1f);
+    const float dLdopt = dLdu * M.kc_h;
+    const float dLdR = dLdopt * (1.0f + rg.dF_dR);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float v = dLdR * g.s[k] * invR;
+      ga[k] += v;
+      tg_pos0[k] -= w_e * v;
+      if (tg_pos1) tg_pos1[k] -= w_e * v;
+    }
+    tg_pos0[2] += w_e * dLdopt * rg.dF_dzm;
+    if (tg_pos1) tg_pos1[2] += w_e * dLdopt * rg.dF_dzm;
+    ga[2] += dLdopt * rg.dF_dza;
+    dn += dLdopt * rg.dF_dN0;
   }
 
   // adjoint main pass: every pair except (Endpoint) the near-Cherenkov ones, for
@@ -417,7 +587,49 @@ struct OpsMixed {
                          t.amp * (b[2] - c * rh[2]) * invR};
     float S[3];
     float dLdu = 0.0f, dLdh = 0.0f;
-    if (klo == khi) {
+    if constexpr (LIN) {
+      float slo, shi;
+      const int Jlo = lin_cell(ulo, N, slo);
+      const int Jhi = lin_cell(uhi, N, shi);
+      float sl[3];
+      if (Jlo == Jhi) {
+        if (Jlo < 0 || Jlo > N) return;
+        gather_lin(G, N, Jlo, 0.5f * (slo + shi), S, sl);
+        dLdu = Av[0] * sl[0] + Av[1] * sl[1] + Av[2] * sl[2];
+      } else {
+        const float invW = __fdividef(1.0f, 2.0f * hh);
+        const LinEnds z = lin_ends(Jlo, slo, Jhi, shi, invW);
+        double ix = 0.0, iy = 0.0, iz = 0.0;  // G summed over the bins strictly between the ends
+        const int kb = Jlo + 1 < 0 ? 0 : Jlo + 1;
+        const int ke = Jhi - 2 > N - 1 ? N - 1 : Jhi - 2;
+        if (kb <= ke) {
+          const Acc4D p1 = Gp[ke + 1], p0 = Gp[kb];
+          ix = p1.x - p0.x;
+          iy = p1.y - p0.y;
+          iz = p1.z - p0.z;
+        }
+        S[0] = invW * (float)ix;
+        S[1] = invW * (float)iy;
+        S[2] = invW * (float)iz;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (i < z.n && z.k[i] >= 0 && z.k[i] < N) {
+            const float4 g = G[z.k[i]];
+            S[0] += z.w[i] * g.x;
+            S[1] += z.w[i] * g.y;
+            S[2] += z.w[i] * g.z;
+          }
+        }
+        float glo[3], ghi[3];
+        gather_lin(G, N, Jlo, slo, glo, sl);
+        gather_lin(G, N, Jhi, shi, ghi, sl);
+        const float p_lo = Av[0] * glo[0] + Av[1] * glo[1] + Av[2] * glo[2];
+        const float p_hi = Av[0] * ghi[0] + Av[1] * ghi[1] + Av[2] * ghi[2];
+        const float AS = Av[0] * S[0] + Av[1] * S[1] + Av[2] * S[2];
+        dLdu = (p_hi - p_lo) * invW;
+        dLdh = (p_hi + p_lo - 2.0f * AS) * invW;
+      }
+    } else if (klo == khi) {
       if (klo < 0 || klo >= N) return;
       const float4 g = G[klo];
       S[0] = g.x; S[1] = g.y; S[2] = g.z;
@@ -497,9 +709,129 @@ struct OpsMixed {
     tg[7] += (0.5f * dLdu + dLd_dtau) * idt;
   }
 
+  // gradients of the linear (two-bin) Endpoint deposits of an evaluated pair:
+  // the amplitude as for one bin, against the spread of dL/dtrace that the
+  // deposit sees, plus its slide with the arrival, dL/du = l(G_J - G_{J-1}),
+  // taken through the arrival time (and near Cherenkov through
+  // u_a, u_b = u_m -/+ D (t1 - t0)/(2 dt)).  Times in ns, positions in m.
+  static __device__ __forceinline__ void adj_deposits_lin(const TrackM& t, const EndpointEvalM& e,
+                                                          const MedParams& M, const float4* G, float tg[11],
+                                                          float ga[3], float& dn) {
+    const int N = M.n_bins;
+    float sa, sb;
+    const int Ja = lin_cell(e.ua, N, sa);
+    const int Jb = lin_cell(e.ub, N, sb);
+    const float dNdz_fac = (KIND == C8R_EXPONENTIAL) ? -M.N0f * M.invH_h : 0.0f;
+    const float idt = M.idt_h;
+    const float amp = t.amp;
+    float dd[3], db[3], dns, gv[3], sl[3];
+    if (e.branch == 0) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int J = j == 0 ? Ja : Jb;
+        if (J < 0 || J > N) continue;
+        const GeoM& g = j == 0 ? e.g0 : e.g1;
+        const FieldM& f = j == 0 ? e.f0 : e.f1;
+        const float E = j == 0 ? t.E0h : t.E1h;
+        const float kap = j == 0 ? amp : -amp;
+        gather_lin(G, N, J, j == 0 ? sa : sb, gv, sl);
+        deposit_grad(g, f, 1.0f + (j == 0 ? t.nm1_0 : t.nm1_1), gv, kap, dd, db, dns);
+        for (int c = 0; c < 3; ++c) {
+          tg[3 * j + c] -= dd[c];
+          ga[c] += dd[c];
+          tg[8 + c] += db[c];
+        }
+        tg[3 * j + 2] += dns * dNdz_fac * E;
+        dn += dns * E;
+        const float cj = __fdividef(kap, f.D * g.R0) * (f.invR * f.invR);
+        const float dLdu = cj * (f.V[0] * sl[0] + f.V[1] * sl[1] + f.V[2] * sl[2]);
+        arrival_grad(g, f.invR, E, M, dLdu, tg + 3 * j, nullptr, 1.0f, ga, dn);
+        tg[6 + j] += dLdu * idt;
+      }
+      return;
+    }
+    const float invR = e.fm.invR;
+    if (Ja == Jb) {
+      // l = amp (t1 - t0)/dt (g.V)/R with g = G_{J-1} - G_J: the deposit adjoint
+      // with D = 1 and n = 0, and dl/d(t1 - t0) = l/(t1 - t0)
+      if (Ja < 0 || Ja > N) return;
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 g0 = (Ja >= 1 && Ja - 1 < N) ? G[Ja - 1] : z4;
+      const float4 g1 = (Ja < N) ? G[Ja] : z4;
+      gv[0] = g0.x - g1.x;
+      gv[1] = g0.y - g1.y;
+      gv[2] = g0.z - g1.z;
+      const float kap = amp * t.dtauh;
+      deposit_grad(e.gm, e.fm, 1.0f, 0.0f, gv, kap, dd, db, dns);
+      for (int c = 0; c < 3; ++c) {
+        tg[c] -= 0.5f * dd[c];
+        tg[3 + c] -= 0.5f * dd[c];
+        ga[c] += dd[c];
+        tg[8 + c] += db[c];
+      }
+      const float l_dtau =
+          amp * (gv[0] * e.fm.V[0] + gv[1] * e.fm.V[1] + gv[2] * e.fm.V[2]) * (invR * invR * invR);
+      tg[6] -= l_dtau * idt;
+      tg[7] += l_dtau * idt;
+      return;
+    }
+    float ga_[3], gb_[3], sla[3], slb[3];
+    gather_lin(G, N, Ja, sa, ga_, sla);
+    gather_lin(G, N, Jb, sb, gb_, slb);
+    gv[0] = ga_[0] - gb_[0];
+    gv[1] = ga_[1] - gb_[1];
+    gv[2] = ga_[2] - gb_[2];
+    deposit_grad(e.gm, e.fm, 1.0f + t.nm1_m, gv, amp, dd, db, dns);
+    for (int c = 0; c < 3; ++c) {
+      tg[c] -= 0.5f * dd[c];
+      tg[3 + c] -= 0.5f * dd[c];
+      ga[c] += dd[c];
+      tg[8 + c] += db[c];
+    }
+    tg[2] += 0.5f * dns * dNdz_fac * t.Emh;
+    tg[5] += 0.5f * dns * dNdz_fac * t.Emh;
+    dn += dns * t.Emh;
+    // the slide of the two spread deposits +/- c V
+    const float Dm = e.fm.D;
+    const float cm = __fdividef(amp, Dm * e.gm.R0) * (invR * invR);
+    const float dLdua = cm * (e.fm.V[0] * sla[0] + e.fm.V[1] * sla[1] + e.fm.V[2] * sla[2]);
+    const float dLdub = -cm * (e.fm.V[0] * slb[0] + e.fm.V[1] * slb[1] + e.fm.V[2] * slb[2]);
+    const float dLdum = dLdua + dLdub;
+    const float dLdD = (dLdub - dLdua) * 0.5f * t.dtauh;
+    const float dLd_dtau = (dLdub - dLdua) * 0.5f * Dm;
+    // D = 1 - n (beta.rhat), rhat = d/R, d = x_a - x_m
+    const float n = 1.0f + t.nm1_m;
+    const float rh[3] = {e.gm.s[0] * invR, e.gm.s[1] * invR, e.gm.s[2] * invR};
+    const float b[3] = {t.bx, t.by, t.bz};
+    const float cr = e.fm.bd * invR;
+    float dLdr[3];
+    for (int k = 0; k < 3; ++k) {
+      tg[8 + k] -= n * rh[k] * dLdD;
+      dLdr[k] = -n * b[k] * dLdD;
+    }
+    const float rdr = dLdr[0] * rh[0] + dLdr[1] * rh[1] + dLdr[2] * rh[2];
+    for (int k = 0; k < 3; ++k) {
+      const float v = (dLdr[k] - rdr * rh[k]) * invR;
+      tg[k] -= 0.5f * v;
+      tg[3 + k] -= 0.5f * v;
+      ga[k] += v;
+    }
+    const float dLdn = -cr * dLdD;
+    tg[2] += 0.5f * dLdn * dNdz_fac * t.Emh;
+    tg[5] += 0.5f * dLdn * dNdz_fac * t.Emh;
+    dn += dLdn * t.Emh;
+    arrival_grad(e.gm, invR, t.Emh, M, dLdum, tg, tg + 3, 0.5f, ga, dn);
+    tg[6] += (0.5f * dLdum - dLd_dtau) * idt;
+    tg[7] += (0.5f * dLdum + dLd_dtau) * idt;
+  }
+
   // gradients of the deposits of an evaluated pair
   static __device__ __forceinline__ void adj_deposits(const TrackM& t, const EndpointEvalM& e, const MedParams& M,
                                                       const float4* G, float tg[11], float ga[3], float& dn) {
+    if constexpr (LIN) {
+      adj_deposits_lin(t, e, M, G, tg, ga, dn);
+      return;
+    }
     const int N = M.n_bins;
     float fa, fb;
     const int ka = bin_raw(e.ua, N, fa);
@@ -549,5 +881,37 @@ struct OpsMixed {
 };
 
 #undef TF
+
+// forward and adjoint launches for one deposit shape (one-bin, or linear in a
+// translation unit of its own so that the two compile in parallel)
+template <bool LIN>
+cudaError_t forward_mixed(int formalism, const void* tiles, int64_t n_tiles, const AntRec* ants, int n_ant,
+                          const MedParams& M, void* acc, const FwdShape& shape, int sm_count, int* err,
+                          cudaStream_t st) {
+  FwdArgs a{tiles, n_tiles, ants, n_ant, shape.a_tile, acc, err, FwdGrid{}, M};
+  auto go = [&](auto ops) {
+    using O = decltype(ops);
+    const int64_t ctas = forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile),
+                                      sizeof(float4) * O::kAccRows);
+    return launch_forward_ops<O>(a, ctas, st);
+  };
+  const bool ex = M.kind == C8R_EXPONENTIAL;
+  if (M.kind == C8R_EXPONENTIAL_SPHERICAL)
+    return formalism == C8R_ENDPOINT ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL_SPHERICAL, LIN>{})
+                                     : go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL_SPHERICAL, LIN>{});
+  if (formalism == C8R_ENDPOINT)
+    return ex ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, LIN>{}) : go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, LIN>{});
+  return ex ? go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, LIN>{}) : go(OpsMixed<C8R_ZHS, C8R_UNIFORM, LIN>{});
+}
+
+template <bool LIN>
+cudaError_t backward_mixed(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st) {
+  const bool ex = a.M.kind == C8R_EXPONENTIAL;
+  if (formalism == C8R_ZHS)
+    return ex ? launch_backward_ops<OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, LIN>>(a, shape, sm_count, st)
+              : launch_backward_ops<OpsMixed<C8R_ZHS, C8R_UNIFORM, LIN>>(a, shape, sm_count, st);
+  return ex ? launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, LIN>>(a, shape, sm_count, st)
+            : launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, LIN>>(a, shape, sm_count, st);
+}
 
 }  // namespace c8r
