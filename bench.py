@@ -43,16 +43,16 @@ FP32_LANES_PER_SM = 128
 # and amplitude): 56 arithmetic + 6 special-function operations
 ALG_OPS_PER_ENDPOINT_PAIR = 62
 # DRAM bytes (read + write) per pair of the Endpoint forward kernel: one ncu
-# capture of a 4e6-track x 160-antenna launch (6.4e8 pairs) read 407.6 MB and
-# wrote 5.3 MB; the traffic is the staged track tiles, so it scales with the
+# capture of a 4e6-track x 160-antenna launch (6.4e8 pairs) read 408.7 MB and
+# wrote 5.4 MB; the traffic is the staged track tiles, so it scales with the
 # pairs at a fixed antenna count.  Set to None when the kernel changes.
-DRAM_BYTES_PER_ENDPOINT_PAIR = 412.9e6 / 6.4e8
+DRAM_BYTES_PER_ENDPOINT_PAIR = 414.1e6 / 6.4e8
 # The same capture: warp instructions issued per pair and the share of issue
 # slots busy (smsp__issue_active) -- the bound the kernel actually meets, since
 # the float-float arrival time makes its instruction count ~8x the plain
 # formula's.  Set to None when the kernel changes.
-ENDPOINT_WARP_INST_PER_PAIR = 1.0905501354e10 / 6.4e8
-ENDPOINT_ISSUE_ACTIVE_NCU = 0.864
+ENDPOINT_WARP_INST_PER_PAIR = 1.0793240733e10 / 6.4e8
+ENDPOINT_ISSUE_ACTIVE_NCU = 0.858
 
 
 def parse():
@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tracks", type=int, default=None, help="override the track count (testing only)")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--cpu-sample-tracks", type=int, default=40000)
+    ap.add_argument("--cpu-sample-tracks", type=int, default=400000)
     return ap.parse_args()
 
 
@@ -237,7 +237,7 @@ def run_reference(args):
         return
     from paper_2309_03717_gb300 import synth
     w = synth.workload(1)
-    n = 10 * args.cpu_sample_tracks
+    n = args.cpu_sample_tracks
     op = OraclePool(w, n, ("endpoint", "zhs"))
     try:
         for _ in range(args.warmup):
@@ -435,7 +435,7 @@ def main():
         # the metric's second part: adjoint / forward time on the differentiable workload
         result["bwd_fwd_ratio"] = result["extras"]["bwd_fwd_ratio"]
         single = cpu_baseline(w, args.cpu_sample_tracks, ("endpoint", "zhs"))
-        result["cpu_baseline"] = cpu_baseline_all_cores(w, 10 * args.cpu_sample_tracks, ("endpoint", "zhs"))
+        result["cpu_baseline"] = cpu_baseline_all_cores(w, 5 * args.cpu_sample_tracks // 2, ("endpoint", "zhs"))
         result["cpu_baseline"]["single_core"] = {k: single[k] for k in ("value", "cores", "sample")}
     if rank == 0:
         print(json.dumps(result))
@@ -464,13 +464,32 @@ def extras(torch, c8r, synth, w):
         out[f"fp64_{f}_pairs_per_s"] = 2 * n64 * A / (e0.elapsed_time(e1) * 1e-3)
         p.close()
     del d64
+    # the linear (two-bin) deposit, mixed precision, on 4e6 tracks of the same
+    # shower (drawn on the device by the counter-based generator) and array
+    n_lin = 4_000_000
+    d_lin = c8r.c8r_generate_tracks(98, 0, n_lin, w["zenith"])
+    for f in ("endpoint", "zhs"):
+        p = c8r.RadioProcess(w["medium"], w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], f, "mixed",
+                             deposit="linear")
+        p.push(d_lin)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            p.push(d_lin)
+        e1.record()
+        torch.cuda.synchronize()
+        out[f"linear_{f}_pairs_per_s"] = 3 * n_lin * A / (e0.elapsed_time(e1) * 1e-3)
+        p.close()
+    del d_lin
     # adjoint / forward on the differentiable workload (1e6 tracks x 64 antennas,
     # 2048 bins): the Endpoint adjoint the workload names, and the ZHS one
     w4 = synth.workload(4)
     tr4 = synth.workload_tracks(w4)
     d4 = {k: torch.from_numpy(v).cuda() for k, v in tr4.items()}
-    for f, tag in (("endpoint", "diff"), ("zhs", "diff_zhs")):
-        fwd_ms, bwd_ms = adjoint_timing(torch, c8r, w4, d4, f)
+    for f, tag, dep in (("endpoint", "diff", "bin"), ("zhs", "diff_zhs", "bin"),
+                        ("endpoint", "diff_linear", "linear"), ("zhs", "diff_zhs_linear", "linear")):
+        fwd_ms, bwd_ms = adjoint_timing(torch, c8r, w4, d4, f, dep)
         out[f"{tag}_fwd_ms"] = fwd_ms
         out[f"{tag}_bwd_ms"] = bwd_ms
         out[f"{tag}_bwd_fwd_ratio"] = bwd_ms / fwd_ms
@@ -561,9 +580,10 @@ def extras(torch, c8r, synth, w):
     return out
 
 
-def adjoint_timing(torch, c8r, w4, d4, formalism):
+def adjoint_timing(torch, c8r, w4, d4, formalism, deposit="bin"):
     """(forward ms, adjoint ms) per pass; both include their ingest."""
-    p = c8r.RadioProcess(w4["medium"], w4["ant_xyz"], w4["t_start_ns"], w4["n_bins"], w4["dt_ns"], formalism, "mixed")
+    p = c8r.RadioProcess(w4["medium"], w4["ant_xyz"], w4["t_start_ns"], w4["n_bins"], w4["dt_ns"], formalism, "mixed",
+                         deposit=deposit)
     n4 = d4["x0"].numel()
     g = torch.randn((len(w4["ant_xyz"]), 3, w4["n_bins"]), device="cuda")
     tg = {f: torch.zeros(n4, dtype=torch.float32, device="cuda") for f in c8r.GRAD_FIELDS}
