@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-UNIFORM, EXPONENTIAL, EXPONENTIAL_SPHERICAL = 0, 1, 2
+UNIFORM, EXPONENTIAL, EXPONENTIAL_SPHERICAL, EXPONENTIAL_RAY, RAY_LINEAR_N2 = 0, 1, 2, 3, 4
 ENDPOINT, ZHS = 0, 1
 MODE_NORMAL, MODE_FORCE_MIDPOINT, MODE_ZHS_EDGE_SAMPLED, MODE_ABS = 0, 1, 2, 3
 DEPOSIT_BIN, DEPOSIT_LINEAR = 0, 1
@@ -39,17 +39,20 @@ class _Tracks(ctypes.Structure):
 
 class _Medium(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_double), ("N0", ctypes.c_double), ("H", ctypes.c_double),
-                ("R_E", ctypes.c_double)]
+                ("R_E", ctypes.c_double), ("dn2dz", ctypes.c_double)]
 
 
 def _medium_struct(medium):
-    """medium dict: kind "uniform" (n), "exponential" (N0, H) or
-    "exponential_spherical" (N0, H, R_E)."""
+    """medium dict: kind "uniform" (n), "exponential" (N0, H),
+    "exponential_spherical" (N0, H, R_E), "exponential_ray" (N0, H; curved rays)
+    or the pin-only "ray_linear_n2" (n at z = 0, dn2dz: n(z)^2 = n^2 + dn2dz z)."""
     kind = medium["kind"]
     k = {UNIFORM: UNIFORM, "uniform": UNIFORM, EXPONENTIAL: EXPONENTIAL, "exponential": EXPONENTIAL,
-         EXPONENTIAL_SPHERICAL: EXPONENTIAL_SPHERICAL, "exponential_spherical": EXPONENTIAL_SPHERICAL}[kind]
+         EXPONENTIAL_SPHERICAL: EXPONENTIAL_SPHERICAL, "exponential_spherical": EXPONENTIAL_SPHERICAL,
+         EXPONENTIAL_RAY: EXPONENTIAL_RAY, "exponential_ray": EXPONENTIAL_RAY,
+         RAY_LINEAR_N2: RAY_LINEAR_N2, "ray_linear_n2": RAY_LINEAR_N2}[kind]
     return _Medium(k, float(medium.get("n", 1.0)), float(medium.get("N0", 0.0)), float(medium.get("H", 1.0)),
-                   float(medium.get("R_E", 0.0)))
+                   float(medium.get("R_E", 0.0)), float(medium.get("dn2dz", 0.0)))
 
 
 class _Antennas(ctypes.Structure):
@@ -163,8 +166,8 @@ def backward(tracks, ant_xyz, t_ref, n_bins, dt, medium, grad_traces, eps_C=1e-3
     Not defined for the spherical-Earth atmosphere."""
     lib = _load()
     p = _Pack(tracks, ant_xyz, t_ref, n_bins, dt, medium)
-    if p.M.kind == EXPONENTIAL_SPHERICAL:
-        raise ValueError("the adjoint is not defined for the spherical-Earth atmosphere")
+    if p.M.kind in (EXPONENTIAL_SPHERICAL, EXPONENTIAL_RAY, RAY_LINEAR_N2):
+        raise ValueError("the adjoint is not defined for the spherical-Earth atmosphere or curved rays")
     G = np.ascontiguousarray(grad_traces, dtype=np.float64)
     if G.shape != (len(p.xyz), 3, int(n_bins)):
         raise ValueError("grad_traces shape")
@@ -180,15 +183,25 @@ def backward(tracks, ant_xyz, t_ref, n_bins, dt, medium, grad_traces, eps_C=1e-3
     return tg, ag, float(dn[0])
 
 
-def propagate(medium, x_e, x_a):
-    """(R, n_src, n_avg, delay_s) of the straight path x_e -> x_a."""
+def _propagate(medium, x_e, x_a):
     lib = _load()
     M = _medium_struct(medium)
     xe = np.ascontiguousarray(x_e, dtype=np.float64)
     xa = np.ascontiguousarray(x_a, dtype=np.float64)
-    out = np.zeros(4)
+    out = np.zeros(7)
     lib.oracle_propagate(ctypes.byref(M), _dptr(xe), _dptr(xa), _dptr(out))
-    return tuple(float(v) for v in out)
+    return out
+
+
+def propagate(medium, x_e, x_a):
+    """(R, n_src, n_avg, delay_s) of the path x_e -> x_a."""
+    return tuple(float(v) for v in _propagate(medium, x_e, x_a)[:4])
+
+
+def emission_direction(medium, x_e, x_a):
+    """Unit direction of the path at x_e (the straight direction, or the ray's
+    tangent for curved rays)."""
+    return _propagate(medium, x_e, x_a)[4:7].copy()
 
 
 def keep_mask(tracks):

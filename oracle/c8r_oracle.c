@@ -28,6 +28,20 @@
  *     h(x) = |x - centre| - R_E, n(x) = 1 + N0 exp(-h(x)/H); n_avg R is the
  *     integral of n along the path, by composite 8-point Gauss-Legendre
  *     quadrature (64 panels).
+ *  RB curved rays in the flat exponential atmosphere (the propagator's "heavier"
+ *     form, §2): the signal follows the ray from x_e to x_a in the vertical plane
+ *     through both that keeps n(z) sin(theta) = p (theta from the vertical;
+ *     Snell's law for horizontal layers), with rho = horizontal distance,
+ *     rho = integral over z between z_a and z_e of p / sqrt(n^2 - p^2), and
+ *     arrival delay (1/c) integral of n^2 / sqrt(n^2 - p^2).  The field and the
+ *     Doppler factor use the ray's direction at x_e, (sin(theta_e) rhat_h,
+ *     +/- cos(theta_e)) with sin(theta_e) = p / n(z_e); the amplitude keeps the
+ *     straight distance R (the ray's spreading differs from 1/R by the relative
+ *     bending, ~1e-4).  In n decreasing upward the direct ray is the only one for
+ *     rho below its grazing limit (some 1e2 km here); a path within 1e-3 of the
+ *     horizontal (|z_a - z_e| < 1e-3 R) keeps the straight line.  Integrals by
+ *     composite 8-point Gauss-Legendre quadrature (64 panels); p by Newton's
+ *     method safeguarded by bisection.
  *  T  binning: bin k of antenna a covers [t_ref + k dt, t_ref + (k+1) dt); a
  *     deposit with k outside [0, N) is dropped.
  *  E  Endpoint: at the start (sign +1) and the end (sign -1) of the track a
@@ -75,7 +89,9 @@
 #define OR_QE 1.602176634e-19           /* C                          */
 #define OR_PI 3.14159265358979323846
 
-enum { OR_UNIFORM = 0, OR_EXPONENTIAL = 1, OR_EXPONENTIAL_SPHERICAL = 2 };
+/* OR_RAY_LINEAR_N2 is an oracle-only profile for the ray tracer's pins:
+   n(z)^2 = n^2 + dn2dz z, whose rays have closed forms */
+enum { OR_UNIFORM = 0, OR_EXPONENTIAL = 1, OR_EXPONENTIAL_SPHERICAL = 2, OR_EXPONENTIAL_RAY = 3, OR_RAY_LINEAR_N2 = 4 };
 enum { OR_ENDPOINT = 0, OR_ZHS = 1 };
 /* oracle-only evaluation modes used by the tests: the identity tests force the
    Endpoint midpoint form or sample the ZHS potential at bin edges; MODE_ABS
@@ -98,6 +114,7 @@ typedef struct {
   double N0;       /* exponential: refractivity at z = 0                    */
   double H;        /* exponential: scale height, m                          */
   double R_E;      /* spherical: Earth radius, m                            */
+  double dn2dz;    /* OR_RAY_LINEAR_N2: d(n^2)/dz, 1/m                       */
 } or_medium;
 
 typedef struct {
@@ -179,10 +196,96 @@ static double sphere_refractive_path(const or_medium* m, const double xe[3], con
   return sum;
 }
 
+/* reading RB: the index profile the ray sees */
+static double ray_index(const or_medium* m, double z) {
+  if (m->kind == OR_RAY_LINEAR_N2) return sqrt(m->n * m->n + m->dn2dz * z);
+  return 1.0 + m->N0 * exp(-z / m->H);
+}
+
+/* integrals over z in [zlo, zhi] for ray parameter p: out[0] = int p/sqrt(n^2-p^2),
+   out[1] = its derivative in p, int n^2/(n^2-p^2)^(3/2), out[2] = int n^2/sqrt(n^2-p^2) */
+static void ray_integrals(const or_medium* m, double zlo, double zhi, double p, double out[3]) {
+  static const double xg[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+  static const double wg[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+  const int panels = 64;
+  double h = (zhi - zlo) / panels, hw = 0.5 * h;
+  out[0] = out[1] = out[2] = 0.0;
+  for (int pn = 0; pn < panels; ++pn) {
+    double mid = zlo + (pn + 0.5) * h;
+    for (int j = 0; j < 4; ++j) {
+      for (int sg = -1; sg <= 1; sg += 2) {
+        double n = ray_index(m, mid + sg * hw * xg[j]);
+        double q = n * n - p * p;
+        double rq = sqrt(q);
+        out[0] += wg[j] * hw * p / rq;
+        out[1] += wg[j] * hw * n * n / (q * rq);
+        out[2] += wg[j] * hw * n * n / rq;
+      }
+    }
+  }
+}
+
+/* reading RB: direction at x_e and arrival delay of the ray from x_e to x_a */
+static void ray_path(const or_medium* m, const double xe[3], const double xa[3], or_path* p) {
+  double dz = xa[2] - xe[2];
+  double rho = sqrt(p->d[0] * p->d[0] + p->d[1] * p->d[1]);
+  double n_e = ray_index(m, xe[2]);
+  p->n_src = n_e;
+  p->dn_src_dN0 = NAN; /* the adjoint is not defined for this medium */
+  p->dn_src_dze = NAN;
+  double zlo = fmin(xe[2], xa[2]), zhi = fmax(xe[2], xa[2]);
+  if (fabs(dz) < 1e-3 * p->R) {
+    /* near-horizontal path: the straight line; n_avg = mean of n along it */
+    double sum = 0.0;
+    static const double xg[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+    static const double wg[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+    for (int pn = 0; pn < 64; ++pn)
+      for (int j = 0; j < 4; ++j)
+        for (int sg = -1; sg <= 1; sg += 2) {
+          double f = ((pn + 0.5) + sg * 0.5 * xg[j]) / 64.0;
+          sum += wg[j] * 0.5 / 64.0 * ray_index(m, xe[2] + f * dz);
+        }
+    p->n_avg = sum;
+    return;
+  }
+  if (rho == 0.0) {
+    double I[3];
+    ray_integrals(m, zlo, zhi, 0.0, I);
+    p->n_avg = I[2] / p->R;
+    return;
+  }
+  /* Newton's method for p in (0, n_top), safeguarded by bisection */
+  double n_top = ray_index(m, zhi);
+  double lo = 0.0, hi = n_top, pp = n_top * rho / p->R, I[3];
+  for (int it = 0; it < 200; ++it) {
+    ray_integrals(m, zlo, zhi, pp, I);
+    double F = I[0] - rho;
+    if (F > 0.0) hi = pp; else lo = pp;
+    double step = F / I[1];
+    double next = pp - step;
+    if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
+    if (fabs(next - pp) <= 1e-17 * pp || hi - lo <= 1e-17 * pp) {
+      pp = next;
+      break;
+    }
+    pp = next;
+  }
+  ray_integrals(m, zlo, zhi, pp, I);
+  double s_e = pp / n_e, c_e = sqrt(1.0 - s_e * s_e);
+  p->rh[0] = s_e * p->d[0] / rho;
+  p->rh[1] = s_e * p->d[1] / rho;
+  p->rh[2] = (dz < 0.0 ? -1.0 : 1.0) * c_e;
+  p->n_avg = I[2] / p->R; /* so that n_avg R / c is the ray's delay */
+}
+
 static void propagate(const or_medium* m, const double xe[3], const double xa[3], or_path* p) {
   for (int c = 0; c < 3; ++c) p->d[c] = xa[c] - xe[c];
   p->R = sqrt(p->d[0] * p->d[0] + p->d[1] * p->d[1] + p->d[2] * p->d[2]);
   for (int c = 0; c < 3; ++c) p->rh[c] = p->d[c] / p->R;
+  if (m->kind == OR_EXPONENTIAL_RAY || m->kind == OR_RAY_LINEAR_N2) {
+    ray_path(m, xe, xa, p);
+    return;
+  }
   if (m->kind == OR_EXPONENTIAL_SPHERICAL) {
     double E = exp(-sphere_altitude(m, xe) / m->H);
     p->n_src = 1.0 + m->N0 * E;
@@ -842,8 +945,8 @@ int64_t oracle_filter(const or_tracks* T, int64_t n, uint8_t* keep) {
   return kept;
 }
 
-/* straight-path quantities for one emission point / antenna pair:
-   out = {R, n_src, n_avg, arrival delay n_avg R / c (s)} */
+/* propagator quantities for one emission point / antenna pair:
+   out = {R, n_src, n_avg, arrival delay n_avg R / c (s), direction at x_e (3)} */
 void oracle_propagate(const or_medium* m, const double* xe, const double* xa, double* out) {
   or_path p;
   propagate(m, xe, xa, &p);
@@ -851,4 +954,5 @@ void oracle_propagate(const or_medium* m, const double* xe, const double* xa, do
   out[1] = p.n_src;
   out[2] = p.n_avg;
   out[3] = p.n_avg * p.R / OR_C_LIGHT;
+  for (int c = 0; c < 3; ++c) out[4 + c] = p.rh[c];
 }
