@@ -40,7 +40,7 @@
  *     bending, ~1e-4).  In n decreasing upward the direct ray is the only one for
  *     rho below its grazing limit (some 1e2 km here); a path within 1e-3 of the
  *     horizontal (|z_a - z_e| < 1e-3 R) keeps the straight line.  Integrals by
- *     composite 8-point Gauss-Legendre quadrature (64 panels); p by Newton's
+ *     composite 8-point Gauss-Legendre quadrature (16 panels); p by Newton's
  *     method safeguarded by bisection.
  *  T  binning: bin k of antenna a covers [t_ref + k dt, t_ref + (k+1) dt); a
  *     deposit with k outside [0, N) is dropped.
@@ -207,7 +207,7 @@ static double ray_index(const or_medium* m, double z) {
 static void ray_integrals(const or_medium* m, double zlo, double zhi, double p, double out[3]) {
   static const double xg[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
   static const double wg[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
-  const int panels = 64;
+  const int panels = 16;
   double h = (zhi - zlo) / panels, hw = 0.5 * h;
   out[0] = out[1] = out[2] = 0.0;
   for (int pn = 0; pn < panels; ++pn) {
@@ -254,21 +254,29 @@ static void ray_path(const or_medium* m, const double xe[3], const double xa[3],
     p->n_avg = I[2] / p->R;
     return;
   }
-  /* Newton's method for p in (0, n_top), safeguarded by bisection */
+  /* Newton's method for p in (0, n_top), safeguarded by bisection, from the
+     straight line's sine times the mean index over the heights crossed */
   double n_top = ray_index(m, zhi);
-  double lo = 0.0, hi = n_top, pp = n_top * rho / p->R, I[3];
-  for (int it = 0; it < 200; ++it) {
+  double n_mean = 0.0;
+  {
+    static const double xg[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+    static const double wg[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+    for (int j = 0; j < 4; ++j)
+      for (int sg = -1; sg <= 1; sg += 2) n_mean += 0.5 * wg[j] * ray_index(m, 0.5 * (zlo + zhi) + sg * 0.5 * (zhi - zlo) * xg[j]);
+  }
+  double lo = 0.0, hi = n_top, pp = fmin(n_mean * rho / p->R, 0.5 * (n_top + n_mean * rho / p->R)), I[3];
+  for (int it = 0; it < 100; ++it) {
     ray_integrals(m, zlo, zhi, pp, I);
     double F = I[0] - rho;
+    if (F == 0.0) break;
     if (F > 0.0) hi = pp; else lo = pp;
     double step = F / I[1];
     double next = pp - step;
     if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
-    if (fabs(next - pp) <= 1e-17 * pp || hi - lo <= 1e-17 * pp) {
-      pp = next;
-      break;
-    }
+    /* converged once the step is within a few rounding units of p */
+    int done = fabs(next - pp) <= 4e-16 * pp;
     pp = next;
+    if (done) break;
   }
   ray_integrals(m, zlo, zhi, pp, I);
   double s_e = pp / n_e, c_e = sqrt(1.0 - s_e * s_e);
