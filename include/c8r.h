@@ -48,6 +48,7 @@ extern "C" {
 #define C8R_UNIFORM 0      /* n constant                                              */
 #define C8R_EXPONENTIAL 1  /* n(z) = 1 + N0 exp(-z / H), z = altitude in metres         */
 #define C8R_EXPONENTIAL_SPHERICAL 2 /* the same over a spherical Earth (c8r_set_medium_spherical) */
+#define C8R_EXPONENTIAL_RAY 3 /* flat exponential atmosphere with curved (refracted) rays        */
 
 /* formalisms (§1) */
 #define C8R_ENDPOINT 0
@@ -133,6 +134,15 @@ const char* c8r_last_error(const c8r_ctx* ctx);
  * refractivity N0 >= 0 at altitude 0 and scale_height_m is H > 0.
  * Along a straight path the propagator uses the path-averaged index for the
  * travel time and the index at the emission point in the Doppler factor.
+ * kind = C8R_EXPONENTIAL_RAY (not in the paper; its "heavier" propagator): the
+ * same atmosphere, with the signal following the refracted ray instead of the
+ * straight line: the ray in the vertical plane through the emission point and
+ * the antenna that keeps n(z) sin(theta) constant (Snell's law for horizontal
+ * layers).  Its travel time and its direction at the emission point (for the
+ * field vector and the Doppler factor) replace the straight line's; the
+ * amplitude keeps the straight distance R.  Paths within 1e-3 of the horizontal
+ * keep the straight line.  The adjoint, the batch runner and
+ * c8r_traces_noalloc do not take this medium.
  * May be called before or after c8r_set_antennas; traces already accumulated
  * are kept.  EINVAL on non-finite or out-of-range values. */
 int c8r_set_medium(c8r_ctx* ctx, int kind, double n_or_N0, double scale_height_m);

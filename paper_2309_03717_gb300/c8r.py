@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libc8r.so")
 
 C8R_OK = 0
 C8R_EINVAL, C8R_ENOMEM, C8R_ECUDA, C8R_ECANCELLED, C8R_ETOOBIG, C8R_ESTATE = -1, -2, -3, -4, -5, -6
-C8R_UNIFORM, C8R_EXPONENTIAL, C8R_EXPONENTIAL_SPHERICAL = 0, 1, 2
+C8R_UNIFORM, C8R_EXPONENTIAL, C8R_EXPONENTIAL_SPHERICAL, C8R_EXPONENTIAL_RAY = 0, 1, 2, 3
 C8R_ENDPOINT, C8R_ZHS = 0, 1
 C8R_FP64, C8R_MIXED = 0, 1
 C8R_F32, C8R_F64 = 0, 1
@@ -306,7 +306,8 @@ def c8r_generate_tracks(seed: int, first: int, n: int, zenith_deg: float = 0.0, 
 # ---------------------------------------------------------------------------
 # paper-level convenience objects
 # ---------------------------------------------------------------------------
-_MEDIUM = {"uniform": C8R_UNIFORM, "exponential": C8R_EXPONENTIAL, "exponential_spherical": C8R_EXPONENTIAL_SPHERICAL}
+_MEDIUM = {"uniform": C8R_UNIFORM, "exponential": C8R_EXPONENTIAL, "exponential_spherical": C8R_EXPONENTIAL_SPHERICAL,
+           "exponential_ray": C8R_EXPONENTIAL_RAY}
 _FORMALISM = {"endpoint": C8R_ENDPOINT, "coreas": C8R_ENDPOINT, "zhs": C8R_ZHS}
 _PRECISION = {"fp64": C8R_FP64, "mixed": C8R_MIXED}
 _DEPOSIT = {"bin": C8R_DEPOSIT_BIN, "linear": C8R_DEPOSIT_LINEAR}

@@ -283,7 +283,7 @@ int c8r_set_medium(c8r_ctx* c, int kind, double n_or_N0, double H) {
   if (!c) return C8R_EINVAL;
   if (kind == C8R_UNIFORM) {
     if (!std::isfinite(n_or_N0) || !(n_or_N0 > 0.0)) return fail(c, C8R_EINVAL, "uniform medium needs finite n > 0");
-  } else if (kind == C8R_EXPONENTIAL) {
+  } else if (kind == C8R_EXPONENTIAL || kind == C8R_EXPONENTIAL_RAY) {
     if (!std::isfinite(n_or_N0) || n_or_N0 < 0.0) return fail(c, C8R_EINVAL, "exponential medium needs finite N0 >= 0");
     if (!std::isfinite(H) || !(H > 0.0)) return fail(c, C8R_EINVAL, "exponential medium needs finite H > 0");
   } else if (kind == C8R_EXPONENTIAL_SPHERICAL) {
@@ -572,8 +572,8 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
   int r = ready(c);
   if (r != C8R_OK) return r;
   if ((r = check_tracks(c, t, n)) != C8R_OK) return r;
-  if (c->med_kind == C8R_EXPONENTIAL_SPHERICAL)
-    return fail(c, C8R_EINVAL, "c8r_backward does not take the spherical-Earth medium");
+  if (c->med_kind == C8R_EXPONENTIAL_SPHERICAL || c->med_kind == C8R_EXPONENTIAL_RAY)
+    return fail(c, C8R_EINVAL, "c8r_backward does not take the spherical-Earth medium or curved rays");
   if (!grad_traces || !out || !ant_grad || !dN0) return fail(c, C8R_EINVAL, "NULL gradient pointer");
   const int want = c->precision == C8R_FP64 ? C8R_F64 : C8R_F32;
   if (out->dtype != want) return fail(c, C8R_EINVAL, "out_tracks.dtype must match the context precision");

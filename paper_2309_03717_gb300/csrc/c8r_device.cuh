@@ -218,6 +218,98 @@ __device__ __forceinline__ T sphere_path_correction(T ax, T ay, T az, T dx, T dy
   return N0 * R * sum;
 }
 
+// ---------------------------------------------------------------------------
+// curved rays in the flat exponential atmosphere (C8R_EXPONENTIAL_RAY).  The ray
+// from x_e to the antenna keeps n(z) sin(theta) = p.  Written p = S m, with S =
+// rho/R and C = |dz|/R the straight line's sine and cosine from the vertical and
+// mu = m - 1 an effective refractivity, the ray's turn away from the straight
+// line at height z is
+//   sin(theta - theta_s) = S Q,  Q = (mu - nu)(2 + mu + nu) / (n^2 (C m/n + cos theta)),
+// nu = n - 1, free of the cancellation of the direct difference.  The end-point
+// condition, integral over z of (tan theta - tan theta_s) = 0, reads
+// sum_j w_j k_j (mu - nu_j) = 0 with k_j = (2 + mu + nu_j)/(n_j^2 (C m/n_j +
+// cos theta_j) cos theta_j) > 0 at the Gauss-Legendre nodes, so mu is the
+// k-weighted mean of nu: a fixed point whose contraction factor is ~1e-4 (each
+// iteration gains about four digits).  The optical path then differs from the
+// straight line's by exactly
+//   - integral over z of 2 n sin^2((theta - theta_s)/2)/C
+//   = - R S^2 sum_j w_j n_j Q_j^2 / (1 + cos(theta_j - theta_s))
+// (Fermat: from n sin(theta) = p and the shared end points), a small negative
+// quantity formed directly, which is added to the straight path's closed form.
+// Paths within 1e-3 of the horizontal, and vertical ones, keep the straight line.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct RayFix {
+  T Q;    // sin(turn at x_e) = S Q
+  T dop;  // ray's optical path minus the straight line's (m, <= 0)
+};
+// rho2 = squared horizontal distance, dz = z_a - z_e, nu_e = n(z_e) - 1
+template <typename T, int ITERS>
+__device__ __forceinline__ RayFix<T> ray_fix(T rho2, T dz, T R, T nu_e, T invH) {
+  RayFix<T> r{T(0), T(0)};
+  const T adz = fabs(dz);
+  if (!(rho2 > T(0)) || !(adz >= T(1e-3) * R)) return r;
+  const T invR = T(1) / R;
+  const T S = sqrt(rho2) * invR, C = adz * invR;
+  T nu[kSphNodes];
+  T mu = T(0);
+#pragma unroll
+  for (int j = 0; j < kSphNodes; ++j) {
+    nu[j] = nu_e * exp(-T(kSphSigma[j]) * dz * invH);  // z = z_e + sigma dz
+    mu += T(kSphWeight[j]) * nu[j];
+  }
+#pragma unroll
+  for (int it = 0; it < ITERS; ++it) {
+    const T m = T(1) + mu;
+    T num = T(0), den = T(0);
+#pragma unroll
+    for (int j = 0; j < kSphNodes; ++j) {
+      const T in = T(1) / (T(1) + nu[j]);
+      const T a = S * m * in;
+      const T c2 = T(1) - a * a;
+      if (!(c2 > T(0))) return RayFix<T>{T(0), T(0)};
+      const T c = sqrt(c2);
+      const T k = (T(2) + mu + nu[j]) * in * in / ((C * m * in + c) * c);
+      num += T(kSphWeight[j]) * k * nu[j];
+      den += T(kSphWeight[j]) * k;
+    }
+    mu = num / den;
+  }
+  const T m = T(1) + mu;
+  T sum = T(0);
+#pragma unroll
+  for (int j = 0; j < kSphNodes; ++j) {
+    const T n = T(1) + nu[j];
+    const T in = T(1) / n;
+    const T a = S * m * in;
+    const T c = sqrt(T(1) - a * a);
+    const T Q = (mu - nu[j]) * (T(2) + mu + nu[j]) * in * in / (C * m * in + c);
+    const T sd = S * Q;
+    sum += T(kSphWeight[j]) * n * Q * Q / (T(1) + sqrt(T(1) - sd * sd));
+  }
+  r.dop = -R * S * S * sum;
+  const T in = T(1) / (T(1) + nu_e);
+  const T a = S * m * in;
+  const T c = sqrt(T(1) - a * a);
+  r.Q = (mu - nu_e) * (T(2) + mu + nu_e) * in * in / (C * m * in + c);
+  return r;
+}
+
+// the turn of the direction d = x_a - x_e (length R) at x_e in the vertical plane,
+// as the change of R rhat: sin(delta) R t + (cos(delta) - 1) d, with t the unit
+// vector away from the vertical, R t = (|dz| d_h/rho, -sgn(dz) rho) and
+// sin(delta) = (rho/R) Q
+template <typename T>
+__device__ __forceinline__ void ray_turn_vector(T dx, T dy, T dz, T R, T Q, T out[3]) {
+  const T rho2 = dx * dx + dy * dy;
+  const T sd = sqrt(rho2) / R * Q;
+  const T cdm1 = -sd * sd / (T(1) + sqrt(T(1) - sd * sd));
+  const T f = cdm1 + Q * fabs(dz) / R;
+  out[0] = f * dx;
+  out[1] = f * dy;
+  out[2] = cdm1 * dz - (dz < T(0) ? T(-1) : T(1)) * Q * rho2 / R;
+}
+
 // straight emission path x_e -> antenna (propagator, §2): distance, direction,
 // source index and path-averaged index of the medium
 __device__ __forceinline__ void geo_f64(const MedParams& M, const AntRec& A, double xe, double ye, double ze,
@@ -249,6 +341,14 @@ __device__ __forceinline__ void geo_f64(const MedParams& M, const AntRec& A, dou
       g.n_src = 1.0 + M.N0 * Ee * exp(-sphere_excess(xe, ye, ze, M.R_E) * M.invH);
       g.n_avg += sphere_path_correction<double>(A.x, A.y, A.z, g.d[0], g.d[1], g.d[2], g.R, M.N0, M.invH, M.R_E) /
                  g.R;
+    } else if (M.kind == C8R_EXPONENTIAL_RAY) {
+      // the refracted ray: its direction at x_e and its optical path
+      const RayFix<double> r =
+          ray_fix<double, 4>(g.d[0] * g.d[0] + g.d[1] * g.d[1], g.d[2], g.R, M.N0 * Ee, M.invH);
+      double t[3];
+      ray_turn_vector<double>(g.d[0], g.d[1], g.d[2], g.R, r.Q, t);
+      for (int c = 0; c < 3; ++c) g.rh[c] = (g.d[c] + t[c]) * invR;
+      g.n_avg += r.dop * invR;
     }
   }
 }
@@ -325,9 +425,10 @@ __device__ __forceinline__ void geo_mixed(const AntRec& A, float pxh, float pyh,
 // tau_e = t_e/dt and the antenna's tau = t_ref/dt come in float-float.
 // KIND: the medium kind (a template argument, so each kernel carries only its own
 // medium's arithmetic; it equals M.kind)
+// `dop` (curved rays only): the ray's optical path minus the straight line's, m
 template <int KIND>
 __device__ __forceinline__ ff arrival_mixed(const MedParams& M, const AntRec& A, const GeoM& g, float tauh, float taul,
-                                            float Eeh, float Eel) {
+                                            float Eeh, float Eel, float dop = 0.0f) {
   float ts, te;
   two_sum(tauh, -A.tauh, ts, te);
   te = __fadd_rn(te, __fsub_rn(taul, A.taul));
@@ -378,6 +479,12 @@ __device__ __forceinline__ ff arrival_mixed(const MedParams& M, const AntRec& A,
           sphere_path_correction<float>(A.xh, A.yh, A.zh, g.s[0], g.s[1], g.s[2], g.R0, M.N0f, M.invH_h, M.RE_f),
           M.kc_h);
       fast_two_sum(p, cs, p2, pe2);
+      p = p2;
+      pe = __fadd_rn(pe, pe2);
+    }
+    if constexpr (KIND == C8R_EXPONENTIAL_RAY) {
+      // the ray's time saved against the straight line (<~1 bin; FP32 is enough)
+      fast_two_sum(p, __fmul_rn(dop, M.kc_h), p2, pe2);
       p = p2;
       pe = __fadd_rn(pe, pe2);
     }

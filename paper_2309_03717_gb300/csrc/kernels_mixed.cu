@@ -207,6 +207,15 @@ cudaError_t launch_bin_running_sums(int precision, const void* g, int n_ant, int
 cudaError_t launch_arrivals_mixed(int formalism, const void* tiles, int64_t n, const AntRec* ants, int n_ant,
                                   const MedParams& M, int32_t* branch, int32_t* bin, float* frac, cudaStream_t st) {
   const unsigned blocks = (unsigned)((n * (int64_t)n_ant + 255) / 256);
+  if (M.kind == C8R_EXPONENTIAL_RAY) {
+    if (formalism == C8R_ENDPOINT)
+      k_arrivals<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL_RAY>><<<blocks, 256, 0, st>>>(tiles, n, ants, n_ant, M, branch,
+                                                                                     bin, frac);
+    else
+      k_arrivals<OpsMixed<C8R_ZHS, C8R_EXPONENTIAL_RAY>><<<blocks, 256, 0, st>>>(tiles, n, ants, n_ant, M, branch, bin,
+                                                                                frac);
+    return cudaGetLastError();
+  }
   if (M.kind == C8R_EXPONENTIAL_SPHERICAL) {
     if (formalism == C8R_ENDPOINT)
       k_arrivals<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL_SPHERICAL>><<<blocks, 256, 0, st>>>(tiles, n, ants, n_ant, M,

@@ -88,18 +88,60 @@ struct EndpointEvalM {
   int branch;     // 0 two endpoints, 1 midpoint
   ff ua, ub;      // arrivals (start/end, or the two linearised midpoint arrivals)
   bool valid;
+  float dop0, dop1;  // curved rays: optical-path change of the start and end paths (m)
 };
+
+// curved rays (C8R_EXPONENTIAL_RAY): turn the direction of g (a copy used for
+// the field arithmetic; the straight geometry stays with the arrival time and
+// the amplitude's R) and return the ray's optical-path change and the change of
+// D = 1 - n beta.rhat that the turn makes
+__device__ __forceinline__ void ray_turn_mixed(GeoM& g, float nu_e, float bx, float by, float bz, const MedParams& M,
+                                               float& dop, float& dD) {
+  const float dx = g.s[0], dy = g.s[1], dz = g.s[2], R = g.R0;
+  const RayFix<float> r = ray_fix<float, 2>(dx * dx + dy * dy, dz, R, nu_e, M.invH_h);
+  float t[3];
+  ray_turn_vector<float>(dx, dy, dz, R, r.Q, t);
+  g.s[0] = __fadd_rn(g.s[0], t[0]);
+  g.s[1] = __fadd_rn(g.s[1], t[1]);
+  g.s[2] = __fadd_rn(g.s[2], t[2]);
+  dop = r.dop;
+  dD = -(1.0f + nu_e) * (bx * t[0] + by * t[1] + bz * t[2]) * g.y;
+}
+
+// D in float-float plus a small FP32 change, renormalised
+__device__ __forceinline__ ff ff_add_small(ff D, float d) {
+  float h, l;
+  two_sum(D.h, d, h, l);
+  l = __fadd_rn(l, D.l);
+  ff r;
+  r.h = __fadd_rn(h, l);
+  r.l = __fsub_rn(l, __fsub_rn(r.h, h));
+  return r;
+}
 
 // Endpoint evaluation in three steps, shared by the forward pass (which runs
 // the near-Cherenkov pairs apart from the others) and the adjoint.
 // (1) propagator and field at both endpoints; false when an emission point
 // sits on the antenna (outside the domain of the formula)
-__device__ __forceinline__ bool endpoint_fields(const TrackM& t, const AntRec& A, EndpointEvalM& e) {
+template <int KIND>
+__device__ __forceinline__ bool endpoint_fields(const TrackM& t, const AntRec& A, const MedParams& M,
+                                                EndpointEvalM& e) {
   geo_lite(A, t.x0, t.y0, t.z0, e.g0);
   geo_lite(A, t.x1, t.y1, t.z1, e.g1);
   if (e.g0.R0 == 0.0f || e.g1.R0 == 0.0f) return false;
-  field_mixed(e.g0, t.bx, t.by, t.bz, t.bmag, t.om0, __fadd_rn(1.0f, t.nm1_0), e.f0);
-  field_mixed(e.g1, t.bx, t.by, t.bz, t.bmag, t.om1, __fadd_rn(1.0f, t.nm1_1), e.f1);
+  if constexpr (KIND == C8R_EXPONENTIAL_RAY) {
+    // the field along the ray's direction at each endpoint
+    GeoM r0 = e.g0, r1 = e.g1;
+    float dD;
+    ray_turn_mixed(r0, t.nm1_0, t.bx, t.by, t.bz, M, e.dop0, dD);
+    ray_turn_mixed(r1, t.nm1_1, t.bx, t.by, t.bz, M, e.dop1, dD);
+    field_mixed(r0, t.bx, t.by, t.bz, t.bmag, t.om0, __fadd_rn(1.0f, t.nm1_0), e.f0);
+    field_mixed(r1, t.bx, t.by, t.bz, t.bmag, t.om1, __fadd_rn(1.0f, t.nm1_1), e.f1);
+  } else {
+    e.dop0 = e.dop1 = 0.0f;
+    field_mixed(e.g0, t.bx, t.by, t.bz, t.bmag, t.om0, __fadd_rn(1.0f, t.nm1_0), e.f0);
+    field_mixed(e.g1, t.bx, t.by, t.bz, t.bmag, t.om1, __fadd_rn(1.0f, t.nm1_1), e.f1);
+  }
   return true;
 }
 
@@ -115,8 +157,8 @@ __device__ __forceinline__ void endpoint_arrivals(const TrackM& t, const AntRec&
   GeoM g0 = e.g0, g1 = e.g1;
   geo_refine(g0);
   geo_refine(g1);
-  e.ua = arrival_mixed<KIND>(M, A, g0, t.tau0h, t.tau0l, t.E0h, t.E0l);
-  e.ub = arrival_mixed<KIND>(M, A, g1, t.tau1h, t.tau1l, t.E1h, t.E1l);
+  e.ua = arrival_mixed<KIND>(M, A, g0, t.tau0h, t.tau0l, t.E0h, t.E0l, e.dop0);
+  e.ub = arrival_mixed<KIND>(M, A, g1, t.tau1h, t.tau1l, t.E1h, t.E1l, e.dop1);
   e.branch = 0;
 }
 
@@ -125,12 +167,27 @@ __device__ __forceinline__ void endpoint_arrivals(const TrackM& t, const AntRec&
 template <int KIND>
 __device__ __forceinline__ bool endpoint_midpoint(const TrackM& t, const AntRec& A, const MedParams& M,
                                                   EndpointEvalM& e) {
-  midpoint_from_endpoints(e.g0, e.g1, e.f0, e.f1, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), e.gm, e.fm);
-  if (e.gm.R0 == 0.0f) return false;
+  float dopm = 0.0f, dDm = 0.0f;
+  if constexpr (KIND == C8R_EXPONENTIAL_RAY) {
+    // the midpoint's own ray (its direction is not the mean of the endpoints')
+    float mx, mxl, my, myl, mz, mzl;
+    two_sum(t.x0, t.x1, mx, mxl);
+    two_sum(t.y0, t.y1, my, myl);
+    two_sum(t.z0, t.z1, mz, mzl);
+    geo_lite(A, 0.5f * mx, 0.5f * my, 0.5f * mz, 0.5f * mxl, 0.5f * myl, 0.5f * mzl, e.gm);
+    if (e.gm.R0 == 0.0f) return false;
+    GeoM r = e.gm;
+    ray_turn_mixed(r, t.nm1_m, t.bx, t.by, t.bz, M, dopm, dDm);
+    field_mixed(r, t.bx, t.by, t.bz, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), e.fm);
+  } else {
+    midpoint_from_endpoints(e.g0, e.g1, e.f0, e.f1, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), e.gm, e.fm);
+    if (e.gm.R0 == 0.0f) return false;
+  }
   GeoM g = e.gm;
   geo_refine(g);
-  const ff u0 = arrival_mixed<KIND>(M, A, g, t.tmh, t.tml, t.Emh, t.Eml);
-  const ff Dm = doppler_ff(g, t.bx, t.by, t.bz, t.nm1_m);
+  const ff u0 = arrival_mixed<KIND>(M, A, g, t.tmh, t.tml, t.Emh, t.Eml, dopm);
+  ff Dm = doppler_ff(g, t.bx, t.by, t.bz, t.nm1_m);
+  if constexpr (KIND == C8R_EXPONENTIAL_RAY) Dm = ff_add_small(Dm, dDm);
   // the amplitude's 1/D_m, too, from the float-float D: here |D_m| can be far
   // below the FP32 form's absolute accuracy
   e.fm.D = __fadd_rn(Dm.h, Dm.l);
@@ -151,7 +208,7 @@ template <int KIND>
 __device__ __forceinline__ void endpoint_eval_mixed(const TrackM& t, const AntRec& A, const MedParams& M,
                                                     EndpointEvalM& e) {
   e.valid = false;
-  if (!endpoint_fields(t, A, e)) return;
+  if (!endpoint_fields<KIND>(t, A, M, e)) return;
   if (endpoint_near_cherenkov(e, M)) {
     if (!endpoint_midpoint<KIND>(t, A, M, e)) return;
   } else {
@@ -216,7 +273,9 @@ struct OpsMixed {
   static constexpr int kPrec = C8R_MIXED;
   static constexpr int kTileBytes = kTileBytesMixed;
   // CTAs of 128 threads per SM the register budget is set for
-  static constexpr int kMinBlocks = FORM == C8R_ENDPOINT ? 6 : 8;
+  // (curved rays carry the ray solve as well: fewer CTAs, more registers each)
+  static constexpr int kMinBlocks =
+      FORM == C8R_ENDPOINT ? (KIND == C8R_EXPONENTIAL_RAY ? 4 : 6) : (KIND == C8R_EXPONENTIAL_RAY ? 6 : 8);
   // Endpoint: the near-Cherenkov pairs (a minority, spread over most warps)
   // are set aside by the main pass and evaluated together afterwards
   static constexpr bool kDefers = FORM == C8R_ENDPOINT;
@@ -345,10 +404,18 @@ struct OpsMixed {
     geo_lite(A, t.mx, t.my, t.mz, t.mxl, t.myl, t.mzl, gm);
     if (gm.R0 == 0.0f) return;
     FieldM f;
-    field_mixed(gm, t.bx, t.by, t.bz, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), f);
+    float dop = 0.0f, dD = 0.0f;
+    if constexpr (KIND == C8R_EXPONENTIAL_RAY) {
+      GeoM r = gm;
+      ray_turn_mixed(r, t.nm1_m, t.bx, t.by, t.bz, M, dop, dD);
+      field_mixed(r, t.bx, t.by, t.bz, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), f);
+    } else {
+      field_mixed(gm, t.bx, t.by, t.bz, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), f);
+    }
     geo_refine(gm);
-    const ff um = arrival_mixed<KIND>(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml);
+    const ff um = arrival_mixed<KIND>(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml, dop);
     ff aD = doppler_ff(gm, t.bx, t.by, t.bz, t.nm1_m);
+    if constexpr (KIND == C8R_EXPONENTIAL_RAY) aD = ff_add_small(aD, dD);
     if (aD.h < 0.0f) {
       aD.h = -aD.h;
       aD.l = -aD.l;
@@ -415,7 +482,7 @@ struct OpsMixed {
   static __device__ __forceinline__ bool pair_main(const TrackM& t, const AntRec& A, const MedParams& M, Sink& out) {
     if constexpr (FORM == C8R_ENDPOINT) {
       EndpointEvalM e;
-      if (!endpoint_fields(t, A, e)) return false;
+      if (!endpoint_fields<KIND>(t, A, M, e)) return false;
       if (endpoint_near_cherenkov(e, M)) return true;
       endpoint_arrivals<KIND>(t, A, M, e);
       endpoint_deposit(t, e, M, out);
@@ -432,7 +499,7 @@ struct OpsMixed {
                                                        Sink& out) {
     if constexpr (FORM == C8R_ENDPOINT) {
       EndpointEvalM e;
-      if (!endpoint_fields(t, A, e)) return;
+      if (!endpoint_fields<KIND>(t, A, M, e)) return;
       if (!endpoint_midpoint<KIND>(t, A, M, e)) return;
       endpoint_deposit(t, e, M, out);
     }
@@ -520,7 +587,7 @@ struct OpsMixed {
       return false;
     } else {
       EndpointEvalM e;
-      if (!endpoint_fields(t, A, e)) return false;
+      if (!endpoint_fields<KIND>(t, A, M, e)) return false;
       if (endpoint_near_cherenkov(e, M)) return true;
       endpoint_arrivals<KIND>(t, A, M, e);
       adj_deposits(t, e, M, G, tg, ga, dn);
@@ -532,7 +599,7 @@ struct OpsMixed {
                                                       float& dn) {
     if constexpr (FORM == C8R_ENDPOINT) {
       EndpointEvalM e;
-      if (!endpoint_fields(t, A, e)) return;
+      if (!endpoint_fields<KIND>(t, A, M, e)) return;
       if (!endpoint_midpoint<KIND>(t, A, M, e)) return;
       adj_deposits(t, e, M, G, tg, ga, dn);
     }
@@ -899,6 +966,9 @@ cudaError_t forward_mixed(int formalism, const void* tiles, int64_t n_tiles, con
   if (M.kind == C8R_EXPONENTIAL_SPHERICAL)
     return formalism == C8R_ENDPOINT ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL_SPHERICAL, LIN>{})
                                      : go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL_SPHERICAL, LIN>{});
+  if (M.kind == C8R_EXPONENTIAL_RAY)
+    return formalism == C8R_ENDPOINT ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL_RAY, LIN>{})
+                                     : go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL_RAY, LIN>{});
   if (formalism == C8R_ENDPOINT)
     return ex ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, LIN>{}) : go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, LIN>{});
   return ex ? go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, LIN>{}) : go(OpsMixed<C8R_ZHS, C8R_UNIFORM, LIN>{});

@@ -194,3 +194,33 @@ def test_mixed_accepts_fp64_input_rounded_to_fp32():
     p.close()
     assert np.array_equal(a != 0, b != 0)
     assert rel_l2(b, a) < 1e-6
+
+
+@pytest.mark.parametrize("cfg,n,n_ant", [(2, 2003, 64), (1, 2003, 40)])
+@pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_curved_rays_match_oracle(cfg, n, n_ant, formalism, precision, tol):
+    """The refracted-ray propagator: the ray's direction at the emission point
+    and its travel time (a fixed-point ray solve plus Fermat's form of the time
+    saved on the GPU; Newton on Snell's invariant with composite quadrature in
+    the oracle), on the inclined shower, where the bending shows most."""
+    w = synth.workload(cfg, n_tracks=n, n_ant=n_ant)
+    w["medium"] = dict(synth.AIR_EXPONENTIAL, kind="exponential_ray")
+    if precision == "mixed":
+        w["dtype"] = np.float32
+    tracks = synth.workload_tracks(w)
+    if formalism == "endpoint":
+        keep = endpoint_unambiguous(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"])
+        tracks = drop_tracks(tracks, keep)
+    ref, kept = oracle_traces(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], formalism)
+    flat, _ = oracle_traces(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], synth.AIR_EXPONENTIAL,
+                            formalism)
+    if cfg == 2:  # inclined: the paths are long and slanted, the bending shows
+        assert rel_l2(flat, ref) > 2e-4
+    gpu, arr, st = run(w, tracks, formalism, precision)
+    assert st["tracks_kept"] == kept
+    err = rel_l2(gpu, ref)
+    assert err <= tol, f"relative L2 {err:.3e} > {tol:.0e}"
+    obr, ou = oracle_arrivals(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], formalism)
+    n_cmp, _ = compare_bins(arr[0], arr[1], arr[2], obr, ou, w["n_bins"])
+    assert n_cmp > 0.99 * obr.size
