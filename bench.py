@@ -536,6 +536,20 @@ def extras(torch, c8r, synth, w):
         torch.cuda.synchronize()
         out[f"inclined_spherical_{f}_pairs_per_s"] = 3 * 8_000_000 * len(w2["ant_xyz"]) / (e0.elapsed_time(e1) * 1e-3)
         p.close()
+    # the same with curved rays (a ray solve per emission point and antenna)
+    for f in ("endpoint", "zhs"):
+        p = c8r.RadioProcess(dict(w2["medium"], kind="exponential_ray"), w2["ant_xyz"], w2["t_start_ns"],
+                             w2["n_bins"], w2["dt_ns"], f, "mixed")
+        p.set_launch_shape(0, 0, w2["chunk"])
+        step2()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(3):
+            step2()
+        e1.record()
+        torch.cuda.synchronize()
+        out[f"inclined_ray_{f}_pairs_per_s"] = 3 * 8_000_000 * len(w2["ant_xyz"]) / (e0.elapsed_time(e1) * 1e-3)
+        p.close()
     del d2
     # the whole inclined shower: 1e8 tracks generated on the device by the
     # counter-based generator, 4e6 at a time, each chunk pushed as it is made
