@@ -230,7 +230,8 @@ __device__ __forceinline__ T sphere_path_correction(T ax, T ay, T az, T dx, T dy
 // sum_j w_j k_j (mu - nu_j) = 0 with k_j = (2 + mu + nu_j)/(n_j^2 (C m/n_j +
 // cos theta_j) cos theta_j) > 0 at the Gauss-Legendre nodes, so mu is the
 // k-weighted mean of nu: a fixed point whose contraction factor is ~1e-4 (each
-// iteration gains about four digits).  The optical path then differs from the
+// iteration gains about four digits; from the plain mean, one iteration leaves
+// < 1e-12 of mu for paths up to 40 km, three leave < 1e-18).  The optical path then differs from the
 // straight line's by exactly
 //   - integral over z of 2 n sin^2((theta - theta_s)/2)/C
 //   = - R S^2 sum_j w_j n_j Q_j^2 / (1 + cos(theta_j - theta_s))
@@ -243,19 +244,34 @@ struct RayFix {
   T Q;    // sin(turn at x_e) = S Q
   T dop;  // ray's optical path minus the straight line's (m, <= 0)
 };
+// The FP32 solve needs ~1e-6 relative accuracy (the turn and the saving are
+// themselves ~1e-4 and ~1e-13 s), so it uses the approximate hardware quotient,
+// square root and exponential; the FP64 solve rounds as written.
+template <typename T>
+__device__ __forceinline__ T ray_div(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float ray_div<float>(float a, float b) { return __fdividef(a, b); }
+template <typename T>
+__device__ __forceinline__ T ray_sqrt(T x) { return sqrt(x); }  // x > 0
+template <>
+__device__ __forceinline__ float ray_sqrt<float>(float x) { return x * rsqrtf(x); }
+template <typename T>
+__device__ __forceinline__ T ray_exp(T x) { return exp(x); }
+template <>
+__device__ __forceinline__ float ray_exp<float>(float x) { return __expf(x); }
 // rho2 = squared horizontal distance, dz = z_a - z_e, nu_e = n(z_e) - 1
 template <typename T, int ITERS>
 __device__ __forceinline__ RayFix<T> ray_fix(T rho2, T dz, T R, T nu_e, T invH) {
   RayFix<T> r{T(0), T(0)};
   const T adz = fabs(dz);
   if (!(rho2 > T(0)) || !(adz >= T(1e-3) * R)) return r;
-  const T invR = T(1) / R;
-  const T S = sqrt(rho2) * invR, C = adz * invR;
+  const T invR = ray_div(T(1), R);
+  const T S = ray_sqrt(rho2) * invR, C = adz * invR;
   T nu[kSphNodes];
   T mu = T(0);
 #pragma unroll
   for (int j = 0; j < kSphNodes; ++j) {
-    nu[j] = nu_e * exp(-T(kSphSigma[j]) * dz * invH);  // z = z_e + sigma dz
+    nu[j] = nu_e * ray_exp(-T(kSphSigma[j]) * dz * invH);  // z = z_e + sigma dz
     mu += T(kSphWeight[j]) * nu[j];
   }
 #pragma unroll
@@ -264,34 +280,36 @@ __device__ __forceinline__ RayFix<T> ray_fix(T rho2, T dz, T R, T nu_e, T invH) 
     T num = T(0), den = T(0);
 #pragma unroll
     for (int j = 0; j < kSphNodes; ++j) {
-      const T in = T(1) / (T(1) + nu[j]);
+      const T in = ray_div(T(1), T(1) + nu[j]);
       const T a = S * m * in;
       const T c2 = T(1) - a * a;
       if (!(c2 > T(0))) return RayFix<T>{T(0), T(0)};
-      const T c = sqrt(c2);
-      const T k = (T(2) + mu + nu[j]) * in * in / ((C * m * in + c) * c);
+      const T c = ray_sqrt(c2);
+      const T k = ray_div((T(2) + mu + nu[j]) * in * in, (C * m * in + c) * c);
       num += T(kSphWeight[j]) * k * nu[j];
       den += T(kSphWeight[j]) * k;
     }
-    mu = num / den;
+    mu = ray_div(num, den);
   }
   const T m = T(1) + mu;
   T sum = T(0);
 #pragma unroll
   for (int j = 0; j < kSphNodes; ++j) {
     const T n = T(1) + nu[j];
-    const T in = T(1) / n;
+    const T in = ray_div(T(1), n);
     const T a = S * m * in;
-    const T c = sqrt(T(1) - a * a);
-    const T Q = (mu - nu[j]) * (T(2) + mu + nu[j]) * in * in / (C * m * in + c);
+    const T c2 = T(1) - a * a;
+    if (!(c2 > T(0))) return RayFix<T>{T(0), T(0)};
+    const T Q = ray_div((mu - nu[j]) * (T(2) + mu + nu[j]) * in * in, C * m * in + ray_sqrt(c2));
     const T sd = S * Q;
-    sum += T(kSphWeight[j]) * n * Q * Q / (T(1) + sqrt(T(1) - sd * sd));
+    sum += T(kSphWeight[j]) * ray_div(n * Q * Q, T(1) + ray_sqrt(T(1) - sd * sd));
   }
   r.dop = -R * S * S * sum;
-  const T in = T(1) / (T(1) + nu_e);
+  const T in = ray_div(T(1), T(1) + nu_e);
   const T a = S * m * in;
-  const T c = sqrt(T(1) - a * a);
-  r.Q = (mu - nu_e) * (T(2) + mu + nu_e) * in * in / (C * m * in + c);
+  const T c2 = T(1) - a * a;
+  if (!(c2 > T(0))) return RayFix<T>{T(0), T(0)};
+  r.Q = ray_div((mu - nu_e) * (T(2) + mu + nu_e) * in * in, C * m * in + ray_sqrt(c2));
   return r;
 }
 
@@ -344,7 +362,7 @@ __device__ __forceinline__ void geo_f64(const MedParams& M, const AntRec& A, dou
     } else if (M.kind == C8R_EXPONENTIAL_RAY) {
       // the refracted ray: its direction at x_e and its optical path
       const RayFix<double> r =
-          ray_fix<double, 4>(g.d[0] * g.d[0] + g.d[1] * g.d[1], g.d[2], g.R, M.N0 * Ee, M.invH);
+          ray_fix<double, 3>(g.d[0] * g.d[0] + g.d[1] * g.d[1], g.d[2], g.R, M.N0 * Ee, M.invH);
       double t[3];
       ray_turn_vector<double>(g.d[0], g.d[1], g.d[2], g.R, r.Q, t);
       for (int c = 0; c < 3; ++c) g.rh[c] = (g.d[c] + t[c]) * invR;

@@ -98,7 +98,7 @@ struct EndpointEvalM {
 __device__ __forceinline__ void ray_turn_mixed(GeoM& g, float nu_e, float bx, float by, float bz, const MedParams& M,
                                                float& dop, float& dD) {
   const float dx = g.s[0], dy = g.s[1], dz = g.s[2], R = g.R0;
-  const RayFix<float> r = ray_fix<float, 2>(dx * dx + dy * dy, dz, R, nu_e, M.invH_h);
+  const RayFix<float> r = ray_fix<float, 1>(dx * dx + dy * dy, dz, R, nu_e, M.invH_h);
   float t[3];
   ray_turn_vector<float>(dx, dy, dz, R, r.Q, t);
   g.s[0] = __fadd_rn(g.s[0], t[0]);

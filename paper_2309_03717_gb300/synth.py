@@ -271,8 +271,10 @@ def make_tracks_counter(first: int, n: int, seed: int, zenith_deg: float = 0.0) 
     lo, hi = g & np.uint64(0xFFFFFFFF), g >> np.uint64(32)
     k0, k1 = np.uint64(seed & 0xFFFFFFFF), np.uint64((seed >> 32) & 0xFFFFFFFF)
 
-    def block(b):
-        return philox4x32_10(lo, hi, np.full(n, b, dtype=np.uint64), np.full(n, PHILOX_TAG, dtype=np.uint64), k0, k1)
+    def block(b, sel=slice(None)):
+        m = lo[sel].size
+        return philox4x32_10(lo[sel], hi[sel], np.full(m, b, dtype=np.uint64), np.full(m, PHILOX_TAG, dtype=np.uint64),
+                             k0, k1)
 
     w = block(0)
     r = -30.0 * np.log(_u01(w[0]))
@@ -287,14 +289,16 @@ def make_tracks_counter(first: int, n: int, seed: int, zenith_deg: float = 0.0) 
     ax = sig * (rad * np.cos(ang))
     ay = sig * (rad * np.sin(ang))
     h = np.full(n, 4000.0)
-    done = np.zeros(n, dtype=bool)
+    todo = np.arange(n)  # tracks still without a height (attempts only for them)
     for j in range(H_ATTEMPTS):
-        w = block(2 + j)
+        if todo.size == 0:
+            break
+        w = block(2 + j, todo)
         z = np.sqrt(-2.0 * np.log(_u01(w[0]))) * np.cos((2.0 * math.pi) * _u01(w[1]))
         hj = 4000.0 + 1500.0 * z
-        take = ~done & (hj >= 500.0) & (hj <= 10000.0)
-        h = np.where(take, hj, h)
-        done |= take
+        take = (hj >= 500.0) & (hj <= 10000.0)
+        h[todo[take]] = hj[take]
+        todo = todo[~take]
     ux = -(np.cos(ax) * np.sin(ay))
     uy = np.sin(ax)
     uz = -(np.cos(ax) * np.cos(ay))

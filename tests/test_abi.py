@@ -49,6 +49,14 @@ def test_host_side_validation_without_device_work():
     assert lib.c8r_set_medium(None, 0, 1.0, 1.0) == c8r.C8R_EINVAL
     assert lib.c8r_push_tracks(None, None, 0, None) == c8r.C8R_EINVAL
     assert lib.c8r_measure_peaks(0, None) == c8r.C8R_EINVAL
+    assert lib.c8r_set_deposit(None, c8r.C8R_DEPOSIT_LINEAR) == c8r.C8R_EINVAL
+    # the generator validates its arguments before any launch
+    out = c8r.c8r_tracks(c8r.C8R_F32, *([None] * 12))
+    assert lib.c8r_generate_tracks(1, 0, 10, 0.0, None, None) == c8r.C8R_EINVAL
+    assert lib.c8r_generate_tracks(1, 0, 10, 0.0, ctypes.byref(out), None) == c8r.C8R_EINVAL  # NULL arrays
+    assert lib.c8r_generate_tracks(1, -1, 10, 0.0, ctypes.byref(out), None) == c8r.C8R_EINVAL
+    assert lib.c8r_generate_tracks(1, 0, -1, 0.0, ctypes.byref(out), None) == c8r.C8R_EINVAL
+    assert lib.c8r_generate_tracks(1, 0, 10, float("nan"), ctypes.byref(out), None) == c8r.C8R_EINVAL
     lib.c8r_destroy(None)  # accepted
     assert lib.c8r_batch_create(None, 0, None, 0, 1.0, 1.0) == c8r.C8R_EINVAL
 

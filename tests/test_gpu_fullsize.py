@@ -71,3 +71,45 @@ def test_inclined_1024_antennas_streamed_in_4e6_track_chunks():
     tracks = synth.workload_tracks(w)
     sample = [0, 527, 1023]
     sampled_check(w, tracks, ("endpoint",), sample, chunk=w["chunk"])
+
+
+def test_inclined_shower_1e8_tracks_generated_on_the_device():
+    """The whole inclined shower as the benchmark runs it: 1e8 tracks drawn on
+    the device by the counter-based generator, 4e6 per chunk, each pushed as it
+    is made, against the oracle at three antennas (the oracle's tracks come from
+    the generator's host twin, chunk by chunk in spawned worker processes)."""
+    import multiprocessing as mp
+    import os
+
+    from _chunk_oracle import chunk_job
+    from paper_2309_03717_gb300 import c8r
+    w = synth.workload(2, n_tracks=1000)
+    n_full, chunk, seed, zenith = 100_000_000, w["chunk"], 2309, w["zenith"]
+    assert zenith == 60.0 and len(w["ant_xyz"]) == 1024
+    sample = [0, 527, 1023]
+    jobs = [(first, min(chunk, n_full - first), seed, zenith, np.ascontiguousarray(w["ant_xyz"][sample]),
+             w["t_start_ns"][sample], w["n_bins"], w["dt_ns"], w["medium"], "endpoint")
+            for first in range(0, n_full, chunk)]
+    with mp.get_context("spawn").Pool(max(1, min(len(jobs), os.cpu_count() or 1))) as pool:
+        results = pool.map(chunk_job, jobs)
+    drop = np.concatenate([r[0] for r in results])
+    ref = sum(r[1] for r in results)
+    okept = sum(r[2] for r in results)
+    assert drop.size < 1e-4 * n_full
+    p = c8r.RadioProcess(w["medium"], w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], "endpoint", "mixed")
+    p.set_launch_shape(0, 0, chunk)
+    drop_dev = torch.from_numpy(drop).cuda()
+    for first in range(0, n_full, chunk):
+        m = min(chunk, n_full - first)
+        tr = c8r.c8r_generate_tracks(seed, first, m, zenith)
+        sel = drop_dev[(drop_dev >= first) & (drop_dev < first + m)] - first
+        tr["q"][sel] = 0.0
+        p.push(tr)
+    got = p.traces().cpu().numpy()
+    kept = p.stats()["tracks_kept"]
+    p.close()
+    assert kept == okept
+    for j, a in enumerate(sample):
+        assert np.abs(ref[j]).max() > 0
+        err = rel_l2(got[a], ref[j])
+        assert err <= 1e-4, f"antenna {a}: relative L2 {err:.3e}"

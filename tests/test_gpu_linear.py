@@ -201,3 +201,27 @@ def test_linear_autograd_uses_the_context_deposit():
     (out * torch.randn_like(out)).sum().backward()
     assert leaves["t0"].grad.abs().max() > 0 and leaves["t1"].grad.abs().max() > 0
     p.close()
+
+
+@pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_linear_window_edges(formalism, precision, tol):
+    """A short window (48 bins) whose start sits just after the first arrivals:
+    spread deposits and ZHS intervals are cut by both window ends (cells -1, 0,
+    N and N + 1 of the linear deposit)."""
+    w = synth.workload(0, n_tracks=4001, n_ant=16)
+    if precision == "mixed":
+        w["dtype"] = np.float32
+    tracks = synth.workload_tracks(w)
+    _, u = oracle_arrivals(tracks, w["ant_xyz"], np.zeros(16), 1, w["dt_ns"], w["medium"], formalism)
+    w = dict(w)
+    w["n_bins"] = 48
+    w["t_start_ns"] = (np.median(u.reshape(-1, 16, 2)[..., 0], axis=0) - 24.3) * w["dt_ns"]
+    ref, kept = oracle_linear(tracks, w, formalism)
+    gpu, st = gpu_linear(tracks, w, formalism, precision)
+    assert st["tracks_kept"] == kept
+    _, u2 = oracle_arrivals(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], formalism)
+    assert ((u2 > -1) & (u2 < 0.5)).any() and ((u2 > 47.5) & (u2 < 49)).any()  # both edges are crossed
+    assert np.abs(ref).max() > 0
+    err = rel_l2(gpu, ref)
+    assert err <= tol, f"relative L2 {err:.3e} > {tol:.0e}"
