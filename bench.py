@@ -131,6 +131,23 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of the ranks' values (timing: the job ends with its slowest
+    rank); x itself when not distributed."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, world, seconds):
+    """Weak scaling: every rank processes its own units each step, so the job's
+    rate is all ranks' units over the slowest rank's time."""
+    return units_per_rank_step * steps * world / seconds
+
+
 def host_tracks(w, n, seed_offset):
     from paper_2309_03717_gb300 import synth
     w = dict(w)
@@ -327,12 +344,8 @@ def main():
     prof_z = c8r.c8r_profile_read(procs["zhs"].ctx)
     c8r.c8r_profile(procs["endpoint"].ctx, False)
     c8r.c8r_profile(procs["zhs"].ctx, False)
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = pairs_per_step * args.steps * world / (t_max * 1e-3)
+    t_max = max_over_ranks(ms, dist if world > 1 else None, "cuda")
+    value = whole_job_rate(pairs_per_step, args.steps, world, t_max * 1e-3)
 
     # end to end through the public API: pinned host tracks in, host traces out
     pinned = to_dev(tracks_h, torch, pinned=True)
@@ -371,11 +384,8 @@ def main():
         step_e2e()
     barrier()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = pairs_per_step * args.steps * world / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dist if world > 1 else None, "cuda")
+    e2e_value = whole_job_rate(pairs_per_step, args.steps, world, e2e_s)
     e2e_check = max(float(torch.linalg.vector_norm(host_out[f].cuda() - outs[f]) / torch.linalg.vector_norm(outs[f]))
                     for f in procs)
 
