@@ -196,7 +196,7 @@ int c8r_set_deposit(c8r_ctx* ctx, int deposit);
  * holds one track of a staged tile and evaluates it against all of them) and
  * the target number of waves per launch, a wave being every CTA the device
  * holds at once; it sets how many track ranges each antenna tile is cut into.
- * 0 keeps the automatic choice (16 antennas, 8 waves).  The result does not
+ * 0 keeps the automatic choice (32 antennas, 32 waves).  The result does not
  * depend on the shape beyond the order of floating-point additions (§5:
  * identical pulses for any number of threads).  Also sets the tracks per
  * internal chunk (0 = 2^25): longer pushes are processed chunk by chunk
