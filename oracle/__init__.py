@@ -124,7 +124,6 @@ class _Pack:
         if len(self.t_ref) != len(self.xyz):
             raise ValueError("antenna position / start time counts differ")
         self.A = _Antennas(_dptr(self.xyz), _dptr(self.t_ref), len(self.xyz), int(n_bins), float(dt))
-        kind = medium["kind"]
         self.M = _medium_struct(medium)
 
 

@@ -312,7 +312,7 @@ int enqueue(c8r_batch* b, const TrackPtrs& tp, float* out, int n_items_limit, cu
 
 int autotune(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
   char keybuf[160];
-  std::snprintf(keybuf, sizeof keybuf, "batch2:N%d:f%d:m%d:sm%d:P%lld", b->M.n_bins, b->formalism, b->M.kind,
+  std::snprintf(keybuf, sizeof keybuf, "batch3:N%d:f%d:m%d:sm%d:P%lld", b->M.n_bins, b->formalism, b->M.kind,
                 b->sm_count, (long long)(b->total_pairs >> 26));
   const std::string key = keybuf;
   TuneChoice best{};
@@ -323,7 +323,7 @@ int autotune(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
   }
   std::vector<TuneChoice> cands;
   for (int at : {8, 16, 32})
-    for (int waves : {4, 8, 16}) cands.push_back({at, tpi_for(b, at, waves)});
+    for (int waves : {4, 8, 16, 32}) cands.push_back({at, tpi_for(b, at, waves)});
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
