@@ -76,9 +76,11 @@
  *     gradients; the adjoints hold the bins of the deposits fixed.
  *
  * Parity unpinned: the value eps_C = 1e-3 itself (any value gives a consistent
- * result; the tests pin the branch's formula, not the threshold), and the choice
+ * result; the tests pin the branch's formula, not the threshold), the choice
  * of n_src over n_avg in the Doppler factor for a non-uniform medium (the two
- * coincide in a uniform medium, where the closed-form pins run).
+ * coincide in a uniform medium, where the closed-form pins run), and, for
+ * curved rays (RB), keeping the straight distance R in the amplitude (the ray's
+ * path, time and direction are pinned; the amplitude rule is a choice).
  */
 #include <math.h>
 #include <stdint.h>
