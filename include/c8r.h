@@ -356,7 +356,7 @@ int c8r_traces_noalloc(const c8r_tracks* tracks, int64_t n, int32_t n_ant, const
  * time (10 km - h)/c; the whole shower is rotated about y by zenith_deg.  Track g
  * is drawn from its own Philox4x32-10 blocks, counter (g, block, tag) and key
  * seed, so chunks of a shower can be generated independently (a stream of tracks
- * without a host-to-device copy; the paper's workload is a full shower, §6).
+ * without a host-to-device copy; the paper's workload is a full shower, §5).
  * Not in the paper.  EINVAL on NULL arrays, n < 0, first < 0, a non-finite
  * zenith or dtype other than C8R_F32; ECUDA if the launch fails. */
 int c8r_generate_tracks(uint64_t seed, int64_t first, int64_t n, double zenith_deg, const c8r_tracks_out* out,

@@ -1,6 +1,6 @@
 // generate.cu -- synthetic shower tracks generated on the device, so that a
 // large shower can be streamed through the radio step chunk by chunk without a
-// host-to-device copy of its tracks (the paper's full-shower workload, §6, is a
+// host-to-device copy of its tracks (the paper's full-shower workload, §5, is a
 // stream of tracks from the simulation).  Counter-based: track g of shower
 // `seed` is drawn from its own Philox4x32-10 blocks (Salmon, Moraes, Dror & Shaw,
 // SC'11), so any range of tracks can be generated on its own.  The
