@@ -50,19 +50,18 @@ def test_adjoint_matches_oracle_gradient(precision, tol, formalism):
     c8r, w, tracks, p = setup(precision, formalism=formalism)
     dt = torch.float64 if precision == "fp64" else torch.float32
     dev = to_device(tracks, dt)
-    p.push(dev)
-    tr = p.traces()
-    # loss = sum (trace - target)^2 against traces of 1%-perturbed endpoints and N0 x 1.02
+    # loss = sum (trace - target)^2 against traces of 1%-perturbed endpoints and
+    # N0 x 1.02; dL/dtrace is formed from the oracle's traces (an input of both
+    # adjoints) and scaled to order one, as in FP32 training: unscaled, a squared
+    # loss of ZHS potentials (~1e-19 V s/m) has gradients near 1e-38, below FP32
     tgt_tracks = synth.perturbed_target_tracks(tracks, 77)
     med2 = dict(w["medium"])
     med2["N0"] *= 1.02
-    q = c8r.RadioProcess(med2, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], formalism, precision)
-    q.push(to_device(tgt_tracks, dt))
-    diff = tr - q.traces()
-    q.close()
-    # the loss scaled to order one, as in FP32 training: unscaled, a squared loss of
-    # ZHS potentials (~1e-19 V s/m) has gradients near 1e-38, below the FP32 range
-    G = 2.0 * diff / diff.abs().max()
+    form = oracle.ZHS if formalism == "zhs" else oracle.ENDPOINT
+    args = (w["ant_xyz"], w["t_start_ns"] * 1e-9, w["n_bins"], w["dt_ns"] * 1e-9)
+    diff = (oracle.forward(oracle.tracks_from_ns(tracks), *args, w["medium"], form)[0]
+            - oracle.forward(oracle.tracks_from_ns(tgt_tracks), *args, med2, form)[0])
+    G = torch.from_numpy(2.0 * diff / np.abs(diff).max()).to(dt).cuda()
     n = tracks["x0"].size
     tg = {f: torch.zeros(n, dtype=dt, device="cuda") for f in c8r.GRAD_FIELDS}
     ag = torch.zeros((len(w["ant_xyz"]), 3), dtype=torch.float64, device="cuda")

@@ -70,7 +70,47 @@ def test_inclined_1024_antennas_streamed_in_4e6_track_chunks():
     assert len(w["ant_xyz"]) == 1024 and w["n_bins"] == 8192 and w["chunk"] == 4_000_000
     tracks = synth.workload_tracks(w)
     sample = [0, 527, 1023]
-    sampled_check(w, tracks, ("endpoint",), sample, chunk=w["chunk"])
+    sampled_check(w, tracks, ("endpoint", "zhs"), sample, chunk=w["chunk"])
+
+
+def test_differentiable_workload_adjoint_full_size():
+    """The differentiable workload at its full size (1e6 tracks x 64 antennas,
+    2048 x 0.2 ns), forward and Endpoint adjoint in the default launch shape,
+    every gradient against the oracle's."""
+    import oracle
+    from paper_2309_03717_gb300 import c8r
+    w = synth.workload(4)
+    assert w["n_tracks"] == 1_000_000 and len(w["ant_xyz"]) == 64 and w["n_bins"] == 2048
+    tracks = synth.workload_tracks(w)
+    _, u = oracle_arrivals(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], "endpoint")
+    amb = edge_ambiguous(u, 1e-6).reshape(len(tracks["x0"]), -1).any(axis=1)
+    assert amb.mean() < 1e-2
+    tracks = drop_tracks(tracks, ~amb)
+    args = (w["ant_xyz"], w["t_start_ns"] * 1e-9, w["n_bins"], w["dt_ns"] * 1e-9)
+    tgt = synth.perturbed_target_tracks(tracks, 77)
+    med2 = dict(w["medium"], N0=w["medium"]["N0"] * 1.02)
+    ref, kept = oracle.forward(oracle.tracks_from_ns(tracks), *args, w["medium"], oracle.ENDPOINT)
+    diff = ref - oracle.forward(oracle.tracks_from_ns(tgt), *args, med2, oracle.ENDPOINT)[0]
+    G = 2.0 * diff / np.abs(diff).max()
+    p = c8r.RadioProcess(w["medium"], w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], "endpoint", "mixed")
+    dev = to_device(tracks)
+    p.push(dev)
+    assert rel_l2(p.traces().cpu().numpy(), ref) <= 1e-4
+    assert p.stats()["tracks_kept"] == kept
+    n = tracks["x0"].size
+    tg = {f: torch.zeros(n, dtype=torch.float32, device="cuda") for f in c8r.GRAD_FIELDS}
+    ag = torch.zeros((len(w["ant_xyz"]), 3), dtype=torch.float64, device="cuda")
+    dn = torch.zeros(1, dtype=torch.float64, device="cuda")
+    c8r.c8r_backward(p.ctx, dev, torch.from_numpy(G.astype(np.float32)).cuda(), tg, ag, dn)
+    torch.cuda.synchronize()
+    p.close()
+    tg_ref, ag_ref, dn_ref = oracle.backward(oracle.tracks_from_ns(tracks), *args, w["medium"],
+                                             G.astype(np.float32).astype(np.float64))
+    got = np.stack([tg[f].double().cpu().numpy() for f in c8r.GRAD_FIELDS], axis=1)
+    assert rel_l2(got[:, 0:6], tg_ref[:, 0:6]) <= 1e-4
+    assert rel_l2(got[:, 8:11], tg_ref[:, 8:11]) <= 1e-4
+    assert rel_l2(ag.cpu().numpy(), ag_ref) <= 1e-4
+    assert abs(dn.item() - dn_ref) <= 1e-4 * abs(dn_ref)
 
 
 def test_inclined_shower_1e8_tracks_generated_on_the_device():
