@@ -557,11 +557,11 @@ struct FieldM {
 __device__ __forceinline__ void field_mixed(const GeoM& g, float bx, float by, float bz, float bmag, float om_nb,
                                             float n, FieldM& f) {
   const float sx = g.s[0], sy = g.s[1], sz = g.s[2];
-  const float ex = g.e[0], ey = g.e[1], ez = g.e[2];
-  // w = d x beta, with the low parts of d folded in
-  const float wx = __fadd_rn(__fmaf_rn(sy, bz, -__fmul_rn(sz, by)), __fmaf_rn(ey, bz, -__fmul_rn(ez, by)));
-  const float wy = __fadd_rn(__fmaf_rn(sz, bx, -__fmul_rn(sx, bz)), __fmaf_rn(ez, bx, -__fmul_rn(ex, bz)));
-  const float wz = __fadd_rn(__fmaf_rn(sx, by, -__fmul_rn(sy, bx)), __fmaf_rn(ex, by, -__fmul_rn(ey, bx)));
+  // w = d x beta from the FP32 part of d (the low parts, ~2^-24 |d|, change D by
+  // ~1e-7 relative even near the Cherenkov angle, below the FP32 field arithmetic)
+  const float wx = __fmaf_rn(sy, bz, -__fmul_rn(sz, by));
+  const float wy = __fmaf_rn(sz, bx, -__fmul_rn(sx, bz));
+  const float wz = __fmaf_rn(sx, by, -__fmul_rn(sy, bx));
   const float bd = __fmaf_rn(bx, sx, __fmaf_rn(by, sy, __fmul_rn(bz, sz)));
   const float R = g.R0;
   const float invR = g.y;
