@@ -579,9 +579,18 @@ __device__ __forceinline__ void deposit_adjoint(const T rh[3], const T V[3], T c
                                                 T kappa, T dd[3], T db[3], T& dnsrc) {
   const T gV = g[0] * V[0] + g[1] * V[1] + g[2] * V[2];
   const T rg = rh[0] * g[0] + rh[1] * g[1] + rh[2] * g[2];
-  const T invD = T(1) / D;
-  const T f1 = kappa * invD / (R * R);
-  const T f2 = kappa * invD / R;
+  T invD, f1, f2;
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32 path: correctly rounded reciprocals instead of three full divisions
+    invD = __frcp_rn(D);
+    const float invR = __frcp_rn(R);
+    f2 = kappa * invD * invR;
+    f1 = f2 * invR;
+  } else {
+    invD = T(1) / D;
+    f1 = kappa * invD / (R * R);
+    f2 = kappa * invD / R;
+  }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     dd[k] = f1 * (-rg * V[k] + c * (g[k] - rh[k] * rg) - gV * (n * V[k] * invD + rh[k]));

@@ -771,7 +771,7 @@ struct OpsMixed {
       tg[8 + k] += dLdb[k];
       ga[k] += dLdd[k] + (k == 2 ? dLdza : 0.0f);
     }
-    const float idt = (float)(1.0 / M.dt_ns);
+    const float idt = M.idt_h;  // 1/dt (per ns)
     tg[6] += (0.5f * dLdu - dLd_dtau) * idt;
     tg[7] += (0.5f * dLdu + dLd_dtau) * idt;
   }

@@ -222,3 +222,23 @@ def test_linear_window_edges(formalism, precision, tol):
     assert np.abs(ref).max() > 0
     err = rel_l2(gpu, ref)
     assert err <= tol, f"relative L2 {err:.3e} > {tol:.0e}"
+
+
+@pytest.mark.parametrize("kind", ["exponential_spherical", "exponential_ray"])
+@pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_linear_deposit_with_spherical_and_curved_ray_media(kind, formalism, precision, tol):
+    """The linear deposit combined with the two heavier propagators, on the
+    inclined shower."""
+    w = synth.workload(2, n_tracks=2003, n_ant=48)
+    w["medium"] = dict(synth.AIR_SPHERICAL) if kind == "exponential_spherical" else dict(synth.AIR_EXPONENTIAL,
+                                                                                         kind="exponential_ray")
+    if precision == "mixed":
+        w["dtype"] = np.float32
+    tracks = synth.workload_tracks(w)
+    ref, kept = oracle_linear(tracks, w, formalism)
+    gpu, st = gpu_linear(tracks, w, formalism, precision)
+    assert st["tracks_kept"] == kept
+    assert np.abs(ref).max() > 0
+    err = rel_l2(gpu, ref)
+    assert err <= tol, f"relative L2 {err:.3e} > {tol:.0e}"
