@@ -184,6 +184,23 @@ struct GeoD {
 // N0 exp(-z/H) (exp(-delta/H) - 1), by 8-point Gauss-Legendre quadrature (nodes
 // sigma_j on [0, 1] from the emission point, weights w_j summing to 1).
 // ---------------------------------------------------------------------------
+// Quotient, square root and exponential for the small corrections (the
+// sphere's curvature part of the optical path, the curved ray's turn and time
+// saved): their FP32 forms need ~1e-6 relative accuracy, so they use the
+// approximate hardware operations; the FP64 forms round as written.
+template <typename T>
+__device__ __forceinline__ T approx_div(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float approx_div<float>(float a, float b) { return __fdividef(a, b); }
+template <typename T>
+__device__ __forceinline__ T approx_sqrt(T x) { return sqrt(x); }  // x > 0
+template <>
+__device__ __forceinline__ float approx_sqrt<float>(float x) { return x * rsqrtf(x); }
+template <typename T>
+__device__ __forceinline__ T approx_exp(T x) { return exp(x); }
+template <>
+__device__ __forceinline__ float approx_exp<float>(float x) { return __expf(x); }
+
 constexpr int kSphNodes = 8;
 __device__ __constant__ const double kSphSigma[kSphNodes] = {
     0.019855071751231856, 0.10166676129318664, 0.2372337950418355, 0.4082826787521751,
@@ -196,13 +213,13 @@ template <typename T>
 __device__ __forceinline__ T sphere_excess(T x, T y, T z, T R_E) {
   const T rho2 = x * x + y * y;
   const T zr = z + R_E;
-  return rho2 / (sqrt(rho2 + zr * zr) + zr);
+  return approx_div(rho2, approx_sqrt(rho2 + zr * zr) + zr);
 }
 // exp(-x) - 1 for x >= 0 without cancellation
 template <typename T>
 __device__ __forceinline__ T exp_m1_neg(T x) {
   if (x < T(0.1)) return -x * (T(1) + x * (T(-0.5) + x * (T(1) / T(6) + x * (T(-1) / T(24) + x * (T(1) / T(120))))));
-  return exp(-x) - T(1);
+  return approx_exp(-x) - T(1);
 }
 // the curvature part of the optical path from x_e to the antenna a, d = a - x_e
 template <typename T>
@@ -213,7 +230,7 @@ __device__ __forceinline__ T sphere_path_correction(T ax, T ay, T az, T dx, T dy
     const T f = T(1) - T(kSphSigma[j]);  // the node at x_e + sigma d = a - (1 - sigma) d
     const T x = ax - f * dx, y = ay - f * dy, z = az - f * dz;
     const T ex = sphere_excess(x, y, z, R_E);
-    sum += T(kSphWeight[j]) * exp(-z * invH) * exp_m1_neg(ex * invH);
+    sum += T(kSphWeight[j]) * approx_exp(-z * invH) * exp_m1_neg(ex * invH);
   }
   return N0 * R * sum;
 }
@@ -244,34 +261,18 @@ struct RayFix {
   T Q;    // sin(turn at x_e) = S Q
   T dop;  // ray's optical path minus the straight line's (m, <= 0)
 };
-// The FP32 solve needs ~1e-6 relative accuracy (the turn and the saving are
-// themselves ~1e-4 and ~1e-13 s), so it uses the approximate hardware quotient,
-// square root and exponential; the FP64 solve rounds as written.
-template <typename T>
-__device__ __forceinline__ T ray_div(T a, T b) { return a / b; }
-template <>
-__device__ __forceinline__ float ray_div<float>(float a, float b) { return __fdividef(a, b); }
-template <typename T>
-__device__ __forceinline__ T ray_sqrt(T x) { return sqrt(x); }  // x > 0
-template <>
-__device__ __forceinline__ float ray_sqrt<float>(float x) { return x * rsqrtf(x); }
-template <typename T>
-__device__ __forceinline__ T ray_exp(T x) { return exp(x); }
-template <>
-__device__ __forceinline__ float ray_exp<float>(float x) { return __expf(x); }
-// rho2 = squared horizontal distance, dz = z_a - z_e, nu_e = n(z_e) - 1
 template <typename T, int ITERS>
 __device__ __forceinline__ RayFix<T> ray_fix(T rho2, T dz, T R, T nu_e, T invH) {
   RayFix<T> r{T(0), T(0)};
   const T adz = fabs(dz);
   if (!(rho2 > T(0)) || !(adz >= T(1e-3) * R)) return r;
-  const T invR = ray_div(T(1), R);
-  const T S = ray_sqrt(rho2) * invR, C = adz * invR;
+  const T invR = approx_div(T(1), R);
+  const T S = approx_sqrt(rho2) * invR, C = adz * invR;
   T nu[kSphNodes];
   T mu = T(0);
 #pragma unroll
   for (int j = 0; j < kSphNodes; ++j) {
-    nu[j] = nu_e * ray_exp(-T(kSphSigma[j]) * dz * invH);  // z = z_e + sigma dz
+    nu[j] = nu_e * approx_exp(-T(kSphSigma[j]) * dz * invH);  // z = z_e + sigma dz
     mu += T(kSphWeight[j]) * nu[j];
   }
 #pragma unroll
@@ -280,36 +281,36 @@ __device__ __forceinline__ RayFix<T> ray_fix(T rho2, T dz, T R, T nu_e, T invH) 
     T num = T(0), den = T(0);
 #pragma unroll
     for (int j = 0; j < kSphNodes; ++j) {
-      const T in = ray_div(T(1), T(1) + nu[j]);
+      const T in = approx_div(T(1), T(1) + nu[j]);
       const T a = S * m * in;
       const T c2 = T(1) - a * a;
       if (!(c2 > T(0))) return RayFix<T>{T(0), T(0)};
-      const T c = ray_sqrt(c2);
-      const T k = ray_div((T(2) + mu + nu[j]) * in * in, (C * m * in + c) * c);
+      const T c = approx_sqrt(c2);
+      const T k = approx_div((T(2) + mu + nu[j]) * in * in, (C * m * in + c) * c);
       num += T(kSphWeight[j]) * k * nu[j];
       den += T(kSphWeight[j]) * k;
     }
-    mu = ray_div(num, den);
+    mu = approx_div(num, den);
   }
   const T m = T(1) + mu;
   T sum = T(0);
 #pragma unroll
   for (int j = 0; j < kSphNodes; ++j) {
     const T n = T(1) + nu[j];
-    const T in = ray_div(T(1), n);
+    const T in = approx_div(T(1), n);
     const T a = S * m * in;
     const T c2 = T(1) - a * a;
     if (!(c2 > T(0))) return RayFix<T>{T(0), T(0)};
-    const T Q = ray_div((mu - nu[j]) * (T(2) + mu + nu[j]) * in * in, C * m * in + ray_sqrt(c2));
+    const T Q = approx_div((mu - nu[j]) * (T(2) + mu + nu[j]) * in * in, C * m * in + approx_sqrt(c2));
     const T sd = S * Q;
-    sum += T(kSphWeight[j]) * ray_div(n * Q * Q, T(1) + ray_sqrt(T(1) - sd * sd));
+    sum += T(kSphWeight[j]) * approx_div(n * Q * Q, T(1) + approx_sqrt(T(1) - sd * sd));
   }
   r.dop = -R * S * S * sum;
-  const T in = ray_div(T(1), T(1) + nu_e);
+  const T in = approx_div(T(1), T(1) + nu_e);
   const T a = S * m * in;
   const T c2 = T(1) - a * a;
   if (!(c2 > T(0))) return RayFix<T>{T(0), T(0)};
-  r.Q = ray_div((mu - nu_e) * (T(2) + mu + nu_e) * in * in, C * m * in + ray_sqrt(c2));
+  r.Q = approx_div((mu - nu_e) * (T(2) + mu + nu_e) * in * in, C * m * in + approx_sqrt(c2));
   return r;
 }
 
@@ -320,12 +321,13 @@ __device__ __forceinline__ RayFix<T> ray_fix(T rho2, T dz, T R, T nu_e, T invH) 
 template <typename T>
 __device__ __forceinline__ void ray_turn_vector(T dx, T dy, T dz, T R, T Q, T out[3]) {
   const T rho2 = dx * dx + dy * dy;
-  const T sd = sqrt(rho2) / R * Q;
-  const T cdm1 = -sd * sd / (T(1) + sqrt(T(1) - sd * sd));
-  const T f = cdm1 + Q * fabs(dz) / R;
+  const T invR = approx_div(T(1), R);
+  const T sd = approx_sqrt(rho2) * invR * Q;
+  const T cdm1 = approx_div(-sd * sd, T(1) + approx_sqrt(T(1) - sd * sd));
+  const T f = cdm1 + Q * fabs(dz) * invR;
   out[0] = f * dx;
   out[1] = f * dy;
-  out[2] = cdm1 * dz - (dz < T(0) ? T(-1) : T(1)) * Q * rho2 / R;
+  out[2] = cdm1 * dz - (dz < T(0) ? T(-1) : T(1)) * Q * rho2 * invR;
 }
 
 // straight emission path x_e -> antenna (propagator, §2): distance, direction,

@@ -411,6 +411,12 @@ __device__ __forceinline__ RefrGrad<T> refraction_grad(int kind, T R, T x, T E, 
   if (fabs(x) < T(1e-3)) {
     rho = T(1) + x * (T(-0.5) + x * (T(1) / T(6) + x * (T(-1) / T(24))));
     drho = T(-0.5) + x * (T(1) / T(3) + x * (T(-1) / T(8) + x * (T(1) / T(30))));
+  } else if constexpr (std::is_same<T, float>::value) {
+    // FP32 gradients: the approximate exponential and quotient (a few ulp)
+    const float em = __expf(-x);
+    const float ix = __frcp_rn(x);
+    rho = (1.0f - em) * ix;
+    drho = (em - rho) * ix;
   } else {
     const T em = exp(-x);
     rho = (T(1) - em) / x;
