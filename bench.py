@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tracks", type=int, default=None, help="override the track count (testing only)")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--fp64-only", type=int, default=0, metavar="TRACKS",
+                    help="time only the FP64 path on TRACKS tracks of the shower (a small case for profiling)")
     ap.add_argument("--cpu-sample-tracks", type=int, default=400000)
     return ap.parse_args()
 
@@ -300,6 +302,10 @@ def main():
     from paper_2309_03717_gb300 import build, c8r, synth
     if rank == 0:
         build.build()
+    if args.fp64_only:
+        c8r.load()
+        print(json.dumps({"fp64_only": fp64_timing(torch, c8r, synth.workload(1), args.fp64_only)}))
+        return
     if world > 1:
         dist.barrier()
     c8r.load()
@@ -455,10 +461,9 @@ def main():
         dist.destroy_process_group()
 
 
-def extras(torch, c8r, synth, w):
+def fp64_timing(torch, c8r, w, n64):
+    """The FP64 path on n64 tracks of the shower, both formalisms: pairs/s."""
     out = {}
-    # FP64 path on a sample of the same workload
-    n64 = 1_000_000
     tr = host_tracks(w, n64, 99)
     d64 = {k: torch.from_numpy(v.astype(np.float64)).cuda() for k, v in tr.items()}
     A = len(w["ant_xyz"])
@@ -474,7 +479,12 @@ def extras(torch, c8r, synth, w):
         torch.cuda.synchronize()
         out[f"fp64_{f}_pairs_per_s"] = 2 * n64 * A / (e0.elapsed_time(e1) * 1e-3)
         p.close()
-    del d64
+    return out
+
+
+def extras(torch, c8r, synth, w):
+    # FP64 path on a sample of the same workload
+    out = fp64_timing(torch, c8r, w, 1_000_000)
     # the linear (two-bin) deposit, mixed precision, on 4e6 tracks of the same
     # shower (drawn on the device by the counter-based generator) and array
     n_lin = 4_000_000
