@@ -483,6 +483,7 @@ def fp64_timing(torch, c8r, w, n64):
 
 
 def extras(torch, c8r, synth, w):
+    A = len(w["ant_xyz"])
     # FP64 path on a sample of the same workload
     out = fp64_timing(torch, c8r, w, 1_000_000)
     # the linear (two-bin) deposit, mixed precision, on 4e6 tracks of the same
