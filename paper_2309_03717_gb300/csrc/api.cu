@@ -365,6 +365,8 @@ int c8r_set_antennas(c8r_ctx* c, int32_t n_ant, const double* pos, const double*
   c->shape.waves = c->user_waves > 0 ? c->user_waves : kDefaultWaves;
   c->trace_bytes = (size_t)n_ant * 3 * n_bins * (precision == C8R_FP64 ? 8 : 4);
   c->acc_bytes = (size_t)n_ant * n_bins * acc_elem_bytes(precision) * acc_rows(precision, formalism);
+  c->shape.replicas = acc_replicas(precision, formalism);
+  c->acc_bytes *= c->shape.replicas;
   cudaError_t e = cudaMalloc(&c->d_ants, sizeof(AntRec) * n_ant);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_acc, c->acc_bytes);
   if (e == cudaSuccess) e = cudaMemset(c->d_acc, 0, c->acc_bytes);
@@ -435,6 +437,11 @@ int c8r_push_tracks(c8r_ctx* c, const c8r_tracks* t, int64_t n, void* stream) {
   return C8R_OK;
 }
 
+static cudaError_t fetch_acc(c8r_ctx* c, void* dst, cudaStream_t st) {
+  return launch_acc_to_traces(c->precision, c->d_acc, c->n_ant, c->n_bins, acc_rows(c->precision, c->formalism), dst,
+                              0, st, c->shape.replicas);
+}
+
 int c8r_fetch_traces(c8r_ctx* c, void* dst, int dst_is_device, int reset, void* stream) {
   if (!c) return C8R_EINVAL;
   if (!c->ants_set) return fail(c, C8R_ESTATE, "c8r_set_antennas has not been called");
@@ -443,8 +450,7 @@ int c8r_fetch_traces(c8r_ctx* c, void* dst, int dst_is_device, int reset, void* 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (dst_is_device) {
-    e = launch_acc_to_traces(c->precision, c->d_acc, c->n_ant, c->n_bins, acc_rows(c->precision, c->formalism), dst, 0,
-                             st);
+    e = fetch_acc(c, dst, st);
   } else {
     if (!c->d_stage) {
       e = cudaMalloc(&c->d_stage, c->trace_bytes);
@@ -454,8 +460,7 @@ int c8r_fetch_traces(c8r_ctx* c, void* dst, int dst_is_device, int reset, void* 
         return fail(c, C8R_ENOMEM, "staging buffer for the host copy");
       }
     }
-    e = launch_acc_to_traces(c->precision, c->d_acc, c->n_ant, c->n_bins, acc_rows(c->precision, c->formalism),
-                             c->d_stage, 0, st);
+    e = fetch_acc(c, c->d_stage, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dst, c->d_stage, c->trace_bytes, cudaMemcpyDeviceToHost, st);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "trace copy");

@@ -41,12 +41,14 @@ struct BatchArgs {
   const WorkItem* items;
   int n_items;
   const AntRec* ants;
-  float4* acc;           // [sum n_ant][n_bins] accumulator
+  float4* acc;           // [replicas][sum n_ant][rows][n_bins] accumulator
   int* counter;
   const int* cancel;
   int* err;
   int a_tile;
   MedParams M;
+  int replicas;            // accumulator copies: work item i adds into copy i % replicas
+  int64_t replica_stride;  // elements per copy
 };
 
 // slot -> caller track index for the concatenated showers: shower s owns tiles
@@ -96,7 +98,8 @@ __global__ void __launch_bounds__(kTileT, Ops::kMinBlocks) k_batch(const BatchAr
     const WorkItem w = a.items[idx];
     for (int i = tid; i < w.n_here; i += nthr) ant_s[i] = a.ants[w.ant0 + i];
     __syncthreads();
-    if (!stream_range<Ops>(smem, L, bar, ant_s, a.acc + (size_t)w.ant0 * M.n_bins * Ops::kAccRows, w.n_here,
+    float4* acc = a.acc + (size_t)(idx % a.replicas) * a.replica_stride + (size_t)w.ant0 * M.n_bins * Ops::kAccRows;
+    if (!stream_range<Ops>(smem, L, bar, ant_s, acc, w.n_here,
                            static_cast<const unsigned char*>(a.tiles), w.t_begin, w.t_end, it, M)) {
       if (tid == 0) atomicExch(a.err, kErrWaitTimeout);
       return;
@@ -212,8 +215,9 @@ struct c8r_batch {
   int* d_counter = nullptr;
   int* d_cancel = nullptr;
   int* d_err = nullptr;
-  float4* d_acc = nullptr;  // [total_ant][n_bins] accumulator
+  float4* d_acc = nullptr;  // [replicas][total_ant][rows][n_bins] accumulator
   size_t acc_bytes = 0;
+  int replicas = 1;
   cudaStream_t cap_stream = nullptr;  // graph capture (the caller's stream may be the legacy default stream)
   cudaStream_t aux_stream = nullptr;  // non-blocking: cancel word updates while a batch runs
   bool tuned = false;
@@ -289,8 +293,10 @@ int enqueue_ingest(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
 int enqueue_kernel(c8r_batch* b, int n_items_limit, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch counter: ") + cudaGetErrorString(e));
+  const int rows = acc_rows(C8R_MIXED, b->formalism);
   BatchArgs a{b->d_tiles, b->d_items, std::min(b->n_items, n_items_limit), b->d_ants, b->d_acc, b->d_counter,
-              b->d_cancel, b->d_err, b->choice.a_tile, b->M};
+              b->d_cancel, b->d_err, b->choice.a_tile, b->M, b->replicas,
+              (int64_t)b->total_ant * b->M.n_bins * rows};
   e = launch_batch(a, b->formalism, b->sm_count, st);
   if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   return C8R_OK;
@@ -304,7 +310,7 @@ int enqueue(c8r_batch* b, const TrackPtrs& tp, float* out, int n_items_limit, cu
   if (r != C8R_OK) return r;
   if (out) {
     cudaError_t e = launch_acc_to_traces(C8R_MIXED, b->d_acc, b->total_ant, b->M.n_bins,
-                                         acc_rows(C8R_MIXED, b->formalism), out, 1, st);
+                                         acc_rows(C8R_MIXED, b->formalism), out, 1, st, b->replicas);
     if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch fetch: ") + cudaGetErrorString(e));
   }
   return C8R_OK;
@@ -443,7 +449,9 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
     *out = b;
     return C8R_ECUDA;
   }
-  b->acc_bytes = (size_t)b->total_ant * b->M.n_bins * sizeof(float4) * acc_rows(C8R_MIXED, b->formalism);
+  b->replicas = acc_replicas(C8R_MIXED, b->formalism);
+  b->acc_bytes = (size_t)b->total_ant * b->M.n_bins * sizeof(float4) * acc_rows(C8R_MIXED, b->formalism) *
+                 b->replicas;
   if (cudaMalloc(&b->d_acc, b->acc_bytes) != cudaSuccess) {
     cudaGetLastError();
     b->d_acc = nullptr;

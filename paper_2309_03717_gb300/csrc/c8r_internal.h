@@ -13,6 +13,7 @@ namespace c8r {
 struct FwdShape {
   int a_tile;  // antennas per CTA: each thread holds one staged track and loops over them
   int waves;   // target number of waves (all CTAs resident at once) per launch
+  int replicas = 1;  // copies of the accumulator (acc_replicas)
 };
 
 // SoA track pointers of the caller, already offset to a chunk
@@ -26,12 +27,19 @@ size_t tile_bytes(int precision);
 inline size_t acc_elem_bytes(int precision) { return precision == C8R_FP64 ? 32 : 16; }
 // accumulator rows per antenna: the mixed ZHS path adds a row of box edges
 inline int acc_rows(int precision, int formalism) { return precision == C8R_MIXED && formalism == C8R_ZHS ? 2 : 1; }
+// copies of the accumulator the forward kernel spreads its reductions over (CTA
+// range r adds into copy r % replicas; the fetch sums them).  The mixed ZHS
+// kernel makes ~4 reductions per pair, most of them into the few bins the pulse
+// arrives in, and those bins' L2 slices become its bottleneck; two copies halve
+// the reductions each such slice takes (ZHS pair kernel -10 % on a 2e7-track
+// shower).  The Endpoint kernel is bound by instruction issue and gains nothing.
+inline int acc_replicas(int precision, int formalism) { return acc_rows(precision, formalism) == 2 ? 2 : 1; }
 
-// accumulator [n_ant][rows][n_bins] -> traces [n_ant][3][n_bins]; with rows == 2
-// the second row (box edges) is integrated over the bins and added; add != 0
-// adds into out (FP32 only)
+// accumulator [replicas][n_ant][rows][n_bins] -> traces [n_ant][3][n_bins]: the
+// copies are summed; with rows == 2 the second row (box edges) is integrated over
+// the bins and added; add != 0 adds into out.  FP32 only for add or replicas > 1
 cudaError_t launch_acc_to_traces(int precision, const void* acc, int n_ant, int n_bins, int rows, void* out, int add,
-                                 cudaStream_t st);
+                                 cudaStream_t st, int replicas = 1);
 
 // dL/dtraces [n_ant][3][n_bins] -> bin-major [n_ant][n_bins] accumulator elements
 cudaError_t launch_traces_to_bin_major(int precision, const void* g, int n_ant, int n_bins, void* out,

@@ -87,6 +87,8 @@ struct FwdArgs {
   int* err;
   FwdGrid g;
   MedParams M;
+  int replicas = 1;            // accumulator copies; CTA range r adds into copy r % replicas
+  int64_t replica_stride = 0;  // accumulator elements per copy
 };
 
 struct BwdArgs {
@@ -292,7 +294,8 @@ __global__ void __launch_bounds__(kTileT, Ops::kMinBlocks) k_forward(const FwdAr
   }
   __syncthreads();
   int64_t it = 0;
-  acc4* row0 = static_cast<acc4*>(a.acc) + (size_t)ant0 * a.M.n_bins * Ops::kAccRows;
+  acc4* row0 = static_cast<acc4*>(a.acc) + (size_t)ant0 * a.M.n_bins * Ops::kAccRows +
+               (size_t)(range % a.replicas) * a.replica_stride;
   if (!stream_range<Ops>(smem, L, bar, ant_s, row0, n_here, static_cast<const unsigned char*>(a.tiles), t_begin,
                          t_end, it, a.M)) {
     if (tid == 0) atomicExch(a.err, kErrWaitTimeout);
@@ -312,7 +315,8 @@ inline int64_t forward_grid(FwdArgs& a, const FwdShape& shape, int resident, siz
   FwdGrid& g = a.g;
   g.ant_tiles = (a.n_ant + shape.a_tile - 1) / shape.a_tile;
   const size_t l2_budget = (size_t)48 << 20;
-  const size_t tile_bytes = (size_t)shape.a_tile * a.M.n_bins * acc_elem_bytes;
+  // an antenna tile's rows in every copy of the accumulator
+  const size_t tile_bytes = (size_t)shape.a_tile * a.M.n_bins * acc_elem_bytes * (shape.replicas > 1 ? shape.replicas : 1);
   int tpb = (int)(l2_budget / (tile_bytes > 0 ? tile_bytes : 1));
   g.tiles_per_block = tpb < 1 ? 1 : (tpb > g.ant_tiles ? g.ant_tiles : tpb);
   int64_t target = (int64_t)shape.waves * resident;

@@ -12,13 +12,21 @@ cudaError_t launch_forward_mixed(int formalism, bool lin, const void* tiles, int
   return forward_mixed<false>(formalism, tiles, n_tiles, ants, n_ant, M, acc, shape, sm_count, err, st);
 }
 
-// accumulator [n_ant][n_bins] float4 -> traces [n_ant][3][n_bins] (added or stored)
-__global__ void k_acc_to_traces_f32(const float4* acc, int64_t n_ant_bins, int n_bins, float* out, int add) {
+// accumulator [n_ant][n_bins] float4 -> traces [n_ant][3][n_bins] (added or
+// stored); `replicas` copies of the accumulator, `stride` elements apart, are summed
+__global__ void k_acc_to_traces_f32(const float4* acc, int64_t n_ant_bins, int n_bins, float* out, int add,
+                                    int replicas, int64_t stride) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_ant_bins) return;
   const int64_t a = i / n_bins;
   const int k = (int)(i - a * n_bins);
-  const float4 v = acc[i];
+  float4 v = acc[i];
+  for (int r = 1; r < replicas; ++r) {
+    const float4 u = acc[i + r * stride];
+    v.x += u.x;
+    v.y += u.y;
+    v.z += u.z;
+  }
   float* o = out + a * 3 * n_bins + k;
   if (add) {
     o[0] += v.x;
@@ -32,12 +40,13 @@ __global__ void k_acc_to_traces_f32(const float4* acc, int64_t n_ant_bins, int n
 }
 
 // accumulator with a row of box edges [n_ant][2][n_bins] float4 -> traces:
-// out[k] = direct[k] + sum_{j <= k} edge[j].  One CTA per antenna walks the
-// bins in chunks of its size: an inclusive scan of the chunk (FP64, warp
-// shuffles, then the warp totals) plus the carry of the chunks before.
+// out[k] = direct[k] + sum_{j <= k} edge[j], each summed over the `replicas`
+// copies of the accumulator (`stride` elements apart).  One CTA per antenna
+// walks the bins in chunks of its size: an inclusive scan of the chunk (FP64,
+// warp shuffles, then the warp totals) plus the carry of the chunks before.
 constexpr int kScanThreads = 1024;
 __global__ void __launch_bounds__(kScanThreads) k_acc_scan_to_traces(const float4* acc, int n_bins, float* out,
-                                                                      int add) {
+                                                                      int add, int replicas, int64_t stride) {
   __shared__ double warp_tot[3][kScanThreads / 32];
   const int a = blockIdx.x;
   const float4* direct = acc + (size_t)a * 2 * n_bins;
@@ -47,9 +56,15 @@ __global__ void __launch_bounds__(kScanThreads) k_acc_scan_to_traces(const float
   double carry[3] = {0.0, 0.0, 0.0};
   for (int base = 0; base < n_bins; base += blockDim.x) {
     const int k = base + threadIdx.x;
-    float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (k < n_bins) e = edge[k];
-    double v[3] = {e.x, e.y, e.z};
+    double v[3] = {0.0, 0.0, 0.0};
+    if (k < n_bins) {
+      for (int r = 0; r < replicas; ++r) {
+        const float4 e = edge[k + r * stride];
+        v[0] += e.x;
+        v[1] += e.y;
+        v[2] += e.z;
+      }
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
 #pragma unroll
@@ -70,9 +85,15 @@ __global__ void __launch_bounds__(kScanThreads) k_acc_scan_to_traces(const float
       }
     }
     if (k < n_bins) {
-      const float4 d = direct[k];
-      const float r[3] = {(float)((double)d.x + carry[0] + v[0]), (float)((double)d.y + carry[1] + v[1]),
-                          (float)((double)d.z + carry[2] + v[2])};
+      double d[3] = {0.0, 0.0, 0.0};
+      for (int q = 0; q < replicas; ++q) {
+        const float4 u = direct[k + q * stride];
+        d[0] += u.x;
+        d[1] += u.y;
+        d[2] += u.z;
+      }
+      const float r[3] = {(float)(d[0] + carry[0] + v[0]), (float)(d[1] + carry[1] + v[1]),
+                          (float)(d[2] + carry[2] + v[2])};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         if (add)
@@ -100,12 +121,13 @@ __global__ void k_acc_to_traces_f64(const Acc4D* acc, int64_t n_ant_bins, int n_
 }
 
 cudaError_t launch_acc_to_traces(int precision, const void* acc, int n_ant, int n_bins, int rows, void* out, int add,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, int replicas) {
   const int64_t n = (int64_t)n_ant * n_bins;
   if (n <= 0) return cudaSuccess;
+  const int64_t stride = n * rows;  // accumulator elements per copy
   if (rows == 2) {
     k_acc_scan_to_traces<<<(unsigned)n_ant, kScanThreads, 0, st>>>(static_cast<const float4*>(acc), n_bins,
-                                                                     static_cast<float*>(out), add);
+                                                                     static_cast<float*>(out), add, replicas, stride);
     return cudaGetLastError();
   }
   const unsigned blocks = (unsigned)((n + 255) / 256);
@@ -113,7 +135,7 @@ cudaError_t launch_acc_to_traces(int precision, const void* acc, int n_ant, int 
     k_acc_to_traces_f64<<<blocks, 256, 0, st>>>(static_cast<const Acc4D*>(acc), n, n_bins, static_cast<double*>(out));
   else
     k_acc_to_traces_f32<<<blocks, 256, 0, st>>>(static_cast<const float4*>(acc), n, n_bins, static_cast<float*>(out),
-                                                  add);
+                                                  add, replicas, stride);
   return cudaGetLastError();
 }
 

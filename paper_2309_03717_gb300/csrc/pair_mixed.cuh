@@ -958,6 +958,8 @@ cudaError_t forward_mixed(int formalism, const void* tiles, int64_t n_tiles, con
   FwdArgs a{tiles, n_tiles, ants, n_ant, shape.a_tile, acc, err, FwdGrid{}, M};
   auto go = [&](auto ops) {
     using O = decltype(ops);
+    a.replicas = shape.replicas > 1 ? shape.replicas : 1;
+    a.replica_stride = (int64_t)n_ant * M.n_bins * O::kAccRows;
     const int64_t ctas = forward_grid(a, shape, sm_count * forward_blocks_per_sm<O>(shape.a_tile),
                                       sizeof(float4) * O::kAccRows);
     return launch_forward_ops<O>(a, ctas, st);
