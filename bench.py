@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--fp64-only", type=int, default=0, metavar="TRACKS",
                     help="time only the FP64 path on TRACKS tracks of the shower (a small case for profiling)")
+    ap.add_argument("--adjoint-only", choices=["endpoint", "zhs"], default=None,
+                    help="time only the forward pass and the adjoint of one formalism on the differentiable "
+                         "workload (1e6 tracks x 64 antennas; a small case for profiling)")
     ap.add_argument("--cpu-sample-tracks", type=int, default=400000)
     return ap.parse_args()
 
@@ -306,6 +309,14 @@ def main():
         c8r.load()
         print(json.dumps({"fp64_only": fp64_timing(torch, c8r, synth.workload(1), args.fp64_only)}))
         return
+    if args.adjoint_only:
+        c8r.load()
+        w4 = synth.workload(4)
+        d4 = {k: torch.from_numpy(v).cuda() for k, v in synth.workload_tracks(w4).items()}
+        fwd_ms, bwd_ms = adjoint_timing(torch, c8r, w4, d4, args.adjoint_only)
+        print(json.dumps({"adjoint_only": {"formalism": args.adjoint_only, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+                                           "bwd_fwd_ratio": bwd_ms / fwd_ms}}))
+        return
     if world > 1:
         dist.barrier()
     c8r.load()
@@ -361,9 +372,12 @@ def main():
     d2h = sum(v.numel() * v.element_size() for v in host_out.values())
 
     # the host->device copy of chunk c+1 (copy stream) overlaps the radio
-    # processes' work on chunk c (compute stream); the traces come back at the end
-    n_chunks = 4
-    bounds = np.linspace(0, T, n_chunks + 1).astype(np.int64)
+    # processes' work on chunk c (compute stream); the traces come back at the end.
+    # Chunks grow (1/32, 3/32, 1/4, 1/4, 3/8 of the tracks) so that only the
+    # small first copy is exposed: a chunk's compute takes several times longer
+    # than the copy of the next, larger one.
+    bounds = np.unique((T * np.array([0.0, 1 / 32, 1 / 8, 3 / 8, 5 / 8, 1.0])).astype(np.int64))
+    n_chunks = len(bounds) - 1
     copy_stream = torch.cuda.Stream()
     dev_buf = {k: torch.empty(v.shape, dtype=v.dtype, device="cuda") for k, v in pinned.items()}
 
@@ -415,7 +429,7 @@ def main():
                    "l2": "inputs larger than L2 (tracks %.2f GB per GPU)" % (T * 48 / 1e9),
                    "parallelism": f"{world} independent showers (weak)"},
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "note": f"pinned host tracks copied in {n_chunks} chunks on a second stream, overlapping the "
+                "note": f"pinned host tracks copied in {n_chunks} growing chunks on a second stream, overlapping the "
                         f"processes' work on the previous chunk; traces copied back to pinned host memory",
                 "traces_vs_device_path_rel_l2": e2e_check},
         "gpu_launches": int(prof_e["pair_launches"] + prof_e["ingest_launches"] + prof_z["pair_launches"]

@@ -107,7 +107,7 @@ struct c8r_ctx {
   size_t acc_bytes = 0;
   void* d_stage = nullptr;   // [n_ant][3][n_bins] staging for copies to host
   void* d_gbm = nullptr;     // backward: dL/dtraces, bin-major [n_ant][n_bins] accumulator elements
-  Acc4D* d_gpre = nullptr;   // backward (ZHS): running sums of d_gbm over the bins, [n_ant][n_bins + 1]
+  PrefixFF* d_gpre = nullptr;  // backward (mixed ZHS): running sums of d_gbm over the bins, [n_ant][n_bins + 1]
   size_t trace_bytes = 0;
   // scratch: derived-track tiles for one chunk
   void* d_tiles = nullptr;
@@ -605,8 +605,9 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
       return fail(c, C8R_ENOMEM, "backward gradient buffer");
     }
   }
-  if (c->formalism == C8R_ZHS && !c->d_gpre) {
-    cudaError_t e = cudaMalloc(&c->d_gpre, (size_t)c->n_ant * (c->n_bins + 1) * sizeof(Acc4D));
+  const bool prefix = c->formalism == C8R_ZHS && c->precision == C8R_MIXED;  // the FP64 adjoint sums bin by bin
+  if (prefix && !c->d_gpre) {
+    cudaError_t e = cudaMalloc(&c->d_gpre, (size_t)c->n_ant * (c->n_bins + 1) * sizeof(PrefixFF));
     if (e != cudaSuccess) {
       cudaGetLastError();
       c->d_gpre = nullptr;
@@ -615,8 +616,7 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
   }
   {
     cudaError_t e = launch_traces_to_bin_major(c->precision, grad_traces, c->n_ant, c->n_bins, c->d_gbm, st);
-    if (e == cudaSuccess && c->formalism == C8R_ZHS)
-      e = launch_bin_running_sums(c->precision, c->d_gbm, c->n_ant, c->n_bins, c->d_gpre, st);
+    if (e == cudaSuccess && prefix) e = launch_bin_running_sums(c->d_gbm, c->n_ant, c->n_bins, c->d_gpre, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "gradient layout");
   }
   for (int64_t off = 0; off < n; off += chunk) {
@@ -627,7 +627,7 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
     void** og[11] = {&o.x0, &o.y0, &o.z0, &o.x1, &o.y1, &o.z1, &o.t0, &o.t1, &o.bx, &o.by, &o.bz};
     for (int k = 0; k < 11; ++k) *og[k] = static_cast<char*>(*og[k]) + off * es;
     BwdArgs ba{c->d_tiles, m, (m + kTileT - 1) / kTileT, c->d_ants, c->n_ant, c->shape.a_tile, c->d_gbm,
-               c->formalism == C8R_ZHS ? c->d_gpre : nullptr, o, ant_grad, dN0, c->d_err, FwdGrid{}, c->M};
+               prefix ? c->d_gpre : nullptr, o, ant_grad, dN0, c->d_err, FwdGrid{}, c->M};
     e = (c->precision == C8R_FP64) ? launch_backward_f64(c->formalism, lin, ba, c->shape, c->sm_count, st)
                                    : launch_backward_mixed(c->formalism, lin, ba, c->shape, c->sm_count, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "backward launch");

@@ -77,10 +77,16 @@ cudaError_t launch_backward_mixed(int formalism, bool lin, BwdArgs& a, const Fwd
 cudaError_t launch_backward_f64_lin(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st);
 cudaError_t launch_backward_mixed_lin(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count,
                                       cudaStream_t st);
-// running sums over the bins of a bin-major gradient (FP64): [n_ant][n_bins + 1]
-struct Acc4D;
-cudaError_t launch_bin_running_sums(int precision, const void* g, int n_ant, int n_bins, Acc4D* out,
-                                    cudaStream_t st);
+// one running sum of the gradient over the bins, (x, y, z) as float-float
+// (h + l): formed in FP64, stored as two FP32 parts so that the mixed adjoint
+// takes the sum over a run of bins as (h1 - h0) + (l1 - l0) on the FP32 pipe
+struct alignas(32) PrefixFF {
+  float hx, hy, hz, hpad;
+  float lx, ly, lz, lpad;
+};
+// running sums over the bins of a bin-major FP32 gradient [n_ant][n_bins]
+// (mixed path): out [n_ant][n_bins + 1], entry k = the sum over bins < k
+cudaError_t launch_bin_running_sums(const void* g, int n_ant, int n_bins, PrefixFF* out, cudaStream_t st);
 
 // helpers shared by the context and the batch runner
 void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, double dt_ns, double eps_C,

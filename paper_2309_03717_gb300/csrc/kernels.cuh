@@ -99,7 +99,7 @@ struct BwdArgs {
   int n_ant;
   int a_tile;
   const void* G;      // dL/dtraces, bin-major [n_ant][n_bins] of (x, y, z, 0) accumulator elements
-  const Acc4D* Gp;    // ZHS: running sums of G over the bins, [n_ant][n_bins + 1] (entry k: bins < k)
+  const PrefixFF* Gp;  // mixed ZHS: running sums of G over the bins, [n_ant][n_bins + 1] (entry k: bins < k)
   c8r_track_grads out;
   double* ant_grad;   // [n_ant][3]
   double* dN0;
@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int N = M.n_bins;
   const acc4* G = static_cast<const acc4*>(a.G) + (size_t)ant0 * N;
-  const Acc4D* Gp = a.Gp ? a.Gp + (size_t)ant0 * (N + 1) : nullptr;
+  const PrefixFF* Gp = a.Gp ? a.Gp + (size_t)ant0 * (N + 1) : nullptr;
   for (int i = tid; i < n_here; i += nthr) ant_s[i] = a.ants[ant0 + i];
   for (int i = tid; i < 3 * n_here + 1; i += nthr) sg[i] = acc_t(0);
   const uint32_t bytes = (uint32_t)L.stage_bytes;
@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
 #pragma unroll 1
       for (int ant = 0; ant < n_here; ++ant) {
         acc_t ga[3] = {0, 0, 0};
-        const Acc4D* Gp_a = Gp ? Gp + (size_t)ant * (N + 1) : nullptr;
+        const PrefixFF* Gp_a = Gp ? Gp + (size_t)ant * (N + 1) : nullptr;
         if (live && Ops::adj_main(tr, Ops::load_ant(ant_s + ant), M, G + (size_t)ant * N, Gp_a, tg, ga, dn_acc) &&
             Ops::kDefers)
           queue[atomicAdd(&q_cnt[st], 1)] = (uint16_t)(l | (ant << 7));

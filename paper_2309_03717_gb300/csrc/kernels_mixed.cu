@@ -170,22 +170,32 @@ cudaError_t launch_traces_to_bin_major(int precision, const void* g, int n_ant, 
   return cudaGetLastError();
 }
 
-// running sums over the bins of a bin-major gradient, in FP64:
-// out[a][k] = sum_{j < k} g[a][j], k = 0 .. n_bins (one CTA per antenna)
-template <typename T4>
-__global__ void __launch_bounds__(kScanThreads) k_bin_running_sums(const T4* g, int n_bins, Acc4D* out) {
+// running sums over the bins of a bin-major gradient, in FP64, stored as
+// float-float: out[a][k] = sum_{j < k} g[a][j], k = 0 .. n_bins (one CTA per antenna)
+__device__ __forceinline__ PrefixFF prefix_ff(double x, double y, double z) {
+  PrefixFF p;
+  p.hx = (float)x;
+  p.hy = (float)y;
+  p.hz = (float)z;
+  p.lx = (float)(x - (double)p.hx);
+  p.ly = (float)(y - (double)p.hy);
+  p.lz = (float)(z - (double)p.hz);
+  p.hpad = p.lpad = 0.0f;
+  return p;
+}
+__global__ void __launch_bounds__(kScanThreads) k_bin_running_sums(const float4* g, int n_bins, PrefixFF* out) {
   __shared__ double warp_tot[3][kScanThreads / 32];
   const int a = blockIdx.x;
-  const T4* row = g + (size_t)a * n_bins;
-  Acc4D* o = out + (size_t)a * (n_bins + 1);
+  const float4* row = g + (size_t)a * n_bins;
+  PrefixFF* o = out + (size_t)a * (n_bins + 1);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double carry[3] = {0.0, 0.0, 0.0};
-  if (threadIdx.x == 0) o[0] = Acc4D{0.0, 0.0, 0.0, 0.0};
+  if (threadIdx.x == 0) o[0] = prefix_ff(0.0, 0.0, 0.0);
   for (int base = 0; base < n_bins; base += blockDim.x) {
     const int k = base + threadIdx.x;
     double v[3] = {0.0, 0.0, 0.0};
     if (k < n_bins) {
-      const T4 e = row[k];
+      const float4 e = row[k];
       v[0] = e.x;
       v[1] = e.y;
       v[2] = e.z;
@@ -209,20 +219,16 @@ __global__ void __launch_bounds__(kScanThreads) k_bin_running_sums(const T4* g, 
         tot[c] += t;
       }
     }
-    if (k < n_bins) o[k + 1] = Acc4D{carry[0] + v[0], carry[1] + v[1], carry[2] + v[2], 0.0};
+    if (k < n_bins) o[k + 1] = prefix_ff(carry[0] + v[0], carry[1] + v[1], carry[2] + v[2]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) carry[c] += tot[c];
     __syncthreads();
   }
 }
 
-cudaError_t launch_bin_running_sums(int precision, const void* g, int n_ant, int n_bins, Acc4D* out,
-                                    cudaStream_t st) {
+cudaError_t launch_bin_running_sums(const void* g, int n_ant, int n_bins, PrefixFF* out, cudaStream_t st) {
   if (n_ant <= 0 || n_bins <= 0) return cudaSuccess;
-  if (precision == C8R_FP64)
-    k_bin_running_sums<Acc4D><<<(unsigned)n_ant, kScanThreads, 0, st>>>(static_cast<const Acc4D*>(g), n_bins, out);
-  else
-    k_bin_running_sums<float4><<<(unsigned)n_ant, kScanThreads, 0, st>>>(static_cast<const float4*>(g), n_bins, out);
+  k_bin_running_sums<<<(unsigned)n_ant, kScanThreads, 0, st>>>(static_cast<const float4*>(g), n_bins, out);
   return cudaGetLastError();
 }
 

@@ -263,7 +263,7 @@ struct OpsF64 {
   }
 
   static __device__ __forceinline__ bool adj_main(const TrackD& tr, const AntRec& A, const MedParams& M,
-                                                  const Acc4D* G, const Acc4D* Gp, double tg[11], double ga[3],
+                                                  const Acc4D* G, const PrefixFF* Gp, double tg[11], double ga[3],
                                                   double& dn) {
     if constexpr (FORM == C8R_ZHS)
       adj_zhs(tr, A, M, G, Gp, tg, ga, dn);
@@ -272,12 +272,12 @@ struct OpsF64 {
     return false;
   }
   static __device__ __forceinline__ void adj_deferred(const TrackD&, const AntRec&, const MedParams&, const Acc4D*,
-                                                      const Acc4D*, double*, double*, double&) {}
+                                                      const PrefixFF*, double*, double*, double&) {}
 
   // ZHS adjoint (bins of the interval ends held fixed; see the mixed path for
   // the formulas): in FP64, times in ns, positions in m
   static __device__ __forceinline__ void adj_zhs(const TrackD& tr, const AntRec& A, const MedParams& M,
-                                                 const Acc4D* G, const Acc4D*, double tg[11], double ga[3],
+                                                 const Acc4D* G, const PrefixFF*, double tg[11], double ga[3],
                                                  double& dn) {
     const double* T = tr.T;
     const int l = tr.l;

@@ -580,7 +580,7 @@ struct OpsMixed {
   // adjoint main pass: every pair except (Endpoint) the near-Cherenkov ones, for
   // which it adds nothing and returns true
   static __device__ __forceinline__ bool adj_main(const TrackM& t, const AntRec& A, const MedParams& M,
-                                                  const float4* G, const Acc4D* Gp, float tg[11], float ga[3],
+                                                  const float4* G, const PrefixFF* Gp, float tg[11], float ga[3],
                                                   float& dn) {
     if constexpr (FORM == C8R_ZHS) {
       adj_zhs(t, A, M, G, Gp, tg, ga, dn);
@@ -595,7 +595,7 @@ struct OpsMixed {
     }
   }
   static __device__ __forceinline__ void adj_deferred(const TrackM& t, const AntRec& A, const MedParams& M,
-                                                      const float4* G, const Acc4D*, float tg[11], float ga[3],
+                                                      const float4* G, const PrefixFF*, float tg[11], float ga[3],
                                                       float& dn) {
     if constexpr (FORM == C8R_ENDPOINT) {
       EndpointEvalM e;
@@ -605,8 +605,20 @@ struct OpsMixed {
     }
   }
   static __device__ __forceinline__ void adj(const TrackM& t, const AntRec& A, const MedParams& M, const float4* G,
-                                             const Acc4D* Gp, float tg[11], float ga[3], float& dn) {
+                                             const PrefixFF* Gp, float tg[11], float ga[3], float& dn) {
     if (adj_main(t, A, M, G, Gp, tg, ga, dn)) adj_deferred(t, A, M, G, Gp, tg, ga, dn);
+  }
+
+  // G summed over bins kb..ke from the float-float running sums: the FP32
+  // difference of the high parts is exact or rounded relative to the result,
+  // and the low parts restore what the high parts dropped, so the sum comes out
+  // as accurate as an FP64 difference rounded to FP32, without the FP64 pipe
+  static __device__ __forceinline__ void run_sum(const PrefixFF* Gp, int kb, int ke, float& ix, float& iy,
+                                                 float& iz) {
+    const PrefixFF p1 = Gp[ke + 1], p0 = Gp[kb];
+    ix = __fadd_rn(__fsub_rn(p1.hx, p0.hx), __fsub_rn(p1.lx, p0.lx));
+    iy = __fadd_rn(__fsub_rn(p1.hy, p0.hy), __fsub_rn(p1.ly, p0.ly));
+    iz = __fadd_rn(__fsub_rn(p1.hz, p0.hz), __fsub_rn(p1.lz, p0.lz));
   }
 
   // ZHS adjoint (bins of the interval ends held fixed): the forward arithmetic
@@ -617,7 +629,7 @@ struct OpsMixed {
   // for a one-bin interval).  The sum of G over the whole bins in between comes
   // from the running sums Gp.  Times in ns, positions in m.
   static __device__ __forceinline__ void adj_zhs(const TrackM& t, const AntRec& A, const MedParams& M,
-                                                 const float4* G, const Acc4D* Gp, float tg[11], float ga[3],
+                                                 const float4* G, const PrefixFF* Gp, float tg[11], float ga[3],
                                                  float& dn) {
     const int N = M.n_bins;
     GeoM gm;
@@ -666,18 +678,13 @@ struct OpsMixed {
       } else {
         const float invW = __fdividef(1.0f, 2.0f * hh);
         const LinEnds z = lin_ends(Jlo, slo, Jhi, shi, invW);
-        double ix = 0.0, iy = 0.0, iz = 0.0;  // G summed over the bins strictly between the ends
+        float ix = 0.0f, iy = 0.0f, iz = 0.0f;  // G summed over the bins strictly between the ends
         const int kb = Jlo + 1 < 0 ? 0 : Jlo + 1;
         const int ke = Jhi - 2 > N - 1 ? N - 1 : Jhi - 2;
-        if (kb <= ke) {
-          const Acc4D p1 = Gp[ke + 1], p0 = Gp[kb];
-          ix = p1.x - p0.x;
-          iy = p1.y - p0.y;
-          iz = p1.z - p0.z;
-        }
-        S[0] = invW * (float)ix;
-        S[1] = invW * (float)iy;
-        S[2] = invW * (float)iz;
+        if (kb <= ke) run_sum(Gp, kb, ke, ix, iy, iz);
+        S[0] = invW * ix;
+        S[1] = invW * iy;
+        S[2] = invW * iz;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           if (i < z.n && z.k[i] >= 0 && z.k[i] < N) {
@@ -706,18 +713,13 @@ struct OpsMixed {
       const float4 glo = inlo ? G[klo] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 ghi = inhi ? G[khi] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float wlo = (1.0f - flo) * invW, whi = fhi * invW;
-      double ix = 0.0, iy = 0.0, iz = 0.0;  // G summed over the whole bins between
+      float ix = 0.0f, iy = 0.0f, iz = 0.0f;  // G summed over the whole bins between
       const int kb = klo + 1 < 0 ? 0 : klo + 1;
       const int ke = khi - 1 > N - 1 ? N - 1 : khi - 1;
-      if (kb <= ke) {
-        const Acc4D p1 = Gp[ke + 1], p0 = Gp[kb];
-        ix = p1.x - p0.x;
-        iy = p1.y - p0.y;
-        iz = p1.z - p0.z;
-      }
-      S[0] = wlo * glo.x + invW * (float)ix + whi * ghi.x;
-      S[1] = wlo * glo.y + invW * (float)iy + whi * ghi.y;
-      S[2] = wlo * glo.z + invW * (float)iz + whi * ghi.z;
+      if (kb <= ke) run_sum(Gp, kb, ke, ix, iy, iz);
+      S[0] = wlo * glo.x + invW * ix + whi * ghi.x;
+      S[1] = wlo * glo.y + invW * iy + whi * ghi.y;
+      S[2] = wlo * glo.z + invW * iz + whi * ghi.z;
       const float g_lo = Av[0] * glo.x + Av[1] * glo.y + Av[2] * glo.z;
       const float g_hi = Av[0] * ghi.x + Av[1] * ghi.y + Av[2] * ghi.z;
       const float AS = Av[0] * S[0] + Av[1] * S[1] + Av[2] * S[2];
