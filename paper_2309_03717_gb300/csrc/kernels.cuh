@@ -573,7 +573,9 @@ cudaError_t launch_backward_ops(BwdArgs& a, const FwdShape& shape, int sm_count,
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTileT, smem);
   if (e != cudaSuccess) return e;
   FwdArgs f{a.tiles, a.n_tiles, a.ants, a.n_ant, a.a_tile, nullptr, a.err, FwdGrid{}, a.M};
-  const int64_t ctas = forward_grid(f, shape, sm_count * (per_sm < 1 ? 1 : per_sm), sizeof(typename AccOf<typename Ops::acc_t>::type));
+  FwdShape one = shape;  // the L2 grouping covers one bin-major gradient, not the forward's accumulator copies
+  one.replicas = 1;
+  const int64_t ctas = forward_grid(f, one, sm_count * (per_sm < 1 ? 1 : per_sm), sizeof(typename AccOf<typename Ops::acc_t>::type));
   a.g = f.g;
   k<<<(unsigned)ctas, kTileT, smem, st>>>(a);
   return cudaGetLastError();
