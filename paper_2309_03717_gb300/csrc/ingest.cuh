@@ -139,23 +139,19 @@ __device__ __forceinline__ void exp_alt(float zh, float zl, const MedParams& M, 
 }
 
 
-// resident 256-thread blocks per SM the mixed ingest's registers are set for:
-// it is bound by load latency, so more threads mean more loads in flight
-constexpr int kIngestBlocks = 8;
-
 // Map: padded slot g -> index of the caller's track in that slot, or -1 for a
 // padding slot (identity for one shower; a per-shower table for a batch)
 template <typename Tin, class Map>
-__global__ void __launch_bounds__(256, kIngestBlocks) k_ingest_mixed(TrackPtrs t, Map map, int64_t n_pad,
-                                                                     float* tiles, MedParams M,
-                                                                     unsigned long long* kept) {
+__global__ void __launch_bounds__(256) k_ingest_mixed(TrackPtrs t, Map map, int64_t n_pad, float* tiles,
+                                                      MedParams M, unsigned long long* kept) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool keep = false;
   if (i < n_pad) {
-    float* tile = tiles + (i / kTileT) * (int64_t)(fm::NFIELDS * kTileT) + (int)(i % kTileT);
-    // each field is stored as soon as it is formed (field-major: a warp's
-    // stores of one field are contiguous), so few values stay live
-    auto put = [&](int k, float v) { tile[k * kTileT] = v; };
+    float* tile = tiles + (i / kTileT) * (int64_t)(fm::NFIELDS * kTileT);
+    const int l = (int)(i % kTileT);
+    float out[fm::NFIELDS];
+#pragma unroll
+    for (int k = 0; k < fm::NFIELDS; ++k) out[k] = 0.0f;
     const int64_t src = map(i);
     if (src >= 0) {
       // the mixed path takes its inputs as FP32 values; the per-track quantities
@@ -167,49 +163,38 @@ __global__ void __launch_bounds__(256, kIngestBlocks) k_ingest_mixed(TrackPtrs t
       double S = 0.0;
       keep = track_kept_f32(f, S);
       if (keep) {
-        put(fm::X0, f[0]); put(fm::Y0, f[1]); put(fm::Z0, f[2]);
-        put(fm::X1, f[3]); put(fm::Y1, f[4]); put(fm::Z1, f[5]);
-        put(fm::BX, f[8]); put(fm::BY, f[9]); put(fm::BZ, f[10]);
+        out[fm::X0] = f[0]; out[fm::Y0] = f[1]; out[fm::Z0] = f[2];
+        out[fm::X1] = f[3]; out[fm::Y1] = f[4]; out[fm::Z1] = f[5];
+        out[fm::BX] = f[8]; out[fm::BY] = f[9]; out[fm::BZ] = f[10];
         // tau = t/dt, (t1 - t0)/dt = (exact difference) x 1/dt
-        float a, b;
-        mul_f_ff(f[6], M.idt_h, M.idt_l, a, b);
-        put(fm::TAU0H, a); put(fm::TAU0L, b);
-        mul_f_ff(f[7], M.idt_h, M.idt_l, a, b);
-        put(fm::TAU1H, a); put(fm::TAU1L, b);
+        mul_f_ff(f[6], M.idt_h, M.idt_l, out[fm::TAU0H], out[fm::TAU0L]);
+        mul_f_ff(f[7], M.idt_h, M.idt_l, out[fm::TAU1H], out[fm::TAU1L]);
         float dh, dl;
         two_sum(f[7], -f[6], dh, dl);
         float ph, pl;
         mul_f_ff(dh, M.idt_h, M.idt_l, ph, pl);
         pl = __fmaf_rn(dl, M.idt_h, pl);
-        const float dtauh = __fadd_rn(ph, pl);
-        put(fm::DTAUH, dtauh);
-        put(fm::DTAUL, __fsub_rn(pl, __fsub_rn(dtauh, ph)));
-        put(fm::AMPE, __fmul_rn(f[11], M.ampE));
-        put(fm::AMPZ, __fmul_rn(__fmul_rn(f[11], M.kzhs), dtauh));
+        out[fm::DTAUH] = __fadd_rn(ph, pl);
+        out[fm::DTAUL] = __fsub_rn(pl, __fsub_rn(out[fm::DTAUH], ph));
+        out[fm::AMPE] = __fmul_rn(f[11], M.ampE);
+        out[fm::AMPZ] = __fmul_rn(__fmul_rn(f[11], M.kzhs), out[fm::DTAUH]);
         // |beta| = sqrt(S); 1 - |beta| = (1 - S)/(1 + |beta|), 1 - S exact in FP64
         const float bmag = sqrtf((float)S);
-        put(fm::BMAG, bmag);
-        put(fm::OMB, __fdiv_rn((float)__dsub_rn(1.0, S), __fadd_rn(1.0f, bmag)));
+        out[fm::BMAG] = bmag;
+        out[fm::OMB] = __fdiv_rn((float)__dsub_rn(1.0, S), __fadd_rn(1.0f, bmag));
         if (M.kind != C8R_UNIFORM) {  // flat exp(-z/H); the sphere's part comes per pair
-          exp_alt(f[2], 0.0f, M, a, b);
-          put(fm::E0H, a); put(fm::E0L, b);
-          exp_alt(f[5], 0.0f, M, a, b);
-          put(fm::E1H, a); put(fm::E1L, b);
+          exp_alt(f[2], 0.0f, M, out[fm::E0H], out[fm::E0L]);
+          exp_alt(f[5], 0.0f, M, out[fm::E1H], out[fm::E1L]);
           float zmh, zml;  // (z0 + z1)/2, exact
           two_sum(f[2], f[5], zmh, zml);
-          exp_alt(0.5f * zmh, 0.5f * zml, M, a, b);
-          put(fm::EMH, a); put(fm::EML, b);
+          exp_alt(0.5f * zmh, 0.5f * zml, M, out[fm::EMH], out[fm::EML]);
         } else {
-          put(fm::E0H, 1.0f); put(fm::E0L, 0.0f);
-          put(fm::E1H, 1.0f); put(fm::E1L, 0.0f);
-          put(fm::EMH, 1.0f); put(fm::EML, 0.0f);
+          out[fm::E0H] = out[fm::E1H] = out[fm::EMH] = 1.0f;
         }
       }
     }
-    if (!keep) {  // dropped track or padding slot: all fields zero (amplitude 0 marks it)
 #pragma unroll
-      for (int k = 0; k < fm::NFIELDS; ++k) put(k, 0.0f);
-    }
+    for (int k = 0; k < fm::NFIELDS; ++k) tile[k * kTileT + l] = out[k];
   }
   unsigned m = __ballot_sync(0xffffffffu, keep);
   if (kept && (threadIdx.x & 31) == 0 && m) atomicAdd(kept, (unsigned long long)__popc(m));
