@@ -47,6 +47,19 @@ def setup(precision, n=3001, n_ant=16, seed_off=0, formalism="endpoint"):
 @pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
 def test_adjoint_matches_oracle_gradient(precision, tol, formalism):
+    check_adjoint(precision, tol, formalism)
+
+
+def test_mixed_zhs_adjoint_with_a_constant_gradient_part():
+    """The mixed ZHS adjoint sums dL/dtrace over the whole bins of an interval
+    as a difference of running sums over the 2048 bins.  A constant part of
+    dL/dtrace (here twice the size of the varying part) makes the sums grow with
+    the bin index to ~4e3, where FP32 rounds at ~2e-4, while a run of a few bins
+    sums to ~1; the float-float sums keep the bar."""
+    check_adjoint("mixed", 1e-4, "zhs", offset=2.0)
+
+
+def check_adjoint(precision, tol, formalism, offset=0.0):
     c8r, w, tracks, p = setup(precision, formalism=formalism)
     dt = torch.float64 if precision == "fp64" else torch.float32
     dev = to_device(tracks, dt)
@@ -61,7 +74,7 @@ def test_adjoint_matches_oracle_gradient(precision, tol, formalism):
     args = (w["ant_xyz"], w["t_start_ns"] * 1e-9, w["n_bins"], w["dt_ns"] * 1e-9)
     diff = (oracle.forward(oracle.tracks_from_ns(tracks), *args, w["medium"], form)[0]
             - oracle.forward(oracle.tracks_from_ns(tgt_tracks), *args, med2, form)[0])
-    G = torch.from_numpy(2.0 * diff / np.abs(diff).max()).to(dt).cuda()
+    G = torch.from_numpy(2.0 * diff / np.abs(diff).max() + offset).to(dt).cuda()
     n = tracks["x0"].size
     tg = {f: torch.zeros(n, dtype=dt, device="cuda") for f in c8r.GRAD_FIELDS}
     ag = torch.zeros((len(w["ant_xyz"]), 3), dtype=torch.float64, device="cuda")
