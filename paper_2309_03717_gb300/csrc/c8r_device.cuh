@@ -521,7 +521,11 @@ __device__ __forceinline__ ff arrival_mixed(const MedParams& M, const AntRec& A,
 __device__ __forceinline__ int bin_raw(ff u, int n_bins, float& frac) {
   frac = 0.0f;
   if (!(u.h > -1.0f)) return -1;
-  if (!(u.h < (float)n_bins + 1.0f)) return n_bins;
+  // quick reject of arrivals well after the window.  The bound is n_bins + 2, not
+  // n_bins + 1: just below 2^24 (the largest window accepted) FP32 is spaced by 1,
+  // so u = 2^24 - 0.3, in the last bin, has u.h = 2^24 and u.l = -0.3, and
+  // (float)n_bins + 1 rounds to 2^24 itself; n_bins + 2 is exact up to there
+  if (!(u.h < (float)n_bins + 2.0f)) return n_bins;
   float kf = floorf(u.h);
   float f = __fadd_rn(__fsub_rn(u.h, kf), u.l);
   if (f < 0.0f) {

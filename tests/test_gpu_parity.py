@@ -89,6 +89,37 @@ def test_traces_match_oracle(cfg, n, n_ant, formalism, precision, tol):
     assert n_cmp > 0.99 * obr.size
 
 
+@pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_largest_window(formalism, precision, tol):
+    """The largest window accepted, 2^24 bins, ending on the shower front:
+    arrival positions up to 2^24, where FP32 is spaced by 1 and the float-float
+    low part carries the whole fraction (an arrival in the last bin has a high
+    part of 2^24), and many arrivals after the window."""
+    w = synth.workload(1, n_tracks=2003, n_ant=2)
+    if precision == "mixed":
+        w["dtype"] = np.float32
+    tracks = synth.workload_tracks(w)
+    N = 1 << 24
+    # every window starts earlier, so that its first 300 bins (the 50 ns before
+    # the front and the front itself) become the last 300 bins of the large one:
+    # most arrivals fall in the window, ~2 % after it, ~10 in its last bin
+    w["t_start_ns"] = np.asarray(w["t_start_ns"]) - (N - 300) * w["dt_ns"]
+    w["n_bins"] = N
+    if formalism == "endpoint":
+        keep = endpoint_unambiguous(tracks, w["ant_xyz"], w["t_start_ns"], N, w["dt_ns"], w["medium"])
+        tracks = drop_tracks(tracks, keep)
+    ref, kept = oracle_traces(tracks, w["ant_xyz"], w["t_start_ns"], N, w["dt_ns"], w["medium"], formalism)
+    assert np.abs(ref[:, :, N - 16:]).max() > 0 and not ref[:, :, :N - 4096].any()
+    gpu, arr, st = run(w, tracks, formalism, precision)
+    assert st["tracks_kept"] == kept
+    err = rel_l2(gpu, ref)
+    assert err <= tol, f"relative L2 {err:.3e} > {tol:.0e}"
+    obr, ou = oracle_arrivals(tracks, w["ant_xyz"], w["t_start_ns"], N, w["dt_ns"], w["medium"], formalism)
+    n_cmp, _ = compare_bins(arr[0], arr[1], arr[2], obr, ou, N)
+    assert n_cmp > 0.99 * obr.size
+
+
 @pytest.mark.parametrize("cfg,n,n_ant", [(2, 2003, 64), (1, 2003, 40)])
 @pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
@@ -194,6 +225,37 @@ def test_mixed_accepts_fp64_input_rounded_to_fp32():
     p.close()
     assert np.array_equal(a != 0, b != 0)
     assert rel_l2(b, a) < 1e-6
+
+
+@pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_largest_window(formalism, precision, tol):
+    """The largest window accepted, 2^24 bins, ending on the shower front:
+    arrival positions up to 2^24, where FP32 is spaced by 1 and the float-float
+    low part carries the whole fraction (an arrival in the last bin has a high
+    part of 2^24), and many arrivals after the window."""
+    w = synth.workload(1, n_tracks=2003, n_ant=2)
+    if precision == "mixed":
+        w["dtype"] = np.float32
+    tracks = synth.workload_tracks(w)
+    N = 1 << 24
+    # every window starts earlier, so that its first 300 bins (the 50 ns before
+    # the front and the front itself) become the last 300 bins of the large one:
+    # most arrivals fall in the window, ~2 % after it, ~10 in its last bin
+    w["t_start_ns"] = np.asarray(w["t_start_ns"]) - (N - 300) * w["dt_ns"]
+    w["n_bins"] = N
+    if formalism == "endpoint":
+        keep = endpoint_unambiguous(tracks, w["ant_xyz"], w["t_start_ns"], N, w["dt_ns"], w["medium"])
+        tracks = drop_tracks(tracks, keep)
+    ref, kept = oracle_traces(tracks, w["ant_xyz"], w["t_start_ns"], N, w["dt_ns"], w["medium"], formalism)
+    assert np.abs(ref[:, :, N - 16:]).max() > 0 and not ref[:, :, :N - 4096].any()
+    gpu, arr, st = run(w, tracks, formalism, precision)
+    assert st["tracks_kept"] == kept
+    err = rel_l2(gpu, ref)
+    assert err <= tol, f"relative L2 {err:.3e} > {tol:.0e}"
+    obr, ou = oracle_arrivals(tracks, w["ant_xyz"], w["t_start_ns"], N, w["dt_ns"], w["medium"], formalism)
+    n_cmp, _ = compare_bins(arr[0], arr[1], arr[2], obr, ou, N)
+    assert n_cmp > 0.99 * obr.size
 
 
 @pytest.mark.parametrize("cfg,n,n_ant", [(2, 2003, 64), (1, 2003, 40)])
