@@ -113,6 +113,12 @@ def test_largest_window(formalism, precision, tol):
     assert np.abs(ref[:, :, N - 16:]).max() > 0 and not ref[:, :, :N - 4096].any()
     gpu, arr, st = run(w, tracks, formalism, precision)
     assert st["tracks_kept"] == kept
+    if precision == "fp64" and formalism == "zhs":
+        # an arrival position near 1.7e7 bins carries its own FP64 rounding,
+        # ~4e-9 bin (one ulp there, against ~1e-11 in the shower's own window),
+        # and the ZHS bin averages pass it on as ~4e-9/W of a deposit (W the
+        # interval's width in bins): measured 6e-9 in relative L2
+        tol = 2e-8
     err = rel_l2(gpu, ref)
     assert err <= tol, f"relative L2 {err:.3e} > {tol:.0e}"
     obr, ou = oracle_arrivals(tracks, w["ant_xyz"], w["t_start_ns"], N, w["dt_ns"], w["medium"], formalism)
@@ -251,6 +257,12 @@ def test_largest_window(formalism, precision, tol):
     assert np.abs(ref[:, :, N - 16:]).max() > 0 and not ref[:, :, :N - 4096].any()
     gpu, arr, st = run(w, tracks, formalism, precision)
     assert st["tracks_kept"] == kept
+    if precision == "fp64" and formalism == "zhs":
+        # an arrival position near 1.7e7 bins carries its own FP64 rounding,
+        # ~4e-9 bin (one ulp there, against ~1e-11 in the shower's own window),
+        # and the ZHS bin averages pass it on as ~4e-9/W of a deposit (W the
+        # interval's width in bins): measured 6e-9 in relative L2
+        tol = 2e-8
     err = rel_l2(gpu, ref)
     assert err <= tol, f"relative L2 {err:.3e} > {tol:.0e}"
     obr, ou = oracle_arrivals(tracks, w["ant_xyz"], w["t_start_ns"], N, w["dt_ns"], w["medium"], formalism)
