@@ -528,13 +528,12 @@ __device__ __forceinline__ int bin_raw(ff u, int n_bins, float& frac) {
   if (!(u.h < (float)n_bins + 2.0f)) return n_bins;
   float kf = floorf(u.h);
   float f = __fadd_rn(__fsub_rn(u.h, kf), u.l);
-  if (f < 0.0f) {
-    kf -= 1.0f;
-    f += 1.0f;
-  } else if (f >= 1.0f) {
-    kf += 1.0f;
-    f -= 1.0f;
-  }
+  // bring the fraction into [0, 1) by its own floor: the low part is not
+  // renormalised, and for an arrival near 2^24 bins (FP32 spacing 1 or 2 there)
+  // it can exceed 1 in magnitude, so a single step of +-1 would not do
+  const float df = floorf(f);
+  kf = __fadd_rn(kf, df);
+  f = __fsub_rn(f, df);
   int k = (int)kf;
   frac = f;
   if (k < 0) return -1;
