@@ -73,7 +73,13 @@ typedef struct c8r_ctx c8r_ctx;
  * element type (dtype = C8R_F32 or C8R_F64), each of the length passed with them.
  * Track i runs in a straight line from (x0,y0,z0)[i] at time t0[i] to
  * (x1,y1,z1)[i] at t1[i] (m, ns) with velocity (bx,by,bz)[i] in units of c and
- * charge q[i] in units of e.  A C8R_MIXED context rounds FP64 input to FP32. */
+ * charge q[i] in units of e.  A C8R_MIXED context rounds FP64 input to FP32, so
+ * times are best given as offsets from an epoch near the shower and positions
+ * from a nearby origin: FP32 keeps ~7 digits (a time of 1e4 ns to ~1e-3 ns).
+ * The mixed path carries each arrival in float-float (~48 bits): its bin
+ * position is good to ~T x 2^-47 bins, T the largest of |t|/dt, |t_start|/dt
+ * and the travel time in bins, so T up to ~1e8 keeps it below 1e-6 bin (the
+ * edge band inside which either neighbouring bin is correct). */
 typedef struct {
   int32_t dtype;
   const void *x0, *y0, *z0;
