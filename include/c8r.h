@@ -172,9 +172,10 @@ int c8r_set_medium_spherical(c8r_ctx* ctx, double N0, double scale_height_m, dou
  * [t_start_ns[a] + k dt_ns, t_start_ns[a] + (k + 1) dt_ns).  formalism selects
  * Endpoint or ZHS; precision selects C8R_FP64 or C8R_MIXED.  Allocates (and
  * zeroes) the context's trace accumulator, one (x, y, z) element per antenna and
- * bin, FP64 (C8R_FP64) or FP32 (C8R_MIXED), 32 or 16 bytes per element; mixed
- * ZHS keeps a second row per antenna (box edges) and two copies of the whole
- * accumulator (64 bytes per antenna and bin in all).  Replaces
+ * bin, FP64 (C8R_FP64) or FP32 (C8R_MIXED), 32 or 16 bytes per element.  Mixed
+ * ZHS keeps a second row per antenna (box edges), and the mixed path keeps 1 to
+ * 8 copies of the whole accumulator, more for fewer antennas (up to 48 MB in
+ * all), which the fetch sums.  Replaces
  * any previous antenna set and discards its traces.  EINVAL on n_ant < 1,
  * n_bins < 1, dt_ns <= 0 or non-finite values; ETOOBIG if n_bins > 2^24; ENOMEM. */
 int c8r_set_antennas(c8r_ctx* ctx, int32_t n_ant, const double* pos_xyz, const double* t_start_ns,

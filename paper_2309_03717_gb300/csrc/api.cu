@@ -365,7 +365,7 @@ int c8r_set_antennas(c8r_ctx* c, int32_t n_ant, const double* pos, const double*
   c->shape.waves = c->user_waves > 0 ? c->user_waves : kDefaultWaves;
   c->trace_bytes = (size_t)n_ant * 3 * n_bins * (precision == C8R_FP64 ? 8 : 4);
   c->acc_bytes = (size_t)n_ant * n_bins * acc_elem_bytes(precision) * acc_rows(precision, formalism);
-  c->shape.replicas = acc_replicas(precision, formalism);
+  c->shape.replicas = acc_replicas(precision, formalism, n_ant, n_bins, c->shape.a_tile, c->sm_count);
   c->acc_bytes *= c->shape.replicas;
   cudaError_t e = cudaMalloc(&c->d_ants, sizeof(AntRec) * n_ant);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_acc, c->acc_bytes);

@@ -28,13 +28,36 @@ inline size_t acc_elem_bytes(int precision) { return precision == C8R_FP64 ? 32 
 // accumulator rows per antenna: the mixed ZHS path adds a row of box edges
 inline int acc_rows(int precision, int formalism) { return precision == C8R_MIXED && formalism == C8R_ZHS ? 2 : 1; }
 // copies of the accumulator the forward kernel spreads its reductions over (CTA
-// range r adds into copy r % replicas; the fetch sums them).  The mixed ZHS
-// kernel makes ~4 reductions per pair, most of them into the few bins the pulse
-// arrives in, and those bins' L2 slices become its bottleneck; two copies halve
-// the reductions each such slice takes (ZHS pair kernel -10 % on a 2e7-track
-// shower).  The Endpoint kernel is bound by instruction issue and gains nothing.
+// range r adds into copy r % replicas; the fetch sums them).  Most reductions go
+// into the few bins per antenna that the pulse arrives in, and with many CTAs
+// on one antenna tile at a time those bins' L2 slices become the bottleneck.
+// The copies split each hot bin over several addresses.  Measured (pair-kernel
+// time): ZHS on a 160-antenna array (5 antenna tiles) 41 -> 34 ms with 2
+// copies, no better with 4; Endpoint there unchanged (issue-bound) and 2 %
+// slower with the linear deposit; on a 64-antenna array (2 tiles) Endpoint
+// 1.18 -> 0.97 ms with 2 (0.95 with 8), ZHS 1.10 -> 0.73 ms with 4, and with
+// the linear deposit Endpoint 2.68 -> 1.70 ms with 2.  So the count follows the
+// CTAs per antenna tile (resident CTAs / antenna tiles): about one copy per 200
+// for Endpoint and per 100 for ZHS, rounded down to a power of two, at most 8,
+// and only as many as fit the 48 MB of L2 the forward grid budgets for
+// accumulator rows (more would split the antenna tiles into more L2 blocks,
+// with more CTAs per tile again).
 inline int acc_replicas(int precision, int formalism) { return acc_rows(precision, formalism) == 2 ? 2 : 1; }
-
+inline int acc_replicas(int precision, int formalism, int n_ant, int n_bins, int a_tile, int sm_count) {
+  if (precision != C8R_MIXED) return 1;
+  const int64_t ant_tiles = (n_ant + a_tile - 1) / a_tile;
+  const int64_t resident = (int64_t)sm_count * (formalism == C8R_ZHS ? 7 : 6);
+  const int64_t per_tile = resident / (ant_tiles > 0 ? ant_tiles : 1);
+  const int64_t per_copy = formalism == C8R_ZHS ? 100 : 200;
+  int64_t want = (per_tile + per_copy - 1) / per_copy;
+  const size_t one = (size_t)n_ant * n_bins * 16 * acc_rows(precision, formalism);
+  const int64_t fit = (int64_t)(((size_t)48 << 20) / (one > 0 ? one : 1));
+  if (want > fit) want = fit;
+  if (want > 8) want = 8;
+  int r = 1;
+  while (r * 2 <= want) r *= 2;  // a power of two
+  return r;
+}
 // accumulator [replicas][n_ant][rows][n_bins] -> traces [n_ant][3][n_bins]: the
 // copies are summed; with rows == 2 the second row (box edges) is integrated over
 // the bins and added; add != 0 adds into out.  FP32 only for add or replicas > 1
