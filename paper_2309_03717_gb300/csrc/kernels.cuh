@@ -14,9 +14,10 @@
 // L2-resident accumulator [antenna][bin][x, y, z, 0] with one native vector
 // reduction (atomicAdd on float4; three FP64 reductions in the FP64 path); a
 // constant run of bins (ZHS) is added as its two edges into a second row that
-// the fetch integrates, and the mixed ZHS accumulator has two copies (CTA range
-// r adds into copy r % 2) that the fetch sums.  Shared-memory float atomics are not used: they stall
-// the issuing warp, while the global reductions are fire-and-forget.
+// the fetch integrates.  The mixed accumulator has 1 to 8 copies (CTA range r
+// adds into copy r % copies, acc_replicas) that the fetch sums.  Shared-memory
+// float atomics are not used: they stall the issuing warp, while the global
+// reductions are fire-and-forget.
 #pragma once
 
 #include <type_traits>
