@@ -521,11 +521,12 @@ __device__ __forceinline__ ff arrival_mixed(const MedParams& M, const AntRec& A,
 __device__ __forceinline__ int bin_raw(ff u, int n_bins, float& frac) {
   frac = 0.0f;
   if (!(u.h > -1.0f)) return -1;
-  // quick reject of arrivals well after the window.  The bound is n_bins + 2, not
-  // n_bins + 1: just below 2^24 (the largest window accepted) FP32 is spaced by 1,
-  // so u = 2^24 - 0.3, in the last bin, has u.h = 2^24 and u.l = -0.3, and
-  // (float)n_bins + 1 rounds to 2^24 itself; n_bins + 2 is exact up to there
-  if (!(u.h < (float)n_bins + 2.0f)) return n_bins;
+  // quick reject of arrivals well after the window (and of +inf).  The low part
+  // is not renormalised: near 2^24 bins, where FP32 is spaced by 1 or 2, it can
+  // reach a few units (u = 2^24 - 0.35, in the last bin of the largest window,
+  // can come as u.h = 2^24 + 2, u.l = -2.35), so the bound leaves room for a low
+  // part of up to 64 in magnitude (an arrival of ~1e9 bins)
+  if (!(u.h < (float)n_bins + 64.0f)) return n_bins;
   float kf = floorf(u.h);
   float f = __fadd_rn(__fsub_rn(u.h, kf), u.l);
   // bring the fraction into [0, 1) by its own floor: the low part is not
