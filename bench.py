@@ -44,15 +44,15 @@ FP32_LANES_PER_SM = 128
 ALG_OPS_PER_ENDPOINT_PAIR = 62
 # DRAM bytes (read + write) per pair of the Endpoint forward kernel: one ncu
 # capture of a 4e6-track x 160-antenna launch (6.4e8 pairs, default launch
-# shape) read 406.8 MB and wrote 5.3 MB; the traffic is the staged track tiles,
+# shape) read 407.6 MB and wrote 5.6 MB; the traffic is the staged track tiles,
 # so it scales with the pairs at a fixed antenna count.  Set to None when the
 # kernel changes.
-DRAM_BYTES_PER_ENDPOINT_PAIR = 412.1e6 / 6.4e8
+DRAM_BYTES_PER_ENDPOINT_PAIR = 413.1e6 / 6.4e8
 # The same capture: warp instructions issued per pair and the share of issue
 # slots busy (smsp__issue_active) -- the bound the kernel actually meets, since
 # the float-float arrival time makes its instruction count ~8x the plain
 # formula's.  Set to None when the kernel changes.
-ENDPOINT_WARP_INST_PER_PAIR = 1.0095827024e10 / 6.4e8
+ENDPOINT_WARP_INST_PER_PAIR = 1.0095815345e10 / 6.4e8
 ENDPOINT_ISSUE_ACTIVE_NCU = 0.871
 
 
