@@ -42,7 +42,10 @@ inline int acc_rows(int precision, int formalism) { return precision == C8R_MIXE
 // and only as many as fit the 48 MB of L2 the forward grid budgets for
 // accumulator rows (more would split the antenna tiles into more L2 blocks,
 // with more CTAs per tile again).
+// the batched launch: its many showers' antenna tiles spread the CTAs, so 2
+// copies for ZHS and 1 for Endpoint
 inline int acc_replicas(int precision, int formalism) { return acc_rows(precision, formalism) == 2 ? 2 : 1; }
+// a context: from its antenna count, bins and antenna tile
 inline int acc_replicas(int precision, int formalism, int n_ant, int n_bins, int a_tile, int sm_count) {
   if (precision != C8R_MIXED) return 1;
   const int64_t ant_tiles = (n_ant + a_tile - 1) / a_tile;
