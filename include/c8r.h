@@ -176,7 +176,9 @@ int c8r_set_medium_spherical(c8r_ctx* ctx, double N0, double scale_height_m, dou
  * ZHS keeps a second row per antenna (box edges), and the mixed path keeps 1 to
  * 8 copies of the whole accumulator, more for fewer antennas (up to 48 MB in
  * all), which the fetch sums.  Replaces
- * any previous antenna set and discards its traces.  EINVAL on n_ant < 1,
+ * any previous antenna set and discards its traces (a call with the same
+ * n_ant, n_bins, dt_ns, formalism and precision keeps the device memory and
+ * only replaces the table, so moving an array between steps is cheap).  EINVAL on n_ant < 1,
  * n_bins < 1, dt_ns <= 0 or non-finite values; ETOOBIG if n_bins > 2^24; ENOMEM. */
 int c8r_set_antennas(c8r_ctx* ctx, int32_t n_ant, const double* pos_xyz, const double* t_start_ns,
                      int32_t n_bins, double dt_ns, int formalism, int precision);
@@ -339,9 +341,12 @@ int c8r_batch_sync(c8r_batch* b, void* cuda_stream);
  * Arguments as c8r_set_medium / c8r_set_antennas / c8r_push_tracks: tracks are
  * DEVICE arrays, pos_xyz [n_ant][3] (m) and t_start_ns [n_ant] are HOST arrays,
  * out_traces is a DEVICE FP32 array [n_ant][3][n_bins] that the call ACCUMULATES
- * into (zero it first for a fresh result).  Enqueued on cuda_stream on the
- * current device.  Returns C8R_ETOOBIG if n_ant > 1024 or n_bins > 2^24,
- * C8R_EINVAL for other invalid arguments, C8R_ECUDA if a CUDA call fails.
+ * into (zero it first for a fresh result).  The work runs on cuda_stream on the
+ * current device, and the call synchronises that stream before it returns (it
+ * reads the status word back).  Returns C8R_ETOOBIG if n_ant > 1024 or
+ * n_bins > 2^24, C8R_EINVAL for other invalid arguments, C8R_ECUDA if a CUDA
+ * call fails, and C8R_ECANCELLED if a kernel gave up a bounded wait on its
+ * track pipeline and returned early (the traces are then incomplete).
  *
  * The first call on a device looks up the device addresses of the scratch
  * arrays (once per device, with that device current); make that first call
@@ -353,6 +358,27 @@ int c8r_batch_sync(c8r_batch* b, void* cuda_stream);
 int c8r_traces_noalloc(const c8r_tracks* tracks, int64_t n, int32_t n_ant, const double* pos_xyz,
                        const double* t_start_ns, int32_t n_bins, double dt_ns, int formalism, int medium_kind,
                        double n_or_N0, double scale_height_m, float* out_traces, void* cuda_stream);
+
+/* ---- test and diagnostic knobs (not in the paper) ------------------------------ */
+
+/* Polls that each bounded wait of a forward, adjoint, batched or
+ * allocation-free kernel makes on its staged track tile before it gives up
+ * (the kernel then drains the copies it has in flight with the full limit,
+ * sets its status word and returns, and the call reports C8R_ECANCELLED).
+ * polls < 0 restores the default (2^22 polls); 0 makes every such wait give up
+ * at once, which lets a test run the give-up path without a fault or a hang.
+ * Process-wide; applies to kernels launched, and batch graphs captured, after
+ * the call. */
+int c8r_set_wait_limit(int64_t polls);
+
+/* Fault injection on the host: of the library's next device allocations
+ * (contexts, antenna state, derived-track scratch, adjoint and staging buffers,
+ * batches), let `skip` through and make the following n fail as if the device
+ * were out of memory, without calling the allocator.  The calls that make them
+ * return C8R_ENOMEM, free what they had allocated and leave the context as it
+ * was before the call (or unconfigured, for c8r_set_antennas).  n = 0 clears
+ * it.  Process-wide.  EINVAL for a negative argument. */
+int c8r_inject_alloc_failures(int32_t skip, int32_t n);
 
 /* ---- synthetic showers generated on the device --------------------------------- */
 

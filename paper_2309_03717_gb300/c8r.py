@@ -10,7 +10,8 @@ fails loudly when the compiled library is missing.
 Above the one-to-one layer sit two conveniences named after the paper's objects
 (§2, §4): :class:`RadioProcess` (medium + antenna collection + formalism, receives
 tracks, holds the traces) and :class:`RadioTraces`, a ``torch.autograd.Function``
-whose backward is the library's hand-written Endpoint adjoint.
+whose backward is the library's hand-written adjoint of the process's formalism
+(Endpoint or ZHS).
 """
 from __future__ import annotations
 
@@ -108,6 +109,8 @@ _SIGNATURES = [
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                           ctypes.c_int32, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double, _P, _P]),
+    ("c8r_set_wait_limit", ctypes.c_int, [ctypes.c_int64]),
+    ("c8r_inject_alloc_failures", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
 ]
 
 
@@ -303,6 +306,21 @@ def c8r_generate_tracks(seed: int, first: int, n: int, zenith_deg: float = 0.0, 
     return out
 
 
+def c8r_set_wait_limit(polls: int):
+    """Polls of every bounded wait on a staged track tile (< 0: the default;
+    0: give up at once).  Process-wide test knob."""
+    return _check(None, load().c8r_set_wait_limit(int(polls)))
+
+
+def c8r_inject_alloc_failures(skip: int, n: int):
+    """Of the library's next device allocations let ``skip`` through and make
+    the following ``n`` fail (ENOMEM).  Process-wide test knob."""
+    rc = load().c8r_inject_alloc_failures(int(skip), int(n))
+    if rc < 0:
+        raise C8RError(rc, "skip and n must be >= 0")
+    return rc
+
+
 # ---------------------------------------------------------------------------
 # paper-level convenience objects
 # ---------------------------------------------------------------------------
@@ -326,22 +344,60 @@ class RadioProcess:
             device = torch.cuda.current_device()
         self.device = torch.device("cuda", device)
         self.ctx = c8r_create(device)
-        self.n_ant = int(np.asarray(ant_xyz).reshape(-1, 3).shape[0])
+        self.ant_xyz = np.array(ant_xyz, dtype=np.float64).reshape(-1, 3)
+        self.t_start_ns = np.array(t_start_ns, dtype=np.float64).reshape(-1)
+        self.n_ant = int(self.ant_xyz.shape[0])
         self.n_bins = int(n_bins)
+        self.dt_ns = float(dt_ns)
         self.precision = precision
         self.formalism = formalism
-        kind = _MEDIUM[medium["kind"]]
-        if kind == C8R_UNIFORM:
-            c8r_set_medium(self.ctx, kind, medium["n"], 1.0)
-        elif kind == C8R_EXPONENTIAL_SPHERICAL:
-            c8r_set_medium_spherical(self.ctx, medium["N0"], medium["H"], medium["R_E"])
-        else:
-            c8r_set_medium(self.ctx, kind, medium["N0"], medium["H"])
-        c8r_set_antennas(self.ctx, ant_xyz, t_start_ns, n_bins, dt_ns, _FORMALISM[formalism], _PRECISION[precision])
+        self.medium = dict(medium)
+        self._apply_medium()
+        c8r_set_antennas(self.ctx, self.ant_xyz, self.t_start_ns, n_bins, dt_ns, _FORMALISM[formalism],
+                         _PRECISION[precision])
         if eps_C is not None:
             c8r_set_cherenkov_threshold(self.ctx, eps_C)
         c8r_set_deposit(self.ctx, _DEPOSIT[deposit])
         self.deposit = deposit
+
+    def _apply_medium(self):
+        m = self.medium
+        kind = _MEDIUM[m["kind"]]
+        if kind == C8R_UNIFORM:
+            c8r_set_medium(self.ctx, kind, m["n"], 1.0)
+        elif kind == C8R_EXPONENTIAL_SPHERICAL:
+            c8r_set_medium_spherical(self.ctx, m["N0"], m["H"], m["R_E"])
+        else:
+            c8r_set_medium(self.ctx, kind, m["N0"], m["H"])
+
+    @property
+    def refractivity(self) -> float:
+        """N0 of an exponential medium, n - 1 of a uniform one."""
+        m = self.medium
+        return float(m["n"]) - 1.0 if m["kind"] == "uniform" else float(m["N0"])
+
+    def set_refractivity(self, value: float):
+        """Set N0 (exponential media) or n - 1 (uniform medium); traces are kept."""
+        value = float(value)
+        if value == self.refractivity:
+            return
+        if self.medium["kind"] == "uniform":
+            self.medium["n"] = 1.0 + value
+        else:
+            self.medium["N0"] = value
+        self._apply_medium()
+
+    def set_antenna_positions(self, ant_xyz):
+        """Move the antennas (same count; each keeps its trace start time).  The
+        accumulated traces are discarded."""
+        pos = np.array(ant_xyz, dtype=np.float64).reshape(-1, 3)
+        if pos.shape != self.ant_xyz.shape:
+            raise ValueError("antenna count differs from the process's")
+        if np.array_equal(pos, self.ant_xyz):
+            return
+        c8r_set_antennas(self.ctx, pos, self.t_start_ns, self.n_bins, self.dt_ns, _FORMALISM[self.formalism],
+                         _PRECISION[self.precision])
+        self.ant_xyz = pos
 
     @property
     def trace_dtype(self):
@@ -381,18 +437,22 @@ class RadioProcess:
 
 
 class RadioTraces(torch.autograd.Function):
-    """traces = RadioTraces.apply(process, N0_ref, *track_tensors, ant_xyz_tensor)
+    """traces = RadioTraces.apply(process, N0, *track_tensors, ant_xyz_tensor)
 
-    Forward pushes the tracks through ``process`` (reset first) and returns its
-    traces.  Backward runs the library's adjoint (Endpoint or ZHS, the process's
-    formalism) and returns gradients for the twelve track tensors (zero for q),
-    for N0 (a 0-d tensor standing for the refractivity; its value is the one the
-    process was configured with) and for the antenna positions [n_ant, 3]."""
+    A function of all its tensor inputs: forward first configures ``process``
+    with the values of N0 (a 0-d tensor: the refractivity N0 of an exponential
+    medium, n - 1 of a uniform one) and of the antenna positions [n_ant, 3] (the
+    library is reconfigured only when they changed), then pushes the tracks
+    (reset first) and returns the traces.  Backward runs the library's adjoint
+    of the process's formalism (Endpoint or ZHS) and returns gradients for N0,
+    the twelve track tensors (zero for q) and the antenna positions."""
 
     @staticmethod
     def forward(ctx, process: RadioProcess, N0, *args):
         tracks = dict(zip(TRACK_FIELDS, args[:12]))
         ant = args[12]
+        process.set_refractivity(float(N0.detach().cpu()))
+        process.set_antenna_positions(ant.detach().cpu().numpy())
         process.reset()
         process.push(tracks)
         out = process.traces()

@@ -6,9 +6,11 @@
 // make_radio_process_CoREAS/ZHS(detector, propagator, nthreads) (the thread
 // count has no meaning here: the grid covers every track x antenna pair), and
 // c8r_push_tracks that of the radio process receiving tracks (§2 flow).
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -17,6 +19,34 @@
 namespace c8r {
 
 static thread_local std::string g_create_error;
+
+// polls of a bounded wait (c8r_set_wait_limit; < 0: kWaitLimit) and the
+// injected allocation failures (c8r_inject_alloc_failures): allocations to let
+// through first, then allocations to fail
+static std::atomic<int64_t> g_wait_polls{-1};
+static std::mutex g_alloc_mutex;
+static int32_t g_alloc_skip = 0, g_alloc_fail = 0;
+
+uint32_t current_wait_limit() {
+  const int64_t v = g_wait_polls.load();
+  return v < 0 ? kWaitLimit : (uint32_t)(v > (int64_t)kWaitLimit ? kWaitLimit : v);
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    if (g_alloc_fail > 0) {
+      if (g_alloc_skip > 0) {
+        --g_alloc_skip;
+      } else {
+        --g_alloc_fail;
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
 
 void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, double dt_ns, double eps_C,
                  double earth_radius) {
@@ -27,6 +57,7 @@ void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, d
   };
   M.kind = kind;
   M.n_bins = n_bins;
+  M.wait_limit = kWaitLimit;
   M.dt_ns = dt_ns;
   M.inv_c_ns = 1.0 / kCns;
   M.eps_Cd = eps_C;
@@ -74,6 +105,16 @@ void fill_antenna(AntRec& r, double x, double y, double z, double t_ref_ns, cons
   split(z, r.zh, r.zl);
   split(t_ref_ns / M.dt_ns, r.tauh, r.taul);
   split(r.Ea, r.Eah, r.Eal);
+  // error-bound constants of the FP32 arrival (arrival_bin_fast): bins per
+  // metre (n/(c dt), or (1 + N0)/(c dt) as an upper bound for the exponential
+  // medium) times the neglected low part of the position, plus a floor of
+  // 1e-6 bin; and the relative error of the refractivity term from the low
+  // part of the altitude where the quotient is taken (|dz| > 1e-3 H)
+  const double kc = 1.0 / (kCns * M.dt_ns);
+  const double nmax = M.kind == C8R_UNIFORM ? M.n : 1.0 + M.N0;
+  const double al = std::sqrt((double)r.xl * r.xl + (double)r.yl * r.yl + (double)r.zl * r.zl);
+  r.fb_abs = (float)(1.01 * nmax * kc * al + 1e-6);
+  r.fb_rel_v = M.kind == C8R_UNIFORM ? 0.0f : (float)(1.01 * std::fabs((double)r.zl) / (0.999e-3 * M.H));
 }
 
 // the default launch shape: 32 antennas per CTA, 32 waves (a sweep over
@@ -175,7 +216,7 @@ int ensure_tiles(c8r_ctx* c, int64_t n_tracks) {
   c->d_tiles = nullptr;
   c->tiles_cap = 0;
   size_t bytes = (size_t)need * tile_bytes(c->precision);
-  cudaError_t e = cudaMalloc(&c->d_tiles, bytes);
+  cudaError_t e = dev_malloc(&c->d_tiles, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(c, C8R_ENOMEM, "cudaMalloc of the derived-track scratch (" + std::to_string(bytes) + " bytes) failed");
@@ -252,8 +293,8 @@ int c8r_create(c8r_ctx** out, int device) {
   }
   c->device = device;
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
-  e = cudaMalloc(&c->d_kept, sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+  e = dev_malloc(&c->d_kept, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = dev_malloc(&c->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_kept, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e != cudaSuccess) {
@@ -347,6 +388,18 @@ int c8r_set_antennas(c8r_ctx* c, int32_t n_ant, const double* pos, const double*
     return fail(c, C8R_EINVAL, "antenna positions / start times must be finite");
   if (n_bins > kMaxBins) return fail(c, C8R_ETOOBIG, "n_bins = " + std::to_string(n_bins) + " exceeds 2^24");
   cudaSetDevice(c->device);
+  if (c->ants_set && n_ant == c->n_ant && n_bins == c->n_bins && formalism == c->formalism &&
+      precision == c->precision && dt_ns == c->dt_ns) {
+    // the same layout (an antenna array being moved, e.g. by an optimiser):
+    // keep the device memory, replace the table and discard the traces
+    c->pos.assign(pos, pos + 3 * (size_t)n_ant);
+    c->t_start.assign(t_start, t_start + n_ant);
+    cudaError_t e = cudaMemset(c->d_acc, 0, c->acc_bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "trace reset");
+    c->pushed = 0;
+    cudaMemset(c->d_kept, 0, sizeof(unsigned long long));
+    return rebuild_tables(c);
+  }
   free_antenna_state(c);
   if (c->precision != precision && c->d_tiles) {
     cudaFree(c->d_tiles);
@@ -367,8 +420,8 @@ int c8r_set_antennas(c8r_ctx* c, int32_t n_ant, const double* pos, const double*
   c->acc_bytes = (size_t)n_ant * n_bins * acc_elem_bytes(precision) * acc_rows(precision, formalism);
   c->shape.replicas = acc_replicas(precision, formalism, n_ant, n_bins, c->shape.a_tile, c->sm_count);
   c->acc_bytes *= c->shape.replicas;
-  cudaError_t e = cudaMalloc(&c->d_ants, sizeof(AntRec) * n_ant);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_acc, c->acc_bytes);
+  cudaError_t e = dev_malloc(&c->d_ants, sizeof(AntRec) * n_ant);
+  if (e == cudaSuccess) e = dev_malloc(&c->d_acc, c->acc_bytes);
   if (e == cudaSuccess) e = cudaMemset(c->d_acc, 0, c->acc_bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -421,10 +474,12 @@ int c8r_push_tracks(c8r_ctx* c, const c8r_tracks* t, int64_t n, void* stream) {
     if (e != cudaSuccess) return cuda_fail(c, e, "ingest launch");
     if (c->profiling) cudaEventRecord(e1, st);
     const int64_t n_tiles = (m + kTileT - 1) / kTileT;
+    MedParams M = c->M;
+    M.wait_limit = current_wait_limit();
     e = (c->precision == C8R_FP64)
-            ? launch_forward_f64(c->formalism, lin, c->d_tiles, n_tiles, c->d_ants, c->n_ant, c->M, c->d_acc,
+            ? launch_forward_f64(c->formalism, lin, c->d_tiles, n_tiles, c->d_ants, c->n_ant, M, c->d_acc,
                                  c->shape, c->sm_count, c->d_err, st)
-            : launch_forward_mixed(c->formalism, lin, c->d_tiles, n_tiles, c->d_ants, c->n_ant, c->M, c->d_acc,
+            : launch_forward_mixed(c->formalism, lin, c->d_tiles, n_tiles, c->d_ants, c->n_ant, M, c->d_acc,
                                    c->shape, c->sm_count, c->d_err, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "forward launch");
     if (c->profiling) {
@@ -453,7 +508,7 @@ int c8r_fetch_traces(c8r_ctx* c, void* dst, int dst_is_device, int reset, void* 
     e = fetch_acc(c, dst, st);
   } else {
     if (!c->d_stage) {
-      e = cudaMalloc(&c->d_stage, c->trace_bytes);
+      e = dev_malloc(&c->d_stage, c->trace_bytes);
       if (e != cudaSuccess) {
         cudaGetLastError();
         c->d_stage = nullptr;
@@ -598,7 +653,7 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
   if ((r = ensure_tiles(c, chunk)) != C8R_OK) return r;
   const size_t es = want == C8R_F64 ? 8 : 4;
   if (!c->d_gbm) {
-    cudaError_t e = cudaMalloc(&c->d_gbm, (size_t)c->n_ant * c->n_bins * acc_elem_bytes(c->precision));
+    cudaError_t e = dev_malloc(&c->d_gbm, (size_t)c->n_ant * c->n_bins * acc_elem_bytes(c->precision));
     if (e != cudaSuccess) {
       cudaGetLastError();
       c->d_gbm = nullptr;
@@ -607,7 +662,7 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
   }
   const bool prefix = c->formalism == C8R_ZHS && c->precision == C8R_MIXED;  // the FP64 adjoint sums bin by bin
   if (prefix && !c->d_gpre) {
-    cudaError_t e = cudaMalloc(&c->d_gpre, (size_t)c->n_ant * (c->n_bins + 1) * sizeof(PrefixFF));
+    cudaError_t e = dev_malloc(&c->d_gpre, (size_t)c->n_ant * (c->n_bins + 1) * sizeof(PrefixFF));
     if (e != cudaSuccess) {
       cudaGetLastError();
       c->d_gpre = nullptr;
@@ -628,10 +683,24 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
     for (int k = 0; k < 11; ++k) *og[k] = static_cast<char*>(*og[k]) + off * es;
     BwdArgs ba{c->d_tiles, m, (m + kTileT - 1) / kTileT, c->d_ants, c->n_ant, c->shape.a_tile, c->d_gbm,
                prefix ? c->d_gpre : nullptr, o, ant_grad, dN0, c->d_err, FwdGrid{}, c->M};
+    ba.M.wait_limit = current_wait_limit();
     e = (c->precision == C8R_FP64) ? launch_backward_f64(c->formalism, lin, ba, c->shape, c->sm_count, st)
                                    : launch_backward_mixed(c->formalism, lin, ba, c->shape, c->sm_count, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "backward launch");
   }
+  return C8R_OK;
+}
+
+int c8r_set_wait_limit(int64_t polls) {
+  g_wait_polls.store(polls < 0 ? -1 : polls);
+  return C8R_OK;
+}
+
+int c8r_inject_alloc_failures(int32_t skip, int32_t n) {
+  if (skip < 0 || n < 0) return C8R_EINVAL;
+  std::lock_guard<std::mutex> lock(g_alloc_mutex);
+  g_alloc_skip = skip;
+  g_alloc_fail = n;
   return C8R_OK;
 }
 

@@ -265,7 +265,7 @@ int upload_items(c8r_batch* b, const std::vector<WorkItem>& v) {
   b->d_items = nullptr;
   b->n_items = (int)v.size();
   if (v.empty()) return C8R_OK;
-  cudaError_t e = cudaMalloc(&b->d_items, sizeof(WorkItem) * v.size());
+  cudaError_t e = dev_malloc(&b->d_items, sizeof(WorkItem) * v.size());
   if (e == cudaSuccess) e = cudaMemcpy(b->d_items, v.data(), sizeof(WorkItem) * v.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bfail(b, C8R_ENOMEM, std::string("work list upload: ") + cudaGetErrorString(e));
   return C8R_OK;
@@ -297,6 +297,7 @@ int enqueue_kernel(c8r_batch* b, int n_items_limit, cudaStream_t st) {
   BatchArgs a{b->d_tiles, b->d_items, std::min(b->n_items, n_items_limit), b->d_ants, b->d_acc, b->d_counter,
               b->d_cancel, b->d_err, b->choice.a_tile, b->M, b->replicas,
               (int64_t)b->total_ant * b->M.n_bins * rows};
+  a.M.wait_limit = current_wait_limit();
   e = launch_batch(a, b->formalism, b->sm_count, st);
   if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   return C8R_OK;
@@ -368,7 +369,11 @@ int autotune(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
   cudaEventDestroy(e1);
   b->choice = best;
   b->tuned = true;
-  tune_store(key, best);
+  // timings of kernels that gave up a bounded wait mean nothing: keep the
+  // choice for this batch only (its status word stays set for c8r_batch_sync)
+  int status = kErrNone;
+  if (cudaMemcpy(&status, b->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && status == kErrNone)
+    tune_store(key, best);
   return upload_items(b, make_items(b, best.a_tile, best.tiles_per_item));
 }
 
@@ -421,19 +426,19 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
       return bad(C8R_EINVAL, "antenna values must be finite");
     fill_antenna(recs[a], p[0], p[1], p[2], d->t_start_ns[a], b->M);
   }
-  cudaError_t e = cudaMalloc(&b->d_ants, sizeof(AntRec) * recs.size());
+  cudaError_t e = dev_malloc(&b->d_ants, sizeof(AntRec) * recs.size());
   if (e == cudaSuccess) e = cudaMemcpy(b->d_ants, recs.data(), sizeof(AntRec) * recs.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && b->total_tiles > 0) e = cudaMalloc(&b->d_tiles, (size_t)b->total_tiles * kTileBytesMixed);
+  if (e == cudaSuccess && b->total_tiles > 0) e = dev_malloc(&b->d_tiles, (size_t)b->total_tiles * kTileBytesMixed);
   const size_t sb = sizeof(int64_t) * (b->n_showers + 1);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_tile_off, sb);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_track_off, sb);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_n_tracks, sb);
+  if (e == cudaSuccess) e = dev_malloc(&b->d_tile_off, sb);
+  if (e == cudaSuccess) e = dev_malloc(&b->d_track_off, sb);
+  if (e == cudaSuccess) e = dev_malloc(&b->d_n_tracks, sb);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_tile_off, b->tile_off.data(), sb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_track_off, b->track_off.data(), sizeof(int64_t) * b->n_showers, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_n_tracks, b->n_tracks.data(), sizeof(int64_t) * b->n_showers, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int) * 3);
+  if (e == cudaSuccess) e = dev_malloc(&b->d_counter, sizeof(int) * 3);
   if (e == cudaSuccess) e = cudaMemset(b->d_counter, 0, sizeof(int) * 3);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -452,7 +457,7 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
   b->replicas = acc_replicas(C8R_MIXED, b->formalism);
   b->acc_bytes = (size_t)b->total_ant * b->M.n_bins * sizeof(float4) * acc_rows(C8R_MIXED, b->formalism) *
                  b->replicas;
-  if (cudaMalloc(&b->d_acc, b->acc_bytes) != cudaSuccess) {
+  if (dev_malloc(&b->d_acc, b->acc_bytes) != cudaSuccess) {
     cudaGetLastError();
     b->d_acc = nullptr;
     b->err = "batch accumulator allocation failed";

@@ -68,7 +68,11 @@ struct AntRec {
   float xh, yh, zh, xl, yl, zl;  // position as float-float
   float tauh, taul;              // t_ref / dt as float-float
   float Eah, Eal;                // Ea as float-float
-  float pad2[2];
+  // constants of the error bound of the FP32 arrival (arrival_bin_fast):
+  // fb_abs = bins per metre x |low part of the position| + 1e-6 bin, and
+  // fb_rel_v = |z_l| / (1e-3 H), the relative error of the refractivity term
+  // from the low part of the altitude (exponential medium; 0 otherwise)
+  float fb_abs, fb_rel_v;
 };
 static_assert(sizeof(AntRec) == 96, "antenna record layout");
 
@@ -94,6 +98,7 @@ struct MedParams {
   float nm1f;            // uniform: n - 1 formed in FP64, then rounded (never (1 + x) - 1 in FP32)
   float RE_f;            // spherical: Earth radius (m)
   float eps_C;           // near-Cherenkov threshold
+  uint32_t wait_limit;   // polls of a bounded wait on a staged track tile before it gives up
 };
 
 // ---------------------------------------------------------------------------
@@ -541,6 +546,95 @@ __device__ __forceinline__ int bin_raw(ff u, int n_bins, float& frac) {
   if (k >= n_bins) return n_bins;
   return k;
 }
+// ---------------------------------------------------------------------------
+// Bin of an arrival from plain FP32 arithmetic with a bound on its error, for
+// the one-bin deposit (reading T: only the bin of an arrival matters there).
+// The float-float arrival (arrival_mixed, ~1e-9 bin) costs about four times the
+// FP32 one, and an FP32 arrival of ~1e5 bins is off by up to a few hundredths
+// of a bin.  So the FP32 arrival decides the bin whenever no bin edge (and
+// neither end of the window) lies within its error bound; then it is the bin of
+// the float-float arrival too, which is good to ~1e-7 bin at most, far inside
+// the bound's 1e-6-bin floor.  Otherwise the caller evaluates the float-float
+// arrival (about 8 % of the arrivals of a shower 1-10 km above 0.2-ns traces).
+//
+// The arithmetic, with u = 2^-24 (the FP32 unit roundoff) and every step
+// rounded once (intrinsics, no contraction):
+//   s = fl(a_h - p): the antenna's high part minus the FP32-exact emission
+//     point; |s| differs from R = |d| by at most u R + |a_l|;
+//   S = fl(s_x^2 + s_y^2 + s_z^2) (two FMAs): within 3u S of |s|^2, so
+//     sqrt(S) is within 1.5u of |s|;
+//   R0 = S rsqrt(S) (MUFU, 2 ulp) and one Newton step with the residual
+//     fma(-R0, R0, S): the step leaves O(u^2) of R0's error, so R' is
+//     sqrt(S) rounded once (u);  in all |R' - R| <= 3.5u R + |a_l|;
+//   p = R' (k_h + k_l), k = n/(c dt) (uniform) or 1/(c dt), rounded once:
+//     |p - kR| <= 4.5u p + k |a_l|;
+//   ts = fl(fl(tau_e,h - tau_a,h) + fl(tau_e,l - tau_a,l)): within 2u |ts|;
+//   v (exponential medium) = N0 H/(c dt) (E_e - E_a)/dz R': the quotient
+//     (2 ulp) or its series for |dz/H| <= 1e-3, four more roundings and R'
+//     give at most 14u |v|, plus |v| |z_l|/|dz| from the antenna altitude's
+//     low part, |dz| > 1e-3 H in the quotient's branch;
+//   uf = fl(fl(ts + p) + v): two more roundings, u |uf| each, and one more
+//     in the window test uf - bound >= n_bins.
+// The bound used is u (4.75 p + 2.25 |ts| + 17 |v| + 3.25 |uf|) +
+// fb_rel_v |v| + fb_abs, each coefficient above its derivation; fb_abs holds
+// k |a_l| and a floor of 1e-6 bin, which covers the float-float arrival's own
+// error for arrivals up to ~1e8 bins from the time origin and the rounding of
+// uf - floor(uf).  A CPU emulation of these steps (2-ulp reciprocal square
+// root and quotient) against the FP64 oracle's arrivals on the benchmark
+// showers stays below 0.4 of the bound.
+// ---------------------------------------------------------------------------
+constexpr int kFastOut = -1;        // the arrival lies outside the window: no deposit
+constexpr int kFastUndecided = -2;  // an edge lies within the bound: the float-float arrival decides
+
+// d = a_h - p in FP32 (no low parts) and R0 = |d| as geo_lite forms it (the
+// same s, y and R0 bit for bit), with S = |d|^2 kept for the Newton step
+__device__ __forceinline__ void geo_fast(const AntRec& A, float px, float py, float pz, GeoM& g, float& S) {
+  g.s[0] = __fadd_rn(A.xh, -px);
+  g.s[1] = __fadd_rn(A.yh, -py);
+  g.s[2] = __fadd_rn(A.zh, -pz);
+  S = __fmaf_rn(g.s[0], g.s[0], __fmaf_rn(g.s[1], g.s[1], __fmul_rn(g.s[2], g.s[2])));
+  g.y = rsqrtf(S);
+  g.R0 = __fmul_rn(S, g.y);
+  g.R1 = 0.0f;
+}
+
+template <int KIND>
+__device__ __forceinline__ int arrival_bin_fast(const MedParams& M, const AntRec& A, const GeoM& g, float S,
+                                                float tauh, float taul, float Eeh, float Eel) {
+  static_assert(KIND == C8R_UNIFORM || KIND == C8R_EXPONENTIAL, "plain straight-line media only");
+  constexpr float u = 5.9604644775390625e-8f;  // 2^-24
+  // R' = sqrt(S) rounded once
+  const float r = __fmaf_rn(-g.R0, g.R0, S);
+  const float R = __fmaf_rn(r, __fmul_rn(0.5f, g.y), g.R0);
+  const float ts = __fadd_rn(__fsub_rn(tauh, A.tauh), __fsub_rn(taul, A.taul));
+  const float kh = KIND == C8R_UNIFORM ? M.s_h : M.kc_h;
+  const float kl = KIND == C8R_UNIFORM ? M.s_l : M.kc_l;
+  const float p = __fmaf_rn(R, kh, __fmul_rn(R, kl));
+  float v = 0.0f;
+  if constexpr (KIND == C8R_EXPONENTIAL) {
+    const float dz = g.s[2];
+    const float x = __fmul_rn(dz, M.invH_h);
+    float q;
+    if (fabsf(x) > 1e-3f) {
+      q = __fdividef(__fadd_rn(__fsub_rn(Eeh, A.Eah), __fsub_rn(Eel, A.Eal)), dz);
+    } else {
+      const float f = __fmul_rn(x, __fmaf_rn(x, __fmaf_rn(x, -1.0f / 24.0f, 1.0f / 6.0f), -0.5f));
+      q = __fmul_rn(__fmul_rn(Eeh, M.invH_h), __fadd_rn(1.0f, f));
+    }
+    v = __fmul_rn(__fmul_rn(q, R), M.cN_h);
+  }
+  const float uf = __fadd_rn(__fadd_rn(ts, p), v);
+  const float eps = __fmaf_rn(4.75f * u, p,
+                              __fmaf_rn(2.25f * u, fabsf(ts),
+                                        __fmaf_rn(__fmaf_rn(17.0f, u, A.fb_rel_v), fabsf(v),
+                                                  __fmaf_rn(3.25f * u, fabsf(uf), A.fb_abs))));
+  if (uf < -eps || __fsub_rn(uf, eps) >= (float)M.n_bins) return kFastOut;
+  const float k = floorf(uf);
+  const float fr = __fsub_rn(uf, k);
+  if (!(fr > eps && fr < __fsub_rn(1.0f, eps))) return kFastUndecided;  // also NaN
+  return (int)k;
+}
+
 __device__ __forceinline__ bool bin_of(ff u, int n_bins, int& k, float& frac) {
   k = bin_raw(u, n_bins, frac);
   return k >= 0 && k < n_bins;

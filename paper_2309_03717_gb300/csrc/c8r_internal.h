@@ -114,6 +114,16 @@ struct alignas(32) PrefixFF {
 // (mixed path): out [n_ant][n_bins + 1], entry k = the sum over bins < k
 cudaError_t launch_bin_running_sums(const void* g, int n_ant, int n_bins, PrefixFF* out, cudaStream_t st);
 
+// process-wide test knobs (c8r_set_wait_limit, c8r_inject_alloc_failures)
+uint32_t current_wait_limit();
+// cudaMalloc, unless an injected allocation failure is pending (then it
+// returns cudaErrorMemoryAllocation without allocating)
+cudaError_t dev_malloc(void** p, size_t bytes);
+template <typename T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
+
 // helpers shared by the context and the batch runner
 void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, double dt_ns, double eps_C,
                  double earth_radius = 0.0);

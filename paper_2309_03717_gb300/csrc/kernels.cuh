@@ -29,11 +29,19 @@ namespace c8r {
 constexpr int kMaxATile = 32;
 constexpr int kFwdMaxThreads = 512;
 
+// what the main pass of a pair leaves for after it (Ops::pair_main): nothing,
+// the whole pair (Endpoint near the Cherenkov angle: Ops::pair_deferred), or
+// one or both endpoints whose bin the FP32 arrival left open
+// (Ops::ends_deferred)
+enum : int { kDeferNone = 0, kDeferPair = 1, kDeferEnd0 = 4, kDeferEnd1 = 8 };
+
 // dynamic shared memory of the forward kernels: two staged track tiles, their
 // mbarriers, the antenna tile and (defer) the queue of set-aside pairs, one
-// 16-bit entry per (track, antenna) pair of a tile
+// 16-bit entry per (track, antenna) pair of a tile (q_cap entries): whole pairs
+// fill it from the front, pairs with set-aside endpoints from the back
 struct FwdLayout {
   size_t stage_bytes, bar_off, ant_off, q_off, total;
+  int q_cap;
 };
 __host__ __device__ inline FwdLayout fwd_layout(int precision, int a_tile, bool defer) {
   FwdLayout L;
@@ -41,7 +49,8 @@ __host__ __device__ inline FwdLayout fwd_layout(int precision, int a_tile, bool 
   L.bar_off = 2 * L.stage_bytes;
   L.ant_off = L.bar_off + 128;
   L.q_off = L.ant_off + (size_t)a_tile * sizeof(AntRec);
-  L.total = L.q_off + (defer ? (size_t)kTileT * a_tile * sizeof(uint16_t) : 0);
+  L.q_cap = defer ? kTileT * a_tile : 0;
+  L.total = L.q_off + (size_t)L.q_cap * sizeof(uint16_t);
   return L;
 }
 
@@ -209,13 +218,16 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
   const int N = M.n_bins;
   const size_t row_stride = (size_t)N * Ops::kAccRows;
   const uint32_t bytes = (uint32_t)L.stage_bytes;
-  // pairs the main pass sets aside (Ops::kDefers): entry = track lane | antenna << 7,
-  // one counter per staging slot
+  // pairs the main pass sets aside (Ops::kDefers): entry = track lane |
+  // antenna << 7 | set-aside endpoints << 10 (kDeferEnd0/1 bits); whole pairs
+  // from the front (q_cnt), pairs with set-aside endpoints from the back
+  // (q_back); one counter each per staging slot.  A pair makes at most one
+  // entry, so the two ends never meet.
   uint16_t* queue = reinterpret_cast<uint16_t*>(smem + L.q_off);
-  __shared__ int q_cnt[2];
+  __shared__ int q_cnt[2], q_back[2];
   if (tid == 0) {
-    q_cnt[0] = 0;
-    q_cnt[1] = 0;
+    q_cnt[0] = q_cnt[1] = 0;
+    q_back[0] = q_back[1] = 0;
     for (int s = 0; s < 2 && t_begin + s < t_end; ++s) {
       const int st = (int)((it + s) & 1);
       mbar_expect_tx(&bar[st], bytes);
@@ -226,7 +238,7 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
   for (int64_t t = t_begin; t < t_end; ++t, ++it) {
     const int st = (int)(it & 1);
     const uint32_t parity = (uint32_t)((it >> 1) & 1);
-    const bool ok = mbar_wait_bounded(&bar[st], parity);
+    const bool ok = mbar_wait_bounded(&bar[st], parity, M.wait_limit);
     if (ok) {
       // one track per thread, held in registers, against every antenna of the tile
       for (int l = tid; l < kTileT; l += nthr) {
@@ -236,8 +248,13 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
 #pragma unroll 1
         for (int ant = 0; ant < n_here; ++ant) {
           GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * row_stride, N};
-          if (Ops::pair_main(tr, Ops::load_ant(ant_s + ant), M, sink) && Ops::kDefers)
-            queue[atomicAdd(&q_cnt[st], 1)] = (uint16_t)(l | (ant << 7));
+          const int code = Ops::pair_main(tr, Ops::load_ant(ant_s + ant), M, sink);
+          if constexpr (Ops::kDefers) {
+            if (code == kDeferPair)
+              queue[atomicAdd(&q_cnt[st], 1)] = (uint16_t)(l | (ant << 7));
+            else if (code != kDeferNone)
+              queue[L.q_cap - 1 - atomicAdd(&q_back[st], 1)] = (uint16_t)(l | (ant << 7) | (code << 10));
+          }
         }
       }
     }
@@ -248,20 +265,24 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
       }
       return false;
     }
-    if (Ops::kDefers) {
-      // the set-aside pairs, evaluated together so that their branch of the
-      // arithmetic runs in full warps; the staged tile is still in place
-      const int nq = q_cnt[st];
+    if constexpr (Ops::kDefers) {
+      // the set-aside work, evaluated together so that each kind runs in full
+      // warps (whole pairs first, then set-aside endpoints); the staged tile is
+      // still in place
+      const int nf = q_cnt[st], nq = nf + q_back[st];
       for (int i = tid; i < nq; i += nthr) {
-        const int e = queue[i];
+        const int e = i < nf ? queue[i] : queue[L.q_cap - 1 - (i - nf)];
         typename Ops::Track tr;
         Ops::load(smem + st * L.stage_bytes, e & (kTileT - 1), M, tr);
-        const int ant = e >> 7;
+        const int ant = (e >> 7) & (kMaxATile - 1);
         GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * row_stride, N};
-        Ops::pair_deferred(tr, Ops::load_ant(ant_s + ant), M, sink);
+        if (i < nf)
+          Ops::pair_deferred(tr, Ops::load_ant(ant_s + ant), M, sink);
+        else
+          Ops::ends_deferred(tr, Ops::load_ant(ant_s + ant), M, sink, (e >> 10) & (kDeferEnd0 | kDeferEnd1));
       }
-      __syncthreads();  // slot st is refilled below; its counter is next used two tiles on
-      if (tid == 0) q_cnt[st] = 0;
+      __syncthreads();  // slot st is refilled below; its counters are next used two tiles on
+      if (tid == 0) q_cnt[st] = q_back[st] = 0;
     }
     if (tid == 0 && t + 2 < t_end) {
       mbar_expect_tx(&bar[st], bytes);
@@ -498,7 +519,7 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
   int64_t it = 0;
   for (int64_t t = t_begin; t < t_end; ++t, ++it) {
     const int st = (int)(it & 1);
-    const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((it >> 1) & 1));
+    const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((it >> 1) & 1), M.wait_limit);
     const unsigned char* stage = smem + st * L.stage_bytes;
     // every lane walks the antennas (dead slots included) so the warp reductions see all 32
     for (int l = tid; l < kTileT; l += nthr) {

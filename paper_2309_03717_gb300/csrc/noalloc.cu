@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_forward_noalloc(const NaA
   int64_t it = 0;
   for (int64_t t = t_begin; t < t_end; ++t, ++it) {
     const int st = (int)(it & 1);
-    const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((it >> 1) & 1));
+    const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((it >> 1) & 1), a.M.wait_limit);
     if (ok) {
       for (int p = tid; p < n_pairs; p += nthr) {
         const int ant = p / kTileT;
@@ -182,6 +182,7 @@ extern "C" int c8r_traces_noalloc(const c8r_tracks* tracks, int64_t n, int32_t n
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   MedParams M;
   fill_medium(M, medium_kind, n_or_N0, scale_height_m, n_bins, dt_ns, 1e-3);
+  M.wait_limit = current_wait_limit();
   // antenna table, built on the host stack in blocks and copied into the scratch
   constexpr int kBlock = 64;
   AntRec block[kBlock];
@@ -235,5 +236,11 @@ extern "C" int c8r_traces_noalloc(const c8r_tracks* tracks, int64_t n, int32_t n
              : launch_na<OpsMixed<C8R_ZHS, C8R_UNIFORM>>(a, grid, st);
     if (e != cudaSuccess) return C8R_ECUDA;
   }
-  return C8R_OK;
+  // the status word: a kernel that gave up a bounded wait returned early, so
+  // the traces are incomplete (read into host memory; the copy and the
+  // synchronisation allocate nothing)
+  int status = kErrNone;
+  if (cudaMemcpyAsync(&status, na.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return C8R_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return C8R_ECUDA;
+  return status == kErrNone ? C8R_OK : C8R_ECANCELLED;
 }

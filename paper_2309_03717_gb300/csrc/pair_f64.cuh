@@ -140,12 +140,14 @@ struct OpsF64 {
       zhs(t.T, t.l, A, M, out);
   }
   template <class Sink>
-  static __device__ __forceinline__ bool pair_main(const TrackD& t, const AntRec& A, const MedParams& M, Sink& out) {
+  static __device__ __forceinline__ int pair_main(const TrackD& t, const AntRec& A, const MedParams& M, Sink& out) {
     pair(t, A, M, out);
-    return false;
+    return kDeferNone;
   }
   template <class Sink>
   static __device__ __forceinline__ void pair_deferred(const TrackD&, const AntRec&, const MedParams&, Sink&) {}
+  template <class Sink>
+  static __device__ __forceinline__ void ends_deferred(const TrackD&, const AntRec&, const MedParams&, Sink&, int) {}
 
   template <class Sink>
   static __device__ __forceinline__ void endpoint(const double* T, int l, const AntRec& A, const MedParams& M,

@@ -282,6 +282,12 @@ struct OpsMixed {
   // Endpoint: the near-Cherenkov pairs (a minority, spread over most warps)
   // are set aside by the main pass and evaluated together afterwards
   static constexpr bool kDefers = FORM == C8R_ENDPOINT;
+  // Endpoint with the one-bin deposit in the plain straight-line media: the
+  // main pass takes each bin from the FP32 arrival with its error bound
+  // (arrival_bin_fast) and sets aside only the endpoints it cannot decide,
+  // for the float-float arrival after the main pass
+  static constexpr bool kFastBins =
+      FORM == C8R_ENDPOINT && !LIN && (KIND == C8R_UNIFORM || KIND == C8R_EXPONENTIAL);
   // adjoint CTAs (128 threads) per SM the registers are set for (the linear
   // Endpoint adjoint carries the slide of each deposit as well)
   static constexpr int kBwdMinBlocks = (LIN && FORM == C8R_ENDPOINT) ? 4 : 6;
@@ -295,7 +301,7 @@ struct OpsMixed {
     AntRec r;
     r.xh = a.x; r.yh = a.y; r.zh = a.z; r.xl = a.w;
     r.yl = b.x; r.zl = b.y; r.tauh = b.z; r.taul = b.w;
-    r.Eah = c.x; r.Eal = c.y;
+    r.Eah = c.x; r.Eal = c.y; r.fb_abs = c.z; r.fb_rel_v = c.w;
     return r;
   }
 
@@ -480,19 +486,72 @@ struct OpsMixed {
   }
 
   // main pass: every pair except (Endpoint) the near-Cherenkov ones, for which
-  // it deposits nothing and returns true
+  // it deposits nothing and returns kDeferPair, and (kFastBins) the endpoints
+  // whose bin the FP32 arrival leaves open, returned as kDeferEnd0/kDeferEnd1
+  // bits after the other endpoint's deposit
   template <class Sink>
-  static __device__ __forceinline__ bool pair_main(const TrackM& t, const AntRec& A, const MedParams& M, Sink& out) {
-    if constexpr (FORM == C8R_ENDPOINT) {
+  static __device__ __forceinline__ int pair_main(const TrackM& t, const AntRec& A, const MedParams& M, Sink& out) {
+    if constexpr (kFastBins) {
+      GeoM g0, g1;
+      float S0, S1;
+      geo_fast(A, t.x0, t.y0, t.z0, g0, S0);
+      geo_fast(A, t.x1, t.y1, t.z1, g1, S1);
+      if (g0.R0 == 0.0f || g1.R0 == 0.0f) return kDeferNone;  // an emission point on the antenna
+      FieldM f0, f1;
+      field_mixed(g0, t.bx, t.by, t.bz, t.bmag, t.om0, __fadd_rn(1.0f, t.nm1_0), f0);
+      field_mixed(g1, t.bx, t.by, t.bz, t.bmag, t.om1, __fadd_rn(1.0f, t.nm1_1), f1);
+      if (!(fminf(fabsf(f0.D), fabsf(f1.D)) >= M.eps_C)) return kDeferPair;
+      const int ka = arrival_bin_fast<KIND>(M, A, g0, S0, t.tau0h, t.tau0l, t.E0h, t.E0l);
+      const int kb = arrival_bin_fast<KIND>(M, A, g1, S1, t.tau1h, t.tau1l, t.E1h, t.E1l);
+      const bool ina = ka >= 0, inb = kb >= 0;  // decided and inside the window
+      const float amp = t.amp;
+      const float c0 = __fdividef(amp, f0.D * g0.R0) * (f0.invR * f0.invR);
+      const float c1 = __fdividef(-amp, f1.D * g1.R0) * (f1.invR * f1.invR);
+      if (ina && inb && ka == kb) {
+        out.dep(ka, c0 * f0.V[0] + c1 * f1.V[0], c0 * f0.V[1] + c1 * f1.V[1], c0 * f0.V[2] + c1 * f1.V[2]);
+      } else {
+        if (ina) out.dep(ka, c0 * f0.V[0], c0 * f0.V[1], c0 * f0.V[2]);
+        if (inb) out.dep(kb, c1 * f1.V[0], c1 * f1.V[1], c1 * f1.V[2]);
+      }
+      return (ka == kFastUndecided ? kDeferEnd0 : 0) | (kb == kFastUndecided ? kDeferEnd1 : 0);
+    } else if constexpr (FORM == C8R_ENDPOINT) {
       EndpointEvalM e;
-      if (!endpoint_fields<KIND>(t, A, M, e)) return false;
-      if (endpoint_near_cherenkov(e, M)) return true;
+      if (!endpoint_fields<KIND>(t, A, M, e)) return kDeferNone;
+      if (endpoint_near_cherenkov(e, M)) return kDeferPair;
       endpoint_arrivals<KIND>(t, A, M, e);
       endpoint_deposit(t, e, M, out);
-      return false;
+      return kDeferNone;
     } else {
       zhs(t, A, M, out);
-      return false;
+      return kDeferNone;
+    }
+  }
+
+  // endpoints set aside by the main pass (kFastBins): the float-float arrival
+  // of each endpoint in `ends` (kDeferEnd0 | kDeferEnd1) decides its bin; the
+  // deposit is the one the main pass would have made (the same geometry and
+  // field functions, so the same values)
+  template <class Sink>
+  static __device__ __forceinline__ void ends_deferred(const TrackM& t, const AntRec& A, const MedParams& M,
+                                                       Sink& out, int ends) {
+    if constexpr (kFastBins) {
+      const int N = M.n_bins;
+#pragma unroll 1
+      for (int j = 0; j < 2; ++j) {
+        if (!(ends & (kDeferEnd0 << j))) continue;
+        GeoM g;
+        geo_lite(A, j ? t.x1 : t.x0, j ? t.y1 : t.y0, j ? t.z1 : t.z0, g);
+        FieldM f;
+        field_mixed(g, t.bx, t.by, t.bz, t.bmag, j ? t.om1 : t.om0, __fadd_rn(1.0f, j ? t.nm1_1 : t.nm1_0), f);
+        geo_refine(g);
+        const ff ua = arrival_mixed<KIND>(M, A, g, j ? t.tau1h : t.tau0h, j ? t.tau1l : t.tau0l, j ? t.E1h : t.E0h,
+                                          j ? t.E1l : t.E0l);
+        float fr;
+        const int k = bin_raw(ua, N, fr);
+        if (k < 0 || k >= N) continue;
+        const float c = __fdividef(j ? -t.amp : t.amp, f.D * g.R0) * (f.invR * f.invR);
+        out.dep(k, c * f.V[0], c * f.V[1], c * f.V[2]);
+      }
     }
   }
 
@@ -508,10 +567,17 @@ struct OpsMixed {
     }
   }
 
-  // one pair, complete
+  // one pair, complete, with float-float arrivals throughout (the arrival
+  // listing records them)
   template <class Sink>
   static __device__ __forceinline__ void pair(const TrackM& t, const AntRec& A, const MedParams& M, Sink& out) {
-    if (pair_main(t, A, M, out)) pair_deferred(t, A, M, out);
+    if constexpr (FORM == C8R_ENDPOINT) {
+      EndpointEvalM e;
+      endpoint_eval_mixed<KIND>(t, A, M, e);
+      if (e.valid) endpoint_deposit(t, e, M, out);
+    } else {
+      zhs(t, A, M, out);
+    }
   }
 
   // one pair from a staged tile (the arrival listing uses this)
