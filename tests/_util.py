@@ -118,9 +118,84 @@ def unambiguous(tracks, ant, t_start_ns, n_bins, dt_ns, medium, formalism, tol=1
 
 
 def endpoint_unambiguous(tracks, ant, t_start_ns, n_bins, dt_ns, medium, tol=1e-6, eps_C=1e-3):
-    """Tracks whose Endpoint deposits are all away from bin edges and whose branch
-    decision is away from the threshold (so the trace is a continuous function of
-    the inputs within the mixed path's rounding)."""
-    br, u = oracle_arrivals(tracks, ant, t_start_ns, n_bins, dt_ns, medium, "endpoint", eps_C)
+    """Tracks none of whose Endpoint arrivals (the two endpoint arrivals, or the
+    two linearised midpoint arrivals near the Cherenkov angle) lies within tol
+    bin of a bin edge at any antenna: their traces do not depend on which of two
+    bins an edge-ambiguous deposit takes."""
+    _, u = oracle_arrivals(tracks, ant, t_start_ns, n_bins, dt_ns, medium, "endpoint", eps_C)
     amb = edge_ambiguous(u, tol).any(axis=-1).any(axis=-1)
     return ~amb
+
+
+def either_bin_reference(gpu, ref, tracks, ant, t_start_ns, n_bins, dt_ns, medium, tol=1e-6, eps_C=1e-3):
+    """The oracle's Endpoint traces `ref` with every deposit whose arrival lies
+    within tol bin of an edge placed in whichever of its two neighbouring bins
+    the GPU's traces agree with better (reading P: there either bin is correct).
+
+    For each (track, antenna) pair with such an arrival the pair's contribution
+    is evaluated by the oracle twice, with the antenna's window as given and with
+    it moved by a fraction of a bin that carries the arrival across its edge
+    (the deposit amplitudes do not depend on the window), and the pair keeps the
+    version nearer the GPU at that antenna.  Only the oracle computes values."""
+    _, u = oracle_arrivals(tracks, ant, t_start_ns, n_bins, dt_ns, medium, "endpoint", eps_C)
+    amb = edge_ambiguous(u, tol)
+    ref = np.array(ref, dtype=np.float64, copy=True)
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ts = np.asarray(t_start_ns, dtype=np.float64)
+    for i, a in np.argwhere(amb.any(axis=-1)):
+        j = int(np.argmax(amb[i, a]))
+        fr = u[i, a, j] - np.floor(u[i, a, j])
+        # moving the window start by s bins moves every arrival of the pair by -s
+        s = (fr + 2 * tol) if fr < 0.5 else -(1.0 - fr + 2 * tol)
+        one = {f: tracks[f][i:i + 1] for f in FIELDS}
+        c0, _ = oracle_traces(one, ant[a:a + 1], ts[a:a + 1], n_bins, dt_ns, medium, "endpoint", eps_C)
+        c1, _ = oracle_traces(one, ant[a:a + 1], ts[a:a + 1] + s * dt_ns, n_bins, dt_ns, medium, "endpoint", eps_C)
+        alt = ref[a] - c0[0] + c1[0]
+        if np.linalg.norm(gpu[a] - alt) < np.linalg.norm(gpu[a] - ref[a]):
+            ref[a] = alt
+    return ref
+
+
+AIR_UNIFORM = {"kind": "uniform", "n": 1.000292}
+AIR_EXP = {"kind": "exponential", "N0": 3.25e-4, "H": 8000.0}
+
+
+def near_cherenkov_pair(D, place, medium, h=1000.0, L=2.0, dt_ns=0.2, n_bins=64, K=32):
+    """One track and one antenna built so that the antenna sees the track's
+    midpoint at the Doppler factor D_m = D (the near-Cherenkov branch of the
+    Endpoint formalism, |D| << eps_C at both endpoints).
+
+    A vertical down-going track from (0, 0, h + L/2) to (0, 0, h - L/2) with
+    beta = (0, 0, -b), b = 1 - 2^-20, and a ground antenna at (d, 0, 0) with
+    h / R = cos(theta) = (1 - D) / (n_m b), n_m the index at the midpoint.  All
+    inputs are FP32-exact (times in ns).  The antenna's window start is placed,
+    from the oracle's own arrival of the midpoint, so that the midpoint arrival
+    u_m lies at K + 1/2 (place 'same': both linearised arrivals
+    u_m -/+ D (t1 - t0)/(2 dt) inside bin K, so the Endpoint pair gives exactly
+    0 and the ZHS interval is one bin) or exactly on the edge K ('straddle': the
+    arrivals in bins K - 1 and K).  Returns (tracks, ant [1, 3], t_start_ns [1])."""
+    b = float(np.float32(1.0 - 2.0 ** -20))
+    if medium["kind"] == "uniform":
+        n = medium["n"]
+    else:
+        n = 1.0 + medium["N0"] * np.exp(-h / medium["H"])
+    cos_t = (1.0 - D) / (n * b)
+    d = float(np.float32(h * np.sqrt(1.0 - cos_t ** 2) / cos_t))
+    c_ns = 0.299792458
+    t0 = 100.0
+    t1 = float(np.float32(t0 + L / (b * c_ns)))
+    vals = [0.0, 0.0, h + L / 2, 0.0, 0.0, h - L / 2, t0, t1, 0.0, 0.0, -b, -1.0]
+    tracks = {f: np.array([v], dtype=np.float64) for f, v in zip(FIELDS, vals)}
+    for f in FIELDS:
+        assert float(np.float32(tracks[f][0])) == tracks[f][0]
+    ant = np.array([[d, 0.0, 0.0]])
+    br, u = oracle_arrivals(tracks, ant, np.zeros(1), n_bins, dt_ns, medium, "endpoint")
+    assert br[0, 0] == 1, "not in the near-Cherenkov branch"
+    um = 0.5 * (u[0, 0, 0] + u[0, 0, 1])
+    f = 0.5 if place == "same" else 0.0
+    t_start = np.array([(um - (K + f)) * dt_ns])
+    return tracks, ant, t_start
+
+
+NEAR_CHERENKOV_CASES = [(m, D, place) for m in ("uniform", "exponential") for D in (1e-4, -1e-4, 1e-6, -1e-6)
+                        for place in ("same", "straddle")]

@@ -120,3 +120,102 @@ def test_autograd_function_routes_to_the_adjoint(formalism):
     assert torch.allclose(ant.grad, ag, rtol=1e-5, atol=1e-6 * float(ag.abs().max()))
     assert torch.allclose(N0.grad, dn.reshape(()), rtol=1e-5, atol=0)
     p.close()
+
+
+def test_autograd_function_follows_n0_and_antenna_positions():
+    """RadioTraces is a function of every tensor it differentiates: moving one
+    antenna by 1 m, or scaling N0 by 1.02 (the differentiable workload's target),
+    changes the forward traces to those of a process configured that way."""
+    from paper_2309_03717_gb300 import c8r
+    w = synth.workload(4, n_tracks=3001, n_ant=8, seed_offset=5)
+    w["dtype"] = np.float32
+    tracks = to_device(synth.workload_tracks(w))
+    args = [tracks[f] for f in synth.FIELDS]
+    p = c8r.RadioProcess(w["medium"], w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], "endpoint", "mixed")
+    N0 = torch.tensor(w["medium"]["N0"], dtype=torch.float64, device="cuda")
+    ant = torch.tensor(w["ant_xyz"], dtype=torch.float64, device="cuda")
+    base = c8r.RadioTraces.apply(p, N0, *args, ant).cpu().numpy()
+
+    def fresh(medium, pos):
+        q = c8r.RadioProcess(medium, pos, w["t_start_ns"], w["n_bins"], w["dt_ns"], "endpoint", "mixed")
+        q.push(tracks)
+        out = q.traces().cpu().numpy()
+        q.close()
+        return out
+
+    moved = ant.clone()
+    moved[3, 0] += 1.0
+    got = c8r.RadioTraces.apply(p, N0, *args, moved).cpu().numpy()
+    ref = fresh(w["medium"], moved.cpu().numpy())
+    assert rel_l2(got[3], base[3]) > 1e-2  # the moved antenna's trace changed
+    assert rel_l2(got, ref) < 1e-5
+    assert rel_l2(np.delete(got, 3, 0), np.delete(base, 3, 0)) < 1e-5
+    med = dict(w["medium"], N0=w["medium"]["N0"] * 1.02)
+    got = c8r.RadioTraces.apply(p, N0 * 1.02, *args, ant).cpu().numpy()
+    assert rel_l2(got, base) > 1e-2
+    assert rel_l2(got, fresh(med, w["ant_xyz"])) < 1e-5
+    p.close()
+
+
+@pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
+def test_autograd_matches_central_differences_fp64(formalism):
+    """Central differences of a loss through RadioTraces (FP64 path, a tiny
+    case) against its backward: N0, every antenna coordinate and a few track
+    coordinates.  Tracks with an arrival (or ZHS interval end) within 2e-3 bin of
+    an edge are left out, so that no step moves a bin."""
+    from paper_2309_03717_gb300 import c8r
+    w = synth.workload(4, n_tracks=400, n_ant=3, seed_offset=9)
+    w["dtype"] = np.float64
+    tracks = synth.workload_tracks(w)
+    keep = unambiguous(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], formalism,
+                       tol=2e-3)
+    tracks = drop_tracks(tracks, keep)
+    n = tracks["x0"].size
+    assert n > 300
+    dev = to_device(tracks)
+    p = c8r.RadioProcess(w["medium"], w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], formalism, "fp64")
+    leaves = {f: dev[f].clone().requires_grad_(f != "q") for f in synth.FIELDS}
+    ant = torch.tensor(w["ant_xyz"], dtype=torch.float64, device="cuda", requires_grad=True)
+    N0 = torch.tensor(w["medium"]["N0"], dtype=torch.float64, device="cuda", requires_grad=True)
+    out = c8r.RadioTraces.apply(p, N0, *[leaves[f] for f in synth.FIELDS], ant)
+    G = torch.from_numpy(np.random.default_rng(3).normal(size=tuple(out.shape))).cuda()
+    scale = 1.0 / float(out.detach().abs().max())
+    (out * G).sum().mul(scale).backward()
+
+    def loss(N0v, antv, trk):
+        with torch.no_grad():
+            o = c8r.RadioTraces.apply(p, N0v, *[trk[f] for f in synth.FIELDS], antv)
+            return float((o * G).sum()) * scale
+
+    base = {f: dev[f].clone() for f in synth.FIELDS}
+    checks = []
+    h = 1e-6 * w["medium"]["N0"]
+    fd = (loss(N0.detach() + h, ant.detach(), base) - loss(N0.detach() - h, ant.detach(), base)) / (2 * h)
+    checks.append(("N0", fd, float(N0.grad)))
+    for a in range(3):
+        for c in range(3):
+            hp = 2e-5  # m: moves an arrival by ~3e-4 bin
+            ap, am = ant.detach().clone(), ant.detach().clone()
+            ap[a, c] += hp
+            am[a, c] -= hp
+            fd = (loss(N0.detach(), ap, base) - loss(N0.detach(), am, base)) / (2 * hp)
+            checks.append((f"ant[{a},{c}]", fd, float(ant.grad[a, c])))
+    # beta does not move the arrivals: a step of 2e-7 changes D by ~1e-7 of
+    # its size (>= 1e-3); tracks with 1 - |beta| > 1e-5 stay below 1 under it
+    bmag = np.sqrt(tracks["bx"] ** 2 + tracks["by"] ** 2 + tracks["bz"] ** 2)
+    slow = np.flatnonzero(1.0 - bmag > 1e-5)
+    for i, ib in zip((0, n // 2, n - 1), (slow[0], slow[len(slow) // 2], slow[-1])):
+        for f in ("x0", "z1", "bx"):
+            if f == "bx":
+                i = ib
+            hp = 2e-5 if f != "bx" else 2e-7
+            tp = {k: v.clone() for k, v in base.items()}
+            tm = {k: v.clone() for k, v in base.items()}
+            tp[f][i] += hp
+            tm[f][i] -= hp
+            fd = (loss(N0.detach(), ant.detach(), tp) - loss(N0.detach(), ant.detach(), tm)) / (2 * hp)
+            checks.append((f"{f}[{i}]", fd, float(leaves[f].grad[i])))
+    floor = 1e-6 * max(abs(c[2]) for c in checks if c[0].startswith("ant"))
+    bad = [c for c in checks if abs(c[1] - c[2]) > 1e-5 * abs(c[2]) + floor]
+    assert not bad, bad
+    p.close()

@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
+from _util import AIR_EXP, AIR_UNIFORM, NEAR_CHERENKOV_CASES, near_cherenkov_pair
 
 FIELDS = oracle.FIELDS
 C = 299792458.0
@@ -676,3 +677,57 @@ def test_abs_mode_bounds_the_signed_traces():
         br, u = oracle.arrivals(one, ant[:1], t_ref[:1], 4096, 0.2e-9, EXP_AIR, f)
         if f == oracle.ENDPOINT and br[0, 0] == 0 and np.floor(u[0, 0, 0]) != np.floor(u[0, 0, 1]):
             assert np.array_equal(a1, np.abs(s1))
+
+
+# ---------------------------------------------------------------------------
+# constructed near-Cherenkov pairs (the branch of reading C), one-bin deposit
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("medium_name,D,place", NEAR_CHERENKOV_CASES)
+def test_constructed_near_cherenkov_pairs(medium_name, D, place):
+    """A track at D_m = +-1e-4 or +-1e-6 from one antenna: the Endpoint pair
+    takes the midpoint branch; with both linearised arrivals in one bin it gives
+    exactly 0, otherwise +-K V/(D R dt) in the two bins, equal to the negative
+    time difference of the edge-sampled ZHS potential; the ZHS deposit over the
+    same tiny interval keeps the closed-form time integral K_A |beta_perp|
+    (t1 - t0)/R_m, in one bin or split evenly over the two bins at the edge."""
+    medium = AIR_UNIFORM if medium_name == "uniform" else AIR_EXP
+    N, K, dtn = 64, 32, 0.2
+    trn, ant, t_start = near_cherenkov_pair(D, place, medium, n_bins=N, K=K, dt_ns=dtn)
+    tr = oracle.tracks_from_ns(trn)
+    dt, t_ref = dtn * 1e-9, t_start * 1e-9
+    br, u = oracle.arrivals(tr, ant, t_ref, N, dt, medium, oracle.ENDPOINT)
+    assert br[0, 0] == 1
+    du = abs(u[0, 0, 1] - u[0, 0, 0])
+    assert du == pytest.approx(abs(D) * (tr["t1"][0] - tr["t0"][0]) / dt, rel=1e-3)
+    E, _ = oracle.forward(tr, ant, t_ref, N, dt, medium, oracle.ENDPOINT)
+    A_edge, _ = oracle.forward(tr, ant, t_ref, N, dt, medium, oracle.ZHS, mode=oracle.MODE_ZHS_EDGE_SAMPLED)
+    if place == "same":
+        assert not E.any()
+    else:
+        nz = np.flatnonzero(np.abs(E[0]).sum(axis=0))
+        assert list(nz) == [K - 1, K]
+        np.testing.assert_array_equal(E[0, :, K - 1], -E[0, :, K])
+        E_from_A = -(A_edge[:, :, 1:] - A_edge[:, :, :-1]) / dt
+        assert rel_l2(E[:, :, :-1], E_from_A) < 1e-12
+    # ZHS: the time integral in closed form (50 digits), one bin or two halves
+    Z, _ = oracle.forward(tr, ant, t_ref, N, dt, medium, oracle.ZHS)
+    mp.mp.dps = 50
+    KA = mp.mpf(MU0) * 1 * mp.mpf(QE) * mp.mpf(C) / (4 * mp.pi)  # |q| = 1; q = -1 flips the sign
+    zm = (mp.mpf(tr["z0"][0]) + mp.mpf(tr["z1"][0])) / 2
+    dx = mp.mpf(ant[0, 0])
+    R = mp.sqrt(dx ** 2 + zm ** 2)
+    b = -mp.mpf(tr["bz"][0])
+    dte = mp.mpf(tr["t1"][0]) - mp.mpf(tr["t0"][0])
+    # beta = (0, 0, -b), rhat = (dx, 0, -zm)/R: beta_perp = beta - (beta.rhat) rhat
+    bpx = -(b * zm / R) * dx / R
+    bpz = -b + (b * zm / R) * zm / R
+    ex, ez = float(-KA * bpx * dte / R), float(-KA * bpz * dte / R)
+    assert Z[0, 0].sum() * dt == pytest.approx(ex, rel=1e-12)
+    assert Z[0, 2].sum() * dt == pytest.approx(ez, rel=1e-12)
+    nz = np.flatnonzero(np.abs(Z[0]).sum(axis=0))
+    if place == "same":
+        assert list(nz) == [K]
+    else:
+        assert list(nz) == [K - 1, K]
+        # the interval is split by the edge in halves (to the placement's rounding, ~1e-12 bin)
+        assert Z[0, 2, K - 1] == pytest.approx(Z[0, 2, K], rel=1e-12 / du + 1e-12)

@@ -47,16 +47,20 @@ def context_traces(c8r, tracks_dev, w, formalism):
     return out
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
 @pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
-def test_noalloc_matches_context_path_on_two_calls(formalism):
+def test_noalloc_matches_context_path_on_two_calls(formalism, dtype):
     from paper_2309_03717_gb300 import c8r
     # first call: 70001 tracks (two internal chunks, ragged tail), 40 antennas;
     # second call: fewer tracks and antennas in a uniform medium, so stale
-    # scratch from the first call would show
+    # scratch from the first call would show.  FP64 input tracks are rounded to
+    # FP32 by the ingest of both paths (and read with 8-byte chunk offsets).
     cases = [synth.workload(1, n_tracks=70001, n_ant=40), synth.workload(0, n_tracks=3001, n_ant=9)]
     for w in cases:
         w["dtype"] = np.float32
         tr = to_device(synth.workload_tracks(w))
+        if dtype == np.float64:
+            tr = {k: v.double() for k, v in tr.items()}
         ref = context_traces(c8r, tr, w, formalism)
         out = torch.zeros((len(w["ant_xyz"]), 3, w["n_bins"]), dtype=torch.float32, device="cuda")
         assert noalloc(c8r, tr, w, formalism, out) == c8r.C8R_OK
@@ -74,3 +78,37 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     out = torch.zeros(1, dtype=torch.float32, device="cuda")
     assert noalloc(c8r, tr, w, "endpoint", out) == c8r.C8R_ETOOBIG
     assert not out.any()
+    w = synth.workload(1, n_tracks=10, n_ant=1)
+    w["n_bins"] = (1 << 24) + 1
+    assert noalloc(c8r, tr, w, "endpoint", out) == c8r.C8R_ETOOBIG
+    assert not out.any()
+
+
+def test_noalloc_without_tracks_is_a_no_op():
+    from paper_2309_03717_gb300 import c8r
+    w = synth.workload(1, n_tracks=10, n_ant=3)
+    w["dtype"] = np.float32
+    tr = {k: v[:0] for k, v in to_device(synth.workload_tracks(w)).items()}
+    out = torch.zeros((3, 3, w["n_bins"]), dtype=torch.float32, device="cuda")
+    assert noalloc(c8r, tr, w, "endpoint", out) == c8r.C8R_OK
+    assert not out.any()
+
+
+def test_noalloc_reports_a_given_up_wait():
+    """A kernel that gives up a bounded wait (here made to give up at once by the
+    test knob) returns early; the call reports it as C8R_ECANCELLED instead of
+    returning incomplete traces as a success, and the next call is whole."""
+    from paper_2309_03717_gb300 import c8r
+    w = synth.workload(1, n_tracks=4001, n_ant=16)
+    w["dtype"] = np.float32
+    tr = to_device(synth.workload_tracks(w))
+    out = torch.zeros((16, 3, w["n_bins"]), dtype=torch.float32, device="cuda")
+    c8r.c8r_set_wait_limit(0)
+    try:
+        assert noalloc(c8r, tr, w, "endpoint", out) == c8r.C8R_ECANCELLED
+    finally:
+        c8r.c8r_set_wait_limit(-1)
+    out.zero_()
+    assert noalloc(c8r, tr, w, "endpoint", out) == c8r.C8R_OK
+    ref = context_traces(c8r, tr, w, "endpoint")
+    assert rel_l2(out.cpu().numpy(), ref) < 1e-5
