@@ -401,8 +401,10 @@ int c8r_generate_tracks(uint64_t seed, int64_t first, int64_t n, double zenith_d
 
 /* Measured issue rates on `device`, in operations per second: FP32 FMA, FP64 FMA,
  * MUFU reciprocal square root, FP32 shared-memory atomic add (scattered bins),
- * FP64 shared-memory atomic add (scattered bins).  out_rates[5].  Runs for a few
- * milliseconds; allocates and frees its own device memory. */
+ * FP64 shared-memory atomic add (scattered bins), and global float4 vector
+ * reductions (atomicAdd on float4) to scattered elements of a 32 MB
+ * L2-resident buffer.  out_rates[6].  Runs for a few milliseconds; allocates
+ * and frees its own device memory. */
 int c8r_measure_peaks(int device, double* out_rates);
 
 #ifdef __cplusplus

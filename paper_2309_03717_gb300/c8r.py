@@ -285,11 +285,12 @@ def c8r_backward(ctx, tracks: dict, grad_traces: torch.Tensor, track_grads: dict
 
 
 def c8r_measure_peaks(device: int = 0):
-    out = (ctypes.c_double * 5)()
+    out = (ctypes.c_double * 6)()
     rc = load().c8r_measure_peaks(int(device), out)
     if rc < 0:
         raise C8RError(rc, "peaks microbenchmark failed")
-    keys = ("ffma_per_s", "dfma_per_s", "rsqrt_per_s", "shared_atomic_f32_per_s", "shared_atomic_f64_per_s")
+    keys = ("ffma_per_s", "dfma_per_s", "rsqrt_per_s", "shared_atomic_f32_per_s", "shared_atomic_f64_per_s",
+            "global_red_f32x4_per_s")
     return dict(zip(keys, list(out)))
 
 

@@ -32,7 +32,7 @@ constexpr int kFwdMaxThreads = 512;
 // what the main pass of a pair leaves for after it (Ops::pair_main): nothing,
 // the whole pair (Endpoint near the Cherenkov angle: Ops::pair_deferred), or
 // one or both endpoints whose bin the FP32 arrival left open
-// (Ops::ends_deferred)
+// (Ops::end_deferred)
 enum : int { kDeferNone = 0, kDeferPair = 1, kDeferEnd0 = 4, kDeferEnd1 = 8 };
 
 // dynamic shared memory of the forward kernels: two staged track tiles, their
@@ -224,10 +224,15 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
   // (q_back); one counter each per staging slot.  A pair makes at most one
   // entry, so the two ends never meet.
   uint16_t* queue = reinterpret_cast<uint16_t*>(smem + L.q_off);
-  __shared__ int q_cnt[2], q_back[2];
+  __shared__ int q_cnt[2], q_back[2], q_second;
+  // second endpoints of pairs with both endpoints set aside, evaluated in a
+  // sweep of their own so that every sweep evaluates one endpoint per lane
+  constexpr int kSecondCap = 256;
+  __shared__ uint16_t second[Ops::kDefers ? kSecondCap : 1];
   if (tid == 0) {
     q_cnt[0] = q_cnt[1] = 0;
     q_back[0] = q_back[1] = 0;
+    q_second = 0;
     for (int s = 0; s < 2 && t_begin + s < t_end; ++s) {
       const int st = (int)((it + s) & 1);
       mbar_expect_tx(&bar[st], bytes);
@@ -272,17 +277,42 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
       const int nf = q_cnt[st], nq = nf + q_back[st];
       for (int i = tid; i < nq; i += nthr) {
         const int e = i < nf ? queue[i] : queue[L.q_cap - 1 - (i - nf)];
-        typename Ops::Track tr;
-        Ops::load(smem + st * L.stage_bytes, e & (kTileT - 1), M, tr);
+        const int l = e & (kTileT - 1), ant = (e >> 7) & (kMaxATile - 1);
+        GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * row_stride, N};
+        const AntRec A = Ops::load_ant(ant_s + ant);
+        if (i < nf) {
+          typename Ops::Track tr;
+          Ops::load(smem + st * L.stage_bytes, l, M, tr);
+          Ops::pair_deferred(tr, A, M, sink);
+        } else {
+          const int ends = (e >> 10) & (kDeferEnd0 | kDeferEnd1);
+          if (ends == (kDeferEnd0 | kDeferEnd1)) {
+            const int k = atomicAdd(&q_second, 1);
+            if (k < kSecondCap) second[k] = (uint16_t)(e & 0xfff);
+          }
+          Ops::end_deferred(smem + st * L.stage_bytes, l, A, M, sink, (ends & kDeferEnd0) ? kDeferEnd0 : kDeferEnd1);
+        }
+      }
+      __syncthreads();
+      // the second endpoints: from the list, or (when more pairs than it holds
+      // had both endpoints set aside, which the whole CTA sees alike) from every
+      // such entry of the queue
+      const int ns = q_second, nb = nq - nf;
+      const bool overflow = ns > kSecondCap;
+      for (int i = tid; i < (overflow ? nb : ns); i += nthr) {
+        int e;
+        if (overflow) {
+          e = queue[L.q_cap - 1 - i];
+          if (((e >> 10) & (kDeferEnd0 | kDeferEnd1)) != (kDeferEnd0 | kDeferEnd1)) continue;
+        } else {
+          e = second[i];
+        }
         const int ant = (e >> 7) & (kMaxATile - 1);
         GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * row_stride, N};
-        if (i < nf)
-          Ops::pair_deferred(tr, Ops::load_ant(ant_s + ant), M, sink);
-        else
-          Ops::ends_deferred(tr, Ops::load_ant(ant_s + ant), M, sink, (e >> 10) & (kDeferEnd0 | kDeferEnd1));
+        Ops::end_deferred(smem + st * L.stage_bytes, e & (kTileT - 1), Ops::load_ant(ant_s + ant), M, sink, kDeferEnd1);
       }
       __syncthreads();  // slot st is refilled below; its counters are next used two tiles on
-      if (tid == 0) q_cnt[st] = q_back[st] = 0;
+      if (tid == 0) q_cnt[st] = q_back[st] = q_second = 0;
     }
     if (tid == 0 && t + 2 < t_end) {
       mbar_expect_tx(&bar[st], bytes);

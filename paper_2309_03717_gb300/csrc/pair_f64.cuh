@@ -147,7 +147,7 @@ struct OpsF64 {
   template <class Sink>
   static __device__ __forceinline__ void pair_deferred(const TrackD&, const AntRec&, const MedParams&, Sink&) {}
   template <class Sink>
-  static __device__ __forceinline__ void ends_deferred(const TrackD&, const AntRec&, const MedParams&, Sink&, int) {}
+  static __device__ __forceinline__ void end_deferred(const void*, int, const AntRec&, const MedParams&, Sink&, int) {}
 
   template <class Sink>
   static __device__ __forceinline__ void endpoint(const double* T, int l, const AntRec& A, const MedParams& M,

@@ -527,31 +527,40 @@ struct OpsMixed {
     }
   }
 
-  // endpoints set aside by the main pass (kFastBins): the float-float arrival
-  // of each endpoint in `ends` (kDeferEnd0 | kDeferEnd1) decides its bin; the
-  // deposit is the one the main pass would have made (the same geometry and
-  // field functions, so the same values)
+  // one endpoint set aside by the main pass (kFastBins; `end` is kDeferEnd0 or
+  // kDeferEnd1), read from the staged tile (lane l): its float-float arrival
+  // decides the bin.  The endpoint's fields are picked by index, so lanes with
+  // different endpoints run one code path and only one endpoint's values are
+  // live; they are formed as load_track_mixed forms them, and the deposit is
+  // the one the main pass would have made (the same geometry and field
+  // functions, so the same values)
   template <class Sink>
-  static __device__ __forceinline__ void ends_deferred(const TrackM& t, const AntRec& A, const MedParams& M,
-                                                       Sink& out, int ends) {
+  static __device__ __forceinline__ void end_deferred(const void* Tv, int l, const AntRec& A, const MedParams& M,
+                                                      Sink& out, int end) {
     if constexpr (kFastBins) {
+      const float* T = static_cast<const float*>(Tv);
       const int N = M.n_bins;
-#pragma unroll 1
-      for (int j = 0; j < 2; ++j) {
-        if (!(ends & (kDeferEnd0 << j))) continue;
-        GeoM g;
-        geo_lite(A, j ? t.x1 : t.x0, j ? t.y1 : t.y0, j ? t.z1 : t.z0, g);
-        FieldM f;
-        field_mixed(g, t.bx, t.by, t.bz, t.bmag, j ? t.om1 : t.om0, __fadd_rn(1.0f, j ? t.nm1_1 : t.nm1_0), f);
-        geo_refine(g);
-        const ff ua = arrival_mixed<KIND>(M, A, g, j ? t.tau1h : t.tau0h, j ? t.tau1l : t.tau0l, j ? t.E1h : t.E0h,
-                                          j ? t.E1l : t.E0l);
-        float fr;
-        const int k = bin_raw(ua, N, fr);
-        if (k < 0 || k >= N) continue;
-        const float c = __fdividef(j ? -t.amp : t.amp, f.D * g.R0) * (f.invR * f.invR);
-        out.dep(k, c * f.V[0], c * f.V[1], c * f.V[2]);
+      const int j = end == kDeferEnd1 ? 1 : 0;
+      const float amp = TF(fm::AMPE);
+      const float bx = TF(fm::BX), by = TF(fm::BY), bz = TF(fm::BZ), bmag = TF(fm::BMAG);
+      float Eh = 1.0f, El = 0.0f, nm1 = M.nm1f;
+      if (KIND != C8R_UNIFORM) {
+        Eh = TF(fm::E0H + 2 * j);
+        El = TF(fm::E0L + 2 * j);
+        nm1 = __fmul_rn(M.N0f, Eh);
       }
+      const float om = __fsub_rn(TF(fm::OMB), __fmul_rn(nm1, bmag));
+      GeoM g;
+      geo_lite(A, TF(fm::X0 + 3 * j), TF(fm::Y0 + 3 * j), TF(fm::Z0 + 3 * j), g);
+      FieldM f;
+      field_mixed(g, bx, by, bz, bmag, om, __fadd_rn(1.0f, nm1), f);
+      geo_refine(g);
+      const ff ua = arrival_mixed<KIND>(M, A, g, TF(fm::TAU0H + 2 * j), TF(fm::TAU0L + 2 * j), Eh, El);
+      float fr;
+      const int k = bin_raw(ua, N, fr);
+      if (k < 0 || k >= N) return;
+      const float c = __fdividef(j ? -amp : amp, f.D * g.R0) * (f.invR * f.invR);
+      out.dep(k, c * f.V[0], c * f.V[1], c * f.V[2]);
     }
   }
 

@@ -1,6 +1,7 @@
 // peaks.cu -- measured issue rates of the units the pair kernels are bound by:
-// FP32 FMA, FP64 FMA, MUFU reciprocal square root, and FP32 / FP64 shared-memory
-// atomic adds to scattered bins.  These are the denominators of the ALU
+// FP32 FMA, FP64 FMA, MUFU reciprocal square root, FP32 / FP64 shared-memory
+// atomic adds to scattered bins, and global float4 vector reductions into an
+// L2-resident buffer (the forward kernels' deposits).  These are the denominators of the ALU
 // roofline the benchmark reports.  Every loop has a fixed trip count and every
 // index is masked into its buffer.
 #include <cuda_runtime.h>
@@ -68,6 +69,17 @@ __global__ void k_peak_satom(T* out, int iters) {
   for (int i = threadIdx.x; i < 4096; i += blockDim.x) out[(size_t)blockIdx.x * 4096 + i] = sm[i];
 }
 
+// global vector reductions (atomicAdd on float4, fire-and-forget) to
+// scattered 16-byte elements of an L2-resident buffer of `mask + 1` elements:
+// the unit the forward kernels deposit with
+__global__ void k_peak_gred4(float4* buf, unsigned mask, int iters) {
+  unsigned h = threadIdx.x * 2654435761u + blockIdx.x * 40503u;
+  for (int i = 0; i < iters; ++i) {
+    h = h * 1664525u + 1013904223u;
+    atomicAdd(buf + ((h >> 7) & mask), make_float4(1.0f, 1.0f, 1.0f, 0.0f));
+  }
+}
+
 }  // namespace
 
 extern "C" int c8r_measure_peaks(int device, double* out_rates) {
@@ -100,6 +112,11 @@ extern "C" int c8r_measure_peaks(int device, double* out_rates) {
   out_rates[2] = timed([&] { k_peak_rsqrt<<<blocks, threads>>>((float*)buf, 1024); }, lanes * kChains * 1024);
   out_rates[3] = timed([&] { k_peak_satom<float><<<blocks, threads>>>((float*)buf, 1024); }, lanes * 1024);
   out_rates[4] = timed([&] { k_peak_satom<double><<<blocks, threads>>>((double*)buf, 512); }, lanes * 512);
+  // 2^21 float4 elements = 32 MB (the buffer holds blocks x 4096 doubles >= 32 MB on 152 SMs)
+  unsigned mask = (1u << 21) - 1;
+  while ((size_t)(mask + 1) * sizeof(float4) > bytes) mask >>= 1;
+  cudaMemset(buf, 0, bytes);
+  out_rates[5] = timed([&] { k_peak_gred4<<<blocks, threads>>>((float4*)buf, mask, 256); }, lanes * 256);
   cudaError_t e = cudaDeviceSynchronize();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -86,3 +86,64 @@ def test_graph_replay_accumulates_and_cancel_word_stops_work():
     b.sync()
     assert rel_l2(again.cpu().numpy(), once.cpu().numpy()) < 2e-6
     b.close()
+
+
+def test_full_batched_workload_sampled_against_oracle():
+    """The 64 uneven showers at their stated sizes (1e5-1e7 tracks, 16-512
+    antennas, zenith 0-65 deg; ~1.4e8 tracks generated on the device, one seed
+    per shower), in the graph-captured persistent launch the benchmark times:
+    the smallest, the median and the largest shower against the oracle at their
+    first, middle and last antenna, over all their tracks (the oracle's tracks
+    from the generator's host twin, chunk by chunk in spawned workers).  Tracks
+    with an arrival within 1e-6 bin of an edge at a sampled antenna get charge 0
+    on both sides."""
+    import multiprocessing as mp
+    import os
+
+    from _chunk_oracle import chunk_job
+    from paper_2309_03717_gb300 import c8r
+    showers = synth.batched_workload(64)
+    n_tr = np.array([s["n_tracks"] for s in showers])
+    order = np.argsort(n_tr)
+    picks = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    assert n_tr[picks[0]] < 2e5 and n_tr[picks[2]] > 5e6
+    off = np.concatenate([[0], np.cumsum(n_tr)[:-1]])
+    total = int(n_tr.sum())
+    cat = {f: torch.empty(total, dtype=torch.float32, device="cuda") for f in synth.FIELDS}
+    for s, sh in enumerate(showers):
+        t = c8r.c8r_generate_tracks(sh["seed"], 0, int(sh["n_tracks"]), sh["zenith"])
+        for f in synth.FIELDS:
+            cat[f][off[s]:off[s] + n_tr[s]].copy_(t[f])
+        del t
+    chunk = 1_000_000
+    jobs, owner = [], []
+    for s in picks:
+        sh = showers[s]
+        A = len(sh["ant_xyz"])
+        sample = sorted({0, A // 2, A - 1})
+        for first in range(0, int(n_tr[s]), chunk):
+            jobs.append((first, min(chunk, int(n_tr[s]) - first), sh["seed"], sh["zenith"],
+                         np.ascontiguousarray(sh["ant_xyz"][sample]), np.asarray(sh["t_start_ns"])[sample], 4096, 0.2,
+                         sh["medium"], "endpoint"))
+            owner.append((s, sample))
+    with mp.get_context("spawn").Pool(max(1, min(len(jobs), os.cpu_count() or 1))) as pool:
+        results = pool.map(chunk_job, jobs)
+    refs = {}
+    for (s, sample), (drop, out, _) in zip(owner, results):
+        q = cat["q"][off[s]:off[s] + n_tr[s]]
+        if drop.size:
+            q[torch.from_numpy(drop).cuda()] = 0.0
+        refs[s] = (sample, refs[s][1] + out if s in refs else out)
+    b = c8r.Batch(showers, synth.AIR_EXPONENTIAL, 4096, 0.2, "endpoint")
+    out = b.new_output()
+    b.run(cat, out, use_graph=True)
+    b.sync()
+    got = out.cpu().numpy()
+    b.close()
+    a_off = np.concatenate([[0], np.cumsum([len(s["ant_xyz"]) for s in showers])[:-1]])
+    for s in picks:
+        sample, ref = refs[s]
+        for j, a in enumerate(sample):
+            assert np.abs(ref[j]).max() > 0
+            err = rel_l2(got[a_off[s] + a], ref[j])
+            assert err <= 1e-4, f"shower {s} ({n_tr[s]} tracks) antenna {a}: relative L2 {err:.3e}"
