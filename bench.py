@@ -44,16 +44,31 @@ FP32_LANES_PER_SM = 128
 ALG_OPS_PER_ENDPOINT_PAIR = 62
 # DRAM bytes (read + write) per pair of the Endpoint forward kernel: one ncu
 # capture of a 4e6-track x 160-antenna launch (6.4e8 pairs, default launch
-# shape) read 407.6 MB and wrote 5.6 MB; the traffic is the staged track tiles,
+# shape) read 407.6 MB and wrote 5.1 MB; the traffic is the staged track tiles,
 # so it scales with the pairs at a fixed antenna count.  Set to None when the
 # kernel changes.
-DRAM_BYTES_PER_ENDPOINT_PAIR = 413.1e6 / 6.4e8
+DRAM_BYTES_PER_ENDPOINT_PAIR = (407597312 + 5079296) / 6.4e8
 # The same capture: warp instructions issued per pair and the share of issue
-# slots busy (smsp__issue_active) -- the bound the kernel actually meets, since
-# the float-float arrival time makes its instruction count ~8x the plain
-# formula's.  Set to None when the kernel changes.
-ENDPOINT_WARP_INST_PER_PAIR = 1.0095815345e10 / 6.4e8
-ENDPOINT_ISSUE_ACTIVE_NCU = 0.871
+# slots busy (smsp__issue_active).  Set to None when the kernel changes.
+ENDPOINT_WARP_INST_PER_PAIR = 7.824939792e9 / 6.4e8
+ENDPOINT_ISSUE_ACTIVE_NCU = 0.6726
+# Algorithmic work per pair of the other kernels, counted from their plain
+# formulas: ZHS one midpoint evaluation (distance, Doppler factor, transverse
+# beta, arrival, interval ends, their bins and weights, up to four deposits):
+# 48 arithmetic + 6 special-function operations; the Endpoint adjoint (per
+# endpoint: the forward geometry and bin, the deposit's chain rule and the
+# accumulation into the track, antenna and N0 gradients): 174 + 10.
+ALG_OPS_PER_ZHS_PAIR = 54
+ALG_OPS_PER_ENDPOINT_ADJOINT_PAIR = 184
+# Per pair, from one ncu capture of each kernel (4e6-track shower x 160
+# antennas for the forward kernels; the differentiable workload for the
+# adjoint): global float4 reductions (lts__t_requests_srcunit_tex_op_red) and
+# DRAM bytes (read + write).  None where not captured.
+RED_PER_PAIR = {"endpoint": 638243634 / 6.4e8, "zhs": 697845122 / 6.4e8, "adjoint": None}
+DRAM_BYTES_PER_PAIR = {"endpoint": DRAM_BYTES_PER_ENDPOINT_PAIR, "zhs": (423814656 + 9532160) / 6.4e8,
+                       "adjoint": None}
+# algorithmic bytes per track of the whole path: the 48-byte FP32 track record
+ALG_BYTES_PER_TRACK = 48.0
 
 
 def parse():
@@ -135,6 +150,36 @@ def peaks():
             return json.load(f), "measured"
     except (OSError, ValueError):
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def roofline_bounds(pairs_per_s, ops_per_pair, red_per_pair, dram_per_pair, fp64_ops_per_pair, rates, pk):
+    """The bounds of a pair kernel (pairs/s each), the binding one (the lowest)
+    and the achieved fraction of it: (i) FP32 issue, the algorithmic FP32-pipe
+    operations per pair against 152 SMs x 128 lanes x the maximum SM clock (the
+    FFMA probe's rate beside it); (ii) FP64 issue, the FP64 operations per pair
+    against the probe's DFMA rate; (iii) global float4 reductions per pair
+    against the probe's rate of scattered reductions into an L2-resident buffer;
+    (iv) HBM, the DRAM bytes per pair against the measured copy bandwidth."""
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    lane_peak = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6
+    b = {"fp32_issue": {"pairs_per_s": lane_peak / ops_per_pair, "peak_lane_ops_per_s": lane_peak,
+                        "ops_per_pair": ops_per_pair, "probe_ffma_lane_ops_per_s": rates.get("ffma_per_s")}}
+    if fp64_ops_per_pair:
+        b["fp64_issue"] = {"pairs_per_s": rates["dfma_per_s"] / fp64_ops_per_pair, "ops_per_pair": fp64_ops_per_pair,
+                           "probe_dfma_per_s": rates.get("dfma_per_s")}
+    else:
+        b["fp64_issue"] = {"pairs_per_s": None, "ops_per_pair": 0, "probe_dfma_per_s": rates.get("dfma_per_s"),
+                           "note": "no FP64 operation per pair"}
+    if red_per_pair and rates.get("global_red_f32x4_per_s"):
+        b["global_reductions"] = {"pairs_per_s": rates["global_red_f32x4_per_s"] / red_per_pair,
+                                  "per_pair": red_per_pair, "probe_red_f32x4_per_s": rates["global_red_f32x4_per_s"]}
+    if dram_per_pair:
+        b["hbm"] = {"pairs_per_s": pk.get("hbm_gbs", 6800.0) * 1e9 / dram_per_pair, "bytes_per_pair": dram_per_pair,
+                    "peak_gbs": pk.get("hbm_gbs", 6800.0)}
+    live = {k: v for k, v in b.items() if v.get("pairs_per_s")}
+    binding = min(live, key=lambda k: live[k]["pairs_per_s"])
+    return {"bounds": b, "binding": binding, "pairs_per_s": pairs_per_s,
+            "frac_of_binding": pairs_per_s / live[binding]["pairs_per_s"]}
 
 
 def max_over_ranks(x, dist, device):
@@ -305,6 +350,8 @@ def main():
     from paper_2309_03717_gb300 import build, c8r, synth
     if rank == 0:
         build.build()
+    c8r.load()
+    rates = c8r.c8r_measure_peaks(local)  # the units' measured rates (a few ms)
     if args.fp64_only:
         c8r.load()
         print(json.dumps({"fp64_only": fp64_timing(torch, c8r, synth.workload(1), args.fp64_only)}))
@@ -367,6 +414,17 @@ def main():
 
     # end to end through the public API: pinned host tracks in, host traces out
     pinned = to_dev(tracks_h, torch, pinned=True)
+    # the pinned host -> device copy bandwidth of this machine, for reading the end-to-end figure
+    probe = torch.empty_like(pinned["x0"], device="cuda")
+    probe.copy_(pinned["x0"], non_blocking=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        probe.copy_(pinned["x0"], non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    h2d_gbs = 3 * probe.numel() * probe.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del probe
     host_out = {f: torch.empty((A, 3, w["n_bins"]), dtype=torch.float32).pin_memory() for f in procs}
     h2d = sum(v.numel() * v.element_size() for v in pinned.values())
     d2h = sum(v.numel() * v.element_size() for v in host_out.values())
@@ -431,7 +489,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "note": f"pinned host tracks copied in {n_chunks} growing chunks on a second stream, overlapping the "
                         f"processes' work on the previous chunk; traces copied back to pinned host memory",
-                "traces_vs_device_path_rel_l2": e2e_check},
+                "traces_vs_device_path_rel_l2": e2e_check, "pinned_h2d_gbs": h2d_gbs},
         "gpu_launches": int(prof_e["pair_launches"] + prof_e["ingest_launches"] + prof_z["pair_launches"]
                             + prof_z["ingest_launches"]),
         "roofline": {"bound": "alu", "kernel": "k_forward<OpsMixed<Endpoint, exponential>>",
@@ -449,7 +507,16 @@ def main():
                      "peak_source": f"152 SMs x 128 FP32 lanes x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
                                     f"({pk_src} max SM clock)",
                      "ops_per_pair": ALG_OPS_PER_ENDPOINT_PAIR, "kernel_ms": kernel_ms,
-                     "pairs_per_launch": pairs_per_launch},
+                     "pairs_per_launch": pairs_per_launch,
+                     "traffic_over_algorithmic": (DRAM_BYTES_PER_ENDPOINT_PAIR * A / ALG_BYTES_PER_TRACK
+                                                  if DRAM_BYTES_PER_ENDPOINT_PAIR and A == 160 else None),
+                     **roofline_bounds(pairs_per_launch / (kernel_ms * 1e-3), ALG_OPS_PER_ENDPOINT_PAIR,
+                                       RED_PER_PAIR["endpoint"], DRAM_BYTES_PER_PAIR["endpoint"], 0, rates, pk)},
+        "roofline_kernels": {
+            "k_forward<OpsMixed<ZHS, exponential>>":
+                roofline_bounds(kept * A * args.steps / (prof_z["pair_ms"] * 1e-3), ALG_OPS_PER_ZHS_PAIR,
+                                RED_PER_PAIR["zhs"], DRAM_BYTES_PER_PAIR["zhs"], 0, rates, pk)},
+        "peaks_measured": rates,
         "kernels": {"endpoint_pair_ms_per_step": prof_e["pair_ms"] / args.steps,
                     "zhs_pair_ms_per_step": prof_z["pair_ms"] / args.steps,
                     "ingest_ms_per_step": (prof_e["ingest_ms"] + prof_z["ingest_ms"]) / args.steps,
@@ -465,6 +532,11 @@ def main():
         result["extras"] = extras(torch, c8r, synth, w)
         # the metric's second part: adjoint / forward time on the differentiable workload
         result["bwd_fwd_ratio"] = result["extras"]["bwd_fwd_ratio"]
+        # the Endpoint adjoint's bounds, from its time per pass (ingest and the
+        # gradient's layout included) on the 1e6-track x 64-antenna workload
+        result["roofline_kernels"]["k_backward<OpsMixed<Endpoint, exponential>>"] = roofline_bounds(
+            6.4e7 / (result["extras"]["diff_bwd_ms"] * 1e-3), ALG_OPS_PER_ENDPOINT_ADJOINT_PAIR,
+            RED_PER_PAIR["adjoint"], DRAM_BYTES_PER_PAIR["adjoint"], 0, rates, pk)
         single = cpu_baseline(w, args.cpu_sample_tracks, ("endpoint", "zhs"))
         result["cpu_baseline"] = cpu_baseline_all_cores(w, 5 * args.cpu_sample_tracks // 2, ("endpoint", "zhs"))
         result["cpu_baseline"]["single_core"] = {k: single[k] for k in ("value", "cores", "sample")}
@@ -475,31 +547,39 @@ def main():
         dist.destroy_process_group()
 
 
-def fp64_timing(torch, c8r, w, n64):
-    """The FP64 path on n64 tracks of the shower, both formalisms: pairs/s."""
+def fp64_timing(torch, c8r, w, n64, reps=2, formalisms=("endpoint", "zhs"), tag="fp64"):
+    """The FP64 path on n64 tracks of workload w (drawn on the device by the
+    counter-based generator, FP32-exact values passed as FP64), each formalism:
+    pairs/s."""
     out = {}
-    tr = host_tracks(w, n64, 99)
-    d64 = {k: torch.from_numpy(v.astype(np.float64)).cuda() for k, v in tr.items()}
+    gen = c8r.c8r_generate_tracks(99, 0, n64, w["zenith"])
+    d64 = {k: v.double() for k, v in gen.items()}
+    del gen
     A = len(w["ant_xyz"])
-    for f in ("endpoint", "zhs"):
+    for f in formalisms:
         p = c8r.RadioProcess(w["medium"], w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], f, "fp64")
         p.push(d64)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(2):
+        for _ in range(reps):
             p.push(d64)
         e1.record()
         torch.cuda.synchronize()
-        out[f"fp64_{f}_pairs_per_s"] = 2 * n64 * A / (e0.elapsed_time(e1) * 1e-3)
+        out[f"{tag}_{f}_pairs_per_s"] = reps * n64 * A / (e0.elapsed_time(e1) * 1e-3)
         p.close()
     return out
 
 
 def extras(torch, c8r, synth, w):
     A = len(w["ant_xyz"])
-    # FP64 path on a sample of the same workload
-    out = fp64_timing(torch, c8r, w, 1_000_000)
+    # the FP64 path on the whole 2e7-track shower (one timed pass per formalism)
+    out = fp64_timing(torch, c8r, w, w["n_tracks"], reps=1)
+    out["fp64_workload"] = f"{w['n_tracks']:.3g} tracks x star 8x20, exponential atmosphere, 4096 x 0.2 ns, FP64"
+    # the 16-antenna FP64 Endpoint workload: 1e5 tracks, east line 25-400 m, uniform n
+    w0 = synth.workload(0)
+    out.update(fp64_timing(torch, c8r, w0, w0["n_tracks"], reps=20, formalisms=("endpoint",), tag="line16"))
+    out["line16_workload"] = "1e5 tracks x 16-antenna line (25-400 m), uniform n = 1.000292, 4096 x 0.2 ns, FP64 Endpoint"
     # the linear (two-bin) deposit, mixed precision, on 4e6 tracks of the same
     # shower (drawn on the device by the counter-based generator) and array
     n_lin = 4_000_000

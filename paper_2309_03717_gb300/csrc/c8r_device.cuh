@@ -635,6 +635,15 @@ __device__ __forceinline__ int arrival_bin_fast(const MedParams& M, const AntRec
   return (int)k;
 }
 
+// distance k + 1 - u from a float-float arrival u in bin k to the bin's upper
+// edge, formed from the arrival rather than as 1 - frac: just below an edge the
+// fraction is close to 1, where FP32 is spaced by 6e-8, while the distance is
+// small and keeps its relative precision ((k + 1) - u_h is exact there).  The
+// first bin of a narrow ZHS interval straddling an edge takes this share.
+__device__ __forceinline__ float gap_to_next_edge(ff u, int k) {
+  return __fsub_rn(__fsub_rn((float)(k + 1), u.h), u.l);
+}
+
 __device__ __forceinline__ bool bin_of(ff u, int n_bins, int& k, float& frac) {
   k = bin_raw(u, n_bins, frac);
   return k >= 0 && k < n_bins;

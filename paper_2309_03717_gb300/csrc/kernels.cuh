@@ -34,6 +34,9 @@ constexpr int kFwdMaxThreads = 512;
 // one or both endpoints whose bin the FP32 arrival left open
 // (Ops::end_deferred)
 enum : int { kDeferNone = 0, kDeferPair = 1, kDeferEnd0 = 4, kDeferEnd1 = 8 };
+// entries of the shared-memory list of second endpoints (pairs with both
+// endpoints set aside); more such pairs in a tile are taken from the queue
+constexpr int kSecondListCap = 128;
 
 // dynamic shared memory of the forward kernels: two staged track tiles, their
 // mbarriers, the antenna tile and (defer) the queue of set-aside pairs, one
@@ -227,7 +230,7 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
   __shared__ int q_cnt[2], q_back[2], q_second;
   // second endpoints of pairs with both endpoints set aside, evaluated in a
   // sweep of their own so that every sweep evaluates one endpoint per lane
-  constexpr int kSecondCap = 256;
+  constexpr int kSecondCap = kSecondListCap;
   __shared__ uint16_t second[Ops::kDefers ? kSecondCap : 1];
   if (tid == 0) {
     q_cnt[0] = q_cnt[1] = 0;
@@ -516,7 +519,10 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
   AntRec* ant_s = reinterpret_cast<AntRec*>(smem + L.ant_off);
   uint16_t* queue = reinterpret_cast<uint16_t*>(smem + L.q_off);
   __shared__ acc_t sg[3 * kMaxATile + 1];  // antenna gradients of the tile, then dN0
-  __shared__ int q_cnt[2];
+  // set-aside work as in the forward kernel: whole pairs from the front of the
+  // queue, pairs with set-aside endpoints from the back, second endpoints listed
+  __shared__ int q_cnt[2], q_back[2], q_second;
+  __shared__ uint16_t second[Ops::kDefers ? kSecondListCap : 1];
   int ant_tile;
   int64_t range;
   a.g.decode(blockIdx.x, ant_tile, range);
@@ -534,8 +540,9 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
   const uint32_t bytes = (uint32_t)L.stage_bytes;
   const unsigned char* src = static_cast<const unsigned char*>(a.tiles);
   if (tid == 0) {
-    q_cnt[0] = 0;
-    q_cnt[1] = 0;
+    q_cnt[0] = q_cnt[1] = 0;
+    q_back[0] = q_back[1] = 0;
+    q_second = 0;
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_barrier_init();
@@ -564,9 +571,15 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
       for (int ant = 0; ant < n_here; ++ant) {
         acc_t ga[3] = {0, 0, 0};
         const PrefixFF* Gp_a = Gp ? Gp + (size_t)ant * (N + 1) : nullptr;
-        if (live && Ops::adj_main(tr, Ops::load_ant(ant_s + ant), M, G + (size_t)ant * N, Gp_a, tg, ga, dn_acc) &&
-            Ops::kDefers)
-          queue[atomicAdd(&q_cnt[st], 1)] = (uint16_t)(l | (ant << 7));
+        const int code =
+            live ? Ops::adj_main(tr, Ops::load_ant(ant_s + ant), M, G + (size_t)ant * N, Gp_a, tg, ga, dn_acc)
+                 : kDeferNone;
+        if constexpr (Ops::kDefers) {
+          if (code == kDeferPair)
+            queue[atomicAdd(&q_cnt[st], 1)] = (uint16_t)(l | (ant << 7));
+          else if (code != kDeferNone)
+            queue[L.q_cap - 1 - atomicAdd(&q_back[st], 1)] = (uint16_t)(l | (ant << 7) | (code << 10));
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const acc_t v = warp_sum(ga[c]);
@@ -582,26 +595,56 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
       }
       return;
     }
-    if (Ops::kDefers) {
-      const int nq = q_cnt[st];
+    if constexpr (Ops::kDefers) {
+      const int nf = q_cnt[st], nq = nf + q_back[st];
       for (int q = tid; q < nq; q += nthr) {
-        const int e = queue[q];
-        const int l = e & (kTileT - 1), ant = e >> 7;
-        typename Ops::Track tr;
-        Ops::load(stage, l, M, tr);
-        acc_t tg[11];
-#pragma unroll
-        for (int k = 0; k < 11; ++k) tg[k] = acc_t(0);
+        const int e = q < nf ? queue[q] : queue[L.q_cap - 1 - (q - nf)];
+        const int l = e & (kTileT - 1), ant = (e >> 7) & (kMaxATile - 1);
+        const AntRec A = Ops::load_ant(ant_s + ant);
         acc_t ga[3] = {0, 0, 0};
-        Ops::adj_deferred(tr, Ops::load_ant(ant_s + ant), M, G + (size_t)ant * N,
-                          Gp ? Gp + (size_t)ant * (N + 1) : nullptr, tg, ga, dn_acc);
-        add_track_grads<acc_t>(a.out, t * kTileT + l, tg);
+        if (q < nf) {
+          typename Ops::Track tr;
+          Ops::load(stage, l, M, tr);
+          acc_t tg[11];
+#pragma unroll
+          for (int k = 0; k < 11; ++k) tg[k] = acc_t(0);
+          Ops::adj_deferred(tr, A, M, G + (size_t)ant * N, Gp ? Gp + (size_t)ant * (N + 1) : nullptr, tg, ga, dn_acc);
+          add_track_grads<acc_t>(a.out, t * kTileT + l, tg);
+        } else {
+          const int ends = (e >> 10) & (kDeferEnd0 | kDeferEnd1);
+          if (ends == (kDeferEnd0 | kDeferEnd1)) {
+            const int k = atomicAdd(&q_second, 1);
+            if (k < kSecondListCap) second[k] = (uint16_t)(e & 0xfff);
+          }
+          Ops::adj_end_deferred(stage, l, A, M, G + (size_t)ant * N, a.out, t * kTileT + l, ga, dn_acc,
+                                (ends & kDeferEnd0) ? kDeferEnd0 : kDeferEnd1);
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
           if (ga[c] != acc_t(0)) atomicAdd(&sg[3 * ant + c], ga[c]);
       }
-      __syncthreads();  // slot st is refilled below; its counter is next used two tiles on
-      if (tid == 0) q_cnt[st] = 0;
+      __syncthreads();
+      // the second endpoints (from the list, or from the queue when it overflowed)
+      const int ns = q_second, nb = nq - nf;
+      const bool overflow = ns > kSecondListCap;
+      for (int q = tid; q < (overflow ? nb : ns); q += nthr) {
+        int e;
+        if (overflow) {
+          e = queue[L.q_cap - 1 - q];
+          if (((e >> 10) & (kDeferEnd0 | kDeferEnd1)) != (kDeferEnd0 | kDeferEnd1)) continue;
+        } else {
+          e = second[q];
+        }
+        const int l = e & (kTileT - 1), ant = (e >> 7) & (kMaxATile - 1);
+        acc_t ga[3] = {0, 0, 0};
+        Ops::adj_end_deferred(stage, l, Ops::load_ant(ant_s + ant), M, G + (size_t)ant * N, a.out, t * kTileT + l,
+                              ga, dn_acc, kDeferEnd1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (ga[c] != acc_t(0)) atomicAdd(&sg[3 * ant + c], ga[c]);
+      }
+      __syncthreads();  // slot st is refilled below; its counters are next used two tiles on
+      if (tid == 0) q_cnt[st] = q_back[st] = q_second = 0;
     }
     if (tid == 0 && t + 2 < t_end) {
       mbar_expect_tx(&bar[st], bytes);

@@ -264,17 +264,20 @@ struct OpsF64 {
       zhs(T, l, A, M, out);
   }
 
-  static __device__ __forceinline__ bool adj_main(const TrackD& tr, const AntRec& A, const MedParams& M,
-                                                  const Acc4D* G, const PrefixFF* Gp, double tg[11], double ga[3],
-                                                  double& dn) {
+  static __device__ __forceinline__ int adj_main(const TrackD& tr, const AntRec& A, const MedParams& M,
+                                                 const Acc4D* G, const PrefixFF* Gp, double tg[11], double ga[3],
+                                                 double& dn) {
     if constexpr (FORM == C8R_ZHS)
       adj_zhs(tr, A, M, G, Gp, tg, ga, dn);
     else
       adj(tr, A, M, G, tg, ga, dn);
-    return false;
+    return kDeferNone;
   }
   static __device__ __forceinline__ void adj_deferred(const TrackD&, const AntRec&, const MedParams&, const Acc4D*,
                                                       const PrefixFF*, double*, double*, double&) {}
+  static __device__ __forceinline__ void adj_end_deferred(const void*, int, const AntRec&, const MedParams&,
+                                                          const Acc4D*, const c8r_track_grads&, int64_t, double*,
+                                                          double&, int) {}
 
   // ZHS adjoint (bins of the interval ends held fixed; see the mixed path for
   // the formulas): in FP64, times in ns, positions in m

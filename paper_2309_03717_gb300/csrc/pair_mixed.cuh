@@ -472,7 +472,7 @@ struct OpsMixed {
     const float invW = __fdividef(1.0f, 2.0f * hh);  // 1 / interval length in bins
     // partly covered first and last bins
     if (klo >= 0 && klo < N) {
-      const float w = (1.0f - flo) * invW;
+      const float w = gap_to_next_edge(ulo, klo) * invW;
       if (w > 0.0f) out.dep(klo, Mx * w, My * w, Mz * w);
     }
     if (khi >= 0 && khi < N) {
@@ -655,21 +655,112 @@ struct OpsMixed {
     dn += dLdopt * rg.dF_dN0;
   }
 
+  // chain rule of one one-bin Endpoint deposit (endpoint J, bin held fixed,
+  // dL/dtrace g4 at its bin) into the track gradients tg (positions of endpoint
+  // J, beta), the antenna gradient ga and dL/dN0
+  template <int J>
+  static __device__ __forceinline__ void adj_end(const GeoM& g, const FieldM& f, float nm1, float E, float kappa,
+                                                 const float4 g4, const MedParams& M, float tg[11], float ga[3],
+                                                 float& dn) {
+    const float dNdz_fac = (KIND == C8R_EXPONENTIAL) ? -M.N0f * M.invH_h : 0.0f;
+    const float gv[3] = {g4.x, g4.y, g4.z};
+    float dd[3], db[3], dns;
+    deposit_grad(g, f, 1.0f + nm1, gv, kappa, dd, db, dns);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      tg[3 * J + c] -= dd[c];
+      ga[c] += dd[c];
+      tg[8 + c] += db[c];
+    }
+    tg[3 * J + 2] += dns * dNdz_fac * E;
+    dn += dns * E;
+  }
+
   // adjoint main pass: every pair except (Endpoint) the near-Cherenkov ones, for
-  // which it adds nothing and returns true
-  static __device__ __forceinline__ bool adj_main(const TrackM& t, const AntRec& A, const MedParams& M,
-                                                  const float4* G, const PrefixFF* Gp, float tg[11], float ga[3],
-                                                  float& dn) {
+  // which it adds nothing and returns kDeferPair, and (kFastBins) the endpoints
+  // whose bin the FP32 arrival leaves open (kDeferEnd0/kDeferEnd1 bits), after
+  // the other endpoint's part
+  static __device__ __forceinline__ int adj_main(const TrackM& t, const AntRec& A, const MedParams& M,
+                                                 const float4* G, const PrefixFF* Gp, float tg[11], float ga[3],
+                                                 float& dn) {
     if constexpr (FORM == C8R_ZHS) {
       adj_zhs(t, A, M, G, Gp, tg, ga, dn);
-      return false;
+      return kDeferNone;
+    } else if constexpr (kFastBins) {
+      GeoM g0, g1;
+      float S0, S1;
+      geo_fast(A, t.x0, t.y0, t.z0, g0, S0);
+      geo_fast(A, t.x1, t.y1, t.z1, g1, S1);
+      if (g0.R0 == 0.0f || g1.R0 == 0.0f) return kDeferNone;
+      FieldM f0, f1;
+      field_mixed(g0, t.bx, t.by, t.bz, t.bmag, t.om0, __fadd_rn(1.0f, t.nm1_0), f0);
+      field_mixed(g1, t.bx, t.by, t.bz, t.bmag, t.om1, __fadd_rn(1.0f, t.nm1_1), f1);
+      if (!(fminf(fabsf(f0.D), fabsf(f1.D)) >= M.eps_C)) return kDeferPair;
+      const int ka = arrival_bin_fast<KIND>(M, A, g0, S0, t.tau0h, t.tau0l, t.E0h, t.E0l);
+      const int kb = arrival_bin_fast<KIND>(M, A, g1, S1, t.tau1h, t.tau1l, t.E1h, t.E1l);
+      if (ka >= 0) adj_end<0>(g0, f0, t.nm1_0, t.E0h, t.amp, G[ka], M, tg, ga, dn);
+      if (kb >= 0) adj_end<1>(g1, f1, t.nm1_1, t.E1h, -t.amp, G[kb], M, tg, ga, dn);
+      return (ka == kFastUndecided ? kDeferEnd0 : 0) | (kb == kFastUndecided ? kDeferEnd1 : 0);
     } else {
       EndpointEvalM e;
-      if (!endpoint_fields<KIND>(t, A, M, e)) return false;
-      if (endpoint_near_cherenkov(e, M)) return true;
+      if (!endpoint_fields<KIND>(t, A, M, e)) return kDeferNone;
+      if (endpoint_near_cherenkov(e, M)) return kDeferPair;
       endpoint_arrivals<KIND>(t, A, M, e);
       adj_deposits(t, e, M, G, tg, ga, dn);
-      return false;
+      return kDeferNone;
+    }
+  }
+
+  // the adjoint of one endpoint set aside by the main pass (kFastBins; `end` is
+  // kDeferEnd0 or kDeferEnd1), read from the staged tile (lane l) as
+  // end_deferred reads it: the float-float arrival gives the bin, the chain
+  // rule is adj_end's, and the track gradients (positions of that endpoint,
+  // beta) go to the output of track i with one reduction each; ga and dn
+  // collect the antenna and N0 parts
+  static __device__ __forceinline__ void adj_end_deferred(const void* Tv, int l, const AntRec& A, const MedParams& M,
+                                                          const float4* G, const c8r_track_grads& out, int64_t i,
+                                                          float ga[3], float& dn, int end) {
+    if constexpr (kFastBins) {
+      const float* T = static_cast<const float*>(Tv);
+      const int N = M.n_bins;
+      const int j = end == kDeferEnd1 ? 1 : 0;
+      const float amp = TF(fm::AMPE);
+      const float bx = TF(fm::BX), by = TF(fm::BY), bz = TF(fm::BZ), bmag = TF(fm::BMAG);
+      float Eh = 1.0f, El = 0.0f, nm1 = M.nm1f;
+      if (KIND != C8R_UNIFORM) {
+        Eh = TF(fm::E0H + 2 * j);
+        El = TF(fm::E0L + 2 * j);
+        nm1 = __fmul_rn(M.N0f, Eh);
+      }
+      const float om = __fsub_rn(TF(fm::OMB), __fmul_rn(nm1, bmag));
+      GeoM g;
+      geo_lite(A, TF(fm::X0 + 3 * j), TF(fm::Y0 + 3 * j), TF(fm::Z0 + 3 * j), g);
+      FieldM f;
+      field_mixed(g, bx, by, bz, bmag, om, __fadd_rn(1.0f, nm1), f);
+      GeoM gr = g;
+      geo_refine(gr);
+      const ff ua = arrival_mixed<KIND>(M, A, gr, TF(fm::TAU0H + 2 * j), TF(fm::TAU0L + 2 * j), Eh, El);
+      float fr;
+      const int k = bin_raw(ua, N, fr);
+      if (k < 0 || k >= N) return;
+      const float dNdz_fac = (KIND == C8R_EXPONENTIAL) ? -M.N0f * M.invH_h : 0.0f;
+      const float4 g4 = G[k];
+      const float gv[3] = {g4.x, g4.y, g4.z};
+      float dd[3], db[3], dns;
+      deposit_grad(g, f, 1.0f + nm1, gv, j ? -amp : amp, dd, db, dns);
+      float* px = static_cast<float*>(j ? out.x1 : out.x0);
+      float* py = static_cast<float*>(j ? out.y1 : out.y0);
+      float* pz = static_cast<float*>(j ? out.z1 : out.z0);
+      const float gz = -dd[2] + dns * dNdz_fac * Eh;
+      if (dd[0] != 0.0f) atomicAdd(px + i, -dd[0]);
+      if (dd[1] != 0.0f) atomicAdd(py + i, -dd[1]);
+      if (gz != 0.0f) atomicAdd(pz + i, gz);
+      if (db[0] != 0.0f) atomicAdd(static_cast<float*>(out.bx) + i, db[0]);
+      if (db[1] != 0.0f) atomicAdd(static_cast<float*>(out.by) + i, db[1]);
+      if (db[2] != 0.0f) atomicAdd(static_cast<float*>(out.bz) + i, db[2]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ga[c] += dd[c];
+      dn += dns * Eh;
     }
   }
   static __device__ __forceinline__ void adj_deferred(const TrackM& t, const AntRec& A, const MedParams& M,
@@ -790,7 +881,7 @@ struct OpsMixed {
       const bool inlo = klo >= 0 && klo < N, inhi = khi >= 0 && khi < N;
       const float4 glo = inlo ? G[klo] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 ghi = inhi ? G[khi] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float wlo = (1.0f - flo) * invW, whi = fhi * invW;
+      const float wlo = inlo ? gap_to_next_edge(ulo, klo) * invW : 0.0f, whi = fhi * invW;
       float ix = 0.0f, iy = 0.0f, iz = 0.0f;  // G summed over the whole bins between
       const int kb = klo + 1 < 0 ? 0 : klo + 1;
       const int ke = khi - 1 > N - 1 ? N - 1 : khi - 1;

@@ -113,8 +113,11 @@ def test_autograd_function_routes_to_the_adjoint(formalism):
     ag = torch.zeros((len(w["ant_xyz"]), 3), dtype=torch.float64, device="cuda")
     dn = torch.zeros(1, dtype=torch.float64, device="cuda")
     c8r.c8r_backward(p.ctx, dev, G, tg, ag, dn)
+    # a track's gradients are summed with FP32 reductions (one per antenna tile,
+    # and one per endpoint evaluated after the main pass) whose order differs
+    # between two runs: equal to FP32 rounding of the largest terms
     for f in c8r.GRAD_FIELDS:
-        assert torch.allclose(leaves[f].grad, tg[f], rtol=1e-5, atol=0), f
+        assert torch.allclose(leaves[f].grad, tg[f], rtol=1e-5, atol=1e-6 * float(tg[f].abs().max())), f
     # antenna and N0 gradients are summed with shared-memory atomics in FP32: the
     # order, and so the last bits, differ between two runs
     assert torch.allclose(ant.grad, ag, rtol=1e-5, atol=1e-6 * float(ag.abs().max()))
