@@ -598,9 +598,13 @@ __device__ __forceinline__ void geo_fast(const AntRec& A, float px, float py, fl
   g.R1 = 0.0f;
 }
 
+// The FP32 arrival uf of the emission point of g (and S = |d|^2) and its error
+// bound, returned; p_extra adds a relative term u * p_extra * p for geometry
+// whose d carries more than the one rounding of a_h - p (the midpoint)
 template <int KIND>
-__device__ __forceinline__ int arrival_bin_fast(const MedParams& M, const AntRec& A, const GeoM& g, float S,
-                                                float tauh, float taul, float Eeh, float Eel) {
+__device__ __forceinline__ float arrival_fast(const MedParams& M, const AntRec& A, const GeoM& g, float S,
+                                              float tauh, float taul, float Eeh, float Eel, float p_extra,
+                                              float& uf_out) {
   static_assert(KIND == C8R_UNIFORM || KIND == C8R_EXPONENTIAL, "plain straight-line media only");
   constexpr float u = 5.9604644775390625e-8f;  // 2^-24
   // R' = sqrt(S) rounded once
@@ -624,10 +628,18 @@ __device__ __forceinline__ int arrival_bin_fast(const MedParams& M, const AntRec
     v = __fmul_rn(__fmul_rn(q, R), M.cN_h);
   }
   const float uf = __fadd_rn(__fadd_rn(ts, p), v);
-  const float eps = __fmaf_rn(4.75f * u, p,
-                              __fmaf_rn(2.25f * u, fabsf(ts),
-                                        __fmaf_rn(__fmaf_rn(17.0f, u, A.fb_rel_v), fabsf(v),
-                                                  __fmaf_rn(3.25f * u, fabsf(uf), A.fb_abs))));
+  uf_out = uf;
+  return __fmaf_rn(__fmaf_rn(p_extra, u, 4.75f * u), p,
+                   __fmaf_rn(2.25f * u, fabsf(ts),
+                             __fmaf_rn(__fmaf_rn(17.0f, u, A.fb_rel_v), fabsf(v),
+                                       __fmaf_rn(3.25f * u, fabsf(uf), A.fb_abs))));
+}
+
+template <int KIND>
+__device__ __forceinline__ int arrival_bin_fast(const MedParams& M, const AntRec& A, const GeoM& g, float S,
+                                                float tauh, float taul, float Eeh, float Eel) {
+  float uf;
+  const float eps = arrival_fast<KIND>(M, A, g, S, tauh, taul, Eeh, Eel, 0.0f, uf);
   if (uf < -eps || __fsub_rn(uf, eps) >= (float)M.n_bins) return kFastOut;
   const float k = floorf(uf);
   const float fr = __fsub_rn(uf, k);

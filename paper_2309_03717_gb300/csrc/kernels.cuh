@@ -34,9 +34,12 @@ constexpr int kFwdMaxThreads = 512;
 // one or both endpoints whose bin the FP32 arrival left open
 // (Ops::end_deferred)
 enum : int { kDeferNone = 0, kDeferPair = 1, kDeferEnd0 = 4, kDeferEnd1 = 8 };
-// entries of the shared-memory list of second endpoints (pairs with both
-// endpoints set aside); more such pairs in a tile are taken from the queue
-constexpr int kSecondListCap = 128;
+// entries of each shared-memory list of the third sweep (second endpoints of
+// pairs with both endpoints set aside; near-Cherenkov pairs the FP32 check did
+// not settle as zero), forward and adjoint kernels; more such entries in a tile
+// are taken from the queue
+constexpr int kFwdListCap = 128;
+constexpr int kBwdListCap = 64;
 
 // dynamic shared memory of the forward kernels: two staged track tiles, their
 // mbarriers, the antenna tile and (defer) the queue of set-aside pairs, one
@@ -227,15 +230,17 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
   // (q_back); one counter each per staging slot.  A pair makes at most one
   // entry, so the two ends never meet.
   uint16_t* queue = reinterpret_cast<uint16_t*>(smem + L.q_off);
-  __shared__ int q_cnt[2], q_back[2], q_second;
-  // second endpoints of pairs with both endpoints set aside, evaluated in a
-  // sweep of their own so that every sweep evaluates one endpoint per lane
-  constexpr int kSecondCap = kSecondListCap;
-  __shared__ uint16_t second[Ops::kDefers ? kSecondCap : 1];
+  __shared__ int q_cnt[2], q_back[2], q_second, q_exact;
+  // two short lists for a third sweep, so that every sweep runs one kind of
+  // work per lane: the second endpoints of pairs with both endpoints set aside
+  // (list[0, cap)), and the near-Cherenkov pairs that the FP32 check could not
+  // settle as zero (list[cap, 2 cap))
+  constexpr int kCap = kFwdListCap;
+  __shared__ uint16_t list[Ops::kDefers ? 2 * kCap : 1];
   if (tid == 0) {
     q_cnt[0] = q_cnt[1] = 0;
     q_back[0] = q_back[1] = 0;
-    q_second = 0;
+    q_second = q_exact = 0;
     for (int s = 0; s < 2 && t_begin + s < t_end; ++s) {
       const int st = (int)((it + s) & 1);
       mbar_expect_tx(&bar[st], bytes);
@@ -284,38 +289,61 @@ __device__ bool stream_range(unsigned char* smem, const FwdLayout& L, uint64_t* 
         GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * row_stride, N};
         const AntRec A = Ops::load_ant(ant_s + ant);
         if (i < nf) {
-          typename Ops::Track tr;
-          Ops::load(smem + st * L.stage_bytes, l, M, tr);
-          Ops::pair_deferred(tr, A, M, sink);
+          if constexpr (Ops::kFastBins) {
+            if (!Ops::near_zero_fast(smem + st * L.stage_bytes, l, A, M)) {
+              const int k = atomicAdd(&q_exact, 1);
+              if (k < kCap) list[kCap + k] = (uint16_t)(e & 0xfff);
+            }
+          } else {
+            typename Ops::Track tr;
+            Ops::load(smem + st * L.stage_bytes, l, M, tr);
+            Ops::pair_deferred(tr, A, M, sink);
+          }
         } else {
           const int ends = (e >> 10) & (kDeferEnd0 | kDeferEnd1);
           if (ends == (kDeferEnd0 | kDeferEnd1)) {
             const int k = atomicAdd(&q_second, 1);
-            if (k < kSecondCap) second[k] = (uint16_t)(e & 0xfff);
+            if (k < kCap) list[k] = (uint16_t)(e & 0xfff);
           }
           Ops::end_deferred(smem + st * L.stage_bytes, l, A, M, sink, (ends & kDeferEnd0) ? kDeferEnd0 : kDeferEnd1);
         }
       }
       __syncthreads();
-      // the second endpoints: from the list, or (when more pairs than it holds
-      // had both endpoints set aside, which the whole CTA sees alike) from every
-      // such entry of the queue
-      const int ns = q_second, nb = nq - nf;
-      const bool overflow = ns > kSecondCap;
-      for (int i = tid; i < (overflow ? nb : ns); i += nthr) {
+      // the third sweep: the second endpoints, then the near-Cherenkov pairs for
+      // the float-float evaluation; each from its list or, when more than the
+      // list holds were set aside (the whole CTA sees the counts alike), from
+      // the queue: every pair with both endpoints set aside, every
+      // near-Cherenkov pair (those decided zero come out zero again)
+      const int ns = q_second, ne = q_exact, nb = nq - nf;
+      const bool ov2 = ns > kCap, ovE = ne > kCap;
+      const int nA = ov2 ? nb : ns, nB = Ops::kFastBins ? (ovE ? nf : ne) : 0;
+      for (int i = tid; i < nA + nB; i += nthr) {
         int e;
-        if (overflow) {
-          e = queue[L.q_cap - 1 - i];
-          if (((e >> 10) & (kDeferEnd0 | kDeferEnd1)) != (kDeferEnd0 | kDeferEnd1)) continue;
+        if (i < nA) {
+          if (ov2) {
+            e = queue[L.q_cap - 1 - i];
+            if (((e >> 10) & (kDeferEnd0 | kDeferEnd1)) != (kDeferEnd0 | kDeferEnd1)) continue;
+          } else {
+            e = list[i];
+          }
         } else {
-          e = second[i];
+          e = ovE ? queue[i - nA] : list[kCap + (i - nA)];
         }
-        const int ant = (e >> 7) & (kMaxATile - 1);
+        const int l = e & (kTileT - 1), ant = (e >> 7) & (kMaxATile - 1);
         GlobalSink<acc_t> sink{acc_row0 + (size_t)ant * row_stride, N};
-        Ops::end_deferred(smem + st * L.stage_bytes, e & (kTileT - 1), Ops::load_ant(ant_s + ant), M, sink, kDeferEnd1);
+        const AntRec A = Ops::load_ant(ant_s + ant);
+        if (i < nA) {
+          Ops::end_deferred(smem + st * L.stage_bytes, l, A, M, sink, kDeferEnd1);
+        } else {
+          typename Ops::Track tr;
+          Ops::load(smem + st * L.stage_bytes, l, M, tr);
+          Ops::pair_deferred(tr, A, M, sink);
+        }
       }
-      __syncthreads();  // slot st is refilled below; its counters are next used two tiles on
-      if (tid == 0) q_cnt[st] = q_back[st] = q_second = 0;
+      // slot st is refilled below (after the third sweep has read it); its
+      // counters are next used two tiles on
+      if (nA + nB > 0) __syncthreads();
+      if (tid == 0) q_cnt[st] = q_back[st] = q_second = q_exact = 0;
     }
     if (tid == 0 && t + 2 < t_end) {
       mbar_expect_tx(&bar[st], bytes);
@@ -520,9 +548,11 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
   uint16_t* queue = reinterpret_cast<uint16_t*>(smem + L.q_off);
   __shared__ acc_t sg[3 * kMaxATile + 1];  // antenna gradients of the tile, then dN0
   // set-aside work as in the forward kernel: whole pairs from the front of the
-  // queue, pairs with set-aside endpoints from the back, second endpoints listed
-  __shared__ int q_cnt[2], q_back[2], q_second;
-  __shared__ uint16_t second[Ops::kDefers ? kSecondListCap : 1];
+  // queue, pairs with set-aside endpoints from the back, and two short lists for
+  // a third sweep (second endpoints; near-Cherenkov pairs not settled as zero)
+  __shared__ int q_cnt[2], q_back[2], q_second, q_exact;
+  constexpr int kCap = kBwdListCap;
+  __shared__ uint16_t list[Ops::kDefers ? 2 * kCap : 1];
   int ant_tile;
   int64_t range;
   a.g.decode(blockIdx.x, ant_tile, range);
@@ -542,7 +572,7 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
   if (tid == 0) {
     q_cnt[0] = q_cnt[1] = 0;
     q_back[0] = q_back[1] = 0;
-    q_second = 0;
+    q_second = q_exact = 0;
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_barrier_init();
@@ -603,18 +633,30 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
         const AntRec A = Ops::load_ant(ant_s + ant);
         acc_t ga[3] = {0, 0, 0};
         if (q < nf) {
-          typename Ops::Track tr;
-          Ops::load(stage, l, M, tr);
-          acc_t tg[11];
+          bool exact = true;
+          if constexpr (Ops::kFastBins) {
+            // a pair settled as zero has no adjoint either
+            exact = false;
+            if (!Ops::near_zero_fast(stage, l, A, M)) {
+              const int k = atomicAdd(&q_exact, 1);
+              if (k < kCap) list[kCap + k] = (uint16_t)(e & 0xfff);
+            }
+          }
+          if (exact) {
+            typename Ops::Track tr;
+            Ops::load(stage, l, M, tr);
+            acc_t tg[11];
 #pragma unroll
-          for (int k = 0; k < 11; ++k) tg[k] = acc_t(0);
-          Ops::adj_deferred(tr, A, M, G + (size_t)ant * N, Gp ? Gp + (size_t)ant * (N + 1) : nullptr, tg, ga, dn_acc);
-          add_track_grads<acc_t>(a.out, t * kTileT + l, tg);
+            for (int k = 0; k < 11; ++k) tg[k] = acc_t(0);
+            Ops::adj_deferred(tr, A, M, G + (size_t)ant * N, Gp ? Gp + (size_t)ant * (N + 1) : nullptr, tg, ga,
+                              dn_acc);
+            add_track_grads<acc_t>(a.out, t * kTileT + l, tg);
+          }
         } else {
           const int ends = (e >> 10) & (kDeferEnd0 | kDeferEnd1);
           if (ends == (kDeferEnd0 | kDeferEnd1)) {
             const int k = atomicAdd(&q_second, 1);
-            if (k < kSecondListCap) second[k] = (uint16_t)(e & 0xfff);
+            if (k < kCap) list[k] = (uint16_t)(e & 0xfff);
           }
           Ops::adj_end_deferred(stage, l, A, M, G + (size_t)ant * N, a.out, t * kTileT + l, ga, dn_acc,
                                 (ends & kDeferEnd0) ? kDeferEnd0 : kDeferEnd1);
@@ -624,27 +666,46 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
           if (ga[c] != acc_t(0)) atomicAdd(&sg[3 * ant + c], ga[c]);
       }
       __syncthreads();
-      // the second endpoints (from the list, or from the queue when it overflowed)
-      const int ns = q_second, nb = nq - nf;
-      const bool overflow = ns > kSecondListCap;
-      for (int q = tid; q < (overflow ? nb : ns); q += nthr) {
+      // the third sweep, as in the forward kernel: second endpoints, then the
+      // near-Cherenkov pairs for the float-float evaluation (from the lists, or
+      // from the queue when a list overflowed)
+      const int ns = q_second, ne = q_exact, nb = nq - nf;
+      const bool ov2 = ns > kCap, ovE = ne > kCap;
+      const int nA = ov2 ? nb : ns, nB = Ops::kFastBins ? (ovE ? nf : ne) : 0;
+      for (int q = tid; q < nA + nB; q += nthr) {
         int e;
-        if (overflow) {
-          e = queue[L.q_cap - 1 - q];
-          if (((e >> 10) & (kDeferEnd0 | kDeferEnd1)) != (kDeferEnd0 | kDeferEnd1)) continue;
+        if (q < nA) {
+          if (ov2) {
+            e = queue[L.q_cap - 1 - q];
+            if (((e >> 10) & (kDeferEnd0 | kDeferEnd1)) != (kDeferEnd0 | kDeferEnd1)) continue;
+          } else {
+            e = list[q];
+          }
         } else {
-          e = second[q];
+          e = ovE ? queue[q - nA] : list[kCap + (q - nA)];
         }
         const int l = e & (kTileT - 1), ant = (e >> 7) & (kMaxATile - 1);
+        const AntRec A = Ops::load_ant(ant_s + ant);
         acc_t ga[3] = {0, 0, 0};
-        Ops::adj_end_deferred(stage, l, Ops::load_ant(ant_s + ant), M, G + (size_t)ant * N, a.out, t * kTileT + l,
-                              ga, dn_acc, kDeferEnd1);
+        if (q < nA) {
+          Ops::adj_end_deferred(stage, l, A, M, G + (size_t)ant * N, a.out, t * kTileT + l, ga, dn_acc, kDeferEnd1);
+        } else {
+          typename Ops::Track tr;
+          Ops::load(stage, l, M, tr);
+          acc_t tg[11];
+#pragma unroll
+          for (int k = 0; k < 11; ++k) tg[k] = acc_t(0);
+          Ops::adj_deferred(tr, A, M, G + (size_t)ant * N, Gp ? Gp + (size_t)ant * (N + 1) : nullptr, tg, ga, dn_acc);
+          add_track_grads<acc_t>(a.out, t * kTileT + l, tg);
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
           if (ga[c] != acc_t(0)) atomicAdd(&sg[3 * ant + c], ga[c]);
       }
-      __syncthreads();  // slot st is refilled below; its counters are next used two tiles on
-      if (tid == 0) q_cnt[st] = q_back[st] = q_second = 0;
+      // slot st is refilled below (after the third sweep has read it); its
+      // counters are next used two tiles on
+      if (nA + nB > 0) __syncthreads();
+      if (tid == 0) q_cnt[st] = q_back[st] = q_second = q_exact = 0;
     }
     if (tid == 0 && t + 2 < t_end) {
       mbar_expect_tx(&bar[st], bytes);

@@ -121,6 +121,7 @@ struct OpsF64 {
   static constexpr int kTileBytes = kTileBytesF64;
   static constexpr int kMinBlocks = 4;
   static constexpr bool kDefers = false;  // every pair is evaluated in the main pass
+  static constexpr bool kFastBins = false;
   static constexpr int kBwdMinBlocks = 2;
   static constexpr int kAccRows = 1;      // no box deposits
 
@@ -148,6 +149,9 @@ struct OpsF64 {
   static __device__ __forceinline__ void pair_deferred(const TrackD&, const AntRec&, const MedParams&, Sink&) {}
   template <class Sink>
   static __device__ __forceinline__ void end_deferred(const void*, int, const AntRec&, const MedParams&, Sink&, int) {}
+  static __device__ __forceinline__ bool near_zero_fast(const void*, int, const AntRec&, const MedParams&) {
+    return false;
+  }
 
   template <class Sink>
   static __device__ __forceinline__ void endpoint(const double* T, int l, const AntRec& A, const MedParams& M,

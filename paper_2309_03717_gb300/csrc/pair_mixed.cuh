@@ -527,6 +527,67 @@ struct OpsMixed {
     }
   }
 
+  // A near-Cherenkov pair (kFastBins) whose two linearised arrivals
+  // u_m -/+ D_m (t1 - t0)/(2 dt) lie in one bin, or both before or both after
+  // the window, contributes exactly 0 (reading C), and so does its adjoint.
+  // Decided here from FP32 midpoint geometry, as arrival_bin_fast decides a
+  // bin: the midpoint d_m = (s0 + s1)/2 from the endpoints' FP32 d (the
+  // float-float path's high part; its rounding adds u (R + L) to the distance,
+  // so the arrival bound takes 1 more u p and 2 u k L1, L1 >= L), the FP32
+  // Doppler factor D_m (field_mixed: off the float-float D_m by at most
+  // 8 u n + 16 u |D_m|, from the direction's rounding and its own), and two
+  // more roundings on the interval ends.  True when the pair is decided to be
+  // zero, false when the float-float evaluation must run (about 4 % of the
+  // near-Cherenkov pairs of a shower).
+  static __device__ __forceinline__ bool near_zero_fast(const void* Tv, int l, const AntRec& A, const MedParams& M) {
+    if constexpr (kFastBins) {
+      constexpr float u = 5.9604644775390625e-8f;  // 2^-24
+      const float* T = static_cast<const float*>(Tv);
+      const float x0 = TF(fm::X0), y0 = TF(fm::Y0), z0 = TF(fm::Z0);
+      const float x1 = TF(fm::X1), y1 = TF(fm::Y1), z1 = TF(fm::Z1);
+      const float a0x = __fadd_rn(A.xh, -x0), a0y = __fadd_rn(A.yh, -y0), a0z = __fadd_rn(A.zh, -z0);
+      const float a1x = __fadd_rn(A.xh, -x1), a1y = __fadd_rn(A.yh, -y1), a1z = __fadd_rn(A.zh, -z1);
+      GeoM g;
+      g.s[0] = 0.5f * __fadd_rn(a0x, a1x);
+      g.s[1] = 0.5f * __fadd_rn(a0y, a1y);
+      g.s[2] = 0.5f * __fadd_rn(a0z, a1z);
+      const float S = __fmaf_rn(g.s[0], g.s[0], __fmaf_rn(g.s[1], g.s[1], __fmul_rn(g.s[2], g.s[2])));
+      g.y = rsqrtf(S);
+      g.R0 = __fmul_rn(S, g.y);
+      g.R1 = 0.0f;
+      if (g.R0 == 0.0f) return true;  // the midpoint on the antenna: no deposit
+      const float L1 = fabsf(__fsub_rn(a0x, a1x)) + fabsf(__fsub_rn(a0y, a1y)) + fabsf(__fsub_rn(a0z, a1z));
+      const float bx = TF(fm::BX), by = TF(fm::BY), bz = TF(fm::BZ), bmag = TF(fm::BMAG);
+      float Eh = 1.0f, El = 0.0f, nm1 = M.nm1f;
+      if (KIND != C8R_UNIFORM) {
+        Eh = TF(fm::EMH);
+        El = TF(fm::EML);
+        nm1 = __fmul_rn(M.N0f, Eh);
+      }
+      const float om = __fsub_rn(TF(fm::OMB), __fmul_rn(nm1, bmag));
+      FieldM f;
+      field_mixed(g, bx, by, bz, bmag, om, __fadd_rn(1.0f, nm1), f);
+      // midpoint time (t0 + t1)/(2 dt), float-float, as load_track_mixed forms it
+      float tmh, tml;
+      two_sum(TF(fm::TAU0H), TF(fm::TAU1H), tmh, tml);
+      tml = __fadd_rn(tml, __fadd_rn(TF(fm::TAU0L), TF(fm::TAU1L)));
+      tmh *= 0.5f;
+      tml *= 0.5f;
+      float uf;
+      const float kh = KIND == C8R_UNIFORM ? M.s_h : M.kc_h;
+      const float eps_u = __fmaf_rn(2.0f * u * kh, L1, arrival_fast<KIND>(M, A, g, S, tmh, tml, Eh, El, 1.0f, uf));
+      const float dtau = TF(fm::DTAUH);
+      const float aD = fabsf(f.D);
+      const float h = 0.5f * __fmul_rn(aD, dtau);
+      const float dh = __fmul_rn(__fmaf_rn(16.0f * u, aD, 8.0f * u * __fadd_rn(1.0f, nm1)), dtau);
+      const float e = __fadd_rn(__fadd_rn(eps_u, dh), 2.0f * u * __fadd_rn(fabsf(uf), h));
+      const float lo = __fsub_rn(__fsub_rn(uf, h), e), hi = __fadd_rn(__fadd_rn(uf, h), e);
+      return hi < 0.0f || lo >= (float)M.n_bins || floorf(lo) == floorf(hi);
+    } else {
+      return false;
+    }
+  }
+
   // one endpoint set aside by the main pass (kFastBins; `end` is kDeferEnd0 or
   // kDeferEnd1), read from the staged tile (lane l): its float-float arrival
   // decides the bin.  The endpoint's fields are picked by index, so lanes with
