@@ -474,6 +474,28 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// The sums over the 32 lanes of a warp of three values (a, b, c) by a
+// reduce-scatter: at offset 16 the lower half keeps (a, b) and the upper half
+// (c, 0), each sending the pair it does not keep; at offset 8 each lane keeps
+// one of its two partial sums; offsets 4, 2 and 1 finish them.  Six shuffles
+// instead of three sums' fifteen.  Lanes 0-7 return the sum of a, lanes 8-15
+// that of b, lanes 16-23 that of c (lanes 24-31: 0).  Every lane must call it.
+template <typename T>
+__device__ __forceinline__ T warp_sum3(T a, T b, T c, int lane) {
+  const bool h16 = (lane & 16) != 0;
+  T k0 = h16 ? c : a, k1 = h16 ? T(0) : b;
+  const T s0 = h16 ? a : c, s1 = h16 ? b : T(0);
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+  const bool h8 = (lane & 8) != 0;
+  T v = h8 ? k1 : k0;
+  v += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
 // Refractivity part F = (n_avg - 1) R of the optical path R + F and its
 // derivatives (reading M; the ZHS adjoint needs them, the Endpoint deposits do
 // not depend on the arrival time).  Exponential medium: F = N0 E_m R rho(x),
@@ -610,11 +632,9 @@ __global__ void __launch_bounds__(kTileT, Ops::kBwdMinBlocks) k_backward(const B
           else if (code != kDeferNone)
             queue[L.q_cap - 1 - atomicAdd(&q_back[st], 1)] = (uint16_t)(l | (ant << 7) | (code << 10));
         }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const acc_t v = warp_sum(ga[c]);
-          if ((tid & 31) == 0 && v != acc_t(0)) atomicAdd(&sg[3 * ant + c], v);
-        }
+        const int lane = tid & 31;
+        const acc_t v = warp_sum3(ga[0], ga[1], ga[2], lane);  // x at lane 0, y at 8, z at 16
+        if ((lane & 7) == 0 && lane < 24 && v != acc_t(0)) atomicAdd(&sg[3 * ant + (lane >> 3)], v);
       }
       if (live) add_track_grads<acc_t>(a.out, i, tg);
     }
