@@ -301,3 +301,42 @@ def test_constructed_near_cherenkov_pairs(medium_name, D, place, formalism, prec
     err = np.abs(gpu - ref).max() / np.abs(ref).max()
     assert err <= tol, f"largest element difference {err:.3e} of the largest element (bar {tol:.1e})"
     np.testing.assert_array_equal(gpu != 0, ref != 0)
+
+
+@pytest.mark.parametrize("medium", [{"kind": "uniform", "n": 1.78},
+                                    {"kind": "exponential", "N0": 0.1, "H": 1000.0}])
+@pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_dense_media_match_oracle(medium, formalism, precision, tol):
+    """Dense media, where the FP32 arrival's error bound (and the refractivity
+    term in it) is far from the air showers': ice (n = 1.78, a wide Cherenkov
+    cone, many near-Cherenkov pairs, most arrivals outside the window) and a
+    steep exponential atmosphere (N0 = 0.1, H = 1 km).  In ice the antennas lie
+    0.6-3 km from the axis on one line, where some tracks see them near the 56
+    degree cone.  Every window is placed around the median of the oracle's
+    arrivals at that antenna."""
+    w = synth.workload(0, n_tracks=8009, n_ant=16)
+    w["medium"] = dict(medium)
+    if medium["kind"] == "uniform":
+        w["ant_xyz"] = np.stack([np.linspace(600.0, 3000.0, 16), np.zeros(16), np.zeros(16)], 1)
+    if precision == "mixed":
+        w["dtype"] = np.float32
+    tracks = synth.workload_tracks(w)
+    _, u0 = oracle_arrivals(tracks, w["ant_xyz"], np.zeros(16), 1, w["dt_ns"], w["medium"], formalism)
+    w["t_start_ns"] = np.median(u0.reshape(len(tracks["x0"]), 16, 2)[..., 0], axis=0) * w["dt_ns"] - 300.0
+    ref, kept = oracle_traces(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], formalism)
+    gpu, arr, st = run(w, tracks, formalism, precision)
+    assert st["tracks_kept"] == kept
+    assert np.abs(ref).max() > 0
+    obr, ou = oracle_arrivals(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], formalism)
+    if formalism == "endpoint":
+        ref = either_bin_reference(gpu, ref, tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"],
+                                   w["medium"])
+        assert (obr == 1).sum() > 0
+    err = rel_l2(gpu, ref)
+    assert err <= tol, f"relative L2 {err:.3e} > {tol:.0e}"
+    n_cmp, _ = compare_bins(arr[0], arr[1], arr[2], obr, ou, w["n_bins"])
+    # most arrivals here lie outside the window, where the listing clamps a ZHS
+    # interval to one bin; every arrival of a pair that reaches it is compared
+    reach = ~((ou < 0).all(axis=-1) | (ou >= w["n_bins"]).all(axis=-1))
+    assert reach.sum() > 1000 and n_cmp > 0.99 * 2 * reach.sum()
