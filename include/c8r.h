@@ -67,6 +67,11 @@ extern "C" {
 #define C8R_DEPOSIT_BIN 0     /* each deposit in the bin of its arrival time (default)    */
 #define C8R_DEPOSIT_LINEAR 1  /* spread over one bin width centred on the arrival time    */
 
+/* form of the FP32 arrival of the mixed one-bin Endpoint kernels (c8r_set_arrival_form) */
+#define C8R_FORM_AUTO 0    /* chosen per push from earlier pushes' tracks (default)      */
+#define C8R_FORM_SPLIT 1   /* lines of sight near the vertical                           */
+#define C8R_FORM_DIRECT 2  /* inclined lines of sight                                    */
+
 typedef struct c8r_ctx c8r_ctx;
 
 /* Particle tracks in structure-of-arrays form: twelve DEVICE arrays of one
@@ -105,6 +110,8 @@ typedef struct {
   int64_t tracks_pushed; /* tracks passed to c8r_push_tracks since creation/reset    */
   int64_t tracks_kept;   /* of those, tracks the track filter let through           */
   int64_t pairs;         /* kept tracks x antennas evaluated                         */
+  int64_t arrival_form;  /* C8R_FORM_SPLIT or C8R_FORM_DIRECT: the FP32 arrival form the
+                            next mixed one-bin Endpoint launch takes (c8r_set_arrival_form) */
 } c8r_stats_t;
 
 /* Writable DEVICE arrays for c8r_generate_tracks, one per track field. */
@@ -214,6 +221,25 @@ int c8r_set_deposit(c8r_ctx* ctx, int deposit);
  * through the same scratch.  EINVAL outside a_tile 0..32, waves 0..1024,
  * chunk_tracks >= 0. */
 int c8r_set_launch_shape(c8r_ctx* ctx, int a_tile, int waves, int64_t chunk_tracks);
+
+/* Form of the FP32 arrival with which the mixed-precision Endpoint kernels of
+ * the one-bin deposit (uniform and exponential media) take each bin: the
+ * arrival t_e/dt - t_a/dt + n R/(c dt) is evaluated as (T_e - T_a) + k x,
+ * T = t/dt + k z formed once per track endpoint and per antenna, x = R - (z_e -
+ * z_a), either as rho^2 / (R + z_e - z_a) (C8R_FORM_SPLIT: small errors for
+ * emission points seen from the antenna near the vertical) or as R - (z_e -
+ * z_a) (C8R_FORM_DIRECT: inclined lines of sight).  A bin is taken from the FP32
+ * arrival only where its error bound leaves no bin edge in reach, otherwise
+ * from the float-float arrival, so both forms give the same bins; the form only
+ * sets how many arrivals need the float-float evaluation, i.e. the speed.
+ * C8R_FORM_AUTO (default): the ingest of every push counts the tracks whose
+ * start point sees the antenna array's centroid from above within 45 degrees,
+ * the counts are copied back asynchronously, and later pushes and adjoints use
+ * the split form when at least half of the tracks counted do (the split form
+ * until a count has arrived; c8r_set_antennas with a new layout starts over).
+ * Other precisions, media and deposits ignore the setting.  EINVAL for another
+ * value. */
+int c8r_set_arrival_form(c8r_ctx* ctx, int form);
 
 /* ---- the hot path ----------------------------------------------------------- */
 

@@ -31,6 +31,7 @@ C8R_ENDPOINT, C8R_ZHS = 0, 1
 C8R_FP64, C8R_MIXED = 0, 1
 C8R_F32, C8R_F64 = 0, 1
 C8R_DEPOSIT_BIN, C8R_DEPOSIT_LINEAR = 0, 1
+C8R_FORM_AUTO, C8R_FORM_SPLIT, C8R_FORM_DIRECT = 0, 1, 2
 
 TRACK_FIELDS = ("x0", "y0", "z0", "x1", "y1", "z1", "t0", "t1", "bx", "by", "bz", "q")
 GRAD_FIELDS = TRACK_FIELDS[:-1]
@@ -51,7 +52,8 @@ class c8r_track_grads(ctypes.Structure):
 
 
 class c8r_stats_t(ctypes.Structure):
-    _fields_ = [("tracks_pushed", ctypes.c_int64), ("tracks_kept", ctypes.c_int64), ("pairs", ctypes.c_int64)]
+    _fields_ = [("tracks_pushed", ctypes.c_int64), ("tracks_kept", ctypes.c_int64), ("pairs", ctypes.c_int64),
+                ("arrival_form", ctypes.c_int64)]
 
 
 class c8r_batch_desc(ctypes.Structure):
@@ -85,6 +87,7 @@ _SIGNATURES = [
     ("c8r_set_cherenkov_threshold", ctypes.c_int, [_P, ctypes.c_double]),
     ("c8r_set_deposit", ctypes.c_int, [_P, ctypes.c_int]),
     ("c8r_set_launch_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64]),
+    ("c8r_set_arrival_form", ctypes.c_int, [_P, ctypes.c_int]),
     ("c8r_push_tracks", ctypes.c_int, [_P, ctypes.POINTER(c8r_tracks), ctypes.c_int64, _P]),
     ("c8r_fetch_traces", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P]),
     ("c8r_reset", ctypes.c_int, [_P, _P]),
@@ -220,6 +223,10 @@ def c8r_set_launch_shape(ctx, a_tile=0, waves=0, chunk_tracks=0):
     return _check(ctx, load().c8r_set_launch_shape(ctx, int(a_tile), int(waves), int(chunk_tracks)))
 
 
+def c8r_set_arrival_form(ctx, form):
+    return _check(ctx, load().c8r_set_arrival_form(ctx, int(form)))
+
+
 def c8r_push_tracks(ctx, tracks: dict, stream=None):
     s = tracks_struct(tracks)
     n = tracks["x0"].numel()
@@ -240,7 +247,8 @@ def c8r_reset(ctx, stream=None):
 def c8r_stats(ctx):
     st = c8r_stats_t()
     _check(ctx, load().c8r_stats(ctx, ctypes.byref(st)))
-    return {"tracks_pushed": st.tracks_pushed, "tracks_kept": st.tracks_kept, "pairs": st.pairs}
+    return {"tracks_pushed": st.tracks_pushed, "tracks_kept": st.tracks_kept, "pairs": st.pairs,
+            "arrival_form": {C8R_FORM_SPLIT: "split", C8R_FORM_DIRECT: "direct"}.get(st.arrival_form, "?")}
 
 
 def c8r_profile(ctx, enable=True):
@@ -330,6 +338,7 @@ _MEDIUM = {"uniform": C8R_UNIFORM, "exponential": C8R_EXPONENTIAL, "exponential_
 _FORMALISM = {"endpoint": C8R_ENDPOINT, "coreas": C8R_ENDPOINT, "zhs": C8R_ZHS}
 _PRECISION = {"fp64": C8R_FP64, "mixed": C8R_MIXED}
 _DEPOSIT = {"bin": C8R_DEPOSIT_BIN, "linear": C8R_DEPOSIT_LINEAR}
+_FORM = {"auto": C8R_FORM_AUTO, "split": C8R_FORM_SPLIT, "direct": C8R_FORM_DIRECT}
 
 
 class RadioProcess:
@@ -406,6 +415,11 @@ class RadioProcess:
 
     def set_launch_shape(self, a_tile=0, waves=0, chunk_tracks=0):
         c8r_set_launch_shape(self.ctx, a_tile, waves, chunk_tracks)
+
+    def set_arrival_form(self, form="auto"):
+        """Pin ("split", "direct") or free ("auto") the form of the FP32 arrival
+        of the mixed one-bin Endpoint kernels; the bins are the same either way."""
+        c8r_set_arrival_form(self.ctx, _FORM[form])
 
     def push(self, tracks: dict, stream=None):
         c8r_push_tracks(self.ctx, tracks, stream)

@@ -105,16 +105,34 @@ void fill_antenna(AntRec& r, double x, double y, double z, double t_ref_ns, cons
   split(z, r.zh, r.zl);
   split(t_ref_ns / M.dt_ns, r.tauh, r.taul);
   split(r.Ea, r.Eah, r.Eal);
-  // error-bound constants of the FP32 arrival (arrival_bin_fast): bins per
-  // metre (n/(c dt), or (1 + N0)/(c dt) as an upper bound for the exponential
-  // medium) times the neglected low part of the position, plus a floor of
-  // 1e-6 bin; and the relative error of the refractivity term from the low
-  // part of the altitude where the quotient is taken (|dz| > 1e-3 H)
+  // the antenna's shifted time of the FP32 arrival (arrival_fast): t_ref/dt +
+  // k z with the same float-float k the kernels use (n/(c dt) in the uniform
+  // medium, 1/(c dt) in the exponential one), at the exact altitude
+  const double kff = M.kind == C8R_UNIFORM ? (double)M.s_h + (double)M.s_l : (double)M.kc_h + (double)M.kc_l;
+  const double Ta = t_ref_ns / M.dt_ns + kff * z;
+  split(Ta, r.Tah, r.Tal);
+  // error-bound constants of the FP32 arrival (arrival_bin_fast): twice the
+  // bins per metre (n/(c dt), or (1 + N0)/(c dt) as an upper bound for the
+  // exponential medium) times the neglected low part of the position, 16 u^2
+  // |T_a| (u = 2^-24) for the float-float shifted times, and a floor of 1e-6
+  // bin; and the relative error of the refractivity term from the low part of
+  // the altitude where the quotient is taken (|dz| > 1e-3 H)
   const double kc = 1.0 / (kCns * M.dt_ns);
   const double nmax = M.kind == C8R_UNIFORM ? M.n : 1.0 + M.N0;
   const double al = std::sqrt((double)r.xl * r.xl + (double)r.yl * r.yl + (double)r.zl * r.zl);
-  r.fb_abs = (float)(1.01 * nmax * kc * al + 1e-6);
+  const double u = 1.0 / 16777216.0;
+  r.fb_abs = (float)(2.02 * nmax * kc * al + 16.0 * u * u * std::fabs(Ta) + 1e-6);
   r.fb_rel_v = M.kind == C8R_UNIFORM ? 0.0f : (float)(1.01 * std::fabs((double)r.zl) / (0.999e-3 * M.H));
+}
+
+void set_form_centroid(MedParams& M, const double* pos_xyz, int n_ant) {
+  double c[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < n_ant; ++a)
+    for (int k = 0; k < 3; ++k) c[k] += pos_xyz[3 * (size_t)a + k];
+  const double inv = n_ant > 0 ? 1.0 / n_ant : 0.0;
+  M.cen_x = (float)(c[0] * inv);
+  M.cen_y = (float)(c[1] * inv);
+  M.cen_z = (float)(c[2] * inv);
 }
 
 // the default launch shape: 32 antennas per CTA, 32 waves (a sweep over
@@ -154,9 +172,17 @@ struct c8r_ctx {
   void* d_tiles = nullptr;
   int64_t tiles_cap = 0;      // tiles allocated
   int64_t chunk_tracks = (int64_t)1 << 25;
-  // counters (device): kept tracks, error word
+  // counters (device): kept tracks, then the two arrival-form votes of the
+  // ingest (kept tracks, tracks seeing the array from above); error word
   unsigned long long* d_kept = nullptr;
   int* d_err = nullptr;
+  // the arrival form of the one-bin Endpoint kernels (MedParams::split) and
+  // the asynchronous read-back of the votes it is chosen from
+  bool split = true;
+  int form_mode = C8R_FORM_AUTO;         // c8r_set_arrival_form
+  unsigned long long* h_form = nullptr;  // pinned: [kept tracks, seen from above]
+  cudaEvent_t ev_form = nullptr;
+  bool form_pending = false;
   int64_t pushed = 0;
   cudaStream_t last_stream = nullptr;
   FwdShape shape{1, 8};
@@ -178,6 +204,55 @@ int cuda_fail(c8r_ctx* c, cudaError_t e, const char* where) {
   return fail(c, C8R_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// the arrival form of the one-bin Endpoint kernels (MedParams::split), from the
+// ingest's votes of earlier pushes: the split form when at least half of the
+// tracks counted see the antenna array's centroid from above within 45
+// degrees.  The votes are copied to pinned memory after a push and read once
+// the copy has landed, so no launch waits for them; both forms give the same
+// bins, the choice only sets the speed.
+void form_poll(c8r_ctx* c) {
+  if (c->form_mode != C8R_FORM_AUTO) {
+    c->split = c->form_mode == C8R_FORM_SPLIT;
+    c->M.split = c->split ? 1 : 0;
+    return;
+  }
+  if (!c->form_pending) return;
+  const cudaError_t q = cudaEventQuery(c->ev_form);
+  if (q == cudaErrorNotReady) {
+    if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();
+    return;
+  }
+  c->form_pending = false;
+  if (q != cudaSuccess || c->h_form[0] == 0) return;
+  c->split = 2 * c->h_form[1] >= c->h_form[0];
+  c->M.split = c->split ? 1 : 0;
+}
+
+void form_fetch(c8r_ctx* c, cudaStream_t st) {
+  if (c->form_mode != C8R_FORM_AUTO || c->form_pending || !c->h_form || !c->ev_form || c->precision != C8R_MIXED)
+    return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
+  if (cudaMemcpyAsync(c->h_form, c->d_kept + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaEventRecord(c->ev_form, st) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  c->form_pending = true;
+}
+
+// a new antenna layout or medium: earlier votes no longer apply
+void form_reset(c8r_ctx* c) {
+  if (c->form_pending) cudaEventSynchronize(c->ev_form);
+  c->form_pending = false;
+  cudaMemset(c->d_kept + 1, 0, 2 * sizeof(unsigned long long));
+  c->split = c->form_mode != C8R_FORM_DIRECT;
+}
+
 bool finite_all(const double* p, size_t n) {
   for (size_t i = 0; i < n; ++i)
     if (!std::isfinite(p[i])) return false;
@@ -187,6 +262,8 @@ bool finite_all(const double* p, size_t n) {
 int rebuild_tables(c8r_ctx* c) {
   if (!c->ants_set) return C8R_OK;
   fill_medium(c->M, c->med_kind, c->med_a, c->med_H, c->n_bins, c->dt_ns, c->eps_C, c->med_RE);
+  set_form_centroid(c->M, c->pos.data(), c->n_ant);
+  c->M.split = c->split ? 1 : 0;
   std::vector<AntRec> recs(c->n_ant);
   for (int a = 0; a < c->n_ant; ++a)
     fill_antenna(recs[a], c->pos[3 * a], c->pos[3 * a + 1], c->pos[3 * a + 2], c->t_start[a], c->M);
@@ -293,14 +370,24 @@ int c8r_create(c8r_ctx** out, int device) {
   }
   c->device = device;
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
-  e = dev_malloc(&c->d_kept, sizeof(unsigned long long));
+  e = dev_malloc(&c->d_kept, 3 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = dev_malloc(&c->d_err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(c->d_kept, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(c->d_kept, 0, 3 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e != cudaSuccess) {
     g_create_error = std::string("context allocation: ") + cudaGetErrorString(e);
     c8r_destroy(c);
     return C8R_ENOMEM;
+  }
+  // the read-back of the arrival-form votes is an optimisation: without its
+  // pinned buffer or event the split form stays chosen
+  if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_form), 2 * sizeof(unsigned long long), cudaHostAllocDefault) !=
+          cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_form, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->h_form) cudaFreeHost(c->h_form);
+    c->h_form = nullptr;
+    c->ev_form = nullptr;
   }
   *out = c;
   return C8R_OK;
@@ -319,6 +406,8 @@ void c8r_destroy(c8r_ctx* c) {
   if (c->d_tiles) cudaFree(c->d_tiles);
   if (c->d_kept) cudaFree(c->d_kept);
   if (c->d_err) cudaFree(c->d_err);
+  if (c->ev_form) cudaEventDestroy(c->ev_form);
+  if (c->h_form) cudaFreeHost(c->h_form);
   delete c;
 }
 
@@ -431,6 +520,7 @@ int c8r_set_antennas(c8r_ctx* c, int32_t n_ant, const double* pos, const double*
   c->ants_set = true;
   c->pushed = 0;
   cudaMemset(c->d_kept, 0, sizeof(unsigned long long));
+  form_reset(c);
   return rebuild_tables(c);
 }
 
@@ -449,6 +539,18 @@ int c8r_set_launch_shape(c8r_ctx* c, int a_tile, int waves, int64_t chunk_tracks
   return C8R_OK;
 }
 
+int c8r_set_arrival_form(c8r_ctx* c, int form) {
+  if (!c) return C8R_EINVAL;
+  if (form != C8R_FORM_AUTO && form != C8R_FORM_SPLIT && form != C8R_FORM_DIRECT)
+    return fail(c, C8R_EINVAL, "unknown arrival form");
+  c->form_mode = form;
+  if (form != C8R_FORM_AUTO) {
+    c->split = form == C8R_FORM_SPLIT;
+    c->M.split = c->split ? 1 : 0;
+  }
+  return C8R_OK;
+}
+
 int c8r_push_tracks(c8r_ctx* c, const c8r_tracks* t, int64_t n, void* stream) {
   int r = ready(c);
   if (r != C8R_OK) return r;
@@ -460,6 +562,7 @@ int c8r_push_tracks(c8r_ctx* c, const c8r_tracks* t, int64_t n, void* stream) {
   const int64_t chunk = n < c->chunk_tracks ? n : c->chunk_tracks;
   if ((r = ensure_tiles(c, chunk)) != C8R_OK) return r;
   const bool lin = c->deposit == C8R_DEPOSIT_LINEAR;
+  form_poll(c);
   for (int64_t off = 0; off < n; off += chunk) {
     const int64_t m = (n - off) < chunk ? (n - off) : chunk;
     TrackPtrs p = offset_tracks(t, off);
@@ -470,7 +573,7 @@ int c8r_push_tracks(c8r_ctx* c, const c8r_tracks* t, int64_t n, void* stream) {
       e2 = take_event(c);
       cudaEventRecord(e0, st);
     }
-    cudaError_t e = launch_ingest(c->precision, p, m, c->d_tiles, c->M, c->d_kept, st);
+    cudaError_t e = launch_ingest(c->precision, p, m, c->d_tiles, c->M, c->d_kept, st, c->d_kept + 1);
     if (e != cudaSuccess) return cuda_fail(c, e, "ingest launch");
     if (c->profiling) cudaEventRecord(e1, st);
     const int64_t n_tiles = (m + kTileT - 1) / kTileT;
@@ -488,6 +591,7 @@ int c8r_push_tracks(c8r_ctx* c, const c8r_tracks* t, int64_t n, void* stream) {
       c->ev_pair.push_back({e1, e2});
     }
   }
+  form_fetch(c, st);
   c->pushed += n;
   return C8R_OK;
 }
@@ -597,6 +701,10 @@ int c8r_stats(c8r_ctx* c, c8r_stats_t* out) {
   out->tracks_pushed = c->pushed;
   out->tracks_kept = (int64_t)kept;
   out->pairs = (int64_t)kept * c->n_ant;
+  // the stream has drained: the votes' copy, if one was made, has landed
+  if (c->form_pending) cudaEventSynchronize(c->ev_form);
+  form_poll(c);
+  out->arrival_form = c->split ? C8R_FORM_SPLIT : C8R_FORM_DIRECT;
   if (err != kErrNone) {
     cudaMemset(c->d_err, 0, sizeof(int));
     return fail(c, C8R_ECANCELLED, "a kernel gave up a bounded wait on its track pipeline; results are incomplete");
@@ -674,6 +782,7 @@ int c8r_backward(c8r_ctx* c, const c8r_tracks* t, int64_t n, const void* grad_tr
     if (e == cudaSuccess && prefix) e = launch_bin_running_sums(c->d_gbm, c->n_ant, c->n_bins, c->d_gpre, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "gradient layout");
   }
+  form_poll(c);
   for (int64_t off = 0; off < n; off += chunk) {
     const int64_t m = (n - off) < chunk ? (n - off) : chunk;
     cudaError_t e = launch_ingest(c->precision, offset_tracks(t, off), m, c->d_tiles, c->M, nullptr, st);

@@ -108,8 +108,6 @@ __global__ void __launch_bounds__(kTileT, Ops::kMinBlocks) k_batch(const BatchAr
   }
 }
 
-using BatchOps = OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>;
-
 // resident CTAs per SM of the batch kernel for antenna tiles of a_tile
 template <class Ops>
 int batch_blocks_per_sm(int a_tile) {
@@ -132,21 +130,25 @@ cudaError_t launch_batch_ops(const BatchArgs& a, int sm_count, cudaStream_t st) 
 }
 
 template <class F>
-auto with_batch_ops(int formalism, int kind, F f) {
+auto with_batch_ops(int formalism, int kind, bool split, F f) {
   const bool ex = kind == C8R_EXPONENTIAL;
-  if (formalism == C8R_ENDPOINT)
+  if (formalism == C8R_ENDPOINT) {
+    if (split)  // the arrival form of the one-bin Endpoint kernel (OpsMixed::kSplit)
+      return ex ? f(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, false, true>{})
+                : f(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, false, true>{});
     return ex ? f(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>{}) : f(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>{});
+  }
   return ex ? f(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL>{}) : f(OpsMixed<C8R_ZHS, C8R_UNIFORM>{});
 }
 
 cudaError_t launch_batch(const BatchArgs& a, int formalism, int sm_count, cudaStream_t st) {
-  return with_batch_ops(formalism, a.M.kind,
+  return with_batch_ops(formalism, a.M.kind, a.M.split != 0,
                         [&](auto ops) { return launch_batch_ops<decltype(ops)>(a, sm_count, st); });
 }
 
 int batch_resident(int formalism, int kind, int a_tile, int sm_count) {
-  return sm_count *
-         with_batch_ops(formalism, kind, [&](auto ops) { return batch_blocks_per_sm<decltype(ops)>(a_tile); });
+  return sm_count * with_batch_ops(formalism, kind, false,
+                                   [&](auto ops) { return batch_blocks_per_sm<decltype(ops)>(a_tile); });
 }
 
 // ---------------------------------------------------------------------------
@@ -215,6 +217,7 @@ struct c8r_batch {
   int* d_counter = nullptr;
   int* d_cancel = nullptr;
   int* d_err = nullptr;
+  unsigned long long* d_form = nullptr;  // the ingest's arrival-form votes (kept, seen from above)
   float4* d_acc = nullptr;  // [replicas][total_ant][rows][n_bins] accumulator
   size_t acc_bytes = 0;
   int replicas = 1;
@@ -317,7 +320,28 @@ int enqueue(c8r_batch* b, const TrackPtrs& tp, float* out, int n_items_limit, cu
   return C8R_OK;
 }
 
+// the arrival form of the one-bin Endpoint kernel (MedParams::split) from the
+// ingest's votes over the whole batch: the split form when at least half of the
+// tracks see the antenna array's centroid from above within 45 degrees (one
+// ingest and a synchronous read, once per batch, before the first run)
+int choose_form(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
+  BatchMap map{b->d_tile_off, b->d_track_off, b->d_n_tracks, b->n_showers};
+  unsigned long long h[2] = {0, 0};
+  cudaError_t e = cudaMemsetAsync(b->d_form, 0, sizeof(h), st);
+  if (e == cudaSuccess)
+    e = launch_ingest_map(C8R_MIXED, tp, map, b->total_tiles * kTileT, b->d_tiles, b->M, nullptr, st, b->d_form);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, b->d_form, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch form votes: ") + cudaGetErrorString(e));
+  if (h[0] > 0) b->M.split = 2 * h[1] >= h[0] ? 1 : 0;
+  return C8R_OK;
+}
+
 int autotune(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
+  if (b->formalism == C8R_ENDPOINT && (b->M.kind == C8R_UNIFORM || b->M.kind == C8R_EXPONENTIAL)) {
+    const int r = choose_form(b, tp, st);
+    if (r != C8R_OK) return r;
+  }
   char keybuf[160];
   std::snprintf(keybuf, sizeof keybuf, "batch3:N%d:f%d:m%d:sm%d:P%lld", b->M.n_bins, b->formalism, b->M.kind,
                 b->sm_count, (long long)(b->total_pairs >> 26));
@@ -419,6 +443,8 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
     b->total_pairs += b->n_tracks[s] * (int64_t)b->n_ant[s];
   }
   b->total_tiles = b->tile_off[d->n_showers];
+  set_form_centroid(b->M, d->pos_xyz, b->total_ant);
+  b->M.split = 1;
   std::vector<AntRec> recs(b->total_ant);
   for (int a = 0; a < b->total_ant; ++a) {
     const double* p = d->pos_xyz + 3 * (size_t)a;
@@ -438,8 +464,8 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
     e = cudaMemcpy(b->d_track_off, b->track_off.data(), sizeof(int64_t) * b->n_showers, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_n_tracks, b->n_tracks.data(), sizeof(int64_t) * b->n_showers, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = dev_malloc(&b->d_counter, sizeof(int) * 3);
-  if (e == cudaSuccess) e = cudaMemset(b->d_counter, 0, sizeof(int) * 3);
+  if (e == cudaSuccess) e = dev_malloc(&b->d_counter, sizeof(int) * 8);
+  if (e == cudaSuccess) e = cudaMemset(b->d_counter, 0, sizeof(int) * 8);
   if (e != cudaSuccess) {
     cudaGetLastError();
     b->err = std::string("batch allocation: ") + cudaGetErrorString(e);
@@ -447,6 +473,7 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
     return C8R_ENOMEM;
   }
   b->d_cancel = b->d_counter + 1;
+  b->d_form = reinterpret_cast<unsigned long long*>(b->d_counter + 4);
   b->d_err = b->d_counter + 2;
   if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->aux_stream, cudaStreamNonBlocking) != cudaSuccess) {

@@ -8,6 +8,7 @@
 // interface.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -64,17 +65,23 @@ struct AntRec {
   double x, y, z;        // m
   double t_ref;          // ns, first bin edge
   double Ea;             // exp(-z/H) (exponential medium), 1 otherwise
-  double pad;
+  // t_ref/dt + k z (k = n/(c dt) in the uniform medium, 1/(c dt) in the
+  // exponential one) as float-float: the antenna's part of the shifted arrival
+  // time of the FP32 arrival (arrival_fast)
+  float Tah, Tal;
   float xh, yh, zh, xl, yl, zl;  // position as float-float
   float tauh, taul;              // t_ref / dt as float-float
   float Eah, Eal;                // Ea as float-float
   // constants of the error bound of the FP32 arrival (arrival_bin_fast):
-  // fb_abs = bins per metre x |low part of the position| + 1e-6 bin, and
-  // fb_rel_v = |z_l| / (1e-3 H), the relative error of the refractivity term
-  // from the low part of the altitude (exponential medium; 0 otherwise)
+  // fb_abs = 2 x bins per metre x |low part of the position| + 16 u^2 |T_a| +
+  // 1e-6 bin, and fb_rel_v = |z_l| / (1e-3 H), the relative error of the
+  // refractivity term from the low part of the altitude (exponential medium;
+  // 0 otherwise)
   float fb_abs, fb_rel_v;
 };
 static_assert(sizeof(AntRec) == 96, "antenna record layout");
+static_assert(offsetof(AntRec, xh) % 16 == 0 && offsetof(AntRec, Tah) % 8 == 0,
+              "the mixed path loads the float part as float4s and the shifted time as a float2");
 
 // medium + binning parameters (kernel argument)
 struct MedParams {
@@ -99,6 +106,12 @@ struct MedParams {
   float RE_f;            // spherical: Earth radius (m)
   float eps_C;           // near-Cherenkov threshold
   uint32_t wait_limit;   // polls of a bounded wait on a staged track tile before it gives up
+  // the form of the FP32 arrival (Endpoint, one-bin deposit, plain media): the
+  // centroid of the antenna array, which the ingest's count of tracks seen
+  // from above within 45 degrees refers to, and the host's choice from that
+  // count (1: the split form of x = R - w)
+  float cen_x, cen_y, cen_z;
+  int split;
 };
 
 // ---------------------------------------------------------------------------
@@ -402,7 +415,7 @@ __device__ __forceinline__ void geo_lite(const AntRec& A, float pxh, float pyh, 
   g.e[0] = __fadd_rn(g.e[0], __fsub_rn(A.xl, pxl));
   g.e[1] = __fadd_rn(g.e[1], __fsub_rn(A.yl, pyl));
   g.e[2] = __fadd_rn(g.e[2], __fsub_rn(A.zl, pzl));
-  const float S = __fmaf_rn(g.s[0], g.s[0], __fmaf_rn(g.s[1], g.s[1], __fmul_rn(g.s[2], g.s[2])));
+  const float S = __fmaf_rn(g.s[2], g.s[2], __fmaf_rn(g.s[0], g.s[0], __fmul_rn(g.s[1], g.s[1])));
   g.y = rsqrtf(S);
   g.R0 = __fmul_rn(S, g.y);
   g.R1 = 0.0f;
@@ -418,7 +431,7 @@ __device__ __forceinline__ void geo_lite(const AntRec& A, float px, float py, fl
   g.e[0] = __fadd_rn(g.e[0], A.xl);
   g.e[1] = __fadd_rn(g.e[1], A.yl);
   g.e[2] = __fadd_rn(g.e[2], A.zl);
-  const float S = __fmaf_rn(g.s[0], g.s[0], __fmaf_rn(g.s[1], g.s[1], __fmul_rn(g.s[2], g.s[2])));
+  const float S = __fmaf_rn(g.s[2], g.s[2], __fmaf_rn(g.s[0], g.s[0], __fmul_rn(g.s[1], g.s[1])));
   g.y = rsqrtf(S);
   g.R0 = __fmul_rn(S, g.y);
   g.R1 = 0.0f;
@@ -550,96 +563,157 @@ __device__ __forceinline__ int bin_raw(ff u, int n_bins, float& frac) {
 // Bin of an arrival from plain FP32 arithmetic with a bound on its error, for
 // the one-bin deposit (reading T: only the bin of an arrival matters there).
 // The float-float arrival (arrival_mixed, ~1e-9 bin) costs about four times the
-// FP32 one, and an FP32 arrival of ~1e5 bins is off by up to a few hundredths
-// of a bin.  So the FP32 arrival decides the bin whenever no bin edge (and
-// neither end of the window) lies within its error bound; then it is the bin of
-// the float-float arrival too, which is good to ~1e-7 bin at most, far inside
-// the bound's 1e-6-bin floor.  Otherwise the caller evaluates the float-float
-// arrival (about 8 % of the arrivals of a shower 1-10 km above 0.2-ns traces).
+// FP32 one.  The FP32 arrival decides the bin whenever no bin edge (and neither
+// end of the window) lies within its error bound; then it is the bin of the
+// float-float arrival too, which is good to ~1e-7 bin at most, far inside the
+// bound's 1e-6-bin floor.  Otherwise the caller evaluates the float-float
+// arrival.
 //
-// The arithmetic, with u = 2^-24 (the FP32 unit roundoff) and every step
-// rounded once (intrinsics, no contraction):
-//   s = fl(a_h - p): the antenna's high part minus the FP32-exact emission
-//     point; |s| differs from R = |d| by at most u R + |a_l|;
-//   S = fl(s_x^2 + s_y^2 + s_z^2) (two FMAs): within 3u S of |s|^2, so
-//     sqrt(S) is within 1.5u of |s|;
-//   R0 = S rsqrt(S) (MUFU, 2 ulp) and one Newton step with the residual
-//     fma(-R0, R0, S): the step leaves O(u^2) of R0's error, so R' is
-//     sqrt(S) rounded once (u);  in all |R' - R| <= 3.5u R + |a_l|;
-//   p = R' (k_h + k_l), k = n/(c dt) (uniform) or 1/(c dt), rounded once:
-//     |p - kR| <= 4.5u p + k |a_l|;
-//   ts = fl(fl(tau_e,h - tau_a,h) + fl(tau_e,l - tau_a,l)): within 2u |ts|;
+// Vertical split.  With w = z_e - z_a (the emission point's height above the
+// antenna) and rho^2 = d_x^2 + d_y^2, the distance is R = w + x, where
+// x = R - w = rho^2 / (R + w) since R^2 = w^2 + rho^2.  So
+//   u = (tau_e - tau_a) + k R + v = (T_e - T_a) + k x + v,
+//   T_e = tau_e + k z_e (per track endpoint), T_a = tau_a + k z_a (per antenna),
+// with k = n/(c dt) in the uniform medium and 1/(c dt) in the exponential one
+// (where v carries the refractivity).  T_e and T_a are formed once, in
+// float-float, so no per-pair FP32 rounding acts on a term as large as k R
+// (~1e5 bins): FP32 rounds T_e - T_a, about the arrival's own distance from
+// the window start, and k x, which is small for emission points high above the
+// antenna (x ~ R theta^2 / 2 at an angle theta off the vertical).  The split
+// form x = rho^2 / (R + w) pays where x is small against R; elsewhere (an
+// inclined line of sight, or a point below the antenna, w <= 0) the direct form
+// x = R - w = fl(R + s_z) has the smaller error, and the caller picks the form
+// (SPLIT below) for a whole warp: the split one when every lane's emission
+// point lies within 45 degrees of the antenna's vertical (2 rho^2 < S, w > 0).
+//
+// The errors, with u = 2^-24 (the FP32 unit roundoff) and every step rounded
+// once (intrinsics, no contraction):
+//   s = fl(a_h - p): each component is off the exact d = a - p by at most
+//     u |s_i| and the antenna's low part a_l.  x changes with s_z at the rate
+//     x/R and with s_x, s_y at |s_{x,y}|/R, so the rounding moves x by at most
+//     u (x + rho^2 / R) <= 3u x (also for w <= 0, where x >= R); a_l moves it by
+//     at most 2 |a_l| (T_a holds the exact z_a);
+//   rho^2 = fl(s_x^2 + s_y^2) (two roundings, 2u) and S = fl(s_z^2 + rho^2):
+//     R' = S rsqrt(S) plus one Newton step with the residual fma(-R0, R0, S) is
+//     sqrt(S) rounded once, within 2.5u R of |s|;
+//   split form, w > 0: x = rho^2 / fl(R' - s_z) with __fdividef (2 ulp: 4u);
+//     the denominator R + |s_z| >= R carries 3.5u; with rho^2, 9.5u x.  (w <= 0
+//     takes the direct form, x >= R: 3.5u x.)  Direct form: x = fl(R' + s_z),
+//     2.5u R + u x;
+//   q = fl(x k_h): u, and u more for the dropped k_l;
+//   Td = fl(fl(T_e,h - T_a,h) + fl(T_e,l - T_a,l)): 2u |Td|, plus terms of
+//     u^2 |T_e| and u^2 |T_a| from the float-float forms of T_e and T_a;
 //   v (exponential medium) = N0 H/(c dt) (E_e - E_a)/dz R': the quotient
 //     (2 ulp) or its series for |dz/H| <= 1e-3, four more roundings and R'
 //     give at most 14u |v|, plus |v| |z_l|/|dz| from the antenna altitude's
 //     low part, |dz| > 1e-3 H in the quotient's branch;
-//   uf = fl(fl(ts + p) + v): two more roundings, u |uf| each, and one more
-//     in the window test uf - bound >= n_bins.
-// The bound used is u (4.75 p + 2.25 |ts| + 17 |v| + 3.25 |uf|) +
-// fb_rel_v |v| + fb_abs, each coefficient above its derivation; fb_abs holds
-// k |a_l| and a floor of 1e-6 bin, which covers the float-float arrival's own
-// error for arrivals up to ~1e8 bins from the time origin and the rounding of
-// uf - floor(uf).  A CPU emulation of these steps (2-ulp reciprocal square
-// root and quotient) against the FP64 oracle's arrivals on the benchmark
-// showers stays below 0.4 of the bound.
+//   uf = fl(fl(Td + q) + v): u |Td + q| <= u (|uf| + |v|) (Td + q is uf - v
+//     before the last rounding, small against Td and q once the arrival is
+//     near the window) and u |uf|, and one more u |uf| in the window test
+//     uf - bound >= n_bins.
+// The bound used is u (2.25 |Td| + c_q q + 17 |v| + 3.25 |uf|) + fb_rel_v |v| +
+// fb_abs, with c_q = 15 in the split form (14.5 derived) and c_q = 6.25 plus
+// 2.5u k_h R in the direct one (6 and 2.5), each coefficient above its
+// derivation; fb_abs holds 2 k |a_l|,
+// 16 u^2 |T_a| (the share of T_e, |T_e| <= |Td| + |T_a|, beyond what the |Td|
+// term covers) and a floor of 1e-6 bin for the float-float arrival's own error
+// and the rounding of uf - floor(uf).  A CPU emulation of these steps (2-ulp
+// reciprocal square root and quotient) against the FP64 oracle's arrivals
+// stays below 0.5 of the bound on the benchmark showers; on a vertical shower
+// 1-10 km above 0.2-ns traces the bound is ~6e-4 bin and ~0.1 % of the
+// endpoints are left to the float-float arrival (8 % with k R rounded in FP32
+// per pair).  On a shower inclined by 60 degrees x is about R/2 and the direct
+// form holds the bound near that of an arrival rounded in FP32 throughout.
 // ---------------------------------------------------------------------------
 constexpr int kFastOut = -1;        // the arrival lies outside the window: no deposit
 constexpr int kFastUndecided = -2;  // an edge lies within the bound: the float-float arrival decides
 
-// d = a_h - p in FP32 (no low parts) and R0 = |d| as geo_lite forms it (the
-// same s, y and R0 bit for bit), with S = |d|^2 kept for the Newton step
-__device__ __forceinline__ void geo_fast(const AntRec& A, float px, float py, float pz, GeoM& g, float& S) {
+// d = a_h - p in FP32 (no low parts), rho^2 = d_x^2 + d_y^2, S = |d|^2 and
+// R0 = |d| as geo_lite forms them (the same s, y and R0 bit for bit)
+__device__ __forceinline__ void geo_fast(const AntRec& A, float px, float py, float pz, GeoM& g, float& S,
+                                         float& rho2) {
   g.s[0] = __fadd_rn(A.xh, -px);
   g.s[1] = __fadd_rn(A.yh, -py);
   g.s[2] = __fadd_rn(A.zh, -pz);
-  S = __fmaf_rn(g.s[0], g.s[0], __fmaf_rn(g.s[1], g.s[1], __fmul_rn(g.s[2], g.s[2])));
+  rho2 = __fmaf_rn(g.s[0], g.s[0], __fmul_rn(g.s[1], g.s[1]));
+  S = __fmaf_rn(g.s[2], g.s[2], rho2);
   g.y = rsqrtf(S);
   g.R0 = __fmul_rn(S, g.y);
   g.R1 = 0.0f;
 }
 
-// The FP32 arrival uf of the emission point of g (and S = |d|^2) and its error
-// bound, returned; p_extra adds a relative term u * p_extra * p for geometry
-// whose d carries more than the one rounding of a_h - p (the midpoint)
-template <int KIND>
-__device__ __forceinline__ float arrival_fast(const MedParams& M, const AntRec& A, const GeoM& g, float S,
-                                              float tauh, float taul, float Eeh, float Eel, float p_extra,
+// T = tau + k z as float-float, the shifted time of arrival_fast, for a height
+// z = zh + zl (zl = 0 for an FP32-exact endpoint)
+__device__ __forceinline__ void shifted_time(float tauh, float taul, float zh, float zl, float kh, float kl,
+                                             float& Th, float& Tl) {
+  float p, e;
+  two_prod(zh, kh, p, e);
+  e = __fmaf_rn(zh, kl, __fmaf_rn(zl, kh, e));
+  float s, e2;
+  two_sum(tauh, p, s, e2);
+  e2 = __fadd_rn(e2, __fadd_rn(taul, e));
+  fast_two_sum(s, e2, Th, Tl);
+}
+
+// whether the split form of x pays for the emission point of g: within 45
+// degrees of the antenna's vertical and above it
+__device__ __forceinline__ bool split_pays(const GeoM& g, float S, float rho2) {
+  return g.s[2] < 0.0f && __fadd_rn(rho2, rho2) < S;
+}
+
+// The FP32 arrival uf of the emission point of g (S = |d|^2, rho2 = d_x^2 +
+// d_y^2, T_e = Teh + Tel) and its error bound, returned; SPLIT picks the form
+// of x; q_extra adds a term u * q_extra * k x for geometry whose d carries
+// more than the one rounding of a_h - p (the midpoint)
+template <int KIND, bool SPLIT>
+__device__ __forceinline__ float arrival_fast(const MedParams& M, const AntRec& A, const GeoM& g, float S, float rho2,
+                                              float Teh, float Tel, float Eeh, float Eel, float q_extra,
                                               float& uf_out) {
   static_assert(KIND == C8R_UNIFORM || KIND == C8R_EXPONENTIAL, "plain straight-line media only");
   constexpr float u = 5.9604644775390625e-8f;  // 2^-24
   // R' = sqrt(S) rounded once
   const float r = __fmaf_rn(-g.R0, g.R0, S);
   const float R = __fmaf_rn(r, __fmul_rn(0.5f, g.y), g.R0);
-  const float ts = __fadd_rn(__fsub_rn(tauh, A.tauh), __fsub_rn(taul, A.taul));
+  // x = R - w, w = z_e - z_a = -s_z
+  const float sz = g.s[2];
+  float x;
+  if constexpr (SPLIT) {
+    x = sz < 0.0f ? __fdividef(rho2, __fsub_rn(R, sz)) : __fadd_rn(R, sz);
+  } else {
+    x = __fadd_rn(R, sz);
+  }
   const float kh = KIND == C8R_UNIFORM ? M.s_h : M.kc_h;
-  const float kl = KIND == C8R_UNIFORM ? M.s_l : M.kc_l;
-  const float p = __fmaf_rn(R, kh, __fmul_rn(R, kl));
+  const float q = __fmul_rn(x, kh);
+  const float Td = __fadd_rn(__fsub_rn(Teh, A.Tah), __fsub_rn(Tel, A.Tal));
   float v = 0.0f;
   if constexpr (KIND == C8R_EXPONENTIAL) {
-    const float dz = g.s[2];
-    const float x = __fmul_rn(dz, M.invH_h);
-    float q;
+    const float x = __fmul_rn(sz, M.invH_h);
+    float qv;
     if (fabsf(x) > 1e-3f) {
-      q = __fdividef(__fadd_rn(__fsub_rn(Eeh, A.Eah), __fsub_rn(Eel, A.Eal)), dz);
+      qv = __fdividef(__fadd_rn(__fsub_rn(Eeh, A.Eah), __fsub_rn(Eel, A.Eal)), sz);
     } else {
       const float f = __fmul_rn(x, __fmaf_rn(x, __fmaf_rn(x, -1.0f / 24.0f, 1.0f / 6.0f), -0.5f));
-      q = __fmul_rn(__fmul_rn(Eeh, M.invH_h), __fadd_rn(1.0f, f));
+      qv = __fmul_rn(__fmul_rn(Eeh, M.invH_h), __fadd_rn(1.0f, f));
     }
-    v = __fmul_rn(__fmul_rn(q, R), M.cN_h);
+    v = __fmul_rn(__fmul_rn(qv, R), M.cN_h);
   }
-  const float uf = __fadd_rn(__fadd_rn(ts, p), v);
+  const float uf = __fadd_rn(__fadd_rn(Td, q), v);
   uf_out = uf;
-  return __fmaf_rn(__fmaf_rn(p_extra, u, 4.75f * u), p,
-                   __fmaf_rn(2.25f * u, fabsf(ts),
-                             __fmaf_rn(__fmaf_rn(17.0f, u, A.fb_rel_v), fabsf(v),
-                                       __fmaf_rn(3.25f * u, fabsf(uf), A.fb_abs))));
+  const float tail = __fmaf_rn(2.25f * u, fabsf(Td),
+                               __fmaf_rn(__fmaf_rn(17.0f, u, A.fb_rel_v), fabsf(v),
+                                         __fmaf_rn(3.25f * u, fabsf(uf), A.fb_abs)));
+  if constexpr (SPLIT) {
+    return __fmaf_rn(__fmaf_rn(q_extra, u, 15.0f * u), q, tail);
+  } else {
+    return __fmaf_rn(__fmaf_rn(q_extra, u, 6.25f * u), q, __fmaf_rn(__fmul_rn(2.5f * u, kh), R, tail));
+  }
 }
 
-template <int KIND>
+template <int KIND, bool SPLIT>
 __device__ __forceinline__ int arrival_bin_fast(const MedParams& M, const AntRec& A, const GeoM& g, float S,
-                                                float tauh, float taul, float Eeh, float Eel) {
+                                                float rho2, float Teh, float Tel, float Eeh, float Eel) {
   float uf;
-  const float eps = arrival_fast<KIND>(M, A, g, S, tauh, taul, Eeh, Eel, 0.0f, uf);
+  const float eps = arrival_fast<KIND, SPLIT>(M, A, g, S, rho2, Teh, Tel, Eeh, Eel, 0.0f, uf);
   if (uf < -eps || __fsub_rn(uf, eps) >= (float)M.n_bins) return kFastOut;
   const float k = floorf(uf);
   const float fr = __fsub_rn(uf, k);

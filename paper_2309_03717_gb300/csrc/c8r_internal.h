@@ -72,9 +72,11 @@ cudaError_t launch_traces_to_bin_major(int precision, const void* g, int n_ant, 
                                        cudaStream_t st);
 
 // ingest: filter + derived per-track quantities into tiles; counts kept tracks
-// into *kept unless kept is NULL
+// into *kept unless kept is NULL, and (mixed precision, form not NULL) adds the
+// kept tracks to form[0] and those whose start point sees the antenna array's
+// centroid (M.cen_*) from above within 45 degrees to form[1]
 cudaError_t launch_ingest(int precision, const TrackPtrs& t, int64_t n, void* tiles, const MedParams& M,
-                          unsigned long long* kept, cudaStream_t st);
+                          unsigned long long* kept, cudaStream_t st, unsigned long long* form = nullptr);
 
 struct BwdArgs;
 
@@ -128,5 +130,8 @@ inline cudaError_t dev_malloc(T** p, size_t bytes) {
 void fill_medium(MedParams& M, int kind, double n_or_N0, double H, int n_bins, double dt_ns, double eps_C,
                  double earth_radius = 0.0);
 void fill_antenna(AntRec& r, double x, double y, double z, double t_ref_ns, const MedParams& M);
+// the antenna array's centroid (MedParams::cen_*), which the ingest's votes for
+// the arrival form of the one-bin Endpoint kernels refer to
+void set_form_centroid(MedParams& M, const double* pos_xyz, int n_ant);
 
 }  // namespace c8r

@@ -143,9 +143,10 @@ __device__ __forceinline__ void exp_alt(float zh, float zl, const MedParams& M, 
 // padding slot (identity for one shower; a per-shower table for a batch)
 template <typename Tin, class Map>
 __global__ void __launch_bounds__(256) k_ingest_mixed(TrackPtrs t, Map map, int64_t n_pad, float* tiles,
-                                                      MedParams M, unsigned long long* kept) {
+                                                      MedParams M, unsigned long long* kept,
+                                                      unsigned long long* form) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool keep = false;
+  bool keep = false, from_above = false;
   if (i < n_pad) {
     float* tile = tiles + (i / kTileT) * (int64_t)(fm::NFIELDS * kTileT);
     const int l = (int)(i % kTileT);
@@ -164,6 +165,11 @@ __global__ void __launch_bounds__(256) k_ingest_mixed(TrackPtrs t, Map map, int6
       keep = track_kept_f32(f, S);
       if (keep) {
         out[fm::X0] = f[0]; out[fm::Y0] = f[1]; out[fm::Z0] = f[2];
+        // the start point sees the antenna array's centroid from above, within
+        // 45 degrees of the vertical (the vote for the split arrival form)
+        const float sx = M.cen_x - f[0], sy = M.cen_y - f[1], sz = M.cen_z - f[2];
+        const float P = sx * sx + sy * sy;
+        from_above = sz < 0.0f && P < sz * sz;
         out[fm::X1] = f[3]; out[fm::Y1] = f[4]; out[fm::Z1] = f[5];
         out[fm::BX] = f[8]; out[fm::BY] = f[9]; out[fm::BZ] = f[10];
         // tau = t/dt, (t1 - t0)/dt = (exact difference) x 1/dt
@@ -196,8 +202,17 @@ __global__ void __launch_bounds__(256) k_ingest_mixed(TrackPtrs t, Map map, int6
 #pragma unroll
     for (int k = 0; k < fm::NFIELDS; ++k) tile[k * kTileT + l] = out[k];
   }
-  unsigned m = __ballot_sync(0xffffffffu, keep);
-  if (kept && (threadIdx.x & 31) == 0 && m) atomicAdd(kept, (unsigned long long)__popc(m));
+  // counts summed over the block first: one reduction per block and counter
+  // (from every warp, these same-address reductions cost more than the ingest)
+  const int nk = __syncthreads_count(keep);
+  const int nv = form ? __syncthreads_count(from_above) : 0;  // form: uniform over the grid
+  if (threadIdx.x == 0 && nk) {
+    if (kept) atomicAdd(kept, (unsigned long long)nk);
+    if (form) {
+      atomicAdd(form, (unsigned long long)nk);  // kept tracks, and those seen from above
+      if (nv) atomicAdd(form + 1, (unsigned long long)nv);
+    }
+  }
 }
 
 template <typename Tin, class Map>
@@ -236,8 +251,8 @@ __global__ void __launch_bounds__(256) k_ingest_f64(TrackPtrs t, Map map, int64_
 #pragma unroll
     for (int k = 0; k < fd::NFIELDS; ++k) tile[k * kTileT + l] = out[k];
   }
-  unsigned m = __ballot_sync(0xffffffffu, keep);
-  if (kept && (threadIdx.x & 31) == 0 && m) atomicAdd(kept, (unsigned long long)__popc(m));
+  const int nk = __syncthreads_count(keep);
+  if (kept && threadIdx.x == 0 && nk) atomicAdd(kept, (unsigned long long)nk);
 }
 
 
@@ -250,7 +265,8 @@ struct IdentityMap {
 
 template <class Map>
 cudaError_t launch_ingest_map(int precision, const TrackPtrs& t, const Map& map, int64_t n_pad, void* tiles,
-                              const MedParams& M, unsigned long long* kept, cudaStream_t st) {
+                              const MedParams& M, unsigned long long* kept, cudaStream_t st,
+                              unsigned long long* form = nullptr) {
   using namespace ingest_detail;
   if (n_pad <= 0) return cudaSuccess;
   const int threads = 256;
@@ -262,9 +278,9 @@ cudaError_t launch_ingest_map(int precision, const TrackPtrs& t, const Map& map,
       k_ingest_f64<float, Map><<<(unsigned)blocks, threads, 0, st>>>(t, map, n_pad, (double*)tiles, M, kept);
   } else {
     if (t.dtype == C8R_F64)
-      k_ingest_mixed<double, Map><<<(unsigned)blocks, threads, 0, st>>>(t, map, n_pad, (float*)tiles, M, kept);
+      k_ingest_mixed<double, Map><<<(unsigned)blocks, threads, 0, st>>>(t, map, n_pad, (float*)tiles, M, kept, form);
     else
-      k_ingest_mixed<float, Map><<<(unsigned)blocks, threads, 0, st>>>(t, map, n_pad, (float*)tiles, M, kept);
+      k_ingest_mixed<float, Map><<<(unsigned)blocks, threads, 0, st>>>(t, map, n_pad, (float*)tiles, M, kept, form);
   }
   return cudaGetLastError();
 }

@@ -24,6 +24,7 @@ struct TrackM {
   float bx, by, bz, bmag;
   float amp;                     // q K/dt (Endpoint) or q K_A (t1-t0)/dt (ZHS); 0 = dropped
   float tau0h, tau0l, tau1h, tau1l, dtauh, dtaul;
+  float T0h, T0l, T1h, T1l;      // Endpoint, plain media: tau + k z at start and end (arrival_fast)
   float E0h, E0l, E1h, E1l, Emh, Eml;
   float nm1_0, nm1_1, nm1_m;     // n - 1 at start, end, midpoint
   float om0, om1, om_m;          // 1 - n|beta| at start, end, midpoint
@@ -43,6 +44,12 @@ __device__ __forceinline__ void load_track_mixed(const float* T, int l, const Me
   t.tau0h = TF(fm::TAU0H); t.tau0l = TF(fm::TAU0L);
   t.tau1h = TF(fm::TAU1H); t.tau1l = TF(fm::TAU1L);
   t.dtauh = TF(fm::DTAUH); t.dtaul = TF(fm::DTAUL);
+  if (FORM == C8R_ENDPOINT && (KIND == C8R_UNIFORM || KIND == C8R_EXPONENTIAL)) {
+    // the shifted times of the FP32 arrival, once per track (k = n/(c dt) or 1/(c dt))
+    const float kh = KIND == C8R_UNIFORM ? M.s_h : M.kc_h, kl = KIND == C8R_UNIFORM ? M.s_l : M.kc_l;
+    shifted_time(t.tau0h, t.tau0l, t.z0, 0.0f, kh, kl, t.T0h, t.T0l);
+    shifted_time(t.tau1h, t.tau1l, t.z1, 0.0f, kh, kl, t.T1h, t.T1l);
+  }
   // n - 1 is formed directly (N0 E, or the uniform n - 1 rounded from FP64): as
   // (1 + x) - 1 in FP32 it would lose ~6e-8, comparable to D near Cherenkov
   t.E0h = t.E1h = t.Emh = 1.0f;
@@ -266,7 +273,7 @@ __device__ __forceinline__ LinEnds lin_ends(int Jlo, float slo, int Jhi, float s
   return z;
 }
 
-template <int FORM, int KIND, bool LIN = false>
+template <int FORM, int KIND, bool LIN = false, bool SPLIT = false>
 struct OpsMixed {
   using acc_t = float;
   using Track = TrackM;
@@ -288,20 +295,30 @@ struct OpsMixed {
   // for the float-float arrival after the main pass
   static constexpr bool kFastBins =
       FORM == C8R_ENDPOINT && !LIN && (KIND == C8R_UNIFORM || KIND == C8R_EXPONENTIAL);
+  // the form of x = R - w in the FP32 arrival (arrival_fast): the split one
+  // for lines of sight near the vertical, the direct one otherwise.  Either is
+  // exact to its own bound; the host picks the kernel per launch from the
+  // share of tracks that see the antenna array from above within 45 degrees
+  // (counted by the ingest of earlier launches)
+  static constexpr bool kSplit = SPLIT && kFastBins;
   // adjoint CTAs (128 threads) per SM the registers are set for (the linear
   // Endpoint adjoint carries the slide of each deposit as well)
   static constexpr int kBwdMinBlocks = (LIN && FORM == C8R_ENDPOINT) ? 4 : 6;
   // ZHS: a second accumulator row holds the edges of box deposits
   static constexpr int kAccRows = FORM == C8R_ZHS ? 2 : 1;
 
-  // the float-float part of an antenna record, as three 16-byte shared-memory loads
+  // the float-float part of an antenna record, as three 16-byte shared-memory
+  // loads and one 8-byte load (the shifted time; loads whose fields a pass
+  // does not use are dropped by the compiler)
   static __device__ __forceinline__ AntRec load_ant(const AntRec* p) {
     const float4* f = reinterpret_cast<const float4*>(&p->xh);
     const float4 a = f[0], b = f[1], c = f[2];
+    const float2 T = *reinterpret_cast<const float2*>(&p->Tah);
     AntRec r;
     r.xh = a.x; r.yh = a.y; r.zh = a.z; r.xl = a.w;
     r.yl = b.x; r.zl = b.y; r.tauh = b.z; r.taul = b.w;
     r.Eah = c.x; r.Eal = c.y; r.fb_abs = c.z; r.fb_rel_v = c.w;
+    r.Tah = T.x; r.Tal = T.y;
     return r;
   }
 
@@ -485,6 +502,20 @@ struct OpsMixed {
     if (kb <= ke) out.dep_box(kb, ke, Mx * invW, My * invW, Mz * invW);
   }
 
+  // the bins of both endpoints from the FP32 arrival (kFastBins) in the form
+  // of x = R - w this kernel is compiled for
+  static __device__ __forceinline__ void fast_bins(const TrackM& t, const AntRec& A, const MedParams& M,
+                                                   const GeoM& g0, const GeoM& g1, float S0, float S1, float P0,
+                                                   float P1, int& ka, int& kb) {
+    if constexpr (kSplit) {
+      ka = arrival_bin_fast<KIND, true>(M, A, g0, S0, P0, t.T0h, t.T0l, t.E0h, t.E0l);
+      kb = arrival_bin_fast<KIND, true>(M, A, g1, S1, P1, t.T1h, t.T1l, t.E1h, t.E1l);
+    } else {
+      ka = arrival_bin_fast<KIND, false>(M, A, g0, S0, P0, t.T0h, t.T0l, t.E0h, t.E0l);
+      kb = arrival_bin_fast<KIND, false>(M, A, g1, S1, P1, t.T1h, t.T1l, t.E1h, t.E1l);
+    }
+  }
+
   // main pass: every pair except (Endpoint) the near-Cherenkov ones, for which
   // it deposits nothing and returns kDeferPair, and (kFastBins) the endpoints
   // whose bin the FP32 arrival leaves open, returned as kDeferEnd0/kDeferEnd1
@@ -493,16 +524,16 @@ struct OpsMixed {
   static __device__ __forceinline__ int pair_main(const TrackM& t, const AntRec& A, const MedParams& M, Sink& out) {
     if constexpr (kFastBins) {
       GeoM g0, g1;
-      float S0, S1;
-      geo_fast(A, t.x0, t.y0, t.z0, g0, S0);
-      geo_fast(A, t.x1, t.y1, t.z1, g1, S1);
+      float S0, S1, P0, P1;
+      geo_fast(A, t.x0, t.y0, t.z0, g0, S0, P0);
+      geo_fast(A, t.x1, t.y1, t.z1, g1, S1, P1);
       if (g0.R0 == 0.0f || g1.R0 == 0.0f) return kDeferNone;  // an emission point on the antenna
+      int ka, kb;
+      fast_bins(t, A, M, g0, g1, S0, S1, P0, P1, ka, kb);
       FieldM f0, f1;
       field_mixed(g0, t.bx, t.by, t.bz, t.bmag, t.om0, __fadd_rn(1.0f, t.nm1_0), f0);
       field_mixed(g1, t.bx, t.by, t.bz, t.bmag, t.om1, __fadd_rn(1.0f, t.nm1_1), f1);
       if (!(fminf(fabsf(f0.D), fabsf(f1.D)) >= M.eps_C)) return kDeferPair;
-      const int ka = arrival_bin_fast<KIND>(M, A, g0, S0, t.tau0h, t.tau0l, t.E0h, t.E0l);
-      const int kb = arrival_bin_fast<KIND>(M, A, g1, S1, t.tau1h, t.tau1l, t.E1h, t.E1l);
       const bool ina = ka >= 0, inb = kb >= 0;  // decided and inside the window
       const float amp = t.amp;
       const float c0 = __fdividef(amp, f0.D * g0.R0) * (f0.invR * f0.invR);
@@ -532,8 +563,9 @@ struct OpsMixed {
   // the window, contributes exactly 0 (reading C), and so does its adjoint.
   // Decided here from FP32 midpoint geometry, as arrival_bin_fast decides a
   // bin: the midpoint d_m = (s0 + s1)/2 from the endpoints' FP32 d (the
-  // float-float path's high part; its rounding adds u (R + L) to the distance,
-  // so the arrival bound takes 1 more u p and 2 u k L1, L1 >= L), the FP32
+  // float-float path's high part; its roundings move each component by at most
+  // 2u |s_i| + u L_i / 2, which moves x = R - w by at most 6u x + u L1 / 2, so
+  // the arrival bound takes 3 more u k x and 2 u k L1, L1 >= L), the FP32
   // Doppler factor D_m (field_mixed: off the float-float D_m by at most
   // 8 u n + 16 u |D_m|, from the direction's rounding and its own), and two
   // more roundings on the interval ends.  True when the pair is decided to be
@@ -551,7 +583,8 @@ struct OpsMixed {
       g.s[0] = 0.5f * __fadd_rn(a0x, a1x);
       g.s[1] = 0.5f * __fadd_rn(a0y, a1y);
       g.s[2] = 0.5f * __fadd_rn(a0z, a1z);
-      const float S = __fmaf_rn(g.s[0], g.s[0], __fmaf_rn(g.s[1], g.s[1], __fmul_rn(g.s[2], g.s[2])));
+      const float rho2 = __fmaf_rn(g.s[0], g.s[0], __fmul_rn(g.s[1], g.s[1]));
+      const float S = __fmaf_rn(g.s[2], g.s[2], rho2);
       g.y = rsqrtf(S);
       g.R0 = __fmul_rn(S, g.y);
       g.R1 = 0.0f;
@@ -567,15 +600,23 @@ struct OpsMixed {
       const float om = __fsub_rn(TF(fm::OMB), __fmul_rn(nm1, bmag));
       FieldM f;
       field_mixed(g, bx, by, bz, bmag, om, __fadd_rn(1.0f, nm1), f);
-      // midpoint time (t0 + t1)/(2 dt), float-float, as load_track_mixed forms it
+      // midpoint time (t0 + t1)/(2 dt), float-float, as load_track_mixed forms
+      // it, shifted by k z_m at the exact midpoint height z_m = (z0 + z1)/2
       float tmh, tml;
       two_sum(TF(fm::TAU0H), TF(fm::TAU1H), tmh, tml);
       tml = __fadd_rn(tml, __fadd_rn(TF(fm::TAU0L), TF(fm::TAU1L)));
       tmh *= 0.5f;
       tml *= 0.5f;
+      float zmh, zml;
+      two_sum(z0, z1, zmh, zml);
+      const float kh = KIND == C8R_UNIFORM ? M.s_h : M.kc_h, kl = KIND == C8R_UNIFORM ? M.s_l : M.kc_l;
+      float Tmh, Tml;
+      shifted_time(tmh, tml, 0.5f * zmh, 0.5f * zml, kh, kl, Tmh, Tml);
       float uf;
-      const float kh = KIND == C8R_UNIFORM ? M.s_h : M.kc_h;
-      const float eps_u = __fmaf_rn(2.0f * u * kh, L1, arrival_fast<KIND>(M, A, g, S, tmh, tml, Eh, El, 1.0f, uf));
+      const float eps_a = split_pays(g, S, rho2)
+                              ? arrival_fast<KIND, true>(M, A, g, S, rho2, Tmh, Tml, Eh, El, 3.0f, uf)
+                              : arrival_fast<KIND, false>(M, A, g, S, rho2, Tmh, Tml, Eh, El, 3.0f, uf);
+      const float eps_u = __fmaf_rn(2.0f * u * kh, L1, eps_a);
       const float dtau = TF(fm::DTAUH);
       const float aD = fabsf(f.D);
       const float h = 0.5f * __fmul_rn(aD, dtau);
@@ -749,16 +790,16 @@ struct OpsMixed {
       return kDeferNone;
     } else if constexpr (kFastBins) {
       GeoM g0, g1;
-      float S0, S1;
-      geo_fast(A, t.x0, t.y0, t.z0, g0, S0);
-      geo_fast(A, t.x1, t.y1, t.z1, g1, S1);
+      float S0, S1, P0, P1;
+      geo_fast(A, t.x0, t.y0, t.z0, g0, S0, P0);
+      geo_fast(A, t.x1, t.y1, t.z1, g1, S1, P1);
       if (g0.R0 == 0.0f || g1.R0 == 0.0f) return kDeferNone;
       FieldM f0, f1;
       field_mixed(g0, t.bx, t.by, t.bz, t.bmag, t.om0, __fadd_rn(1.0f, t.nm1_0), f0);
       field_mixed(g1, t.bx, t.by, t.bz, t.bmag, t.om1, __fadd_rn(1.0f, t.nm1_1), f1);
       if (!(fminf(fabsf(f0.D), fabsf(f1.D)) >= M.eps_C)) return kDeferPair;
-      const int ka = arrival_bin_fast<KIND>(M, A, g0, S0, t.tau0h, t.tau0l, t.E0h, t.E0l);
-      const int kb = arrival_bin_fast<KIND>(M, A, g1, S1, t.tau1h, t.tau1l, t.E1h, t.E1l);
+      int ka, kb;
+      fast_bins(t, A, M, g0, g1, S0, S1, P0, P1, ka, kb);
       if (ka >= 0) adj_end<0>(g0, f0, t.nm1_0, t.E0h, t.amp, G[ka], M, tg, ga, dn);
       if (kb >= 0) adj_end<1>(g1, f1, t.nm1_1, t.E1h, -t.amp, G[kb], M, tg, ga, dn);
       return (ka == kFastUndecided ? kDeferEnd0 : 0) | (kb == kFastUndecided ? kDeferEnd1 : 0);
@@ -833,10 +874,6 @@ struct OpsMixed {
       if (!endpoint_midpoint<KIND>(t, A, M, e)) return;
       adj_deposits(t, e, M, G, tg, ga, dn);
     }
-  }
-  static __device__ __forceinline__ void adj(const TrackM& t, const AntRec& A, const MedParams& M, const float4* G,
-                                             const PrefixFF* Gp, float tg[11], float ga[3], float& dn) {
-    if (adj_main(t, A, M, G, Gp, tg, ga, dn)) adj_deferred(t, A, M, G, Gp, tg, ga, dn);
   }
 
   // G summed over bins kb..ke from the float-float running sums: the FP32
@@ -1203,8 +1240,14 @@ cudaError_t forward_mixed(int formalism, const void* tiles, int64_t n_tiles, con
   if (M.kind == C8R_EXPONENTIAL_RAY)
     return formalism == C8R_ENDPOINT ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL_RAY, LIN>{})
                                      : go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL_RAY, LIN>{});
-  if (formalism == C8R_ENDPOINT)
+  if (formalism == C8R_ENDPOINT) {
+    if constexpr (!LIN) {  // the one-bin Endpoint kernels come in both arrival forms (M.split)
+      if (M.split)
+        return ex ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, false, true>{})
+                  : go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, false, true>{});
+    }
     return ex ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, LIN>{}) : go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, LIN>{});
+  }
   return ex ? go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, LIN>{}) : go(OpsMixed<C8R_ZHS, C8R_UNIFORM, LIN>{});
 }
 
@@ -1214,6 +1257,11 @@ cudaError_t backward_mixed(int formalism, BwdArgs& a, const FwdShape& shape, int
   if (formalism == C8R_ZHS)
     return ex ? launch_backward_ops<OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, LIN>>(a, shape, sm_count, st)
               : launch_backward_ops<OpsMixed<C8R_ZHS, C8R_UNIFORM, LIN>>(a, shape, sm_count, st);
+  if constexpr (!LIN) {
+    if (a.M.split)
+      return ex ? launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, false, true>>(a, shape, sm_count, st)
+                : launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, false, true>>(a, shape, sm_count, st);
+  }
   return ex ? launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, LIN>>(a, shape, sm_count, st)
             : launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, LIN>>(a, shape, sm_count, st);
 }

@@ -59,8 +59,10 @@ def test_mixed_zhs_adjoint_with_a_constant_gradient_part():
     check_adjoint("mixed", 1e-4, "zhs", offset=2.0)
 
 
-def check_adjoint(precision, tol, formalism, offset=0.0):
+def check_adjoint(precision, tol, formalism, offset=0.0, form=None):
     c8r, w, tracks, p = setup(precision, formalism=formalism)
+    if form:
+        p.set_arrival_form(form)
     dt = torch.float64 if precision == "fp64" else torch.float32
     dev = to_device(tracks, dt)
     # loss = sum (trace - target)^2 against traces of 1%-perturbed endpoints and
@@ -97,6 +99,13 @@ def check_adjoint(precision, tol, formalism, offset=0.0):
     assert rel_l2(got[:, 8:11], tg_ref[:, 8:11]) <= tol
     assert rel_l2(ag.cpu().numpy(), ag_ref) <= tol
     assert abs(dn.item() - dn_ref) <= tol * abs(dn_ref)
+
+
+@pytest.mark.parametrize("form", ["split", "direct"])
+def test_mixed_endpoint_adjoint_in_both_arrival_forms(form):
+    """The Endpoint adjoint takes its bins as the forward kernel does, from the
+    FP32 arrival in the pinned form where its bound leaves no edge in reach."""
+    check_adjoint("mixed", 1e-4, "endpoint", form=form)
 
 
 @pytest.mark.parametrize("formalism", ["endpoint", "zhs"])

@@ -340,3 +340,74 @@ def test_dense_media_match_oracle(medium, formalism, precision, tol):
     # interval to one bin; every arrival of a pair that reaches it is compared
     reach = ~((ou < 0).all(axis=-1) | (ou >= w["n_bins"]).all(axis=-1))
     assert reach.sum() > 1000 and n_cmp > 0.99 * 2 * reach.sum()
+
+
+ICE = {"kind": "uniform", "n": 1.78}
+FORM_CASES = [
+    # (cfg, n_tracks, n_ant, ice): where each form of the FP32 arrival pays and where not
+    (1, 20011, 160, False),   # vertical shower, star array: lines of sight near the vertical
+    (2, 20011, 256, False),   # 60 degrees, 32 x 32 grid: inclined lines of sight
+    (0, 20011, 16, False),    # uniform medium, a line of antennas
+    (0, 8009, 16, True),      # ice, antennas 0.6-3 km out: near-horizontal lines of sight
+]
+
+
+def form_workload(cfg, n, n_ant, ice):
+    w = synth.workload(cfg, n_tracks=n, n_ant=n_ant)
+    w["dtype"] = np.float32
+    if ice:
+        w["medium"] = dict(ICE)
+        w["ant_xyz"] = np.stack([np.linspace(600.0, 3000.0, 16), np.zeros(16), np.zeros(16)], 1)
+    tracks = synth.workload_tracks(w)
+    if ice:
+        _, u0 = oracle_arrivals(tracks, w["ant_xyz"], np.zeros(16), 1, w["dt_ns"], w["medium"], "endpoint")
+        w["t_start_ns"] = np.median(u0.reshape(len(tracks["x0"]), 16, 2)[..., 0], axis=0) * w["dt_ns"] - 300.0
+    return w, tracks
+
+
+@pytest.mark.parametrize("form", ["split", "direct"])
+@pytest.mark.parametrize("cfg,n,n_ant,ice", FORM_CASES)
+def test_arrival_forms_match_oracle(cfg, n, n_ant, ice, form):
+    """Each form of the FP32 arrival of the mixed one-bin Endpoint kernels,
+    pinned, against the oracle at the mixed bar, antenna by antenna, on a
+    geometry where it pays and on ones where it does not: a bin comes from the
+    FP32 arrival only where its bound leaves no edge in reach."""
+    w, tracks = form_workload(cfg, n, n_ant, ice)
+    ref, kept = oracle_traces(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], "endpoint")
+    p = process(w, "endpoint", "mixed")
+    p.set_arrival_form(form)
+    p.push(to_device(tracks, torch.float32))
+    gpu = p.traces().cpu().numpy()
+    st = p.stats()
+    p.close()
+    assert st["tracks_kept"] == kept and st["arrival_form"] == form
+    ref = either_bin_reference(gpu, ref, tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"])
+    assert np.abs(ref).max() > 0
+    err = rel_l2(gpu, ref)
+    assert err <= 1e-4, f"relative L2 {err:.3e}"
+    per_ant = [rel_l2(gpu[a], ref[a]) for a in range(len(ref)) if np.abs(ref[a]).max() > 0]
+    assert max(per_ant) <= 1e-4, f"worst antenna: relative L2 {max(per_ant):.3e}"
+
+
+@pytest.mark.parametrize("cfg,n_ant,expect", [(1, 160, "split"), (2, 256, "direct")])
+def test_arrival_form_chosen_from_the_tracks(cfg, n_ant, expect):
+    """The automatic choice: before any push the split form; each push's ingest
+    counts the tracks whose start point sees the antenna array from above within
+    45 degrees, and later pushes follow the count (split for the vertical
+    shower, direct for the 60-degree one).  The bins are the same in both forms,
+    so a push in either form gives the same traces up to the order of the
+    additions; a new antenna layout starts over."""
+    w, tracks = form_workload(cfg, 20011, n_ant, False)
+    dev = to_device(tracks, torch.float32)
+    p = process(w, "endpoint", "mixed")
+    assert p.stats()["arrival_form"] == "split"
+    p.push(dev)
+    first = p.traces(reset=True).cpu().numpy()
+    assert p.stats()["arrival_form"] == expect
+    p.push(dev)
+    second = p.traces(reset=True).cpu().numpy()
+    assert rel_l2(second, first) <= 1e-6
+    assert np.abs(second - first).max() <= 1e-5 * np.abs(first).max()
+    p.set_antenna_positions(np.asarray(w["ant_xyz"])[::-1].copy())   # same layout: the count stays
+    assert p.stats()["arrival_form"] == expect
+    p.close()
