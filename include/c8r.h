@@ -375,8 +375,8 @@ int c8r_batch_sync(c8r_batch* b, void* cuda_stream);
  * track pipeline and returned early (the traces are then incomplete).
  *
  * The first call on a device looks up the device addresses of the scratch
- * arrays (once per device, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the same scratch,
+ * arrays (once per device, with that device current).  Every call on a device
+ * shares the same scratch,
  * which keeps the last call's contents (the status word is cleared at the start
  * of each call): calls whose work overlaps on the GPU race, so issue them on one
  * stream or synchronise between them.  The antenna table is copied from pageable

@@ -373,6 +373,10 @@ def test_arrival_forms_match_oracle(cfg, n, n_ant, ice, form):
     geometry where it pays and on ones where it does not: a bin comes from the
     FP32 arrival only where its bound leaves no edge in reach."""
     w, tracks = form_workload(cfg, n, n_ant, ice)
+    check_form(w, tracks, form)
+
+
+def check_form(w, tracks, form):
     ref, kept = oracle_traces(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], "endpoint")
     p = process(w, "endpoint", "mixed")
     p.set_arrival_form(form)
@@ -387,6 +391,33 @@ def test_arrival_forms_match_oracle(cfg, n, n_ant, ice, form):
     assert err <= 1e-4, f"relative L2 {err:.3e}"
     per_ant = [rel_l2(gpu[a], ref[a]) for a in range(len(ref)) if np.abs(ref[a]).max() > 0]
     assert max(per_ant) <= 1e-4, f"worst antenna: relative L2 {max(per_ant):.3e}"
+
+
+@pytest.mark.parametrize("form", ["split", "direct"])
+@pytest.mark.parametrize("case", ["antennas_inside_the_shower", "late_time_origin"])
+def test_arrival_forms_edge_geometries(case, form):
+    """Both forms where their arithmetic changes branch or scale: antennas at
+    4 km, the shower's median track height, so that half of the emission points
+    lie below them (the split form's direct fallback, x = R + s_z >= R); and a
+    time origin 1e6 ns before the shower (shifted times near 5e6 bins, where the
+    float-float forms of T and the u^2 terms of the bound matter)."""
+    w = synth.workload(1, n_tracks=6007, n_ant=16)
+    w["dtype"] = np.float32
+    tracks = synth.workload_tracks(w)
+    if case == "antennas_inside_the_shower":
+        ant = np.asarray(w["ant_xyz"], np.float64).copy()
+        ant[:, 2] = 4000.0
+        w["ant_xyz"] = ant
+        _, u0 = oracle_arrivals(tracks, ant, np.zeros(16), 1, w["dt_ns"], w["medium"], "endpoint")
+        w["t_start_ns"] = np.median(u0.reshape(len(tracks["x0"]), 16, 2)[..., 0], axis=0) * w["dt_ns"] - 300.0
+        assert (tracks["z0"] < 4000.0).mean() > 0.3
+    else:
+        off = 1.0e6
+        tracks = dict(tracks)
+        tracks["t0"] = (tracks["t0"].astype(np.float64) + off).astype(np.float32)
+        tracks["t1"] = (tracks["t1"].astype(np.float64) + off).astype(np.float32)
+        w["t_start_ns"] = np.asarray(w["t_start_ns"], np.float64) + off
+    check_form(w, tracks, form)
 
 
 @pytest.mark.parametrize("cfg,n_ant,expect", [(1, 160, "split"), (2, 256, "direct")])
