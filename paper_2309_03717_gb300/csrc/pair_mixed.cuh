@@ -879,7 +879,8 @@ struct OpsMixed {
   // G summed over bins kb..ke from the float-float running sums: the FP32
   // difference of the high parts is exact or rounded relative to the result,
   // and the low parts restore what the high parts dropped, so the sum comes out
-  // as accurate as an FP64 difference rounded to FP32, without the FP64 pipe
+  // rounded to FP32 plus the running sums' own error (~2k u^2 of the largest
+  // partial sum after k bins), without the FP64 pipe
   static __device__ __forceinline__ void run_sum(const PrefixFF* Gp, int kb, int ke, float& ix, float& iy,
                                                  float& iz) {
     const PrefixFF p1 = Gp[ke + 1], p0 = Gp[kb];
