@@ -406,6 +406,7 @@ void c8r_destroy(c8r_ctx* c) {
   if (c->d_tiles) cudaFree(c->d_tiles);
   if (c->d_kept) cudaFree(c->d_kept);
   if (c->d_err) cudaFree(c->d_err);
+  if (c->form_pending) cudaEventSynchronize(c->ev_form);  // the votes' copy lands before its buffer goes
   if (c->ev_form) cudaEventDestroy(c->ev_form);
   if (c->h_form) cudaFreeHost(c->h_form);
   delete c;
