@@ -125,6 +125,21 @@ void fill_antenna(AntRec& r, double x, double y, double z, double t_ref_ns, cons
   r.fb_rel_v = M.kind == C8R_UNIFORM ? 0.0f : (float)(1.01 * std::fabs((double)r.zl) / (0.999e-3 * M.H));
 }
 
+void set_flat_array(MedParams& M, const double* pos_xyz, int n_ant) {
+  M.flat = 0;
+  if (M.kind != C8R_EXPONENTIAL || n_ant <= 0) return;
+  const double z = pos_xyz[2];
+  for (int a = 1; a < n_ant; ++a)
+    if (pos_xyz[3 * (size_t)a + 2] != z) return;
+  // split as fill_antenna splits the antennas' z and exp(-z/H)
+  M.flat = 1;
+  M.flat_zh = (float)z;
+  M.flat_zl = (float)(z - (double)M.flat_zh);
+  const double E = std::exp(-z / M.H);
+  M.flat_Eh = (float)E;
+  M.flat_El = (float)(E - (double)M.flat_Eh);
+}
+
 void set_form_centroid(MedParams& M, const double* pos_xyz, int n_ant) {
   double c[3] = {0.0, 0.0, 0.0};
   for (int a = 0; a < n_ant; ++a)
@@ -263,6 +278,7 @@ int rebuild_tables(c8r_ctx* c) {
   if (!c->ants_set) return C8R_OK;
   fill_medium(c->M, c->med_kind, c->med_a, c->med_H, c->n_bins, c->dt_ns, c->eps_C, c->med_RE);
   set_form_centroid(c->M, c->pos.data(), c->n_ant);
+  set_flat_array(c->M, c->pos.data(), c->n_ant);
   c->M.split = c->split ? 1 : 0;
   std::vector<AntRec> recs(c->n_ant);
   for (int a = 0; a < c->n_ant; ++a)

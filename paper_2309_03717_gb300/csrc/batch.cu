@@ -130,24 +130,28 @@ cudaError_t launch_batch_ops(const BatchArgs& a, int sm_count, cudaStream_t st) 
 }
 
 template <class F>
-auto with_batch_ops(int formalism, int kind, bool split, F f) {
+auto with_batch_ops(int formalism, int kind, bool split, bool flat, F f) {
   const bool ex = kind == C8R_EXPONENTIAL;
+  // the arrival form of the one-bin Endpoint kernel (OpsMixed::kSplit) and, for
+  // the direct form, the flat-array kernel of the exponential medium
+  // (OpsMixed::kFlat)
   if (formalism == C8R_ENDPOINT) {
-    if (split)  // the arrival form of the one-bin Endpoint kernel (OpsMixed::kSplit)
-      return ex ? f(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, false, true>{})
-                : f(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, false, true>{});
-    return ex ? f(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>{}) : f(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>{});
+    if (!ex)
+      return split ? f(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, false, true>{}) : f(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM>{});
+    if (split) return f(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, false, true>{});
+    return flat ? f(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, false, false, true>{})
+                : f(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL>{});
   }
   return ex ? f(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL>{}) : f(OpsMixed<C8R_ZHS, C8R_UNIFORM>{});
 }
 
 cudaError_t launch_batch(const BatchArgs& a, int formalism, int sm_count, cudaStream_t st) {
-  return with_batch_ops(formalism, a.M.kind, a.M.split != 0,
+  return with_batch_ops(formalism, a.M.kind, a.M.split != 0, a.M.flat != 0,
                         [&](auto ops) { return launch_batch_ops<decltype(ops)>(a, sm_count, st); });
 }
 
 int batch_resident(int formalism, int kind, int a_tile, int sm_count) {
-  return sm_count * with_batch_ops(formalism, kind, false,
+  return sm_count * with_batch_ops(formalism, kind, false, false,
                                    [&](auto ops) { return batch_blocks_per_sm<decltype(ops)>(a_tile); });
 }
 
@@ -444,6 +448,7 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
   }
   b->total_tiles = b->tile_off[d->n_showers];
   set_form_centroid(b->M, d->pos_xyz, b->total_ant);
+  set_flat_array(b->M, d->pos_xyz, b->total_ant);
   b->M.split = 1;
   std::vector<AntRec> recs(b->total_ant);
   for (int a = 0; a < b->total_ant; ++a) {

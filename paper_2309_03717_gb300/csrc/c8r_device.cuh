@@ -112,6 +112,13 @@ struct MedParams {
   // count (1: the split form of x = R - w)
   float cen_x, cen_y, cen_z;
   int split;
+  // a flat antenna array (every antenna at one altitude z_a, exponential
+  // medium): z_a and exp(-z_a/H) as float-float, the same values the antenna
+  // records hold, so that the quotient (E_e - E_a)/(z_a - z_e) of the
+  // refractivity term, the same for every antenna, can be formed once per
+  // track (OpsMixed::kFlat)
+  int flat;
+  float flat_zh, flat_zl, flat_Eh, flat_El;
 };
 
 // ---------------------------------------------------------------------------
@@ -459,14 +466,44 @@ __device__ __forceinline__ void geo_mixed(const AntRec& A, float pxh, float pyh,
   geo_refine(g);
 }
 
-// arrival position u = (t_e - t_ref)/dt + n_avg R / (c dt) in bins, float-float.
-// tau_e = t_e/dt and the antenna's tau = t_ref/dt come in float-float.
-// KIND: the medium kind (a template argument, so each kernel carries only its own
-// medium's arithmetic; it equals M.kind)
-// `dop` (curved rays only): the ray's optical path minus the straight line's, m
+// (E_e - E_a)/dz in float-float, the quotient of the refractivity term of the
+// exponential medium, dz = dzh + dzl the altitude difference a - e: the FP32
+// quotient corrected once from the exact residual, or for |dz/H| <= 1e-3 the
+// series (E_e/H)(1 + f), f = -x/2 + x^2/6 - x^3/24, x = dz/H
+__device__ __forceinline__ void refr_quotient(const MedParams& M, float Eah, float Eal, float dzh, float dzl,
+                                              float Eeh, float Eel, float& q0, float& q1) {
+  const float x = __fmul_rn(dzh, M.invH_h);
+  if (fabsf(x) > 1e-3f) {
+    float Qh, Ql;
+    two_sum(Eeh, -Eah, Qh, Ql);
+    Ql = __fadd_rn(Ql, __fsub_rn(Eel, Eal));
+    q0 = __fdividef(Qh, dzh);
+    float ph, pl;
+    two_prod(q0, dzh, ph, pl);
+    const float r = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(Qh, ph), pl), Ql), __fmul_rn(q0, dzl));
+    q1 = __fdividef(r, dzh);
+  } else {
+    const float f = __fmul_rn(x, __fmaf_rn(x, __fmaf_rn(x, -1.0f / 24.0f, 1.0f / 6.0f), -0.5f));
+    float eh, el;
+    two_prod(Eeh, M.invH_h, eh, el);
+    el = __fmaf_rn(Eeh, M.invH_l, __fmaf_rn(Eel, M.invH_h, el));
+    // (eh + el)(1 + f)
+    float g0, g1;
+    two_sum(eh, __fmul_rn(eh, f), g0, g1);
+    q0 = g0;
+    q1 = __fadd_rn(g1, __fmaf_rn(el, f, el));
+  }
+}
+
+// arrival position u = (t_e - t_ref)/dt + n_avg R / (c dt) in bins, float-float,
+// with the refractivity quotient (q0, q1) given (exponential media; ignored in
+// the uniform one).  tau_e = t_e/dt and the antenna's tau = t_ref/dt come in
+// float-float.  KIND: the medium kind (a template argument, so each kernel
+// carries only its own medium's arithmetic; it equals M.kind).  `dop` (curved
+// rays only): the ray's optical path minus the straight line's, m
 template <int KIND>
-__device__ __forceinline__ ff arrival_mixed(const MedParams& M, const AntRec& A, const GeoM& g, float tauh, float taul,
-                                            float Eeh, float Eel, float dop = 0.0f) {
+__device__ __forceinline__ ff arrival_mixed_q(const MedParams& M, const AntRec& A, const GeoM& g, float tauh,
+                                              float taul, float q0, float q1, float dop = 0.0f) {
   float ts, te;
   two_sum(tauh, -A.tauh, ts, te);
   te = __fadd_rn(te, __fsub_rn(taul, A.taul));
@@ -477,30 +514,6 @@ __device__ __forceinline__ ff arrival_mixed(const MedParams& M, const AntRec& A,
   pe = __fmaf_rn(g.R0, sl, __fmaf_rn(g.R1, sh, pe));
   if constexpr (KIND != C8R_UNIFORM) {
     // refractivity term (n_avg - 1) R/(c dt) = N0 H/(c dt) * (E_e - E_a)/dz * R
-    float q0, q1;
-    float dzh = g.s[2], dzl = g.e[2];
-    float x = __fmul_rn(dzh, M.invH_h);
-    if (fabsf(x) > 1e-3f) {
-      float Qh, Ql;
-      two_sum(Eeh, -A.Eah, Qh, Ql);
-      Ql = __fadd_rn(Ql, __fsub_rn(Eel, A.Eal));
-      q0 = __fdividef(Qh, dzh);
-      float ph, pl;
-      two_prod(q0, dzh, ph, pl);
-      float r = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(Qh, ph), pl), Ql), __fmul_rn(q0, dzl));
-      q1 = __fdividef(r, dzh);
-    } else {
-      // (E_e - E_a)/dz = (E_e/H) (1 - exp(-x))/x = (E_e/H)(1 + f), f = -x/2 + x^2/6 - x^3/24
-      float f = __fmul_rn(x, __fmaf_rn(x, __fmaf_rn(x, -1.0f / 24.0f, 1.0f / 6.0f), -0.5f));
-      float eh, el;
-      two_prod(Eeh, M.invH_h, eh, el);
-      el = __fmaf_rn(Eeh, M.invH_l, __fmaf_rn(Eel, M.invH_h, el));
-      // (eh + el)(1 + f)
-      float g0, g1;
-      two_sum(eh, __fmul_rn(eh, f), g0, g1);
-      q0 = g0;
-      q1 = __fadd_rn(g1, __fmaf_rn(el, f, el));
-    }
     float w, we;
     two_prod(q0, g.R0, w, we);
     we = __fmaf_rn(q0, g.R1, __fmaf_rn(q1, g.R0, we));
@@ -531,6 +544,16 @@ __device__ __forceinline__ ff arrival_mixed(const MedParams& M, const AntRec& A,
   two_sum(ts, p, uh, ue);
   ue = __fadd_rn(ue, __fadd_rn(te, pe));
   return ff{uh, ue};
+}
+
+// the same with the quotient formed here, from the emission point's E_e =
+// exp(-z_e/H) and the altitude difference of g
+template <int KIND>
+__device__ __forceinline__ ff arrival_mixed(const MedParams& M, const AntRec& A, const GeoM& g, float tauh, float taul,
+                                            float Eeh, float Eel, float dop = 0.0f) {
+  float q0 = 0.0f, q1 = 0.0f;
+  if constexpr (KIND != C8R_UNIFORM) refr_quotient(M, A.Eah, A.Eal, g.s[2], g.e[2], Eeh, Eel, q0, q1);
+  return arrival_mixed_q<KIND>(M, A, g, tauh, taul, q0, q1, dop);
 }
 
 // bin index of a float-float arrival, clamped to [-1, n_bins]: -1 stands for
@@ -661,14 +684,26 @@ __device__ __forceinline__ bool split_pays(const GeoM& g, float S, float rho2) {
   return g.s[2] < 0.0f && __fadd_rn(rho2, rho2) < S;
 }
 
+// the FP32 quotient (E_e - E_a)/dz of the refractivity term for the FP32
+// arrival (exponential medium): dz = s_z, the FP32 a_h - p of the emission
+// point (the same for every antenna of a flat array); for |dz/H| <= 1e-3 its
+// series (E_e/H)(1 + f)
+__device__ __forceinline__ float fast_quotient(const MedParams& M, float Eah, float Eal, float sz, float Eeh,
+                                               float Eel) {
+  const float x = __fmul_rn(sz, M.invH_h);
+  if (fabsf(x) > 1e-3f) return __fdividef(__fadd_rn(__fsub_rn(Eeh, Eah), __fsub_rn(Eel, Eal)), sz);
+  const float f = __fmul_rn(x, __fmaf_rn(x, __fmaf_rn(x, -1.0f / 24.0f, 1.0f / 6.0f), -0.5f));
+  return __fmul_rn(__fmul_rn(Eeh, M.invH_h), __fadd_rn(1.0f, f));
+}
+
 // The FP32 arrival uf of the emission point of g (S = |d|^2, rho2 = d_x^2 +
-// d_y^2, T_e = Teh + Tel) and its error bound, returned; SPLIT picks the form
-// of x; q_extra adds a term u * q_extra * k x for geometry whose d carries
-// more than the one rounding of a_h - p (the midpoint)
+// d_y^2, T_e = Teh + Tel, qv the refractivity quotient of fast_quotient) and
+// its error bound, returned; SPLIT picks the form of x; q_extra adds a term
+// u * q_extra * k x for geometry whose d carries more than the one rounding of
+// a_h - p (the midpoint)
 template <int KIND, bool SPLIT>
 __device__ __forceinline__ float arrival_fast(const MedParams& M, const AntRec& A, const GeoM& g, float S, float rho2,
-                                              float Teh, float Tel, float Eeh, float Eel, float q_extra,
-                                              float& uf_out) {
+                                              float Teh, float Tel, float qv, float q_extra, float& uf_out) {
   static_assert(KIND == C8R_UNIFORM || KIND == C8R_EXPONENTIAL, "plain straight-line media only");
   constexpr float u = 5.9604644775390625e-8f;  // 2^-24
   // R' = sqrt(S) rounded once
@@ -686,17 +721,7 @@ __device__ __forceinline__ float arrival_fast(const MedParams& M, const AntRec& 
   const float q = __fmul_rn(x, kh);
   const float Td = __fadd_rn(__fsub_rn(Teh, A.Tah), __fsub_rn(Tel, A.Tal));
   float v = 0.0f;
-  if constexpr (KIND == C8R_EXPONENTIAL) {
-    const float x = __fmul_rn(sz, M.invH_h);
-    float qv;
-    if (fabsf(x) > 1e-3f) {
-      qv = __fdividef(__fadd_rn(__fsub_rn(Eeh, A.Eah), __fsub_rn(Eel, A.Eal)), sz);
-    } else {
-      const float f = __fmul_rn(x, __fmaf_rn(x, __fmaf_rn(x, -1.0f / 24.0f, 1.0f / 6.0f), -0.5f));
-      qv = __fmul_rn(__fmul_rn(Eeh, M.invH_h), __fadd_rn(1.0f, f));
-    }
-    v = __fmul_rn(__fmul_rn(qv, R), M.cN_h);
-  }
+  if constexpr (KIND == C8R_EXPONENTIAL) v = __fmul_rn(__fmul_rn(qv, R), M.cN_h);
   const float uf = __fadd_rn(__fadd_rn(Td, q), v);
   uf_out = uf;
   const float tail = __fmaf_rn(2.25f * u, fabsf(Td),
@@ -711,9 +736,9 @@ __device__ __forceinline__ float arrival_fast(const MedParams& M, const AntRec& 
 
 template <int KIND, bool SPLIT>
 __device__ __forceinline__ int arrival_bin_fast(const MedParams& M, const AntRec& A, const GeoM& g, float S,
-                                                float rho2, float Teh, float Tel, float Eeh, float Eel) {
+                                                float rho2, float Teh, float Tel, float qv) {
   float uf;
-  const float eps = arrival_fast<KIND, SPLIT>(M, A, g, S, rho2, Teh, Tel, Eeh, Eel, 0.0f, uf);
+  const float eps = arrival_fast<KIND, SPLIT>(M, A, g, S, rho2, Teh, Tel, qv, 0.0f, uf);
   if (uf < -eps || __fsub_rn(uf, eps) >= (float)M.n_bins) return kFastOut;
   const float k = floorf(uf);
   const float fr = __fsub_rn(uf, k);

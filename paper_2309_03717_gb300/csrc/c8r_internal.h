@@ -133,5 +133,8 @@ void fill_antenna(AntRec& r, double x, double y, double z, double t_ref_ns, cons
 // the antenna array's centroid (MedParams::cen_*), which the ingest's votes for
 // the arrival form of the one-bin Endpoint kernels refer to
 void set_form_centroid(MedParams& M, const double* pos_xyz, int n_ant);
+// MedParams::flat and its altitude terms: set when the medium is the flat
+// exponential atmosphere and every antenna has the same z (exactly)
+void set_flat_array(MedParams& M, const double* pos_xyz, int n_ant);
 
 }  // namespace c8r

@@ -25,6 +25,10 @@ struct TrackM {
   float amp;                     // q K/dt (Endpoint) or q K_A (t1-t0)/dt (ZHS); 0 = dropped
   float tau0h, tau0l, tau1h, tau1l, dtauh, dtaul;
   float T0h, T0l, T1h, T1l;      // Endpoint, plain media: tau + k z at start and end (arrival_fast)
+  // a flat antenna array (MedParams::flat, exponential medium): the quotient of
+  // the refractivity term, the same for every antenna, per track: FP32 at start
+  // and end (Endpoint, arrival_fast), float-float at the midpoint (ZHS)
+  float q0v, q1v, qmh, qml;
   float E0h, E0l, E1h, E1l, Emh, Eml;
   float nm1_0, nm1_1, nm1_m;     // n - 1 at start, end, midpoint
   float om0, om1, om_m;          // 1 - n|beta| at start, end, midpoint
@@ -32,7 +36,7 @@ struct TrackM {
   float mx, mxl, my, myl, mz, mzl, tmh, tml;
 };
 
-template <int FORM, int KIND>
+template <int FORM, int KIND, bool FLAT = false>
 __device__ __forceinline__ void load_track_mixed(const float* T, int l, const MedParams& M, TrackM& t) {
   t.amp = FORM == C8R_ENDPOINT ? TF(fm::AMPE) : (TF(fm::AMPE) == 0.0f ? 0.0f : TF(fm::AMPZ));
   if (t.amp == 0.0f) return;  // filtered track or padding
@@ -85,6 +89,20 @@ __device__ __forceinline__ void load_track_mixed(const float* T, int l, const Me
     two_sum(t.y0, t.y1, t.my, t.myl);
     two_sum(t.z0, t.z1, t.mz, t.mzl);
     t.mx *= 0.5f; t.mxl *= 0.5f; t.my *= 0.5f; t.myl *= 0.5f; t.mz *= 0.5f; t.mzl *= 0.5f;
+  }
+  if constexpr (FLAT && KIND == C8R_EXPONENTIAL) {
+    // the refractivity quotient against the array's altitude, formed as the
+    // per-pair arithmetic forms it (the altitude difference as geo_fast and
+    // geo_lite form it), so the values are the same
+    if constexpr (FORM == C8R_ENDPOINT) {
+      t.q0v = fast_quotient(M, M.flat_Eh, M.flat_El, __fadd_rn(M.flat_zh, -t.z0), t.E0h, t.E0l);
+      t.q1v = fast_quotient(M, M.flat_Eh, M.flat_El, __fadd_rn(M.flat_zh, -t.z1), t.E1h, t.E1l);
+    } else {
+      float dzh, dzl;
+      two_sum(M.flat_zh, -t.mz, dzh, dzl);
+      dzl = __fadd_rn(dzl, __fsub_rn(M.flat_zl, t.mzl));
+      refr_quotient(M, M.flat_Eh, M.flat_El, dzh, dzl, t.Emh, t.Eml, t.qmh, t.qml);
+    }
   }
 }
 
@@ -273,7 +291,7 @@ __device__ __forceinline__ LinEnds lin_ends(int Jlo, float slo, int Jhi, float s
   return z;
 }
 
-template <int FORM, int KIND, bool LIN = false, bool SPLIT = false>
+template <int FORM, int KIND, bool LIN = false, bool SPLIT = false, bool FLAT = false>
 struct OpsMixed {
   using acc_t = float;
   using Track = TrackM;
@@ -301,6 +319,13 @@ struct OpsMixed {
   // share of tracks that see the antenna array from above within 45 degrees
   // (counted by the ingest of earlier launches)
   static constexpr bool kSplit = SPLIT && kFastBins;
+  // a flat antenna array: the refractivity quotient per track, in the main pass
+  // of the Endpoint forward kernel of the direct arrival form (the host picks
+  // the kernel, MedParams::flat).  Measured on 4e6 tracks: 47.96 -> 44.01 ms on
+  // the 60-degree array; for the near-vertical lines of sight of the split
+  // form it was 0.35 % slower (6.85 -> 6.87 ms), and in the ZHS kernel 0.6 %
+  // slower, so those keep the quotient per pair
+  static constexpr bool kFlat = FLAT && kFastBins && !SPLIT && KIND == C8R_EXPONENTIAL;
   // adjoint CTAs (128 threads) per SM the registers are set for (the linear
   // Endpoint adjoint carries the slide of each deposit as well)
   static constexpr int kBwdMinBlocks = (LIN && FORM == C8R_ENDPOINT) ? 4 : 6;
@@ -323,7 +348,7 @@ struct OpsMixed {
   }
 
   static __device__ __forceinline__ void load(const void* Tv, int l, const MedParams& M, TrackM& t) {
-    load_track_mixed<FORM, KIND>(static_cast<const float*>(Tv), l, M, t);
+    load_track_mixed<FORM, KIND, kFlat>(static_cast<const float*>(Tv), l, M, t);
   }
   static __device__ __forceinline__ bool live(const TrackM& t) { return t.amp != 0.0f; }
 
@@ -439,7 +464,11 @@ struct OpsMixed {
       field_mixed(gm, t.bx, t.by, t.bz, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), f);
     }
     geo_refine(gm);
-    const ff um = arrival_mixed<KIND>(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml, dop);
+    ff um;
+    if constexpr (kFlat)
+      um = arrival_mixed_q<KIND>(M, A, gm, t.tmh, t.tml, t.qmh, t.qml, dop);
+    else
+      um = arrival_mixed<KIND>(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml, dop);
     ff aD = doppler_ff(gm, t.bx, t.by, t.bz, t.nm1_m);
     if constexpr (KIND == C8R_EXPONENTIAL_RAY) aD = ff_add_small(aD, dD);
     if (aD.h < 0.0f) {
@@ -507,13 +536,16 @@ struct OpsMixed {
   static __device__ __forceinline__ void fast_bins(const TrackM& t, const AntRec& A, const MedParams& M,
                                                    const GeoM& g0, const GeoM& g1, float S0, float S1, float P0,
                                                    float P1, int& ka, int& kb) {
-    if constexpr (kSplit) {
-      ka = arrival_bin_fast<KIND, true>(M, A, g0, S0, P0, t.T0h, t.T0l, t.E0h, t.E0l);
-      kb = arrival_bin_fast<KIND, true>(M, A, g1, S1, P1, t.T1h, t.T1l, t.E1h, t.E1l);
-    } else {
-      ka = arrival_bin_fast<KIND, false>(M, A, g0, S0, P0, t.T0h, t.T0l, t.E0h, t.E0l);
-      kb = arrival_bin_fast<KIND, false>(M, A, g1, S1, P1, t.T1h, t.T1l, t.E1h, t.E1l);
+    float qa = 0.0f, qb = 0.0f;
+    if constexpr (kFlat) {
+      qa = t.q0v;
+      qb = t.q1v;
+    } else if constexpr (KIND == C8R_EXPONENTIAL) {
+      qa = fast_quotient(M, A.Eah, A.Eal, g0.s[2], t.E0h, t.E0l);
+      qb = fast_quotient(M, A.Eah, A.Eal, g1.s[2], t.E1h, t.E1l);
     }
+    ka = arrival_bin_fast<KIND, kSplit>(M, A, g0, S0, P0, t.T0h, t.T0l, qa);
+    kb = arrival_bin_fast<KIND, kSplit>(M, A, g1, S1, P1, t.T1h, t.T1l, qb);
   }
 
   // main pass: every pair except (Endpoint) the near-Cherenkov ones, for which
@@ -613,9 +645,10 @@ struct OpsMixed {
       float Tmh, Tml;
       shifted_time(tmh, tml, 0.5f * zmh, 0.5f * zml, kh, kl, Tmh, Tml);
       float uf;
+      const float qv = KIND == C8R_EXPONENTIAL ? fast_quotient(M, A.Eah, A.Eal, g.s[2], Eh, El) : 0.0f;
       const float eps_a = split_pays(g, S, rho2)
-                              ? arrival_fast<KIND, true>(M, A, g, S, rho2, Tmh, Tml, Eh, El, 3.0f, uf)
-                              : arrival_fast<KIND, false>(M, A, g, S, rho2, Tmh, Tml, Eh, El, 3.0f, uf);
+                              ? arrival_fast<KIND, true>(M, A, g, S, rho2, Tmh, Tml, qv, 3.0f, uf)
+                              : arrival_fast<KIND, false>(M, A, g, S, rho2, Tmh, Tml, qv, 3.0f, uf);
       const float eps_u = __fmaf_rn(2.0f * u * kh, L1, eps_a);
       const float dtau = TF(fm::DTAUH);
       const float aD = fabsf(f.D);
@@ -1241,14 +1274,21 @@ cudaError_t forward_mixed(int formalism, const void* tiles, int64_t n_tiles, con
   if (M.kind == C8R_EXPONENTIAL_RAY)
     return formalism == C8R_ENDPOINT ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL_RAY, LIN>{})
                                      : go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL_RAY, LIN>{});
-  if (formalism == C8R_ENDPOINT) {
-    if constexpr (!LIN) {  // the one-bin Endpoint kernels come in both arrival forms (M.split)
-      if (M.split)
-        return ex ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, false, true>{})
-                  : go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, false, true>{});
+  if constexpr (!LIN) {
+    // the one-bin Endpoint kernels come in both arrival forms (M.split) and,
+    // for the direct form in the exponential medium, for a flat antenna array
+    // (M.flat, OpsMixed::kFlat)
+    if (formalism == C8R_ENDPOINT) {
+      if (!ex)
+        return M.split ? go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, false, true>{})
+                       : go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, false, false>{});
+      if (M.split) return go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, false, true>{});
+      return M.flat ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, false, false, true>{})
+                    : go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, false, false>{});
     }
-    return ex ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, LIN>{}) : go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, LIN>{});
   }
+  if (formalism == C8R_ENDPOINT)
+    return ex ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, LIN>{}) : go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, LIN>{});
   return ex ? go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, LIN>{}) : go(OpsMixed<C8R_ZHS, C8R_UNIFORM, LIN>{});
 }
 

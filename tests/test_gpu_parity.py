@@ -442,3 +442,53 @@ def test_arrival_form_chosen_from_the_tracks(cfg, n_ant, expect):
     p.set_antenna_positions(np.asarray(w["ant_xyz"])[::-1].copy())   # same layout: the count stays
     assert p.stats()["arrival_form"] == expect
     p.close()
+
+
+@pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_uneven_antenna_altitudes(formalism, precision, tol):
+    """The exponential atmosphere with antennas at different altitudes (0-150 m),
+    where the refractivity quotient (E_e - E_a)/(z_a - z_e) is formed per pair
+    (a flat array forms it once per track): every antenna at the bar."""
+    w = synth.workload(1, n_tracks=6007, n_ant=16)
+    if precision == "mixed":
+        w["dtype"] = np.float32
+    ant = np.asarray(w["ant_xyz"], np.float64).copy()
+    ant[:, 2] = np.linspace(0.0, 150.0, 16)
+    w["ant_xyz"] = ant
+    tracks = synth.workload_tracks(w)
+    _, u0 = oracle_arrivals(tracks, ant, np.zeros(16), 1, w["dt_ns"], w["medium"], formalism)
+    w["t_start_ns"] = np.median(u0.reshape(len(tracks["x0"]), 16, 2)[..., 0], axis=0) * w["dt_ns"] - 300.0
+    ref, kept = oracle_traces(tracks, ant, w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], formalism)
+    gpu, _, st = run(w, tracks, formalism, precision)
+    assert st["tracks_kept"] == kept and np.abs(ref).max() > 0
+    if formalism == "endpoint":
+        ref = either_bin_reference(gpu, ref, tracks, ant, w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"])
+    per_ant = [rel_l2(gpu[a], ref[a]) for a in range(16) if np.abs(ref[a]).max() > 0]
+    assert max(per_ant) <= tol, f"worst antenna: relative L2 {max(per_ant):.3e}"
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_flat_array_kernel_matches_the_per_pair_quotient(cfg):
+    """A flat array (every antenna at z = 0) takes the Endpoint kernel of the
+    direct arrival form that forms the refractivity quotient once per track;
+    moving one antenna by 1 mm in z takes the kernel that forms it per pair.
+    The quotient is the same arithmetic either way, so the other antennas'
+    traces agree to the order of the additions (vertical and 60-degree
+    showers, the direct form pinned)."""
+    w = synth.workload(cfg, n_tracks=20011, n_ant=32 if cfg == 1 else 64)
+    w["dtype"] = np.float32
+    tracks = synth.workload_tracks(w)
+    dev = to_device(tracks, torch.float32)
+    out = []
+    for dz in (0.0, 1e-3):
+        ant = np.asarray(w["ant_xyz"], np.float64).copy()
+        ant[-1, 2] += dz
+        p = process(dict(w, ant_xyz=ant), "endpoint", "mixed")
+        p.set_arrival_form("direct")
+        p.push(dev)
+        out.append(p.traces().cpu().numpy()[:-1].astype(np.float64))
+        p.close()
+    assert np.abs(out[0]).max() > 0
+    assert rel_l2(out[1], out[0]) <= 1e-6
+    assert np.abs(out[1] - out[0]).max() <= 1e-5 * np.abs(out[0]).max()
