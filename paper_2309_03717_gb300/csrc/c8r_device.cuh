@@ -619,30 +619,32 @@ __device__ __forceinline__ int bin_raw(ff u, int n_bins, float& frac) {
 //   rho^2 = fl(s_x^2 + s_y^2) (two roundings, 2u) and S = fl(s_z^2 + rho^2):
 //     R' = S rsqrt(S) plus one Newton step with the residual fma(-R0, R0, S) is
 //     sqrt(S) rounded once, within 2.5u R of |s|;
-//   split form, w > 0: x = rho^2 / fl(R' - s_z) with __fdividef (2 ulp: 4u);
-//     the denominator R + |s_z| >= R carries 3.5u; with rho^2, 9.5u x.  (w <= 0
-//     takes the direct form, x >= R: 3.5u x.)  Direct form: x = fl(R' + s_z),
+//   split form, w > 0: x = rho^2 / fl(R0 - s_z) with __fdividef (2 ulp: 4u),
+//     from the unrefined R0 = fl(S rsqrtf(S)) (rsqrtf 2 ulp: R0 within 6u R of
+//     |s|, so the denominator R + |s_z| >= R carries 7u); with rho^2, 13u x.
+//     (w <= 0: x = fl(R0 + s_z) >= R, 7u x.)  Direct form: x = fl(R' + s_z),
 //     2.5u R + u x;
 //   q = fl(x k_h): u, and u more for the dropped k_l;
 //   Td = fl(fl(T_e,h - T_a,h) + fl(T_e,l - T_a,l)): 2u |Td|, plus terms of
 //     u^2 |T_e| and u^2 |T_a| from the float-float forms of T_e and T_a;
-//   v (exponential medium) = N0 H/(c dt) (E_e - E_a)/dz R': the quotient
-//     (2 ulp) or its series for |dz/H| <= 1e-3, four more roundings and R'
-//     give at most 14u |v|, plus |v| |z_l|/|dz| from the antenna altitude's
-//     low part, |dz| > 1e-3 H in the quotient's branch;
+//   v (exponential medium) = N0 H/(c dt) (E_e - E_a)/dz R' (R0 in the split
+//     form): the quotient (2 ulp) or its series for |dz/H| <= 1e-3, four more
+//     roundings and R' give at most 14u |v| (17.5u with R0), plus
+//     |v| |z_l|/|dz| from the antenna altitude's low part, |dz| > 1e-3 H in
+//     the quotient's branch;
 //   uf = fl(fl(Td + q) + v): u |Td + q| <= u (|uf| + |v|) (Td + q is uf - v
 //     before the last rounding, small against Td and q once the arrival is
 //     near the window) and u |uf|, and one more u |uf| in the window test
 //     uf - bound >= n_bins.
-// The bound used is u (2.25 |Td| + c_q q + 17 |v| + 3.25 |uf|) + fb_rel_v |v| +
-// fb_abs, with c_q = 15 in the split form (14.5 derived) and c_q = 6.25 plus
-// 2.5u k_h R in the direct one (6 and 2.5), each coefficient above its
-// derivation; fb_abs holds 2 k |a_l|,
+// The bound used is u (2.25 |Td| + c_q q + c_v |v| + 3.25 |uf|) + fb_rel_v |v| +
+// fb_abs, with c_q = 19 and c_v = 22 in the split form (18 and 17.5 derived)
+// and c_q = 6.25, c_v = 17 plus 2.5u k_h R in the direct one (6, 14 and 2.5),
+// each coefficient above its derivation; fb_abs holds 2 k |a_l|,
 // 16 u^2 |T_a| (the share of T_e, |T_e| <= |Td| + |T_a|, beyond what the |Td|
 // term covers) and a floor of 1e-6 bin for the float-float arrival's own error
 // and the rounding of uf - floor(uf).  A CPU emulation of these steps (2-ulp
 // reciprocal square root and quotient) against the FP64 oracle's arrivals
-// stays below 0.5 of the bound on the benchmark showers; on a vertical shower
+// stays below 0.6 of the bound on the benchmark showers; on a vertical shower
 // 1-10 km above 0.2-ns traces the bound is ~6e-4 bin and ~0.1 % of the
 // endpoints are left to the float-float arrival (8 % with k R rounded in FP32
 // per pair).  On a shower inclined by 60 degrees x is about R/2 and the direct
@@ -706,9 +708,15 @@ __device__ __forceinline__ float arrival_fast(const MedParams& M, const AntRec& 
                                               float Teh, float Tel, float qv, float q_extra, float& uf_out) {
   static_assert(KIND == C8R_UNIFORM || KIND == C8R_EXPONENTIAL, "plain straight-line media only");
   constexpr float u = 5.9604644775390625e-8f;  // 2^-24
-  // R' = sqrt(S) rounded once
-  const float r = __fmaf_rn(-g.R0, g.R0, S);
-  const float R = __fmaf_rn(r, __fmul_rn(0.5f, g.y), g.R0);
+  // R' = sqrt(S) rounded once (the direct form), or the unrefined R0 (the
+  // split form, whose x is small: R enters it only through its denominator)
+  float R;
+  if constexpr (SPLIT) {
+    R = g.R0;
+  } else {
+    const float r = __fmaf_rn(-g.R0, g.R0, S);
+    R = __fmaf_rn(r, __fmul_rn(0.5f, g.y), g.R0);
+  }
   // x = R - w, w = z_e - z_a = -s_z
   const float sz = g.s[2];
   float x;
@@ -725,10 +733,10 @@ __device__ __forceinline__ float arrival_fast(const MedParams& M, const AntRec& 
   const float uf = __fadd_rn(__fadd_rn(Td, q), v);
   uf_out = uf;
   const float tail = __fmaf_rn(2.25f * u, fabsf(Td),
-                               __fmaf_rn(__fmaf_rn(17.0f, u, A.fb_rel_v), fabsf(v),
+                               __fmaf_rn(__fmaf_rn(SPLIT ? 22.0f : 17.0f, u, A.fb_rel_v), fabsf(v),
                                          __fmaf_rn(3.25f * u, fabsf(uf), A.fb_abs)));
   if constexpr (SPLIT) {
-    return __fmaf_rn(__fmaf_rn(q_extra, u, 15.0f * u), q, tail);
+    return __fmaf_rn(__fmaf_rn(q_extra, u, 19.0f * u), q, tail);
   } else {
     return __fmaf_rn(__fmaf_rn(q_extra, u, 6.25f * u), q, __fmaf_rn(__fmul_rn(2.5f * u, kh), R, tail));
   }
