@@ -71,6 +71,44 @@ struct BatchMap {
   }
 };
 
+// the arrival-form vote of each shower (Endpoint): of the kept tracks in up
+// to kVoteTiles of its derived-track tiles, those whose start point sees the
+// shower's antenna centroid from above within 45 degrees (the test of the
+// single-shower ingest).  One CTA per shower of a chunk of up to kVoteChunk.
+constexpr int kVoteTiles = 64;
+constexpr int kVoteChunk = 64;
+struct VoteShower {
+  int64_t t_begin, t_end;  // derived-track tiles
+  float cx, cy, cz;        // antenna centroid
+};
+struct VoteArgs {
+  VoteShower s[kVoteChunk];
+};
+__global__ void __launch_bounds__(256) k_batch_votes(const float* tiles, const VoteArgs a, unsigned* out) {
+  const VoteShower v = a.s[blockIdx.x];
+  const int64_t t_end = min(v.t_end, v.t_begin + (int64_t)kVoteTiles);
+  unsigned kept = 0, above = 0;
+  for (int64_t i = v.t_begin * kTileT + threadIdx.x; i < t_end * kTileT; i += blockDim.x) {
+    const float* T = tiles + (i / kTileT) * (int64_t)(fm::NFIELDS * kTileT);
+    const int l = (int)(i % kTileT);
+    if (T[fm::AMPE * kTileT + l] == 0.0f) continue;  // filtered track or padding
+    ++kept;
+    const float sx = v.cx - T[fm::X0 * kTileT + l], sy = v.cy - T[fm::Y0 * kTileT + l];
+    const float sz = v.cz - T[fm::Z0 * kTileT + l];
+    above += (sz < 0.0f && sx * sx + sy * sy < sz * sz) ? 1u : 0u;
+  }
+  __shared__ unsigned sk, sa;
+  if (threadIdx.x == 0) sk = sa = 0;
+  __syncthreads();
+  if (kept) atomicAdd(&sk, kept);
+  if (above) atomicAdd(&sa, above);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = sk;
+    out[2 * blockIdx.x + 1] = sa;
+  }
+}
+
 template <class Ops>
 __global__ void __launch_bounds__(kTileT, Ops::kMinBlocks) k_batch(const BatchArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -221,7 +259,12 @@ struct c8r_batch {
   int* d_counter = nullptr;
   int* d_cancel = nullptr;
   int* d_err = nullptr;
-  unsigned long long* d_form = nullptr;  // the ingest's arrival-form votes (kept, seen from above)
+  // the arrival form of each shower (Endpoint, one-bin: MedParams::split);
+  // the work list holds the split-form showers' items first, n_items_split of
+  // them, then the direct-form showers', each group run by its own launch
+  std::vector<char> shower_split;
+  int n_items_split = 0;
+  std::vector<float> cen;  // per shower: antenna centroid (x, y, z)
   float4* d_acc = nullptr;  // [replicas][total_ant][rows][n_bins] accumulator
   size_t acc_bytes = 0;
   int replicas = 1;
@@ -243,13 +286,18 @@ int bfail(c8r_batch* b, int code, const std::string& m) {
   return code;
 }
 
-std::vector<WorkItem> make_items(const c8r_batch* b, int a_tile, int64_t tpi) {
+// the work list: the split-form showers first, then the direct-form ones (their
+// count of items in *n_split), each group largest shower first
+std::vector<WorkItem> make_items(const c8r_batch* b, int a_tile, int64_t tpi, int* n_split = nullptr) {
   std::vector<int> order(b->n_showers);
   for (int s = 0; s < b->n_showers; ++s) order[s] = s;
+  auto split_of = [&](int s) { return b->shower_split.empty() || b->shower_split[s]; };
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    if (split_of(x) != split_of(y)) return split_of(x);
     return b->n_tracks[x] * (int64_t)b->n_ant[x] > b->n_tracks[y] * (int64_t)b->n_ant[y];
   });
   std::vector<WorkItem> v;
+  if (n_split) *n_split = 0;
   for (int s : order) {
     const int64_t nt = b->tile_off[s + 1] - b->tile_off[s];
     if (nt == 0) continue;
@@ -263,6 +311,7 @@ std::vector<WorkItem> make_items(const c8r_batch* b, int a_tile, int64_t tpi) {
         v.push_back(w);
       }
     }
+    if (n_split && split_of(s)) *n_split = (int)v.size();
   }
   return v;
 }
@@ -297,16 +346,26 @@ int enqueue_ingest(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
 }
 
 // run the persistent kernel over the first n_items_limit items of the work list
+// (the split-form group, then the direct-form group, one launch each, each
+// with its own item counter: d_counter[0] and d_counter[3])
 int enqueue_kernel(c8r_batch* b, int n_items_limit, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
-  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch counter: ") + cudaGetErrorString(e));
   const int rows = acc_rows(C8R_MIXED, b->formalism);
-  BatchArgs a{b->d_tiles, b->d_items, std::min(b->n_items, n_items_limit), b->d_ants, b->d_acc, b->d_counter,
-              b->d_cancel, b->d_err, b->choice.a_tile, b->M, b->replicas,
-              (int64_t)b->total_ant * b->M.n_bins * rows};
-  a.M.wait_limit = current_wait_limit();
-  e = launch_batch(a, b->formalism, b->sm_count, st);
-  if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  const int n = std::min(b->n_items, n_items_limit);
+  const int ns = std::min(b->n_items_split, n);
+  const int first[2] = {0, ns}, count[2] = {ns, n - ns};
+  for (int g = 0; g < 2; ++g) {
+    if (count[g] <= 0) continue;
+    int* counter = b->d_counter + (g == 0 ? 0 : 3);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch counter: ") + cudaGetErrorString(e));
+    BatchArgs a{b->d_tiles, b->d_items + first[g], count[g], b->d_ants, b->d_acc, counter,
+                b->d_cancel, b->d_err, b->choice.a_tile, b->M, b->replicas,
+                (int64_t)b->total_ant * b->M.n_bins * rows};
+    a.M.wait_limit = current_wait_limit();
+    a.M.split = g == 0 ? 1 : 0;
+    e = launch_batch(a, b->formalism, b->sm_count, st);
+    if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  }
   return C8R_OK;
 }
 
@@ -324,26 +383,41 @@ int enqueue(c8r_batch* b, const TrackPtrs& tp, float* out, int n_items_limit, cu
   return C8R_OK;
 }
 
-// the arrival form of the one-bin Endpoint kernel (MedParams::split) from the
-// ingest's votes over the whole batch: the split form when at least half of the
-// tracks see the antenna array's centroid from above within 45 degrees (one
-// ingest and a synchronous read, once per batch, before the first run)
-int choose_form(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
+// the arrival form of each shower's one-bin Endpoint evaluation
+// (MedParams::split) from its votes (k_batch_votes on the ingested tiles): the
+// split form when at least half of the tracks counted see the shower's antenna
+// centroid from above within 45 degrees.  Once per batch, before the first
+// run: one ingest, the vote kernel (its counts written into the accumulator,
+// which every run zeroes first), a synchronous read.
+int choose_forms(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
+  b->shower_split.assign(b->n_showers, 1);
   BatchMap map{b->d_tile_off, b->d_track_off, b->d_n_tracks, b->n_showers};
-  unsigned long long h[2] = {0, 0};
-  cudaError_t e = cudaMemsetAsync(b->d_form, 0, sizeof(h), st);
+  cudaError_t e =
+      launch_ingest_map(C8R_MIXED, tp, map, b->total_tiles * kTileT, b->d_tiles, b->M, nullptr, st);
+  unsigned* counts = reinterpret_cast<unsigned*>(b->d_acc);  // 2 x n_showers <= accumulator elements x 4
+  std::vector<unsigned> h(2 * (size_t)b->n_showers, 0u);
+  for (int s0 = 0; e == cudaSuccess && s0 < b->n_showers; s0 += kVoteChunk) {
+    const int m = std::min(kVoteChunk, b->n_showers - s0);
+    VoteArgs va;
+    for (int i = 0; i < m; ++i) {
+      const int s = s0 + i;
+      va.s[i] = VoteShower{b->tile_off[s], b->tile_off[s + 1], b->cen[3 * s], b->cen[3 * s + 1], b->cen[3 * s + 2]};
+    }
+    k_batch_votes<<<(unsigned)m, 256, 0, st>>>(static_cast<const float*>(b->d_tiles), va, counts + 2 * s0);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess)
-    e = launch_ingest_map(C8R_MIXED, tp, map, b->total_tiles * kTileT, b->d_tiles, b->M, nullptr, st, b->d_form);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h, b->d_form, sizeof(h), cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(h.data(), counts, sizeof(unsigned) * h.size(), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return bfail(b, C8R_ECUDA, std::string("batch form votes: ") + cudaGetErrorString(e));
-  if (h[0] > 0) b->M.split = 2 * h[1] >= h[0] ? 1 : 0;
+  for (int s = 0; s < b->n_showers; ++s)
+    if (h[2 * s] > 0) b->shower_split[s] = 2 * (size_t)h[2 * s + 1] >= h[2 * s] ? 1 : 0;
   return C8R_OK;
 }
 
 int autotune(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
   if (b->formalism == C8R_ENDPOINT && (b->M.kind == C8R_UNIFORM || b->M.kind == C8R_EXPONENTIAL)) {
-    const int r = choose_form(b, tp, st);
+    const int r = choose_forms(b, tp, st);
     if (r != C8R_OK) return r;
   }
   char keybuf[160];
@@ -354,7 +428,7 @@ int autotune(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
   if (tune_lookup(key, best) && best.a_tile <= kMaxATile) {
     b->choice = best;
     b->tuned = true;
-    return upload_items(b, make_items(b, best.a_tile, best.tiles_per_item));
+    return upload_items(b, make_items(b, best.a_tile, best.tiles_per_item, &b->n_items_split));
   }
   std::vector<TuneChoice> cands;
   for (int at : {8, 16, 32})
@@ -370,7 +444,7 @@ int autotune(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
   if (r != C8R_OK) return r;
   for (const TuneChoice& c : cands) {
     b->choice = c;
-    std::vector<WorkItem> v = make_items(b, c.a_tile, c.tiles_per_item);
+    std::vector<WorkItem> v = make_items(b, c.a_tile, c.tiles_per_item, &b->n_items_split);
     const int min_items = 4 * batch_resident(b->formalism, b->M.kind, c.a_tile, b->sm_count);
     int lim = 0;
     double pairs = 0;
@@ -402,7 +476,7 @@ int autotune(c8r_batch* b, const TrackPtrs& tp, cudaStream_t st) {
   int status = kErrNone;
   if (cudaMemcpy(&status, b->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && status == kErrNone)
     tune_store(key, best);
-  return upload_items(b, make_items(b, best.a_tile, best.tiles_per_item));
+  return upload_items(b, make_items(b, best.a_tile, best.tiles_per_item, &b->n_items_split));
 }
 
 }  // namespace
@@ -447,9 +521,15 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
     b->total_pairs += b->n_tracks[s] * (int64_t)b->n_ant[s];
   }
   b->total_tiles = b->tile_off[d->n_showers];
-  set_form_centroid(b->M, d->pos_xyz, b->total_ant);
   set_flat_array(b->M, d->pos_xyz, b->total_ant);
   b->M.split = 1;
+  b->cen.assign(3 * (size_t)b->n_showers, 0.0f);
+  for (int s = 0; s < b->n_showers; ++s) {
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < b->n_ant[s]; ++a)
+      for (int k = 0; k < 3; ++k) c[k] += d->pos_xyz[3 * (size_t)(b->ant_off[s] + a) + k];
+    for (int k = 0; k < 3; ++k) b->cen[3 * (size_t)s + k] = (float)(c[k] / b->n_ant[s]);
+  }
   std::vector<AntRec> recs(b->total_ant);
   for (int a = 0; a < b->total_ant; ++a) {
     const double* p = d->pos_xyz + 3 * (size_t)a;
@@ -478,7 +558,6 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
     return C8R_ENOMEM;
   }
   b->d_cancel = b->d_counter + 1;
-  b->d_form = reinterpret_cast<unsigned long long*>(b->d_counter + 4);
   b->d_err = b->d_counter + 2;
   if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->aux_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -498,7 +577,7 @@ int c8r_batch_create(c8r_batch** out, int device, const c8r_batch_desc* d, int k
   }
   b->choice = {8, tpi_for(b, 8, 8)};
   *out = b;
-  return upload_items(b, make_items(b, b->choice.a_tile, b->choice.tiles_per_item));
+  return upload_items(b, make_items(b, b->choice.a_tile, b->choice.tiles_per_item, &b->n_items_split));
 }
 
 void c8r_batch_destroy(c8r_batch* b) {
