@@ -5,8 +5,10 @@
 // The host cuts every shower into work items (antenna tile x range of derived
 // track tiles) and uploads the list, largest shower first and, inside a shower,
 // antenna tiles fastest (so the items in flight share track tiles in L2 and add
-// into one shower's accumulator rows).  A persistent grid of one CTA per SM pops
-// items from a global atomic counter; for each item a CTA streams the item's
+// into one shower's accumulator rows); for the one-bin Endpoint evaluation the
+// showers are grouped by the form of their FP32 arrival (a vote per shower),
+// and each group gets a launch of its own.  A persistent grid of every CTA the
+// device holds pops items from a global atomic counter; for each item a CTA streams the item's
 // track tiles through the same TMA ring as the single-shower kernel and adds the
 // deposits into the batch accumulator.  The CTA polls a cancel word between
 // items.  Zeroing the accumulator, the ingest of all showers, the counter reset,
