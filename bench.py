@@ -9,8 +9,8 @@ headline is track-antenna pairs per second over both formalisms.
 
 Also reported: the FP64 path on the same workload (a sample of it), the adjoint
 / forward time ratio on the differentiable 1e6-track x 64-antenna workload, the
-batched persistent launch against separate launches (on a scaled-down batch of
-uneven showers), the ALU roofline of the dominant kernel, the oracle timed on
+batched persistent launches against separate launches (64 uneven showers at
+their stated sizes, and scaled down), the ALU roofline of the dominant kernel, the oracle timed on
 the host cores, and GPU clocks during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -698,8 +698,8 @@ def extras(torch, c8r, synth, w):
     p.close()
     del o2
 
-    # batched uneven showers: one persistent graph-captured launch against one
-    # launch per shower (64 showers at their stated track counts, 1e5-1e7 each,
+    # batched uneven showers: the graph-captured persistent launches (one per
+    # arrival form of the Endpoint evaluation) against one launch per shower (64 showers at their stated track counts, 1e5-1e7 each,
     # drawn on the device by the counter-based generator; and with the track
     # counts scaled by 0.01, where per-launch costs show)
     for scale, tag in ((1.0, "batched"), (0.01, "batched_small")):

@@ -305,7 +305,9 @@ int c8r_arrivals(c8r_ctx* ctx, const c8r_tracks* tracks, int64_t n, int32_t* bra
 
 /* ---- batched showers (not in the paper) -------------------------------------- */
 
-/* Many independent showers of uneven size in one persistent launch.  Shower s
+/* Many independent showers of uneven size in persistent launches (one, or for
+ * the Endpoint formalism one per form of the FP32 arrival its showers take,
+ * see c8r_set_arrival_form; the form is chosen per shower).  Shower s
  * has n_tracks[s] tracks stored at offset track_offset[s] of the concatenated
  * track arrays, n_ant[s] antennas at offset ant_offset[s] of the concatenated
  * antenna arrays, and its traces at offset ant_offset[s]*3*n_bins of the

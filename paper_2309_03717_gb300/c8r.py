@@ -494,7 +494,8 @@ class RadioTraces(torch.autograd.Function):
 
 
 class Batch:
-    """Many showers of uneven size in one persistent launch (c8r_batch_*).
+    """Many showers of uneven size in persistent launches (c8r_batch_*; one per
+    form of the Endpoint FP32 arrival that its showers take).
 
     showers: list of dicts with ``n_tracks``, ``ant_xyz`` [A, 3] and ``t_start_ns``
     [A]; their tracks are concatenated in order, and so are the output traces

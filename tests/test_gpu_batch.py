@@ -1,6 +1,6 @@
-"""The batched persistent launch against separate launches per shower (the
-same kernels' arithmetic, so equal up to FP32 addition order), graph replay,
-and the cancel word."""
+"""The batched persistent launches against separate launches per shower (the
+same bins and deposits in either arrival form, so equal up to FP32 addition
+order), graph replay, and the cancel word."""
 import numpy as np
 import pytest
 
@@ -91,7 +91,7 @@ def test_graph_replay_accumulates_and_cancel_word_stops_work():
 def test_full_batched_workload_sampled_against_oracle():
     """The 64 uneven showers at their stated sizes (1e5-1e7 tracks, 16-512
     antennas, zenith 0-65 deg; ~1.4e8 tracks generated on the device, one seed
-    per shower), in the graph-captured persistent launch the benchmark times:
+    per shower), in the graph-captured persistent launches the benchmark times:
     the smallest, the median and the largest shower against the oracle at their
     first, middle and last antenna, over all their tracks (the oracle's tracks
     from the generator's host twin, chunk by chunk in spawned workers).  Tracks
