@@ -511,16 +511,15 @@ struct OpsMixed {
       if (kb <= ke) out.dep_box(kb, ke, Mx * invW, My * invW, Mz * invW);
       return;
     }
-    if (klo == khi) {
-      if (klo >= 0 && klo < N) out.dep(klo, Mx, My, Mz);
-      return;
-    }
-    const float invW = __fdividef(1.0f, 2.0f * hh);  // 1 / interval length in bins
-    // partly covered first and last bins
-    if (klo >= 0 && klo < N) {
-      const float w = gap_to_next_edge(ulo, klo) * invW;
-      if (w > 0.0f) out.dep(klo, Mx * w, My * w, Mz * w);
-    }
+    // the interval's first bin takes the whole deposit (an interval inside one
+    // bin: weight 1, M x 1 = M exactly) or the share it covers, in one
+    // reduction either way, so that lanes of both kinds take one path
+    const bool one = klo == khi;
+    const float invW = __fdividef(1.0f, 2.0f * hh);  // 1 / interval length in bins (unused when one)
+    const float wlo = one ? 1.0f : gap_to_next_edge(ulo, klo) * invW;
+    if (klo >= 0 && klo < N && wlo > 0.0f) out.dep(klo, Mx * wlo, My * wlo, Mz * wlo);
+    if (one) return;
+    // the partly covered last bin
     if (khi >= 0 && khi < N) {
       const float w = fhi * invW;
       if (w > 0.0f) out.dep(khi, Mx * w, My * w, Mz * w);
