@@ -569,12 +569,15 @@ struct OpsMixed {
       const float amp = t.amp;
       const float c0 = __fdividef(amp, f0.D * g0.R0) * (f0.invR * f0.invR);
       const float c1 = __fdividef(-amp, f1.D * g1.R0) * (f1.invR * f1.invR);
-      if (ina && inb && ka == kb) {
-        out.dep(ka, c0 * f0.V[0] + c1 * f1.V[0], c0 * f0.V[1] + c1 * f1.V[1], c0 * f0.V[2] + c1 * f1.V[2]);
-      } else {
-        if (ina) out.dep(ka, c0 * f0.V[0], c0 * f0.V[1], c0 * f0.V[2]);
-        if (inb) out.dep(kb, c1 * f1.V[0], c1 * f1.V[1], c1 * f1.V[2]);
-      }
+      // both deposits in one bin add in registers (one reduction); otherwise
+      // one each.  One code path for both kinds of lane: the start's deposit
+      // carries the end's when they share the bin (the end's weight 0 else)
+      const bool same = ina && inb && ka == kb;
+      const float c1s = same ? c1 : 0.0f;
+      if (ina)
+        out.dep(ka, __fmaf_rn(c1s, f1.V[0], c0 * f0.V[0]), __fmaf_rn(c1s, f1.V[1], c0 * f0.V[1]),
+                __fmaf_rn(c1s, f1.V[2], c0 * f0.V[2]));
+      if (inb && !same) out.dep(kb, c1 * f1.V[0], c1 * f1.V[1], c1 * f1.V[2]);
       return (ka == kFastUndecided ? kDeferEnd0 : 0) | (kb == kFastUndecided ? kDeferEnd1 : 0);
     } else if constexpr (FORM == C8R_ENDPOINT) {
       EndpointEvalM e;
