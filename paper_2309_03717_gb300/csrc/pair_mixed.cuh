@@ -648,9 +648,9 @@ struct OpsMixed {
       shifted_time(tmh, tml, 0.5f * zmh, 0.5f * zml, kh, kl, Tmh, Tml);
       float uf;
       const float qv = KIND == C8R_EXPONENTIAL ? fast_quotient(M, A.Eah, A.Eal, g.s[2], Eh, El) : 0.0f;
-      const float eps_a = split_pays(g, S, rho2)
-                              ? arrival_fast<KIND, true>(M, A, g, S, rho2, Tmh, Tml, qv, 3.0f, uf)
-                              : arrival_fast<KIND, false>(M, A, g, S, rho2, Tmh, Tml, qv, 3.0f, uf);
+      // the kernel's arrival form (either is exact to its own bound; one form
+      // for every lane keeps the warp on one path)
+      const float eps_a = arrival_fast<KIND, kSplit>(M, A, g, S, rho2, Tmh, Tml, qv, 3.0f, uf);
       const float eps_u = __fmaf_rn(2.0f * u * kh, L1, eps_a);
       const float dtau = TF(fm::DTAUH);
       const float aD = fabsf(f.D);
@@ -1006,16 +1006,17 @@ struct OpsMixed {
         dLdu = (p_hi - p_lo) * invW;
         dLdh = (p_hi + p_lo - 2.0f * AS) * invW;
       }
-    } else if (klo == khi) {
-      if (klo < 0 || klo >= N) return;
-      const float4 g = G[klo];
-      S[0] = g.x; S[1] = g.y; S[2] = g.z;
     } else {
-      const float invW = __fdividef(1.0f, 2.0f * hh);
-      const bool inlo = klo >= 0 && klo < N, inhi = khi >= 0 && khi < N;
+      // one path for intervals inside one bin (weight 1 on its bin, 1 G = G
+      // exactly, and no dependence on the interval's ends: 1/W taken as 0) and
+      // for intervals over several bins
+      const bool one = klo == khi;
+      const bool inlo = klo >= 0 && klo < N, inhi = !one && khi >= 0 && khi < N;
+      if (one && !inlo) return;
+      const float invW = one ? 0.0f : __fdividef(1.0f, 2.0f * hh);
       const float4 glo = inlo ? G[klo] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 ghi = inhi ? G[khi] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float wlo = inlo ? gap_to_next_edge(ulo, klo) * invW : 0.0f, whi = fhi * invW;
+      const float wlo = inlo ? (one ? 1.0f : gap_to_next_edge(ulo, klo) * invW) : 0.0f, whi = fhi * invW;
       float ix = 0.0f, iy = 0.0f, iz = 0.0f;  // G summed over the whole bins between
       const int kb = klo + 1 < 0 ? 0 : klo + 1;
       const int ke = khi - 1 > N - 1 ? N - 1 : khi - 1;
