@@ -1,7 +1,9 @@
 // pair_f64.cuh -- per (track, antenna) arithmetic of the FP64 path: the plain
 // formulas of the two formalisms (§1) and the straight-line propagator (§2) in
-// FP64, in the order of their definitions.  This translation unit is compiled
-// without FMA contraction so that every operation rounds as written.
+// FP64, in the order of their definitions (one exception: the ZHS factor
+// K_A/(R |D_m| dt) is formed once per interval rather than once per bin).  This
+// translation unit is compiled without FMA contraction so that every operation
+// rounds as written.
 #pragma once
 
 #include "kernels.cuh"
@@ -28,9 +30,12 @@ __device__ __forceinline__ void field_vec_f64(const double b[3], const GeoD& g, 
   D = 1.0 - g.n_src * c;
 }
 
+// stop_near: a near-Cherenkov pair stops after the branch decision (branch 1,
+// valid false), for a caller that evaluates those pairs in a later pass
 __device__ __forceinline__ void endpoint_eval_f64(const double* T, int l, const AntRec& A, const MedParams& M,
-                                                  EndpointEvalD& e) {
+                                                  EndpointEvalD& e, bool stop_near = false) {
   e.valid = false;
+  e.branch = 0;
   const double b[3] = {TF(fd::BX), TF(fd::BY), TF(fd::BZ)};
   const double x0 = TF(fd::X0), y0 = TF(fd::Y0), z0 = TF(fd::Z0);
   const double x1 = TF(fd::X1), y1 = TF(fd::Y1), z1 = TF(fd::Z1);
@@ -51,6 +56,7 @@ __device__ __forceinline__ void endpoint_eval_f64(const double* T, int l, const 
     return;
   }
   e.branch = 1;
+  if (stop_near) return;
   geo_f64(M, A, 0.5 * (x0 + x1), 0.5 * (y0 + y1), 0.5 * (z0 + z1), e.Em, e.gm);
   if (e.gm.R == 0.0) return;
   field_vec_f64(b, e.gm, e.Vm, e.Dm);
@@ -120,7 +126,12 @@ struct OpsF64 {
   static constexpr int kPrec = C8R_FP64;
   static constexpr int kTileBytes = kTileBytesF64;
   static constexpr int kMinBlocks = 4;
-  static constexpr bool kDefers = false;  // every pair is evaluated in the main pass
+  // Endpoint (one-bin deposit): the near-Cherenkov pairs (about one in ten on a
+  // shower, in most warps) are set aside by the main pass and evaluated
+  // together afterwards, so that the midpoint form's FP64 arithmetic runs in
+  // full warps instead of holding the other lanes of nearly every warp.  The
+  // arithmetic of each pair is the same either way.
+  static constexpr bool kDefers = FORM == C8R_ENDPOINT && !LIN;
   static constexpr bool kFastBins = false;
   static constexpr int kBwdMinBlocks = 2;
   static constexpr int kAccRows = 1;      // no box deposits
@@ -140,28 +151,37 @@ struct OpsF64 {
     else
       zhs(t.T, t.l, A, M, out);
   }
+  // main pass: every pair but (kDefers) the near-Cherenkov ones, returned as
+  // kDeferPair with nothing deposited; pair_deferred evaluates those in full
   template <class Sink>
   static __device__ __forceinline__ int pair_main(const TrackD& t, const AntRec& A, const MedParams& M, Sink& out) {
+    if constexpr (kDefers) return endpoint(t.T, t.l, A, M, out, true);
     pair(t, A, M, out);
     return kDeferNone;
   }
   template <class Sink>
-  static __device__ __forceinline__ void pair_deferred(const TrackD&, const AntRec&, const MedParams&, Sink&) {}
+  static __device__ __forceinline__ void pair_deferred(const TrackD& t, const AntRec& A, const MedParams& M,
+                                                       Sink& out) {
+    if constexpr (kDefers) pair(t, A, M, out);
+  }
   template <class Sink>
   static __device__ __forceinline__ void end_deferred(const void*, int, const AntRec&, const MedParams&, Sink&, int) {}
   static __device__ __forceinline__ bool near_zero_fast(const void*, int, const AntRec&, const MedParams&) {
     return false;
   }
 
+  // returns kDeferPair (nothing deposited) for a near-Cherenkov pair when
+  // defer_near is set, kDeferNone otherwise
   template <class Sink>
-  static __device__ __forceinline__ void endpoint(const double* T, int l, const AntRec& A, const MedParams& M,
-                                                  Sink& out) {
+  static __device__ __forceinline__ int endpoint(const double* T, int l, const AntRec& A, const MedParams& M,
+                                                 Sink& out, bool defer_near = false) {
     const double q = TF(fd::Q);
-    if (q == 0.0) return;
+    if (q == 0.0) return kDeferNone;
     const int N = M.n_bins;
     EndpointEvalD e;
-    endpoint_eval_f64(T, l, A, M, e);
-    if (!e.valid) return;
+    endpoint_eval_f64(T, l, A, M, e, defer_near);
+    if (defer_near && e.branch == 1) return kDeferPair;
+    if (!e.valid) return kDeferNone;
     out.rec(e.branch, e.ua, e.ub);
     const double K = q * kKendpoint;
     const double dt_s = M.dt_ns * 1e-9;
@@ -172,7 +192,7 @@ struct OpsF64 {
         const double s1 = -K / (e.D1 * e.g1.R * dt_s);
         dep_lin_f64(out, N, e.ua, s0 * e.V0[0], s0 * e.V0[1], s0 * e.V0[2]);
         dep_lin_f64(out, N, e.ub, s1 * e.V1[0], s1 * e.V1[1], s1 * e.V1[2]);
-        return;
+        return kDeferNone;
       }
       const double Ja = floor(e.ua + 0.5), Jb = floor(e.ub + 0.5);
       if (Ja == Jb) {
@@ -181,12 +201,12 @@ struct OpsF64 {
         const double B = K * ((TF(fd::T1) - TF(fd::T0)) / M.dt_ns) / (e.gm.R * dt_s);
         if (Ja - 1.0 >= 0.0 && Ja - 1.0 < (double)N) out.dep((int)Ja - 1, B * e.Vm[0], B * e.Vm[1], B * e.Vm[2]);
         if (Ja >= 0.0 && Ja < (double)N) out.dep((int)Ja, -B * e.Vm[0], -B * e.Vm[1], -B * e.Vm[2]);
-        return;
+        return kDeferNone;
       }
       const double s = K / (e.Dm * e.gm.R * dt_s);
       dep_lin_f64(out, N, e.ua, s * e.Vm[0], s * e.Vm[1], s * e.Vm[2]);
       dep_lin_f64(out, N, e.ub, -s * e.Vm[0], -s * e.Vm[1], -s * e.Vm[2]);
-      return;
+      return kDeferNone;
     }
     const double ka = floor(e.ua), kb = floor(e.ub);
     const bool ina = ka >= 0.0 && ka < (double)N, inb = kb >= 0.0 && kb < (double)N;
@@ -195,12 +215,13 @@ struct OpsF64 {
       const double s1 = -K / (e.D1 * e.g1.R * dt_s);
       if (ina) out.dep((int)ka, s0 * e.V0[0], s0 * e.V0[1], s0 * e.V0[2]);
       if (inb) out.dep((int)kb, s1 * e.V1[0], s1 * e.V1[1], s1 * e.V1[2]);
-      return;
+      return kDeferNone;
     }
-    if (ka == kb) return;  // both linearised arrivals in one bin: zero
+    if (ka == kb) return kDeferNone;  // both linearised arrivals in one bin: zero
     const double s = K / (e.Dm * e.gm.R * dt_s);
     if (ina) out.dep((int)ka, s * e.Vm[0], s * e.Vm[1], s * e.Vm[2]);
     if (inb) out.dep((int)kb, -s * e.Vm[0], -s * e.Vm[1], -s * e.Vm[2]);
+    return kDeferNone;
   }
 
   template <class Sink>
@@ -250,11 +271,14 @@ struct OpsF64 {
       return;
     }
     const double kb = fmax(k_lo, 0.0), ke = fmin(k_hi, (double)(N - 1));
+    // K_A beta_perp/(R |D_m|) times the overlap o of the interval with the bin,
+    // over dt; the factor is formed once for the interval's bins
+    const double sc = KA / (gm.R * fabs(Dm) * dt);
     for (double kd = kb; kd <= ke; kd += 1.0) {
       const double e_lo = kd * dt, e_hi = (kd + 1.0) * dt;
       const double o = fmin(t_hi, e_hi) - fmax(t_lo, e_lo);
       if (o <= 0.0) continue;
-      const double s = KA / gm.R * (o / fabs(Dm)) / dt;
+      const double s = sc * o;
       out.dep((int)kd, s * bp[0], s * bp[1], s * bp[2]);
     }
   }
