@@ -320,12 +320,13 @@ struct OpsMixed {
   // (counted by the ingest of earlier launches)
   static constexpr bool kSplit = SPLIT && kFastBins;
   // a flat antenna array: the refractivity quotient per track, in the main pass
-  // of the Endpoint forward kernel of the direct arrival form (the host picks
-  // the kernel, MedParams::flat).  Measured on 4e6 tracks: 47.96 -> 44.01 ms on
-  // the 60-degree array; for the near-vertical lines of sight of the split
-  // form it was 0.35 % slower (6.85 -> 6.87 ms), and in the ZHS kernel 0.6 %
-  // slower, so those keep the quotient per pair
-  static constexpr bool kFlat = FLAT && kFastBins && !SPLIT && KIND == C8R_EXPONENTIAL;
+  // of the Endpoint forward kernel of the direct arrival form and of the ZHS
+  // forward kernel (the host picks the kernel, MedParams::flat).  Measured:
+  // 47.96 -> 44.01 ms on 4e6 tracks of the 60-degree array (Endpoint); ZHS
+  // 31.9 -> 30.9 ms on the 2e7-track vertical shower.  The split-form Endpoint
+  // kernel keeps the quotient per pair (within 0.3 % either way)
+  static constexpr bool kFlat =
+      FLAT && KIND == C8R_EXPONENTIAL && ((kFastBins && !SPLIT) || (FORM == C8R_ZHS && !LIN));
   // adjoint CTAs (128 threads) per SM the registers are set for (the linear
   // Endpoint adjoint carries the slide of each deposit as well)
   static constexpr int kBwdMinBlocks = (LIN && FORM == C8R_ENDPOINT) ? 4 : 6;
@@ -1280,7 +1281,9 @@ cudaError_t forward_mixed(int formalism, const void* tiles, int64_t n_tiles, con
   if constexpr (!LIN) {
     // the one-bin Endpoint kernels come in both arrival forms (M.split) and,
     // for the direct form in the exponential medium, for a flat antenna array
-    // (M.flat, OpsMixed::kFlat)
+    // (M.flat, OpsMixed::kFlat); the one-bin ZHS kernel of the exponential
+    // medium for a flat array too
+    if (formalism == C8R_ZHS && ex && M.flat) return go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, false, false, true>{});
     if (formalism == C8R_ENDPOINT) {
       if (!ex)
         return M.split ? go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, false, true>{})

@@ -468,14 +468,16 @@ def test_uneven_antenna_altitudes(formalism, precision, tol):
     assert max(per_ant) <= tol, f"worst antenna: relative L2 {max(per_ant):.3e}"
 
 
+@pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
 @pytest.mark.parametrize("cfg", [1, 2])
-def test_flat_array_kernel_matches_the_per_pair_quotient(cfg):
-    """A flat array (every antenna at z = 0) takes the Endpoint kernel of the
-    direct arrival form that forms the refractivity quotient once per track;
-    moving one antenna by 1 mm in z takes the kernel that forms it per pair.
-    The quotient is the same arithmetic either way, so the other antennas'
-    traces agree to the order of the additions (vertical and 60-degree
-    showers, the direct form pinned)."""
+def test_flat_array_kernel_matches_the_per_pair_quotient(cfg, formalism):
+    """A flat array (every antenna at z = 0) takes the kernel that forms the
+    refractivity quotient once per track (Endpoint: the direct arrival form;
+    ZHS: the midpoint's quotient in float-float); moving one antenna by 1 mm
+    in z takes the kernel that forms it per pair.  The quotient is the same
+    arithmetic either way, so the other antennas' traces agree to the order of
+    the additions (vertical and 60-degree showers; Endpoint with the direct
+    form pinned)."""
     w = synth.workload(cfg, n_tracks=20011, n_ant=32 if cfg == 1 else 64)
     w["dtype"] = np.float32
     tracks = synth.workload_tracks(w)
@@ -484,8 +486,9 @@ def test_flat_array_kernel_matches_the_per_pair_quotient(cfg):
     for dz in (0.0, 1e-3):
         ant = np.asarray(w["ant_xyz"], np.float64).copy()
         ant[-1, 2] += dz
-        p = process(dict(w, ant_xyz=ant), "endpoint", "mixed")
-        p.set_arrival_form("direct")
+        p = process(dict(w, ant_xyz=ant), formalism, "mixed")
+        if formalism == "endpoint":
+            p.set_arrival_form("direct")
         p.push(dev)
         out.append(p.traces().cpu().numpy()[:-1].astype(np.float64))
         p.close()
