@@ -320,11 +320,12 @@ struct OpsMixed {
   // (counted by the ingest of earlier launches)
   static constexpr bool kSplit = SPLIT && kFastBins;
   // a flat antenna array: the refractivity quotient per track, in the main pass
-  // of the Endpoint forward kernel of the direct arrival form and of the ZHS
-  // forward kernel (the host picks the kernel, MedParams::flat).  Measured:
-  // 47.96 -> 44.01 ms on 4e6 tracks of the 60-degree array (Endpoint); ZHS
-  // 31.9 -> 30.9 ms on the 2e7-track vertical shower.  The split-form Endpoint
-  // kernel keeps the quotient per pair (within 0.3 % either way)
+  // of the Endpoint forward kernel of the direct arrival form and in the ZHS
+  // forward and adjoint kernels (the host picks the kernel, MedParams::flat).
+  // Measured: 47.96 -> 44.01 ms on 4e6 tracks of the 60-degree array
+  // (Endpoint); ZHS 31.9 -> 31.0 ms on the 2e7-track vertical shower alone,
+  // 31.96 -> 29.56 ms inside the two-process bench step.  The split-form
+  // Endpoint kernel keeps the quotient per pair (within 0.3 % either way)
   static constexpr bool kFlat =
       FLAT && KIND == C8R_EXPONENTIAL && ((kFastBins && !SPLIT) || (FORM == C8R_ZHS && !LIN));
   // adjoint CTAs (128 threads) per SM the registers are set for (the linear
@@ -942,7 +943,11 @@ struct OpsMixed {
     FieldM f;
     field_mixed(gm, t.bx, t.by, t.bz, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), f);
     geo_refine(gm);
-    const ff um = arrival_mixed<KIND>(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml);
+    ff um;
+    if constexpr (kFlat)
+      um = arrival_mixed_q<KIND>(M, A, gm, t.tmh, t.tml, t.qmh, t.qml);
+    else
+      um = arrival_mixed<KIND>(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml);
     ff aD = doppler_ff(gm, t.bx, t.by, t.bz, t.nm1_m);
     const float sgn = aD.h < 0.0f ? -1.0f : 1.0f;
     if (aD.h < 0.0f) {
@@ -1301,9 +1306,14 @@ cudaError_t forward_mixed(int formalism, const void* tiles, int64_t n_tiles, con
 template <bool LIN>
 cudaError_t backward_mixed(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st) {
   const bool ex = a.M.kind == C8R_EXPONENTIAL;
-  if (formalism == C8R_ZHS)
+  if (formalism == C8R_ZHS) {
+    if constexpr (!LIN) {
+      if (ex && a.M.flat)
+        return launch_backward_ops<OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, false, false, true>>(a, shape, sm_count, st);
+    }
     return ex ? launch_backward_ops<OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, LIN>>(a, shape, sm_count, st)
               : launch_backward_ops<OpsMixed<C8R_ZHS, C8R_UNIFORM, LIN>>(a, shape, sm_count, st);
+  }
   if constexpr (!LIN) {
     if (a.M.split)
       return ex ? launch_backward_ops<OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, false, true>>(a, shape, sm_count, st)
