@@ -20,10 +20,19 @@ def _lib():
     built_lib()
 
 
-def setup(precision, n=3001, n_ant=16, seed_off=0, formalism="endpoint"):
+def setup(precision, n=3001, n_ant=16, seed_off=0, formalism="endpoint", uneven=False):
     from paper_2309_03717_gb300 import c8r
     w = synth.workload(4, n_tracks=n, n_ant=n_ant, seed_offset=seed_off)
     tracks = synth.workload_tracks(w)
+    if uneven:
+        # antennas at 0-150 m: the refractivity quotient is formed per pair (a
+        # flat array forms it once per track); each trace window is placed
+        # around the antenna's median arrival
+        ant = np.asarray(w["ant_xyz"], np.float64).copy()
+        ant[:, 2] = np.linspace(0.0, 150.0, n_ant)
+        w["ant_xyz"] = ant
+        _, u0 = oracle_arrivals(tracks, ant, np.zeros(n_ant), 1, w["dt_ns"], w["medium"], formalism)
+        w["t_start_ns"] = np.median(u0.reshape(len(tracks["x0"]), n_ant, 2)[..., 0], axis=0) * w["dt_ns"] - 200.0
     # away from the kinks (an arrival within 1e-6 bin of an edge may take either bin)
     keep = unambiguous(tracks, w["ant_xyz"], w["t_start_ns"], w["n_bins"], w["dt_ns"], w["medium"], formalism)
     if formalism == "zhs":
@@ -59,8 +68,8 @@ def test_mixed_zhs_adjoint_with_a_constant_gradient_part():
     check_adjoint("mixed", 1e-4, "zhs", offset=2.0)
 
 
-def check_adjoint(precision, tol, formalism, offset=0.0, form=None):
-    c8r, w, tracks, p = setup(precision, formalism=formalism)
+def check_adjoint(precision, tol, formalism, offset=0.0, form=None, uneven=False):
+    c8r, w, tracks, p = setup(precision, formalism=formalism, uneven=uneven)
     if form:
         p.set_arrival_form(form)
     dt = torch.float64 if precision == "fp64" else torch.float32
@@ -99,6 +108,15 @@ def check_adjoint(precision, tol, formalism, offset=0.0, form=None):
     assert rel_l2(got[:, 8:11], tg_ref[:, 8:11]) <= tol
     assert rel_l2(ag.cpu().numpy(), ag_ref) <= tol
     assert abs(dn.item() - dn_ref) <= tol * abs(dn_ref)
+
+
+@pytest.mark.parametrize("formalism", ["endpoint", "zhs"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_adjoint_with_uneven_antenna_altitudes(precision, tol, formalism):
+    """The adjoints for an array that is not flat (antennas at 0-150 m), where
+    the mixed kernels form the refractivity quotient per pair rather than once
+    per track."""
+    check_adjoint(precision, tol, formalism, uneven=True)
 
 
 @pytest.mark.parametrize("form", ["split", "direct"])
