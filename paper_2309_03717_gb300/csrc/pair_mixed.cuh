@@ -327,7 +327,7 @@ struct OpsMixed {
   // 31.96 -> 29.56 ms inside the two-process bench step.  The split-form
   // Endpoint kernel keeps the quotient per pair (within 0.3 % either way)
   static constexpr bool kFlat =
-      FLAT && KIND == C8R_EXPONENTIAL && ((kFastBins && !SPLIT) || (FORM == C8R_ZHS && !LIN));
+      FLAT && KIND == C8R_EXPONENTIAL && ((kFastBins && !SPLIT) || FORM == C8R_ZHS);
   // adjoint CTAs (128 threads) per SM the registers are set for (the linear
   // Endpoint adjoint carries the slide of each deposit as well)
   static constexpr int kBwdMinBlocks = (LIN && FORM == C8R_ENDPOINT) ? 4 : 6;
@@ -1286,9 +1286,7 @@ cudaError_t forward_mixed(int formalism, const void* tiles, int64_t n_tiles, con
   if constexpr (!LIN) {
     // the one-bin Endpoint kernels come in both arrival forms (M.split) and,
     // for the direct form in the exponential medium, for a flat antenna array
-    // (M.flat, OpsMixed::kFlat); the one-bin ZHS kernel of the exponential
-    // medium for a flat array too
-    if (formalism == C8R_ZHS && ex && M.flat) return go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, false, false, true>{});
+    // (M.flat, OpsMixed::kFlat)
     if (formalism == C8R_ENDPOINT) {
       if (!ex)
         return M.split ? go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, false, true>{})
@@ -1300,6 +1298,9 @@ cudaError_t forward_mixed(int formalism, const void* tiles, int64_t n_tiles, con
   }
   if (formalism == C8R_ENDPOINT)
     return ex ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, LIN>{}) : go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, LIN>{});
+  // ZHS in the exponential medium: for a flat array the kernel that forms the
+  // midpoint's refractivity quotient once per track (OpsMixed::kFlat)
+  if (ex && M.flat) return go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, LIN, false, true>{});
   return ex ? go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, LIN>{}) : go(OpsMixed<C8R_ZHS, C8R_UNIFORM, LIN>{});
 }
 
@@ -1307,10 +1308,8 @@ template <bool LIN>
 cudaError_t backward_mixed(int formalism, BwdArgs& a, const FwdShape& shape, int sm_count, cudaStream_t st) {
   const bool ex = a.M.kind == C8R_EXPONENTIAL;
   if (formalism == C8R_ZHS) {
-    if constexpr (!LIN) {
-      if (ex && a.M.flat)
-        return launch_backward_ops<OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, false, false, true>>(a, shape, sm_count, st);
-    }
+    if (ex && a.M.flat)
+      return launch_backward_ops<OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, LIN, false, true>>(a, shape, sm_count, st);
     return ex ? launch_backward_ops<OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, LIN>>(a, shape, sm_count, st)
               : launch_backward_ops<OpsMixed<C8R_ZHS, C8R_UNIFORM, LIN>>(a, shape, sm_count, st);
   }
