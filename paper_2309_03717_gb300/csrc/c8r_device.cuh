@@ -444,21 +444,64 @@ __device__ __forceinline__ void geo_lite(const AntRec& A, float px, float py, fl
   g.R1 = 0.0f;
 }
 
-__device__ __forceinline__ void geo_refine(GeoM& g) {
-  float p0, q0, p1, q1, p2, q2;
+// the z part of d = a - p that every antenna of a flat array (one altitude)
+// shares: d_z as float-float and the products of it that geo_refine and
+// doppler_ff form, formed once per point as they form them (so the same values)
+struct ZPart {
+  float sh, sl;  // d_z = sh + sl (geo_lite's s[2], e[2])
+  float qh, ql;  // sh^2, exact
+  float se;      // fl(sh sl)
+  float bh, bl;  // b_z sh, exact
+  float be;      // fl(b_z sl)
+};
+__device__ __forceinline__ ZPart z_part(float sh, float sl, float bz) {
+  ZPart z;
+  z.sh = sh;
+  z.sl = sl;
+  two_prod(sh, sh, z.qh, z.ql);
+  z.se = __fmul_rn(sh, sl);
+  two_prod(bz, sh, z.bh, z.bl);
+  z.be = __fmul_rn(bz, sl);
+  return z;
+}
+
+// geo_lite of a float-float point whose z part comes from ZPart
+__device__ __forceinline__ void geo_lite(const AntRec& A, float pxh, float pyh, float pxl, float pyl, const ZPart& z,
+                                         GeoM& g) {
+  two_sum(A.xh, -pxh, g.s[0], g.e[0]);
+  two_sum(A.yh, -pyh, g.s[1], g.e[1]);
+  g.s[2] = z.sh;
+  g.e[2] = z.sl;
+  g.e[0] = __fadd_rn(g.e[0], __fsub_rn(A.xl, pxl));
+  g.e[1] = __fadd_rn(g.e[1], __fsub_rn(A.yl, pyl));
+  const float S = __fmaf_rn(g.s[2], g.s[2], __fmaf_rn(g.s[0], g.s[0], __fmul_rn(g.s[1], g.s[1])));
+  g.y = rsqrtf(S);
+  g.R0 = __fmul_rn(S, g.y);
+  g.R1 = 0.0f;
+}
+
+// R from the exact squares of d's components (p2 + q2 = s_z^2 and se =
+// fl(s_z e_z) given)
+__device__ __forceinline__ void geo_refine(GeoM& g, float p2, float q2, float se) {
+  float p0, q0, p1, q1;
   two_prod(g.s[0], g.s[0], p0, q0);
   two_prod(g.s[1], g.s[1], p1, q1);
-  two_prod(g.s[2], g.s[2], p2, q2);
   float S1, E1, S2, E2;
   two_sum(p0, p1, S1, E1);
   two_sum(S1, p2, S2, E2);
-  const float cross = __fmaf_rn(g.s[0], g.e[0], __fmaf_rn(g.s[1], g.e[1], __fmul_rn(g.s[2], g.e[2])));
+  const float cross = __fmaf_rn(g.s[0], g.e[0], __fmaf_rn(g.s[1], g.e[1], se));
   const float lo = __fadd_rn(__fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2, E1)), __fadd_rn(E2, __fmul_rn(2.0f, cross)));
   float rq, rqe;
   two_prod(g.R0, g.R0, rq, rqe);
   const float rho = __fadd_rn(__fsub_rn(__fsub_rn(S2, rq), rqe), lo);
   g.R1 = __fmul_rn(__fmul_rn(rho, 0.5f), g.y);
 }
+__device__ __forceinline__ void geo_refine(GeoM& g) {
+  float p2, q2;
+  two_prod(g.s[2], g.s[2], p2, q2);
+  geo_refine(g, p2, q2, __fmul_rn(g.s[2], g.e[2]));
+}
+__device__ __forceinline__ void geo_refine(GeoM& g, const ZPart& z) { geo_refine(g, z.qh, z.ql, z.se); }
 
 __device__ __forceinline__ void geo_mixed(const AntRec& A, float pxh, float pyh, float pzh, float pxl, float pyl,
                                           float pzl, GeoM& g) {
@@ -816,17 +859,18 @@ __device__ __forceinline__ void field_mixed(const GeoM& g, float bx, float by, f
 // is what the arrival interval ends u_m -/+ |D| (t1 - t0)/(2 dt) need: the
 // half-width reaches ~10^2 bins, so D must be good to ~1e-9 absolute, which the
 // FP32 form of field_mixed (good to ~1e-7 relative) is not for |D| of order 1.
-__device__ __forceinline__ ff doppler_ff(const GeoM& g, float bx, float by, float bz, float nm1) {
+// (p2 + q2 = b_z s_z exactly and bze = fl(b_z e_z) given)
+__device__ __forceinline__ ff doppler_ff(const GeoM& g, float bx, float by, float p2, float q2, float bze,
+                                         float nm1) {
   // beta . d with d = s + e exact: exact products of the high parts, summed
   // with TwoSum; the low parts and the rounding errors in FP32
-  float p0, q0, p1, q1, p2, q2;
+  float p0, q0, p1, q1;
   two_prod(bx, g.s[0], p0, q0);
   two_prod(by, g.s[1], p1, q1);
-  two_prod(bz, g.s[2], p2, q2);
   float S1, E1, S2, E2;
   two_sum(p0, p1, S1, E1);
   two_sum(S1, p2, S2, E2);
-  const float be = __fmaf_rn(bx, g.e[0], __fmaf_rn(by, g.e[1], __fmul_rn(bz, g.e[2])));
+  const float be = __fmaf_rn(bx, g.e[0], __fmaf_rn(by, g.e[1], bze));
   const float lo = __fadd_rn(__fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2, E1)), __fadd_rn(E2, be));
   // q = (beta . d)/R: FP32 quotient, then one correction from the exact residual
   const float qh = __fmul_rn(S2, g.y);
@@ -847,6 +891,14 @@ __device__ __forceinline__ ff doppler_ff(const GeoM& g, float bx, float by, floa
   D.h = __fadd_rn(dh, dl);
   D.l = __fsub_rn(dl, __fsub_rn(D.h, dh));
   return D;
+}
+__device__ __forceinline__ ff doppler_ff(const GeoM& g, float bx, float by, float bz, float nm1) {
+  float p2, q2;
+  two_prod(bz, g.s[2], p2, q2);
+  return doppler_ff(g, bx, by, p2, q2, __fmul_rn(bz, g.e[2]), nm1);
+}
+__device__ __forceinline__ ff doppler_ff(const GeoM& g, float bx, float by, const ZPart& z, float nm1) {
+  return doppler_ff(g, bx, by, z.bh, z.bl, z.be, nm1);
 }
 
 // the same field quantities at the midpoint of a track, from those of its two

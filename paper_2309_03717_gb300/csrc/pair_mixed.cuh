@@ -29,6 +29,7 @@ struct TrackM {
   // the refractivity term, the same for every antenna, per track: FP32 at start
   // and end (Endpoint, arrival_fast), float-float at the midpoint (ZHS)
   float q0v, q1v, qmh, qml;
+  ZPart zm;                      // ZHS, flat array: the z part of the midpoint's d
   float E0h, E0l, E1h, E1l, Emh, Eml;
   float nm1_0, nm1_1, nm1_m;     // n - 1 at start, end, midpoint
   float om0, om1, om_m;          // 1 - n|beta| at start, end, midpoint
@@ -102,6 +103,7 @@ __device__ __forceinline__ void load_track_mixed(const float* T, int l, const Me
       two_sum(M.flat_zh, -t.mz, dzh, dzl);
       dzl = __fadd_rn(dzl, __fsub_rn(M.flat_zl, t.mzl));
       refr_quotient(M, M.flat_Eh, M.flat_El, dzh, dzl, t.Emh, t.Eml, t.qmh, t.qml);
+      t.zm = z_part(dzh, dzl, t.bz);
     }
   }
 }
@@ -454,7 +456,10 @@ struct OpsMixed {
   static __device__ __forceinline__ void zhs(const TrackM& t, const AntRec& A, const MedParams& M, Sink& out) {
     const int N = M.n_bins;
     GeoM gm;
-    geo_lite(A, t.mx, t.my, t.mz, t.mxl, t.myl, t.mzl, gm);
+    if constexpr (kFlat)
+      geo_lite(A, t.mx, t.my, t.mxl, t.myl, t.zm, gm);
+    else
+      geo_lite(A, t.mx, t.my, t.mz, t.mxl, t.myl, t.mzl, gm);
     if (gm.R0 == 0.0f) return;
     FieldM f;
     float dop = 0.0f, dD = 0.0f;
@@ -465,13 +470,16 @@ struct OpsMixed {
     } else {
       field_mixed(gm, t.bx, t.by, t.bz, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), f);
     }
-    geo_refine(gm);
-    ff um;
-    if constexpr (kFlat)
+    ff um, aD;
+    if constexpr (kFlat) {
+      geo_refine(gm, t.zm);
       um = arrival_mixed_q<KIND>(M, A, gm, t.tmh, t.tml, t.qmh, t.qml, dop);
-    else
+      aD = doppler_ff(gm, t.bx, t.by, t.zm, t.nm1_m);
+    } else {
+      geo_refine(gm);
       um = arrival_mixed<KIND>(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml, dop);
-    ff aD = doppler_ff(gm, t.bx, t.by, t.bz, t.nm1_m);
+      aD = doppler_ff(gm, t.bx, t.by, t.bz, t.nm1_m);
+    }
     if constexpr (KIND == C8R_EXPONENTIAL_RAY) aD = ff_add_small(aD, dD);
     if (aD.h < 0.0f) {
       aD.h = -aD.h;
@@ -938,17 +946,23 @@ struct OpsMixed {
                                                  float& dn) {
     const int N = M.n_bins;
     GeoM gm;
-    geo_lite(A, t.mx, t.my, t.mz, t.mxl, t.myl, t.mzl, gm);
+    if constexpr (kFlat)
+      geo_lite(A, t.mx, t.my, t.mxl, t.myl, t.zm, gm);
+    else
+      geo_lite(A, t.mx, t.my, t.mz, t.mxl, t.myl, t.mzl, gm);
     if (gm.R0 == 0.0f) return;
     FieldM f;
     field_mixed(gm, t.bx, t.by, t.bz, t.bmag, t.om_m, __fadd_rn(1.0f, t.nm1_m), f);
-    geo_refine(gm);
-    ff um;
-    if constexpr (kFlat)
+    ff um, aD;
+    if constexpr (kFlat) {
+      geo_refine(gm, t.zm);
       um = arrival_mixed_q<KIND>(M, A, gm, t.tmh, t.tml, t.qmh, t.qml);
-    else
+      aD = doppler_ff(gm, t.bx, t.by, t.zm, t.nm1_m);
+    } else {
+      geo_refine(gm);
       um = arrival_mixed<KIND>(M, A, gm, t.tmh, t.tml, t.Emh, t.Eml);
-    ff aD = doppler_ff(gm, t.bx, t.by, t.bz, t.nm1_m);
+      aD = doppler_ff(gm, t.bx, t.by, t.bz, t.nm1_m);
+    }
     const float sgn = aD.h < 0.0f ? -1.0f : 1.0f;
     if (aD.h < 0.0f) {
       aD.h = -aD.h;
