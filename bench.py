@@ -44,14 +44,14 @@ FP32_LANES_PER_SM = 128
 ALG_OPS_PER_ENDPOINT_PAIR = 62
 # DRAM bytes (read + write) per pair of the Endpoint forward kernel: one ncu
 # capture of a 4e6-track x 160-antenna launch (6.4e8 pairs, default launch
-# shape, the split arrival form the vertical shower takes) read 406.6 MB and
-# wrote 5.2 MB; the traffic is the staged track tiles, so it scales with the
+# shape, the split arrival form the vertical shower takes) read 407.7 MB and
+# wrote 5.3 MB; the traffic is the staged track tiles, so it scales with the
 # pairs at a fixed antenna count.  Set to None when the kernel changes.
-DRAM_BYTES_PER_ENDPOINT_PAIR = (406576640 + 5176576) / 6.4e8
+DRAM_BYTES_PER_ENDPOINT_PAIR = (407675648 + 5301504) / 6.4e8
 # The same capture: warp instructions issued per pair and the share of issue
 # slots busy (smsp__issue_active).  Set to None when the kernel changes.
-ENDPOINT_WARP_INST_PER_PAIR = 6.417621802e9 / 6.4e8
-ENDPOINT_ISSUE_ACTIVE_NCU = 0.6002
+ENDPOINT_WARP_INST_PER_PAIR = 6.417611830e9 / 6.4e8
+ENDPOINT_ISSUE_ACTIVE_NCU = 0.5998
 # Algorithmic work per pair of the other kernels, counted from their plain
 # formulas: ZHS one midpoint evaluation (distance, Doppler factor, transverse
 # beta, arrival, interval ends, their bins and weights, up to four deposits):
@@ -64,8 +64,8 @@ ALG_OPS_PER_ENDPOINT_ADJOINT_PAIR = 184
 # antennas for the forward kernels; the differentiable workload for the
 # adjoint): global float4 reductions (lts__t_requests_srcunit_tex_op_red) and
 # DRAM bytes (read + write).  None where not captured.
-RED_PER_PAIR = {"endpoint": 565344775 / 6.4e8, "zhs": 649034623 / 6.4e8, "adjoint": None}
-DRAM_BYTES_PER_PAIR = {"endpoint": DRAM_BYTES_PER_ENDPOINT_PAIR, "zhs": (423463680 + 9702144) / 6.4e8,
+RED_PER_PAIR = {"endpoint": 565344812 / 6.4e8, "zhs": 649034623 / 6.4e8, "adjoint": None}
+DRAM_BYTES_PER_PAIR = {"endpoint": DRAM_BYTES_PER_ENDPOINT_PAIR, "zhs": (424902144 + 10217984) / 6.4e8,
                        "adjoint": None}
 # algorithmic bytes per track of the whole path: the 48-byte FP32 track record
 ALG_BYTES_PER_TRACK = 48.0
