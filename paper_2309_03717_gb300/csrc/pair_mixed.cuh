@@ -323,10 +323,12 @@ struct OpsMixed {
   static constexpr bool kSplit = SPLIT && kFastBins;
   // a flat antenna array: the refractivity quotient per track, in the main pass
   // of the Endpoint forward kernel of the direct arrival form and in the ZHS
-  // forward and adjoint kernels (the host picks the kernel, MedParams::flat).
+  // forward and adjoint kernels, which also take the z part of the midpoint's
+  // d once per track (ZPart; the host picks the kernel, MedParams::flat).
   // Measured: 47.96 -> 44.01 ms on 4e6 tracks of the 60-degree array
-  // (Endpoint); ZHS 31.9 -> 31.0 ms on the 2e7-track vertical shower alone,
-  // 31.96 -> 29.56 ms inside the two-process bench step.  The split-form
+  // (Endpoint); ZHS 31.96 -> 29.56 ms with the quotient and -> 28.50 ms with
+  // the z part as well, on the 2e7-track vertical shower in a step that runs
+  // the Endpoint and then the ZHS process on the same tracks.  The split-form
   // Endpoint kernel keeps the quotient per pair (within 0.3 % either way)
   static constexpr bool kFlat =
       FLAT && KIND == C8R_EXPONENTIAL && ((kFastBins && !SPLIT) || FORM == C8R_ZHS);
