@@ -6,8 +6,9 @@
 // Forward (§2 flow: each track goes to every antenna of the collection): a CTA
 // owns a tile of antennas and a contiguous range of derived-track tiles.  It
 // streams its range through a two-slot ring of shared-memory tiles filled by
-// TMA bulk copies (cp.async.bulk + mbarrier, bounded waits).  For every staged tile each thread loads one
-// track into registers and evaluates it against every antenna of the tile;
+// TMA bulk copies (cp.async.bulk + mbarrier, bounded waits).  For every staged
+// tile each thread loads one track into registers and evaluates it against
+// every antenna of the tile;
 // pairs whose arithmetic takes a rare branch (Endpoint near the Cherenkov
 // angle) are queued in shared memory and evaluated together after the main
 // pass, so that both branches run in full warps.  Each deposit goes into the
