@@ -1,0 +1,176 @@
+"""Host check (numpy FP32) of the error bound of the mixed Endpoint kernels'
+FP32 arrival: the arrival from shifted times T = t/dt + k z in its split and
+direct forms of x = R - (z_e - z_a), and the bound the kernels hold a bin edge
+against before they take a bin from it (any endpoint whose bound reaches an
+edge goes to the float-float arrival instead).  Every step is emulated as the
+kernels state it, rounded once per operation, with the reciprocal square root
+and the fast quotients perturbed within their 2-ulp error (both extremes and
+random draws), and compared with the oracle's FP64 arrivals.  Like
+test_numerics, this checks the arithmetic and its bound, not the CUDA code;
+the GPU parity tests compare the kernels' bins with the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_03717_gb300 import synth
+
+F32 = np.float32
+F64 = np.float64
+U = 2.0 ** -24
+ULP2 = 2.0 ** -22  # 2 ulp, relative
+C_M_PER_NS = 0.299792458
+
+
+def r(x):
+    return np.asarray(x, F64).astype(F32)
+
+
+def fma(a, b, c):
+    return r(np.asarray(a, F64) * np.asarray(b, F64) + np.asarray(c, F64))
+
+
+def split(x):
+    h = r(x)
+    return h, r(np.asarray(x, F64) - h.astype(F64))
+
+
+def perturb(x, mode, rng):
+    """An approximate result within 2 ulp of x: +2 ulp, -2 ulp or random."""
+    x = np.asarray(x, F64)
+    if mode == "up":
+        f = np.full_like(x, ULP2)
+    elif mode == "down":
+        f = np.full_like(x, -ULP2)
+    else:
+        f = rng.uniform(-ULP2, ULP2, size=x.shape)
+    return r(x * (1.0 + f))
+
+
+def emulated_arrivals(w, tracks, split_form, mode, rng):
+    """(uf, eps) per endpoint, [2][n_tracks, n_ant]: the FP32 arrival and its
+    bound as the kernels form them, from the antenna constants as the host
+    forms them."""
+    dt = w["dt_ns"]
+    med = w["medium"]
+    expo = med["kind"] == "exponential"
+    kc = 1.0 / (C_M_PER_NS * dt)
+    if expo:
+        N0, H = med["N0"], med["H"]
+        kh, kl = split(kc)
+        cNh, _ = split(N0 * H * kc)
+        invHh, _ = split(1.0 / H)
+        nmax = 1.0 + N0
+    else:
+        kh, kl = split(med["n"] * kc)
+        nmax = med["n"]
+    kff = F64(kh) + F64(kl)
+    A = np.asarray(w["ant_xyz"], F64)
+    Axh, Axl = split(A[:, 0])
+    Ayh, Ayl = split(A[:, 1])
+    Azh, Azl = split(A[:, 2])
+    Ta = np.asarray(w["t_start_ns"], F64) / dt + kff * A[:, 2]
+    Tah, Tal = split(Ta)
+    al = np.sqrt(Axl.astype(F64) ** 2 + Ayl.astype(F64) ** 2 + Azl.astype(F64) ** 2)
+    fb_abs = r(2.02 * nmax * kc * al + 16.0 * U * U * np.abs(Ta) + 1e-6)
+    fb_rel_v = r(1.01 * np.abs(Azl.astype(F64)) / (0.999e-3 * H)) if expo else np.zeros(len(A), F32)
+    if expo:
+        Eah, Eal = split(np.exp(-A[:, 2] / H))
+    out = []
+    for xs, ys, zs, ts in (("x0", "y0", "z0", "t0"), ("x1", "y1", "z1", "t1")):
+        px = tracks[xs].astype(F32)[:, None]
+        py = tracks[ys].astype(F32)[:, None]
+        pz = tracks[zs].astype(F32)[:, None]
+        Teh, Tel = split(tracks[ts].astype(F64) / dt + kff * tracks[zs].astype(F64))
+        Teh, Tel = Teh[:, None], Tel[:, None]
+        s0, s1, s2 = r(Axh[None] - px), r(Ayh[None] - py), r(Azh[None] - pz)
+        rho2 = fma(s0, s0, r(s1.astype(F64) * s1))
+        S = fma(s2, s2, rho2)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            y = perturb(1.0 / np.sqrt(S.astype(F64)), mode, rng)
+            R0 = r(S.astype(F64) * y)
+            if split_form:
+                R = R0
+                xa = perturb(rho2.astype(F64) / r(R.astype(F64) - s2).astype(F64), mode, rng)
+                x = np.where(s2 < 0, xa, r(R.astype(F64) + s2))
+            else:
+                res = fma(-R0, R0, S)
+                R = fma(res, r(0.5 * y.astype(F64)), R0)
+                x = r(R.astype(F64) + s2)
+            q = r(x.astype(F64) * kh)
+            Td = r(r(Teh.astype(F64) - Tah[None]).astype(F64) + r(Tel.astype(F64) - Tal[None]))
+            if expo:
+                Eeh, Eel = split(np.exp(-tracks[zs].astype(F64) / H))
+                Eeh, Eel = Eeh[:, None], Eel[:, None]
+                xq = r(s2.astype(F64) * invHh)
+                num = r(r(Eeh.astype(F64) - Eah[None]).astype(F64) + r(Eel.astype(F64) - Eal[None]))
+                qv_big = perturb(num.astype(F64) / s2, mode, rng)
+                f = r(xq.astype(F64) * fma(xq, fma(xq, r(-1.0 / 24.0), r(1.0 / 6.0)), r(-0.5)))
+                qv_small = r(r(Eeh.astype(F64) * invHh).astype(F64) * r(1.0 + f.astype(F64)))
+                qv = np.where(np.abs(xq) > F32(1e-3), qv_big, qv_small)
+                v = r(r(qv.astype(F64) * R).astype(F64) * cNh)
+            else:
+                v = np.zeros_like(q)
+            uf = r(r(Td.astype(F64) + q).astype(F64) + v)
+            tail = fma(r(2.25 * U), np.abs(Td),
+                       fma(fma(r(22.0 if split_form else 17.0), r(U), fb_rel_v[None]), np.abs(v),
+                           fma(r(3.25 * U), np.abs(uf), fb_abs[None])))
+            if split_form:
+                eps = fma(r(19.0 * U), q, tail)
+            else:
+                eps = fma(r(6.25 * U), q, fma(r(2.5 * U * F64(kh)), R, tail))
+        out.append((uf, eps))
+    return out
+
+
+def workload(name):
+    if name == "vertical":
+        w = synth.workload(1, n_tracks=1500)
+    elif name == "inclined":
+        w = synth.workload(2, n_tracks=1500, n_ant=64)
+    elif name == "uniform":
+        w = synth.workload(0, n_tracks=1500)
+    else:  # a dense uniform medium (n = 1.78), the windows placed around the arrivals
+        w = synth.workload(0, n_tracks=1500)
+        w["medium"] = {"kind": "uniform", "n": 1.78}
+    w["dtype"] = np.float32
+    tracks = synth.workload_tracks(w)
+    if name == "dense":
+        _, u0 = oracle.arrivals(oracle.tracks_from_ns(tracks), w["ant_xyz"], np.zeros(len(w["ant_xyz"])), 1,
+                                w["dt_ns"] * 1e-9, w["medium"], oracle.ENDPOINT)
+        w["t_start_ns"] = np.median(u0[..., 0], axis=0) * w["dt_ns"] - 300.0
+    return w, tracks
+
+
+@pytest.mark.parametrize("name", ["vertical", "inclined", "uniform", "dense"])
+@pytest.mark.parametrize("split_form", [True, False], ids=["split", "direct"])
+def test_fp32_arrival_within_its_bound(name, split_form):
+    w, tracks = workload(name)
+    br, u = oracle.arrivals(oracle.tracks_from_ns(tracks), w["ant_xyz"], w["t_start_ns"] * 1e-9, w["n_bins"],
+                            w["dt_ns"] * 1e-9, w["medium"], oracle.ENDPOINT)
+    two = br == 0  # the pairs evaluated at their two endpoints (near-Cherenkov ones take the midpoint)
+    assert two.mean() > 0.5
+    rng = np.random.default_rng(7)
+    worst = 0.0
+    for mode in ("up", "down", "random", "random"):
+        for j, (uf, eps) in enumerate(emulated_arrivals(w, tracks, split_form, mode, rng)):
+            err = np.abs(uf.astype(F64) - u[..., j])[two]
+            ratio = err / eps.astype(F64)[two]
+            assert np.all(np.isfinite(ratio))
+            worst = max(worst, float(ratio.max()))
+    assert worst <= 1.0, f"the FP32 arrival left its bound: error / bound = {worst:.3f}"
+
+
+def test_split_form_bound_is_small_on_a_vertical_shower():
+    """Where the split form pays (emission points high above the array), its
+    bound leaves almost every in-window endpoint decided: the float-float
+    arrival is needed only within the bound of an edge."""
+    w, tracks = workload("vertical")
+    br, u = oracle.arrivals(oracle.tracks_from_ns(tracks), w["ant_xyz"], w["t_start_ns"] * 1e-9, w["n_bins"],
+                            w["dt_ns"] * 1e-9, w["medium"], oracle.ENDPOINT)
+    rng = np.random.default_rng(3)
+    uf, eps = emulated_arrivals(w, tracks, True, "random", rng)[0]
+    inwin = (br == 0) & (u[..., 0] > 0) & (u[..., 0] < w["n_bins"])
+    assert inwin.mean() > 0.3
+    undecided = np.floor(uf - eps) != np.floor(uf + eps)
+    assert float(np.median(eps[inwin])) < 1e-2
+    assert undecided[inwin].mean() < 0.01
