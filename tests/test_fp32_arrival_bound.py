@@ -319,3 +319,100 @@ def test_near_cherenkov_zero_decision_is_exact(name, split_form):
         # path (97-100 % on these workloads in the form the kernels pick for
         # them, 70-80 % on the 60-degree array)
         assert (zero & mid).sum() >= 0.6 * (oracle_zero & mid).sum()
+
+
+# ---------------------------------------------------------------------------
+# The float-float Doppler factor.  The ZHS interval ends u_m -/+ |D_m| (t1 -
+# t0)/(2 dt) and the near-Cherenkov Endpoint arrivals need D = 1 - n beta.rhat
+# to ~1e-9 absolute (half-widths reach ~1e2 bins); the kernels form it from the
+# float-float midpoint geometry with error-free transformations, to ~1e-10
+# (set by n - 1 rounded to FP32).
+# ---------------------------------------------------------------------------
+def two_sum(a, b):
+    a, b = a.astype(F32), b.astype(F32)
+    s = (a + b).astype(F32)
+    bb = (s - a).astype(F32)
+    return s, ((a - (s - bb).astype(F32)).astype(F32) + (b - bb).astype(F32)).astype(F32)
+
+
+def two_prod(a, b):
+    p = r(a.astype(F64) * b)
+    return p, r(a.astype(F64) * b - p)  # the product's error is an FP32 number
+
+
+def emulated_doppler_ff(w, tracks, mode, rng):
+    """D at the track midpoints as the ZHS kernel forms it, float-float, and
+    the FP64 value of the same formula from the exact inputs."""
+    med = w["medium"]
+    N0, H = med["N0"], med["H"]
+    A = np.asarray(w["ant_xyz"], F64)
+    Axh, Axl = split(A[:, 0])
+    Ayh, Ayl = split(A[:, 1])
+    Azh, Azl = split(A[:, 2])
+    c = lambda k: tracks[k].astype(F32)[:, None]
+    x0, y0, z0, x1, y1, z1 = (c(k) for k in ("x0", "y0", "z0", "x1", "y1", "z1"))
+    bx, by, bz = c("bx"), c("by"), c("bz")
+    # midpoint (x0 + x1)/2, exact in float-float
+    m = []
+    for p0, p1 in ((x0, x1), (y0, y1), (z0, z1)):
+        h, l = two_sum(p0, p1)
+        m.append((r(0.5 * h.astype(F64)), r(0.5 * l.astype(F64))))
+    # geo_lite: d = a - m as float-float
+    s, e = [], []
+    for (ah, al_), (mh, ml) in zip(((Axh, Axl), (Ayh, Ayl), (Azh, Azl)), m):
+        sh, sl = two_sum(np.broadcast_to(ah[None], (len(mh), len(ah))), np.broadcast_to(-mh, (len(mh), len(ah))))
+        s.append(sh)
+        e.append(r(sl.astype(F64) + r(al_[None].astype(F64) - ml)))
+    S = fma(s[2], s[2], fma(s[0], s[0], r(s[1].astype(F64) * s[1])))
+    y = perturb(1.0 / np.sqrt(S.astype(F64)), mode, rng)
+    R0 = r(S.astype(F64) * y)
+    # geo_refine: R = R0 + R1
+    (p0, q0), (p1, q1), (p2, q2) = (two_prod(s[k], s[k]) for k in range(3))
+    S1, E1 = two_sum(p0, p1)
+    S2, E2 = two_sum(S1, p2)
+    cross = fma(s[0], e[0], fma(s[1], e[1], r(s[2].astype(F64) * e[2])))
+    lo = r(r(r(q0.astype(F64) + q1).astype(F64) + r(q2.astype(F64) + E1)).astype(F64)
+           + r(E2.astype(F64) + r(2.0 * cross.astype(F64))))
+    rq, rqe = two_prod(R0, R0)
+    rho = r(r(r(S2.astype(F64) - rq).astype(F64) - rqe).astype(F64) + lo)
+    R1 = r(r(rho.astype(F64) * 0.5).astype(F64) * y)
+    # doppler_ff
+    (p0, q0), (p1, q1), (p2, q2) = two_prod(bx, s[0]), two_prod(by, s[1]), two_prod(bz, s[2])
+    S1, E1 = two_sum(p0, p1)
+    S2, E2 = two_sum(S1, p2)
+    be = fma(bx, e[0], fma(by, e[1], r(bz.astype(F64) * e[2])))
+    lo = r(r(r(q0.astype(F64) + q1).astype(F64) + r(q2.astype(F64) + E1)).astype(F64) + r(E2.astype(F64) + be))
+    qh = r(S2.astype(F64) * y)
+    ph, pl = two_prod(qh, R0)
+    res = r(r(r(r(S2.astype(F64) - ph).astype(F64) - pl).astype(F64) + lo).astype(F64) - r(qh.astype(F64) * R1))
+    ql = r(res.astype(F64) * y)
+    zm = 0.5 * (z0.astype(F64) + z1.astype(F64))
+    Emh, _ = split(np.exp(-zm / H))
+    nm1 = r(F64(r(N0)) * Emh)
+    nh, nl = two_sum(qh, r(nm1.astype(F64) * qh))
+    nl = r(nl.astype(F64) + ql)
+    dh, dl = two_sum(np.ones_like(nh), -nh)
+    dl = r(dl.astype(F64) - nl)
+    D = dh.astype(F64) + dl.astype(F64)
+    # FP64: the same formula from the exact midpoint and antenna positions
+    mx = 0.5 * (x0.astype(F64) + x1.astype(F64))
+    my = 0.5 * (y0.astype(F64) + y1.astype(F64))
+    dx, dy, dz = A[None, :, 0] - mx, A[None, :, 1] - my, A[None, :, 2] - zm
+    R = np.sqrt(dx * dx + dy * dy + dz * dz)
+    n = 1.0 + N0 * np.exp(-zm / H)
+    D64 = 1.0 - n * (bx.astype(F64) * dx + by.astype(F64) * dy + bz.astype(F64) * dz) / R
+    return D, D64
+
+
+@pytest.mark.parametrize("name", ["vertical", "inclined"])
+def test_float_float_doppler_factor(name):
+    w, tracks = workload(name)
+    rng = np.random.default_rng(5)
+    for mode in ("up", "down", "random"):
+        D, D64 = emulated_doppler_ff(w, tracks, mode, rng)
+        err = np.abs(D - D64)
+        # ~1.2e-10 at most on these workloads (n - 1 rounded to FP32, and the
+        # FP32 low parts of the float-float steps); the interval ends need 1e-9
+        assert float(err.max()) < 3e-10, float(err.max())
+        # an FP32 D would be off by up to ~u |D|
+        assert float(np.abs(D64).max()) > 0.05
