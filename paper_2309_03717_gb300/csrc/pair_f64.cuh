@@ -130,7 +130,8 @@ struct OpsF64 {
   // shower, in most warps) are set aside by the main pass and evaluated
   // together afterwards, so that the midpoint form's FP64 arithmetic runs in
   // full warps instead of holding the other lanes of nearly every warp.  The
-  // arithmetic of each pair is the same either way.
+  // arithmetic of each pair is the same either way.  (The adjoint, adj_main,
+  // evaluates every pair in its main pass; its set-aside lists stay empty.)
   static constexpr bool kDefers = FORM == C8R_ENDPOINT && !LIN;
   static constexpr bool kFastBins = false;
   static constexpr int kBwdMinBlocks = 2;
