@@ -1315,7 +1315,8 @@ cudaError_t forward_mixed(int formalism, const void* tiles, int64_t n_tiles, con
   if (formalism == C8R_ENDPOINT)
     return ex ? go(OpsMixed<C8R_ENDPOINT, C8R_EXPONENTIAL, LIN>{}) : go(OpsMixed<C8R_ENDPOINT, C8R_UNIFORM, LIN>{});
   // ZHS in the exponential medium: for a flat array the kernel that forms the
-  // midpoint's refractivity quotient once per track (OpsMixed::kFlat)
+  // midpoint's refractivity quotient and the z part of its d once per track
+  // (OpsMixed::kFlat)
   if (ex && M.flat) return go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, LIN, false, true>{});
   return ex ? go(OpsMixed<C8R_ZHS, C8R_EXPONENTIAL, LIN>{}) : go(OpsMixed<C8R_ZHS, C8R_UNIFORM, LIN>{});
 }
